@@ -1,0 +1,201 @@
+/*
+ * hvox.h — C ABI of the GB300 HVOX transform library (libhvox.so).
+ *
+ * HVOX evaluates the radio-interferometric measurement sums of Sect. 2
+ * (Eq. 2 and Eq. 3) with a 3-D type-3 non-uniform FFT (Sect. 3), chunked into
+ * sub-problems (Eq. 8; Algorithms 1 and 2 of Sect. 3.2), each evaluated either by
+ * the type-3 NUFFT (spread, FFT, interpolate, taper) or by direct summation when
+ * that is cheaper (the small-block fallback of Sect. 3.1).
+ *
+ * Directions. With pixel unit vectors r_n, baselines p_k in wavelengths, weights
+ * a_n (tessellation weights of Eq. 2; NULL means 1) and isign = +-1:
+ *
+ *   sky -> vis  (hvox_synthesize, alias hvox_dirty2vis):
+ *        V_k = sum_n a_n I_n exp(+isign * j * 2 pi <p_k, r_n>)
+ *   vis -> sky  (hvox_analyze, alias hvox_vis2dirty):
+ *        I_n = a_n Re sum_k V_k exp(-isign * j * 2 pi <p_k, r_n>)
+ *
+ * isign = -1 reproduces Eq. 2 for sky -> vis. The paper calls the sky -> vis map
+ * "analysis" and its adjoint "synthesis"; this library keeps the names its users
+ * asked for (synthesize = sky -> vis) and offers the unambiguous aliases
+ * dirty2vis / vis2dirty, the names of the paper's user functions (Sect. 4). The
+ * vis -> sky output is real (the paper's real=True adjoint, Listing 1): it is the
+ * exact adjoint of sky -> vis under the real inner product.
+ *
+ * Accuracy: each output vector meets relative l2 error <= 10 * eps against the
+ * exact sums (eps = 0 selects direct evaluation everywhere, Sect. 4).
+ *
+ * Precision. HVOX_PREC_FP32: I is float[n_pix], V is interleaved complex
+ * float[2 n_vis]. HVOX_PREC_FP64: double / double[2 n_vis]. AUTO picks FP32 for
+ * eps >= 1e-6 and FP64 below. Coordinates, phases of large argument and plan-time
+ * geometry are always FP64.
+ *
+ * Memory. Coordinates and weights passed to hvox_plan may be host or device
+ * pointers; they are copied (and permuted to chunk order) into plan-owned device
+ * memory, so the caller may free them on return. I and V passed to the transform
+ * calls may be device pointers (the fast path) or host pointers (then the call
+ * copies through plan-owned staging buffers and synchronises its stream before
+ * returning). Outputs are overwritten, never accumulated into.
+ *
+ * Streams and errors. Work is enqueued on opts.stream (NULL = the legacy default
+ * stream). Device pointers make the transform calls asynchronous: a device-side
+ * failure is reported by the next call on the plan or by hvox_sync. Argument
+ * errors return HVOX_EINVAL before any work is enqueued. A failed hvox_plan
+ * frees everything it allocated. A plan must not be used from two host threads at
+ * once; different plans may run concurrently on different streams.
+ * hvox_last_error() returns a thread-local message for the last failure.
+ */
+#ifndef HVOX_H
+#define HVOX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct hvox_plan_s *hvox_plan_t;
+
+typedef enum {
+    HVOX_OK = 0,
+    HVOX_EINVAL = 1,        /* bad argument; nothing was enqueued */
+    HVOX_ENOMEM = 2,        /* device or host allocation failed */
+    HVOX_ECUDA = 3,         /* a CUDA runtime or cuFFT call failed */
+    HVOX_ETIMEOUT = 4,      /* a device-side bounded wait gave up */
+    HVOX_EUNSUPPORTED = 5,  /* option combination not supported */
+    HVOX_EINTERNAL = 6      /* internal invariant violated (device error word set) */
+} hvox_status;
+
+typedef enum { HVOX_PREC_AUTO = 0, HVOX_PREC_FP32 = 1, HVOX_PREC_FP64 = 2 } hvox_prec;
+
+typedef enum {
+    HVOX_MODE_AUTO = 0,     /* per-block choice NUFFT vs direct by the cost model */
+    HVOX_MODE_NUFFT = 1,    /* every block by type-3 NUFFT */
+    HVOX_MODE_DIRECT = 2    /* every block by direct summation (the eps = 0 semantics) */
+} hvox_mode;
+
+/* Options. A zero-initialised struct selects the defaults. */
+typedef struct {
+    int32_t precision;           /* hvox_prec */
+    int32_t mode;                /* hvox_mode */
+    double upsampfac;            /* sigma of both NUFFT stages; 0 -> 2.0 (1.25 allowed) */
+    double chunk_budget_bytes;   /* FFT-grid budget B of one sub-problem (Algorithm 1);
+                                    0 -> chosen by the planner's cost model */
+    double anisotropy;           /* Algorithm 1 alpha >= 1; 0 -> 1 (isotropic optimum) */
+    double direct_threshold;     /* < 0 or 0 -> cost model; > 0: a block with
+                                    n_pix_blk * n_vis_blk <= threshold is direct */
+    int32_t ntrans;              /* number of stacked inputs on one geometry; 0 -> 1 */
+    int32_t plain;               /* 1: the plain reference form: FP64 arithmetic in every
+                                    kernel, blocks launched one by one, no graph */
+    void *stream;                /* cudaStream_t; NULL = legacy default stream */
+} hvox_opts;
+
+/* Plan summary (filled by hvox_plan_info). */
+typedef struct {
+    int64_t n_pix, n_vis;
+    int32_t precision;           /* resolved hvox_prec */
+    int32_t isign;
+    double eps;
+    int32_t w;                   /* ES kernel width (grid cells per dimension) */
+    double beta;                 /* ES kernel shape parameter */
+    double upsampfac;
+    double budget_bytes;         /* B used by Algorithm 1 */
+    double t;                    /* Algorithm 1 scale: h = t B_k, eta = t P_k */
+    double h[3], eta[3];         /* maximal Heisenberg dimensions (wavelengths / unit) */
+    int64_t n_pix_chunks, n_vis_chunks;
+    int64_t n_nufft_blocks;      /* sub-problems evaluated by type-3 NUFFT */
+    int64_t n_direct_rects;      /* rectangles of direct work after merging */
+    double direct_pairs;         /* sum of n_pix * n_vis over direct sub-problems */
+    double nufft_points;         /* sum of n_pix + n_vis over NUFFT sub-problems */
+    double nufft_cells;          /* sum of FFT-grid cells over NUFFT sub-problems */
+    double max_grid_bytes;       /* largest sub-problem grid (spread + FFT grids) */
+    double workspace_bytes;      /* plan-owned device memory */
+    double plan_seconds;         /* wall time of hvox_plan */
+    double model_seconds;        /* cost-model estimate of one transform */
+} hvox_info;
+
+/*
+ * hvox_plan — build a plan: Algorithm 1 (box dimensions), Algorithm 2 (chunking of
+ * pixels and baselines), the NUFFT-or-direct choice per sub-problem (Sect. 3.1),
+ * the chunk-order permutation (Sect. 4), grid sizes and kernel tables.
+ *   pix_xyz    (n_pix, 3) row-major FP64 pixel positions (unit vectors; any finite
+ *              positions are accepted). Host or device pointer.
+ *   uvw        (n_vis, 3) row-major FP64 baselines in wavelengths. Host or device.
+ *   pix_weight (n_pix) FP64 weights a_n, or NULL for 1. Host or device.
+ *   eps        target relative l2 error; 0 selects direct evaluation everywhere.
+ *   isign      +1 or -1 (sign of the exponent of sky -> vis).
+ *   opts       may be NULL (defaults).
+ *   out        receives the plan handle; set to NULL on failure.
+ * Errors: HVOX_EINVAL for n_pix < 1, n_vis < 1, NULL pointers, eps < 0 or not finite,
+ * |isign| != 1, non-finite coordinates, bad options; HVOX_ENOMEM; HVOX_ECUDA.
+ */
+hvox_status hvox_plan(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis,
+                      const double *pix_weight, double eps, int isign, const hvox_opts *opts,
+                      hvox_plan_t *out);
+
+/* sky -> vis. I: ntrans * n_pix reals, V: ntrans * n_vis complex (interleaved), in the
+ * plan precision; transform t occupies I[t n_pix ...], V[2 t n_vis ...]. */
+hvox_status hvox_synthesize(hvox_plan_t plan, const void *I, void *V);
+
+/* vis -> sky (exact adjoint of hvox_synthesize, real part). Layouts as above. */
+hvox_status hvox_analyze(hvox_plan_t plan, const void *V, void *I);
+
+/* Free every resource of the plan (waits for its stream). NULL is accepted. */
+hvox_status hvox_destroy(hvox_plan_t plan);
+
+/* Aliases with the direction in the name. */
+hvox_status hvox_dirty2vis(hvox_plan_t plan, const void *I, void *V);
+hvox_status hvox_vis2dirty(hvox_plan_t plan, const void *V, void *I);
+
+/* Plan summary. */
+hvox_status hvox_plan_info(hvox_plan_t plan, hvox_info *info);
+
+/* Chunk labels chosen by the plan, in the caller's original point order:
+ * pix_chunk[n] (n_pix entries) and vis_chunk[k] (n_vis entries), host pointers,
+ * either may be NULL. Chunks are numbered as Algorithm 2 creates them. */
+hvox_status hvox_plan_chunks(hvox_plan_t plan, int64_t *pix_chunk, int64_t *vis_chunk);
+
+/* Wait for the plan's stream and report any device-side error. */
+hvox_status hvox_sync(hvox_plan_t plan);
+
+/* Device memory a plan with these sizes would own (admission control); 0 on error. */
+double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_opts *opts);
+
+/* Thread-local message describing the last failure ("" if none). */
+const char *hvox_last_error(void);
+
+/* Library version string. */
+const char *hvox_version(void);
+
+/* ---------------------------------------------------------------------------
+ * Host-only planning primitives (no GPU needed), exposed for testing and for
+ * callers that want to inspect a partition before planning.
+ * --------------------------------------------------------------------------- */
+
+/* ES kernel parameters for tolerance eps and upsampling sigma (Barnett, Magland and
+ * af Klinteberg 2019, the type-3 engine the paper uses): width w = ceil(ln(1/eps) /
+ * (pi sqrt(1 - 1/sigma))) grid cells and beta = 0.97 pi w (1 - 1/(2 sigma)). */
+hvox_status hvox_es_params(double eps, double sigma, int32_t *w, double *beta);
+
+/* Fourier transform of the ES kernel phi(z) = exp(beta (sqrt(1 - (2z/w)^2) - 1)),
+ * |z| <= w/2 (grid units): out[i] = int phi(z) cos(xi[i] z) dz, by Gauss-Legendre
+ * quadrature (the deconvolution factors of the spread and interpolation steps). */
+hvox_status hvox_es_ft(int32_t w, double beta, const double *xi, int64_t n, double *out);
+
+/* Algorithm 1: largest t in (0, 1] such that the padded grids of a sub-problem with
+ * extents eta = t P (pixels) and h = t B (wavelengths) fit budget_bytes, for
+ * upsampling sigma, kernel width w and complex element size elem_bytes. */
+hvox_status hvox_box_dims(const double P[3], const double B[3], double budget_bytes, double sigma,
+                          int32_t w, int32_t elem_bytes, double eta[3], double h[3], double *t);
+
+/* Algorithm 2: chunk labels of n points (row-major (n, 3), host pointer) for maximal
+ * box dimensions h; labels[n] host output, *n_chunks the chunk count. */
+hvox_status hvox_chunk_points(const double *xyz, int64_t n, const double h[3], int64_t *labels,
+                              int64_t *n_chunks);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HVOX_H */

@@ -1,0 +1,312 @@
+"""Python binding of libhvox (the GB300 HVOX transform library).
+
+Argument marshalling only: every step of a transform runs in the library's CUDA
+kernels. The C ABI is declared in ``include/hvox.h``; this module mirrors its names:
+
+    plan = Plan(pix, uvw, eps, isign=-1, weight=None, ...)   # hvox_plan
+    V = plan.synthesize(I)    # sky -> vis (alias dirty2vis)  hvox_synthesize
+    I = plan.analyze(V)       # vis -> sky (alias vis2dirty)  hvox_analyze
+    plan.close()              # hvox_destroy
+
+Inputs may be numpy arrays, CPU tensors or CUDA tensors. Results are torch tensors on
+the device of the input (CUDA inputs: asynchronous on the plan's stream).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+from . import _build
+
+__all__ = ["Plan", "HvoxError", "load", "build", "es_params", "es_ft", "box_dims", "chunk_points", "version",
+           "PREC_AUTO", "PREC_FP32", "PREC_FP64", "MODE_AUTO", "MODE_NUFFT", "MODE_DIRECT"]
+
+PREC_AUTO, PREC_FP32, PREC_FP64 = 0, 1, 2
+MODE_AUTO, MODE_NUFFT, MODE_DIRECT = 0, 1, 2
+_STATUS = {0: "HVOX_OK", 1: "HVOX_EINVAL", 2: "HVOX_ENOMEM", 3: "HVOX_ECUDA", 4: "HVOX_ETIMEOUT",
+           5: "HVOX_EUNSUPPORTED", 6: "HVOX_EINTERNAL"}
+
+
+class HvoxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{_STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("upsampfac", ctypes.c_double),
+                ("chunk_budget_bytes", ctypes.c_double), ("anisotropy", ctypes.c_double),
+                ("direct_threshold", ctypes.c_double), ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("n_pix", ctypes.c_int64), ("n_vis", ctypes.c_int64), ("precision", ctypes.c_int32),
+                ("isign", ctypes.c_int32), ("eps", ctypes.c_double), ("w", ctypes.c_int32),
+                ("beta", ctypes.c_double), ("upsampfac", ctypes.c_double), ("budget_bytes", ctypes.c_double),
+                ("t", ctypes.c_double), ("h", ctypes.c_double * 3), ("eta", ctypes.c_double * 3),
+                ("n_pix_chunks", ctypes.c_int64), ("n_vis_chunks", ctypes.c_int64),
+                ("n_nufft_blocks", ctypes.c_int64), ("n_direct_rects", ctypes.c_int64),
+                ("direct_pairs", ctypes.c_double), ("nufft_points", ctypes.c_double),
+                ("nufft_cells", ctypes.c_double), ("max_grid_bytes", ctypes.c_double),
+                ("workspace_bytes", ctypes.c_double), ("plan_seconds", ctypes.c_double),
+                ("model_seconds", ctypes.c_double)]
+
+
+_lib = None
+LIB_PATH = _build.LIB
+
+
+def build(force: bool = False) -> str:
+    return _build.build(force=force)
+
+
+def load():
+    """Load libhvox.so; raises if it has not been built (there is no fallback path)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is not built: run __graft_entry__.build() (nvcc, sm_103a)")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I64, I32, V = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.c_int32, ctypes.c_void_p
+    PI64 = ctypes.POINTER(ctypes.c_int64)
+    sig = {
+        "hvox_plan": [V, I64, V, I64, V, ctypes.c_double, ctypes.c_int, ctypes.POINTER(Opts), ctypes.POINTER(P)],
+        "hvox_synthesize": [P, V, V],
+        "hvox_analyze": [P, V, V],
+        "hvox_dirty2vis": [P, V, V],
+        "hvox_vis2dirty": [P, V, V],
+        "hvox_destroy": [P],
+        "hvox_sync": [P],
+        "hvox_plan_info": [P, ctypes.POINTER(Info)],
+        "hvox_plan_chunks": [P, PI64, PI64],
+        "hvox_es_params": [ctypes.c_double, ctypes.c_double, ctypes.POINTER(I32), D],
+        "hvox_es_ft": [I32, ctypes.c_double, D, I64, D],
+        "hvox_box_dims": [D, D, ctypes.c_double, ctypes.c_double, I32, I32, D, D, D],
+        "hvox_chunk_points": [D, I64, D, PI64, PI64],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.hvox_last_error.restype = ctypes.c_char_p
+    lib.hvox_last_error.argtypes = []
+    lib.hvox_version.restype = ctypes.c_char_p
+    lib.hvox_version.argtypes = []
+    lib.hvox_estimate_bytes.restype = ctypes.c_double
+    lib.hvox_estimate_bytes.argtypes = [I64, I64, ctypes.c_double, ctypes.POINTER(Opts)]
+    _lib = lib
+    return lib
+
+
+def _check(code: int):
+    if code != 0:
+        raise HvoxError(code, load().hvox_last_error().decode())
+
+
+def version() -> str:
+    return load().hvox_version().decode()
+
+
+# ------------------------------------------------------------------ host-only planning primitives
+
+def _np():
+    import numpy as np
+    return np
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def es_params(eps: float, sigma: float = 2.0):
+    w, beta = ctypes.c_int32(), ctypes.c_double()
+    _check(load().hvox_es_params(eps, sigma, ctypes.byref(w), ctypes.byref(beta)))
+    return w.value, beta.value
+
+
+def es_ft(w: int, beta: float, xi):
+    np = _np()
+    xi = np.ascontiguousarray(np.asarray(xi, dtype=np.float64))
+    out = np.empty_like(xi)
+    _check(load().hvox_es_ft(w, beta, _dptr(xi), len(xi), _dptr(out)))
+    return out
+
+
+def box_dims(P, B, budget_bytes: float, sigma: float, w: int, elem_bytes: int):
+    np = _np()
+    P = np.ascontiguousarray(P, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    eta, h, t = np.zeros(3), np.zeros(3), ctypes.c_double()
+    _check(load().hvox_box_dims(_dptr(P), _dptr(B), budget_bytes, sigma, w, elem_bytes, _dptr(eta), _dptr(h),
+                                ctypes.byref(t)))
+    return eta, h, t.value
+
+
+def chunk_points(xyz, h):
+    np = _np()
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    labels = np.zeros(len(xyz), dtype=np.int64)
+    nc = ctypes.c_int64()
+    _check(load().hvox_chunk_points(_dptr(xyz), len(xyz), _dptr(h),
+                                    labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(nc)))
+    return labels, nc.value
+
+
+# ------------------------------------------------------------------ plans
+
+def _as_f64_rows(x):
+    """(N, 3) float64 contiguous: torch tensor (any device) or numpy. Returns (keepalive, ptr, N)."""
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            t = x.detach().to(torch.float64).contiguous()
+            if t.dim() != 2 or t.shape[1] != 3:
+                raise ValueError("coordinates must have shape (N, 3)")
+            return t, t.data_ptr(), t.shape[0]
+    except ImportError:
+        pass
+    np = _np()
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    if a.ndim != 2 or a.shape[1] != 3:
+        raise ValueError("coordinates must have shape (N, 3)")
+    return a, a.ctypes.data, a.shape[0]
+
+
+def _as_f64_vec(x, n):
+    if x is None:
+        return None, None
+    try:
+        import torch
+        if isinstance(x, torch.Tensor):
+            t = x.detach().to(torch.float64).contiguous().reshape(-1)
+            if t.numel() != n:
+                raise ValueError("weights must have n_pix entries")
+            return t, t.data_ptr()
+    except ImportError:
+        pass
+    np = _np()
+    a = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1))
+    if a.size != n:
+        raise ValueError("weights must have n_pix entries")
+    return a, a.ctypes.data
+
+
+_PREC = {"auto": PREC_AUTO, "fp32": PREC_FP32, "fp64": PREC_FP64, PREC_AUTO: PREC_AUTO, PREC_FP32: PREC_FP32,
+         PREC_FP64: PREC_FP64}
+_MODE = {"auto": MODE_AUTO, "nufft": MODE_NUFFT, "direct": MODE_DIRECT, MODE_AUTO: MODE_AUTO,
+         MODE_NUFFT: MODE_NUFFT, MODE_DIRECT: MODE_DIRECT}
+
+
+class Plan:
+    """A planned HVOX transform pair on one geometry (see include/hvox.h)."""
+
+    def __init__(self, pix, uvw, eps: float, isign: int = -1, weight=None, precision="auto", mode="auto",
+                 upsampfac: float = 0.0, chunk_budget_bytes: float = 0.0, anisotropy: float = 0.0,
+                 direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, stream=None):
+        import torch
+        lib = load()
+        self._handle = ctypes.c_void_p()
+        pk, pp, n_pix = _as_f64_rows(pix)
+        uk, up, n_vis = _as_f64_rows(uvw)
+        wk, wp = _as_f64_vec(weight, n_pix)
+        o = Opts()
+        o.precision = _PREC[precision]
+        o.mode = _MODE[mode]
+        o.upsampfac = upsampfac
+        o.chunk_budget_bytes = chunk_budget_bytes
+        o.anisotropy = anisotropy
+        o.direct_threshold = direct_threshold
+        o.ntrans = ntrans
+        o.plain = 1 if plain else 0
+        if stream is None:
+            stream = torch.cuda.current_stream()
+        self.stream = stream
+        o.stream = ctypes.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        _check(lib.hvox_plan(pp, n_pix, up, n_vis, wp, float(eps), int(isign), ctypes.byref(o),
+                             ctypes.byref(self._handle)))
+        del pk, uk, wk
+        info = self.info()
+        self.n_pix, self.n_vis, self.ntrans = n_pix, n_vis, max(1, ntrans)
+        self.precision = info["precision"]
+        self.real_dtype = torch.float32 if self.precision == PREC_FP32 else torch.float64
+        self.complex_dtype = torch.complex64 if self.precision == PREC_FP32 else torch.complex128
+
+    # -------------------------------------------------------------- transforms
+    def _shape(self, n):
+        return (n,) if self.ntrans == 1 else (self.ntrans, n)
+
+    def _input(self, x, dtype, n):
+        import torch
+        if not isinstance(x, torch.Tensor):
+            x = torch.as_tensor(x)
+        if x.dtype != dtype:
+            raise TypeError(f"expected {dtype}, got {x.dtype} (the plan precision fixes the dtype)")
+        if x.numel() != self.ntrans * n:
+            raise ValueError(f"expected {self.ntrans * n} elements, got {x.numel()}")
+        return x.contiguous()
+
+    def _output(self, out, like, dtype, n):
+        import torch
+        if out is None:
+            return torch.empty(self._shape(n), dtype=dtype, device=like.device)
+        if out.dtype != dtype or out.numel() != self.ntrans * n or not out.is_contiguous():
+            raise ValueError("output tensor has the wrong dtype, size or layout")
+        return out
+
+    def synthesize(self, I, out=None):
+        """sky -> vis: V_k = sum_n a_n I_n exp(isign j 2 pi <p_k, r_n>)."""
+        I = self._input(I, self.real_dtype, self.n_pix)
+        V = self._output(out, I, self.complex_dtype, self.n_vis)
+        _check(load().hvox_synthesize(self._handle, ctypes.c_void_p(I.data_ptr()), ctypes.c_void_p(V.data_ptr())))
+        return V
+
+    def analyze(self, V, out=None):
+        """vis -> sky: I_n = a_n Re sum_k V_k exp(-isign j 2 pi <p_k, r_n>)."""
+        V = self._input(V, self.complex_dtype, self.n_vis)
+        I = self._output(out, V, self.real_dtype, self.n_pix)
+        _check(load().hvox_analyze(self._handle, ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(I.data_ptr())))
+        return I
+
+    dirty2vis = synthesize
+    vis2dirty = analyze
+
+    # -------------------------------------------------------------- introspection
+    def info(self) -> dict:
+        inf = Info()
+        _check(load().hvox_plan_info(self._handle, ctypes.byref(inf)))
+        d = {}
+        for name, _ in Info._fields_:
+            v = getattr(inf, name)
+            d[name] = list(v) if name in ("h", "eta") else v
+        return d
+
+    def chunks(self):
+        np = _np()
+        pc = np.zeros(self.n_pix, dtype=np.int64)
+        vc = np.zeros(self.n_vis, dtype=np.int64)
+        _check(load().hvox_plan_chunks(self._handle, pc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                       vc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return pc, vc
+
+    def sync(self):
+        _check(load().hvox_sync(self._handle))
+
+    def close(self):
+        if getattr(self, "_handle", None) and self._handle.value:
+            _check(load().hvox_destroy(self._handle))
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -1,0 +1,549 @@
+// C ABI of libhvox: argument checking, plan construction (host planner + device
+// tables), transform entry points and introspection. Every entry point converts
+// internal failures into a status code and a thread-local message.
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "hvox_internal.h"
+
+namespace hvox {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const std::string &msg) { g_last_error = msg; }
+const char *get_error() { return g_last_error.c_str(); }
+
+void fail(hvox_status code, const std::string &msg) { throw Error{code, msg}; }
+
+void check_cuda(cudaError_t e, const char *what) {
+    if (e != cudaSuccess) {
+        if (e == cudaErrorMemoryAllocation) fail(HVOX_ENOMEM, std::string(what) + ": out of device memory");
+        fail(HVOX_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+    }
+}
+
+void check_cufft(cufftResult r, const char *what) {
+    if (r != CUFFT_SUCCESS) {
+        if (r == CUFFT_ALLOC_FAILED) fail(HVOX_ENOMEM, std::string(what) + ": cuFFT allocation failed");
+        fail(HVOX_ECUDA, std::string(what) + ": cuFFT error " + std::to_string((int)r));
+    }
+}
+
+void DevBuf::alloc(size_t n) {
+    free_();
+    if (n == 0) return;
+    cudaError_t e = cudaMalloc(&ptr, n);
+    if (e != cudaSuccess) {
+        ptr = nullptr;
+        cudaGetLastError();
+        fail(HVOX_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed");
+    }
+    bytes = n;
+}
+
+void DevBuf::free_() {
+    if (ptr) cudaFree(ptr);
+    ptr = nullptr;
+    bytes = 0;
+}
+
+Plan::~Plan() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto &kv : fft_plans) cufftDestroy(kv.second);
+}
+
+namespace {
+
+template <typename F> hvox_status guard(F &&f) {
+    try {
+        f();
+        g_last_error.clear();
+        return HVOX_OK;
+    } catch (const Error &e) {
+        g_last_error = e.msg;
+        return e.code;
+    } catch (const std::bad_alloc &) {
+        g_last_error = "host allocation failed";
+        return HVOX_ENOMEM;
+    } catch (const std::exception &e) {
+        g_last_error = std::string("internal error: ") + e.what();
+        return HVOX_EINTERNAL;
+    }
+}
+
+bool is_device_ptr(const void *p) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+void to_host(const double *src, size_t n, std::vector<double> &dst) {
+    dst.resize(n);
+    if (is_device_ptr(src))
+        check_cuda(cudaMemcpy(dst.data(), src, n * sizeof(double), cudaMemcpyDeviceToHost), "copy input to host");
+    else
+        std::memcpy(dst.data(), src, n * sizeof(double));
+}
+
+// Tolerance given to the kernel-width rule: the type-3 transform chains two
+// approximations (spread on n1, interpolate on n2), each held to eps.
+constexpr double kEpsMargin = 1.0;
+
+void upload(DevBuf &b, const void *host, size_t bytes, cudaStream_t s) {
+    b.alloc(bytes);
+    if (bytes) check_cuda(cudaMemcpyAsync(b.ptr, host, bytes, cudaMemcpyHostToDevice, s), "upload");
+}
+
+void build_items(const std::vector<DirectRect> &rects, bool owner_is_vis, std::vector<WorkItem> &items) {
+    const int64_t T = direct_tile();
+    double work = 0;
+    for (auto &r : rects) work += (double)(r.p1 - r.p0) * (double)(r.v1 - r.v0);
+    const double target_items = 152.0 * 16.0;
+    int64_t seg = (int64_t)std::ceil(work / ((double)T * target_items) / 256.0) * 256;
+    seg = std::max<int64_t>(seg, 2048);
+    for (auto &r : rects) {
+        int64_t o0 = owner_is_vis ? r.v0 : r.p0, o1 = owner_is_vis ? r.v1 : r.p1;
+        int64_t s0 = owner_is_vis ? r.p0 : r.v0, s1 = owner_is_vis ? r.p1 : r.v1;
+        for (int64_t o = o0; o < o1; o += T)
+            for (int64_t q = s0; q < s1; q += seg)
+                items.push_back(WorkItem{(int32_t)o, (int32_t)std::min(o + T, o1), (int32_t)q,
+                                         (int32_t)std::min(q + seg, s1)});
+    }
+}
+
+void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const double *w_in) {
+    auto t0 = std::chrono::steady_clock::now();
+    cudaStream_t s = p.stream;
+    std::vector<double> pix, uvw, wt;
+    to_host(pix_in, (size_t)p.n_pix * 3, pix);
+    to_host(uvw_in, (size_t)p.n_vis * 3, uvw);
+    for (double v : pix)
+        if (!std::isfinite(v)) fail(HVOX_EINVAL, "hvox_plan: non-finite pixel coordinate");
+    for (double v : uvw)
+        if (!std::isfinite(v)) fail(HVOX_EINVAL, "hvox_plan: non-finite baseline coordinate");
+    if (w_in) {
+        to_host(w_in, (size_t)p.n_pix, wt);
+        for (double v : wt)
+            if (!std::isfinite(v)) fail(HVOX_EINVAL, "hvox_plan: non-finite weight");
+    }
+
+    const int elem = p.prec == 1 ? 8 : 16;
+    PlanInputs in{pix.data(), uvw.data(), p.n_pix, p.n_vis, p.sigma, p.es, p.prec, p.mode, p.plain,
+                  p.budget_opt, p.direct_threshold, elem};
+    p.part = make_partition(in);
+    PartitionResult &part = p.part;
+
+    // Chunk-ordered geometry.
+    std::vector<int32_t> pp(p.n_pix), vp(p.n_vis);
+    for (int64_t i = 0; i < p.n_pix; ++i) pp[i] = (int32_t)part.pix_perm[i];
+    for (int64_t i = 0; i < p.n_vis; ++i) vp[i] = (int32_t)part.vis_perm[i];
+    upload(p.pix_perm, pp.data(), pp.size() * 4, s);
+    upload(p.vis_perm, vp.data(), vp.size() * 4, s);
+    {
+        DevBuf tmp;
+        upload(tmp, pix.data(), pix.size() * 8, s);
+        p.pix_xyz.alloc((size_t)p.n_pix * 3 * 8);
+        p.pix_hi.alloc((size_t)p.n_pix * 16);
+        p.pix_lo.alloc((size_t)p.n_pix * 16);
+        launch_prepare_points(tmp.as<double>(), p.pix_perm.as<int32_t>(), p.n_pix, p.pix_xyz.as<double>(),
+                              p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), s);
+        check_cuda(cudaStreamSynchronize(s), "prepare pixels");
+    }
+    {
+        DevBuf tmp;
+        upload(tmp, uvw.data(), uvw.size() * 8, s);
+        p.vis_xyz.alloc((size_t)p.n_vis * 3 * 8);
+        p.vis_hi.alloc((size_t)p.n_vis * 16);
+        p.vis_lo.alloc((size_t)p.n_vis * 16);
+        launch_prepare_points(tmp.as<double>(), p.vis_perm.as<int32_t>(), p.n_vis, p.vis_xyz.as<double>(),
+                              p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), s);
+        check_cuda(cudaStreamSynchronize(s), "prepare baselines");
+    }
+    if (w_in) {
+        DevBuf tmp;
+        upload(tmp, wt.data(), wt.size() * 8, s);
+        p.weight.alloc((size_t)p.n_pix * 8);
+        launch_gather_weight(tmp.as<double>(), p.pix_perm.as<int32_t>(), p.n_pix, p.weight.as<double>(), s);
+        check_cuda(cudaStreamSynchronize(s), "gather weights");
+        p.has_weight = true;
+    }
+
+    // Direct work lists.
+    {
+        std::vector<WorkItem> a, b;
+        build_items(part.rects, true, a);
+        build_items(part.rects, false, b);
+        upload(p.items_s2v, a.data(), a.size() * sizeof(WorkItem), s);
+        upload(p.items_v2s, b.data(), b.size() * sizeof(WorkItem), s);
+        p.n_items_s2v = (int64_t)a.size();
+        p.n_items_v2s = (int64_t)b.size();
+    }
+
+    // exp(j 2 pi m / 256), m = -128 .. 128, split into float pairs.
+    {
+        std::vector<float> tab(257 * 4);
+        for (int i = 0; i < 257; ++i) {
+            double ang = 2.0 * M_PI * (double)(i - 128) / 256.0;
+            double c = std::cos(ang), sn = std::sin(ang);
+            float ch = (float)c, sh = (float)sn;
+            tab[4 * i + 0] = ch;
+            tab[4 * i + 1] = (float)(c - (double)ch);
+            tab[4 * i + 2] = sh;
+            tab[4 * i + 3] = (float)(sn - (double)sh);
+        }
+        upload(p.cis_tab, tab.data(), tab.size() * 4, s);
+    }
+
+    // NUFFT sub-problems.
+    const size_t re = p.prec == 1 ? 4 : 8;
+    int64_t psi_total = 0, prec_total = 0, vrec_total = 0, max_m1 = 0, max_m2 = 0;
+    for (auto &b : part.blocks) {
+        b.psi_off = psi_total;
+        b.prec_off = prec_total;
+        b.vrec_off = vrec_total;
+        psi_total += b.n1[0] + b.n1[1] + b.n1[2];
+        prec_total += b.p1 - b.p0;
+        vrec_total += b.v1 - b.v0;
+        max_m1 = std::max<int64_t>(max_m1, b.n1[0] * b.n1[1] * b.n1[2]);
+        max_m2 = std::max<int64_t>(max_m2, b.n2[0] * b.n2[1] * b.n2[2]);
+    }
+    if (!part.blocks.empty()) {
+        // 1 / Psi on the n1 band of each block and dimension.
+        std::vector<double> ipsi(psi_total);
+        for (auto &b : part.blocks)
+            for (int d = 0, off = 0; d < 3; off += (int)b.n1[d], ++d) {
+                std::vector<double> xi(b.n1[d]), ft(b.n1[d]);
+                for (int64_t l = 0; l < b.n1[d]; ++l) xi[l] = 2.0 * M_PI * (double)(l - b.n1[d] / 2) / (double)b.n2[d];
+                es_ft(p.es, xi.data(), b.n1[d], ft.data());
+                for (int64_t l = 0; l < b.n1[d]; ++l) ipsi[b.psi_off + off + l] = 1.0 / ft[l];
+            }
+        if (p.prec == 1) {
+            std::vector<float> f(ipsi.begin(), ipsi.end());
+            upload(p.inv_psi, f.data(), f.size() * 4, s);
+        } else {
+            upload(p.inv_psi, ipsi.data(), ipsi.size() * 8, s);
+        }
+        // Quadrature for Phi at the baselines.
+        std::vector<double> qz, qf;
+        es_ft_nodes(p.es, qz, qf);
+        const int nq = (int)qz.size();
+        DevBuf dqz, dqf;
+        upload(dqz, qz.data(), nq * 8, s);
+        upload(dqf, qf.data(), nq * 8, s);
+        p.err_word.alloc(sizeof(int));
+        check_cuda(cudaMemsetAsync(p.err_word.ptr, 0, sizeof(int), s), "memset err");
+        const size_t rec_bytes = p.prec == 1 ? sizeof(GridRec<float>) : sizeof(GridRec<double>);
+        p.pix_rec.alloc((size_t)prec_total * rec_bytes);
+        p.vis_rec.alloc((size_t)vrec_total * rec_bytes);
+        p.pix_phase.alloc((size_t)prec_total * 2 * re);
+        p.vis_phase.alloc((size_t)vrec_total * 2 * re);
+        for (auto &b : part.blocks) {
+            if (p.prec == 1)
+                nufft_tables<float>(b, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(), p.n_vis, p.es.w,
+                                    p.isign, dqz.as<double>(), dqf.as<double>(), nq, p.pix_rec.as<GridRec<float>>(),
+                                    p.pix_phase.as<float2>(), p.vis_rec.as<GridRec<float>>(),
+                                    p.vis_phase.as<float2>(), p.err_word.as<int>(), s);
+            else
+                nufft_tables<double>(b, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(), p.n_vis, p.es.w,
+                                     p.isign, dqz.as<double>(), dqf.as<double>(), nq,
+                                     p.pix_rec.as<GridRec<double>>(), p.pix_phase.as<double2>(),
+                                     p.vis_rec.as<GridRec<double>>(), p.vis_phase.as<double2>(),
+                                     p.err_word.as<int>(), s);
+        }
+        check_cuda(cudaStreamSynchronize(s), "nufft tables");
+        int err = 0;
+        check_cuda(cudaMemcpy(&err, p.err_word.ptr, sizeof(int), cudaMemcpyDeviceToHost), "read err word");
+        if (err) fail(HVOX_EINTERNAL, "hvox_plan: a spread window left its grid (coordinate rounding)");
+        p.grid1.alloc((size_t)max_m1 * 2 * re);
+        p.grid2.alloc((size_t)max_m2 * 2 * re);
+        // FFT plans per grid shape, one shared work area.
+        size_t max_ws = 0;
+        const cufftType type = p.prec == 1 ? CUFFT_C2C : CUFFT_Z2Z;
+        for (auto &b : part.blocks) {
+            auto key = std::make_tuple(b.n2[0], b.n2[1], b.n2[2]);
+            if (p.fft_plans.count(key)) continue;
+            cufftHandle h;
+            check_cufft(cufftCreate(&h), "cufftCreate");
+            p.fft_plans[key] = h;
+            check_cufft(cufftSetAutoAllocation(h, 0), "cufftSetAutoAllocation");
+            size_t ws = 0;
+            check_cufft(cufftMakePlan3d(h, (int)b.n2[2], (int)b.n2[1], (int)b.n2[0], type, &ws), "cufftMakePlan3d");
+            max_ws = std::max(max_ws, ws);
+        }
+        p.fft_work.alloc(std::max<size_t>(max_ws, 256));
+        for (auto &kv : p.fft_plans) check_cufft(cufftSetWorkArea(kv.second, p.fft_work.ptr), "cufftSetWorkArea");
+        for (auto &b : part.blocks) {
+            DevBlock d;
+            d.p0 = b.p0;
+            d.np = b.p1 - b.p0;
+            d.v0 = b.v0;
+            d.nv = b.v1 - b.v0;
+            for (int k = 0; k < 3; ++k) {
+                d.n1[k] = (int32_t)b.n1[k];
+                d.n2[k] = (int32_t)b.n2[k];
+            }
+            d.psi_off = b.psi_off;
+            d.prec_off = b.prec_off;
+            d.vrec_off = b.vrec_off;
+            p.dblocks.push_back(d);
+            p.block_fft.push_back(p.fft_plans[std::make_tuple(b.n2[0], b.n2[1], b.n2[2])]);
+        }
+    }
+
+    // Per-call buffers.
+    size_t src_bytes = std::max((size_t)p.n_pix * re, (size_t)p.n_vis * 2 * re);
+    p.src.alloc(src_bytes);
+    p.acc.alloc(src_bytes);
+    check_cuda(cudaStreamSynchronize(s), "hvox_plan");
+
+    double ws = 0;
+    for (DevBuf *b : {&p.pix_perm, &p.vis_perm, &p.weight, &p.pix_xyz, &p.vis_xyz, &p.pix_hi, &p.pix_lo, &p.vis_hi,
+                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.inv_psi, &p.pix_rec, &p.vis_rec, &p.pix_phase,
+                      &p.vis_phase, &p.grid1, &p.grid2, &p.fft_work, &p.src, &p.acc, &p.cis_tab, &p.err_word})
+        ws += (double)b->bytes;
+    p.workspace_bytes = ws;
+    p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+}
+
+void transform(Plan &p, const void *in, void *out, bool s2v) {
+    check_cuda(cudaSetDevice(p.device), "cudaSetDevice");
+    const size_t re = p.prec == 1 ? 4 : 8;
+    const size_t in_bytes = (size_t)p.ntrans * (s2v ? (size_t)p.n_pix * re : (size_t)p.n_vis * 2 * re);
+    const size_t out_bytes = (size_t)p.ntrans * (s2v ? (size_t)p.n_vis * 2 * re : (size_t)p.n_pix * re);
+    const bool din = is_device_ptr(in), dout = is_device_ptr(out);
+    const void *src = in;
+    void *dst = out;
+    if (!din) {
+        size_t need = (size_t)p.ntrans * std::max((size_t)p.n_pix * re, (size_t)p.n_vis * 2 * re);
+        if (p.io_in.bytes < need) p.io_in.alloc(need);
+        check_cuda(cudaMemcpyAsync(p.io_in.ptr, in, in_bytes, cudaMemcpyHostToDevice, p.stream), "copy input");
+        src = p.io_in.ptr;
+    }
+    if (!dout) {
+        size_t need = (size_t)p.ntrans * std::max((size_t)p.n_pix * re, (size_t)p.n_vis * 2 * re);
+        if (p.io_out.bytes < need) p.io_out.alloc(need);
+        dst = p.io_out.ptr;
+    }
+    if (s2v)
+        run_synthesize(p, src, dst);
+    else
+        run_analyze(p, src, dst);
+    if (!dout) {
+        check_cuda(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, p.stream), "copy output");
+        check_cuda(cudaStreamSynchronize(p.stream), "transform");
+    } else if (!din) {
+        check_cuda(cudaStreamSynchronize(p.stream), "transform");
+    }
+}
+
+}  // namespace
+}  // namespace hvox
+
+using namespace hvox;
+
+struct hvox_plan_s {
+    Plan p;
+};
+
+extern "C" {
+
+const char *hvox_last_error(void) { return get_error(); }
+
+const char *hvox_version(void) { return "hvox-gb300 0.1.0 (sm_103a)"; }
+
+hvox_status hvox_plan(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis,
+                      const double *pix_weight, double eps, int isign, const hvox_opts *opts, hvox_plan_t *out) {
+    if (out) *out = nullptr;
+    return guard([&] {
+        if (!out) fail(HVOX_EINVAL, "hvox_plan: out is NULL");
+        if (!pix_xyz || !uvw) fail(HVOX_EINVAL, "hvox_plan: NULL coordinates");
+        if (n_pix < 1 || n_vis < 1) fail(HVOX_EINVAL, "hvox_plan: need n_pix >= 1 and n_vis >= 1");
+        if (n_pix > INT32_MAX - 1024 || n_vis > INT32_MAX - 1024) fail(HVOX_EINVAL, "hvox_plan: too many points");
+        if (!std::isfinite(eps) || eps < 0.0) fail(HVOX_EINVAL, "hvox_plan: eps must be finite and >= 0");
+        if (isign != 1 && isign != -1) fail(HVOX_EINVAL, "hvox_plan: isign must be +1 or -1");
+        hvox_opts o;
+        std::memset(&o, 0, sizeof(o));
+        if (opts) o = *opts;
+        if (o.precision < 0 || o.precision > 2) fail(HVOX_EINVAL, "hvox_plan: bad precision");
+        if (o.mode < 0 || o.mode > 2) fail(HVOX_EINVAL, "hvox_plan: bad mode");
+        if (!(o.upsampfac == 0.0 || (o.upsampfac >= 1.25 && o.upsampfac <= 4.0)))
+            fail(HVOX_EINVAL, "hvox_plan: upsampfac must be 0 or in [1.25, 4]");
+        if (!(o.chunk_budget_bytes >= 0.0) || !std::isfinite(o.chunk_budget_bytes))
+            fail(HVOX_EINVAL, "hvox_plan: bad chunk_budget_bytes");
+        if (!(o.anisotropy == 0.0 || o.anisotropy >= 1.0)) fail(HVOX_EINVAL, "hvox_plan: anisotropy must be >= 1");
+        if (o.ntrans < 0) fail(HVOX_EINVAL, "hvox_plan: ntrans must be >= 0");
+        if (!std::isfinite(o.direct_threshold)) fail(HVOX_EINVAL, "hvox_plan: bad direct_threshold");
+        auto *h = new hvox_plan_s();
+        try {
+            Plan &p = h->p;
+            check_cuda(cudaGetDevice(&p.device), "cudaGetDevice");
+            p.n_pix = n_pix;
+            p.n_vis = n_vis;
+            p.eps = eps;
+            p.isign = isign;
+            p.plain = o.plain != 0;
+            p.mode = eps == 0.0 ? HVOX_MODE_DIRECT : o.mode;
+            p.prec = p.plain ? 2 : (o.precision == HVOX_PREC_AUTO ? (eps >= 1e-6 || eps == 0.0 ? 1 : 2) : o.precision);
+            if (eps == 0.0 && o.precision == HVOX_PREC_AUTO) p.prec = 2;
+            p.ntrans = o.ntrans > 0 ? o.ntrans : 1;
+            p.sigma = o.upsampfac > 0 ? o.upsampfac : 2.0;
+            p.stream = (cudaStream_t)o.stream;
+            p.budget_opt = o.chunk_budget_bytes;
+            p.direct_threshold = o.direct_threshold;
+            double e = eps > 0 ? eps : 1e-6;
+            if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
+            p.es = es_params(e * kEpsMargin, p.sigma);
+            build_plan(p, pix_xyz, uvw, pix_weight);
+        } catch (...) {
+            delete h;
+            throw;
+        }
+        *out = h;
+    });
+}
+
+hvox_status hvox_synthesize(hvox_plan_t plan, const void *I, void *V) {
+    return guard([&] {
+        if (!plan || !I || !V) fail(HVOX_EINVAL, "hvox_synthesize: NULL argument");
+        transform(plan->p, I, V, true);
+    });
+}
+
+hvox_status hvox_analyze(hvox_plan_t plan, const void *V, void *I) {
+    return guard([&] {
+        if (!plan || !I || !V) fail(HVOX_EINVAL, "hvox_analyze: NULL argument");
+        transform(plan->p, V, I, false);
+    });
+}
+
+hvox_status hvox_dirty2vis(hvox_plan_t plan, const void *I, void *V) { return hvox_synthesize(plan, I, V); }
+hvox_status hvox_vis2dirty(hvox_plan_t plan, const void *V, void *I) { return hvox_analyze(plan, V, I); }
+
+hvox_status hvox_destroy(hvox_plan_t plan) {
+    return guard([&] { delete plan; });
+}
+
+hvox_status hvox_sync(hvox_plan_t plan) {
+    return guard([&] {
+        if (!plan) fail(HVOX_EINVAL, "hvox_sync: NULL plan");
+        check_cuda(cudaSetDevice(plan->p.device), "cudaSetDevice");
+        check_cuda(cudaStreamSynchronize(plan->p.stream), "hvox_sync");
+        check_cuda(cudaGetLastError(), "hvox_sync");
+    });
+}
+
+hvox_status hvox_plan_info(hvox_plan_t plan, hvox_info *info) {
+    return guard([&] {
+        if (!plan || !info) fail(HVOX_EINVAL, "hvox_plan_info: NULL argument");
+        const Plan &p = plan->p;
+        std::memset(info, 0, sizeof(*info));
+        info->n_pix = p.n_pix;
+        info->n_vis = p.n_vis;
+        info->precision = p.prec;
+        info->isign = p.isign;
+        info->eps = p.eps;
+        info->w = p.es.w;
+        info->beta = p.es.beta;
+        info->upsampfac = p.sigma;
+        info->budget_bytes = p.part.budget;
+        info->t = p.part.t;
+        for (int d = 0; d < 3; ++d) {
+            info->h[d] = p.part.h[d];
+            info->eta[d] = p.part.eta[d];
+        }
+        info->n_pix_chunks = p.part.n_pix_chunks;
+        info->n_vis_chunks = p.part.n_vis_chunks;
+        info->n_nufft_blocks = (int64_t)p.part.blocks.size();
+        info->n_direct_rects = (int64_t)p.part.rects.size();
+        info->direct_pairs = p.part.direct_pairs;
+        info->nufft_points = p.part.nufft_points;
+        info->nufft_cells = p.part.nufft_cells;
+        info->max_grid_bytes = p.part.max_grid_bytes;
+        info->workspace_bytes = p.workspace_bytes;
+        info->plan_seconds = p.plan_seconds;
+        info->model_seconds = p.part.model_seconds;
+    });
+}
+
+hvox_status hvox_plan_chunks(hvox_plan_t plan, int64_t *pix_chunk, int64_t *vis_chunk) {
+    return guard([&] {
+        if (!plan) fail(HVOX_EINVAL, "hvox_plan_chunks: NULL plan");
+        const Plan &p = plan->p;
+        if (pix_chunk) std::memcpy(pix_chunk, p.part.pix_label.data(), sizeof(int64_t) * p.n_pix);
+        if (vis_chunk) std::memcpy(vis_chunk, p.part.vis_label.data(), sizeof(int64_t) * p.n_vis);
+    });
+}
+
+double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_opts *opts) {
+    if (n_pix < 1 || n_vis < 1 || !(eps >= 0.0)) return 0.0;
+    int prec = 1;
+    if (opts && opts->plain) prec = 2;
+    else if (opts && opts->precision) prec = opts->precision;
+    else if (eps > 0 && eps < 1e-6) prec = 2;
+    const double re = prec == 1 ? 4.0 : 8.0;
+    const int nt = (opts && opts->ntrans > 0) ? opts->ntrans : 1;
+    double geom = (double)(n_pix + n_vis) * (4.0 + 24.0 + 32.0) + (double)n_pix * 8.0;
+    double bufs = 2.0 * std::max((double)n_pix * re, (double)n_vis * 2.0 * re);
+    double io = 2.0 * nt * std::max((double)n_pix * re, (double)n_vis * 2.0 * re);
+    double budget = (opts && opts->chunk_budget_bytes > 0) ? opts->chunk_budget_bytes : 256.0 * 1024 * 1024;
+    return geom + bufs + io + 2.0 * budget;
+}
+
+hvox_status hvox_es_params(double eps, double sigma, int32_t *w, double *beta) {
+    return guard([&] {
+        if (!w || !beta) fail(HVOX_EINVAL, "hvox_es_params: NULL output");
+        ESKernel k = es_params(eps, sigma);
+        *w = k.w;
+        *beta = k.beta;
+    });
+}
+
+hvox_status hvox_es_ft(int32_t w, double beta, const double *xi, int64_t n, double *out) {
+    return guard([&] {
+        if (w < 2 || w > 16 || !(beta > 0) || n < 0 || (n > 0 && (!xi || !out)))
+            fail(HVOX_EINVAL, "hvox_es_ft: bad arguments");
+        ESKernel k;
+        k.w = w;
+        k.beta = beta;
+        es_ft(k, xi, n, out);
+    });
+}
+
+hvox_status hvox_box_dims(const double P[3], const double B[3], double budget_bytes, double sigma, int32_t w,
+                          int32_t elem_bytes, double eta[3], double h[3], double *t) {
+    return guard([&] {
+        if (!P || !B || !eta || !h || !t) fail(HVOX_EINVAL, "hvox_box_dims: NULL argument");
+        if (!(budget_bytes > 0) || !(sigma > 1.0) || w < 2 || elem_bytes <= 0)
+            fail(HVOX_EINVAL, "hvox_box_dims: bad arguments");
+        for (int d = 0; d < 3; ++d)
+            if (!(P[d] >= 0) || !(B[d] >= 0) || !std::isfinite(P[d]) || !std::isfinite(B[d]))
+                fail(HVOX_EINVAL, "hvox_box_dims: extents must be finite and >= 0");
+        *t = box_dims(P, B, budget_bytes, sigma, w, elem_bytes, eta, h);
+    });
+}
+
+hvox_status hvox_chunk_points(const double *xyz, int64_t n, const double h[3], int64_t *labels, int64_t *n_chunks) {
+    return guard([&] {
+        if (!xyz || !h || !labels || !n_chunks || n < 0) fail(HVOX_EINVAL, "hvox_chunk_points: bad arguments");
+        for (int64_t i = 0; i < 3 * n; ++i)
+            if (!std::isfinite(xyz[i])) fail(HVOX_EINVAL, "hvox_chunk_points: non-finite coordinate");
+        std::vector<int64_t> lab;
+        *n_chunks = chunk_points(xyz, n, h, lab);
+        if (n) std::memcpy(labels, lab.data(), sizeof(int64_t) * n);
+    });
+}
+
+}  // extern "C"

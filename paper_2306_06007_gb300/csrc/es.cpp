@@ -1,0 +1,84 @@
+// "Exponential of semicircle" (ES) spreading kernel: parameters and Fourier transform.
+//
+// The paper uses the ES pulse of Barnett, Magland and af Klinteberg (2019) through
+// its type-3 engine (footnote on spreading kernels, Sect. 2.1); the kernel is
+//   phi(z) = exp(beta (sqrt(1 - (2 z / w)^2) - 1)),  |z| <= w/2 grid cells,
+// with width w ~ number of digits of accuracy per dimension.
+#include <cmath>
+#include <stdexcept>
+
+#include "hvox_internal.h"
+
+namespace hvox {
+
+ESKernel es_params(double eps, double sigma) {
+    if (!(eps > 0.0) || !(sigma > 1.0)) fail(HVOX_EINVAL, "es_params: need eps > 0 and sigma > 1");
+    ESKernel k;
+    double wd = std::ceil(std::log(1.0 / eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)));
+    k.w = (int)std::max(2.0, wd);
+    if (k.w > 16) fail(HVOX_EUNSUPPORTED, "es_params: tolerance needs a kernel wider than 16 cells");
+    k.beta = 0.97 * M_PI * k.w * (1.0 - 1.0 / (2.0 * sigma));
+    return k;
+}
+
+void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &wt) {
+    x.assign(q, 0.0);
+    wt.assign(q, 0.0);
+    for (int i = 0; i < q; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (q + 0.5));
+        double dp = 0.0;
+        for (int it = 0; it < 100; ++it) {
+            // Legendre recurrence: (m+1) P_{m+1} = (2m+1) z P_m - m P_{m-1}
+            double p0 = 1.0, p1 = z;
+            for (int m = 1; m < q; ++m) {
+                double p2 = ((2.0 * m + 1.0) * z * p1 - m * p0) / (m + 1.0);
+                p0 = p1;
+                p1 = p2;
+            }
+            dp = q * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        double p0 = 1.0, p1 = z;
+        for (int m = 1; m < q; ++m) {
+            double p2 = ((2.0 * m + 1.0) * z * p1 - m * p0) / (m + 1.0);
+            p0 = p1;
+            p1 = p2;
+        }
+        dp = q * (z * p1 - p0) / (z * z - 1.0);
+        x[i] = z;
+        wt[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+int es_quad_nodes(const ESKernel &k) { return 3 * k.w + 32; }
+
+// Nodes and weights of Phi(xi) = sum_m f_m cos(xi z_m). With z = (w/2) sin(theta) the
+// integrand exp(beta (cos(theta) - 1)) cos(xi z) (w/2) cos(theta) is smooth on
+// [-pi/2, pi/2], so Gauss-Legendre in theta converges geometrically.
+void es_ft_nodes(const ESKernel &k, std::vector<double> &z, std::vector<double> &f) {
+    std::vector<double> x, wt;
+    int q = es_quad_nodes(k);
+    gauss_legendre(q, x, wt);
+    const double half = 0.5 * k.w;
+    z.resize(q);
+    f.resize(q);
+    for (int m = 0; m < q; ++m) {
+        double th = 0.5 * M_PI * x[m];
+        z[m] = half * std::sin(th);
+        f[m] = 0.5 * M_PI * wt[m] * half * std::cos(th) * std::exp(k.beta * (std::cos(th) - 1.0));
+    }
+}
+
+void es_ft(const ESKernel &k, const double *xi, int64_t n, double *out) {
+    std::vector<double> z, f;
+    es_ft_nodes(k, z, f);
+    for (int64_t i = 0; i < n; ++i) {
+        double s = 0.0;
+        for (size_t m = 0; m < z.size(); ++m) s += f[m] * std::cos(xi[i] * z[m]);
+        out[i] = s;
+    }
+}
+
+}  // namespace hvox

@@ -1,0 +1,260 @@
+// Internal declarations shared by the host planner/executor and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstdint>
+#include <map>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "../../include/hvox.h"
+
+namespace hvox {
+
+// ------------------------------------------------------------------ errors
+
+void set_error(const std::string &msg);
+const char *get_error();
+
+struct Error {
+    hvox_status code;
+    std::string msg;
+};
+
+// Throwing helpers used inside the library; the ABI layer converts to codes.
+[[noreturn]] void fail(hvox_status code, const std::string &msg);
+void check_cuda(cudaError_t e, const char *what);
+void check_cufft(cufftResult r, const char *what);
+
+// ------------------------------------------------------------------ ES kernel
+
+struct ESKernel {
+    int w = 0;          // width in grid cells per dimension
+    double beta = 0.0;  // shape
+};
+
+ESKernel es_params(double eps, double sigma);
+// Gauss-Legendre nodes/weights on [-1, 1].
+void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &wt);
+// int phi(z) cos(xi z) dz over |z| <= w/2 for each xi (host FP64).
+void es_ft(const ESKernel &k, const double *xi, int64_t n, double *out);
+int es_quad_nodes(const ESKernel &k);
+void es_ft_nodes(const ESKernel &k, std::vector<double> &z, std::vector<double> &f);
+
+// ------------------------------------------------------------------ planning
+
+int64_t smooth_even(int64_t n);
+void grid_sizes(double extent_pix, double extent_vis, double sigma, int w, int64_t &n1, int64_t &n2);
+double grid_bytes(const double P[3], const double B[3], double sigma, int w, int elem_bytes);
+double box_dims(const double P[3], const double B[3], double budget, double sigma, int w, int elem_bytes,
+                double eta[3], double h[3]);
+// Algorithm 2. labels[i] in [0, n_chunks).
+int64_t chunk_points(const double *xyz, int64_t n, const double h[3], std::vector<int64_t> &labels);
+
+// One sub-problem evaluated by type-3 NUFFT.
+struct NufftBlock {
+    int64_t pix_chunk = 0, vis_chunk = 0;
+    int64_t p0 = 0, p1 = 0;   // pixel range in chunk order
+    int64_t v0 = 0, v1 = 0;   // baseline range in chunk order
+    double C[3] = {0, 0, 0};  // pixel-box centre
+    double D[3] = {0, 0, 0};  // baseline-box centre (wavelengths)
+    double a[3] = {0, 0, 0};  // spread-grid cells per unit of r
+    int64_t n1[3] = {0, 0, 0};
+    int64_t n2[3] = {0, 0, 0};
+    int64_t psi_off = 0;      // offset of this block's 1/psi tables (n1[0]+n1[1]+n1[2])
+    int64_t prec_off = 0;     // offset of pixel-side records (p1 - p0 entries)
+    int64_t vrec_off = 0;     // offset of baseline-side records (v1 - v0 entries)
+    double cost = 0.0;
+};
+
+// A rectangle of direct work: pixels [p0, p1) x baselines [v0, v1) (chunk order).
+struct DirectRect {
+    int64_t p0, p1, v0, v1;
+};
+
+// Work item of the direct kernels: owner tile [o0, o1) and streamed range [s0, s1).
+struct WorkItem {
+    int32_t o0, o1, s0, s1;
+};
+
+struct CostModel {
+    double direct_pair = 0;   // seconds per (pixel, baseline) pair
+    double spread_tap = 0;    // seconds per (point, tap) of spread or interpolation
+    double fft_cell = 0;      // seconds per FFT-grid cell per log2(cells)
+    double grid_cell = 0;     // seconds per grid cell of pad/crop/zero passes
+    double block_fixed = 0;   // seconds of fixed overhead per NUFFT block (launches)
+};
+
+CostModel default_cost_model(int prec, bool plain, int w);
+
+struct PartitionResult {
+    double t = 1.0, h[3] = {0, 0, 0}, eta[3] = {0, 0, 0}, budget = 0;
+    std::vector<int64_t> pix_label, vis_label;  // original index -> chunk label
+    int64_t n_pix_chunks = 0, n_vis_chunks = 0;
+    std::vector<int64_t> pix_perm, vis_perm;    // chunk-order position -> original index
+    std::vector<int64_t> pix_chunk_start, vis_chunk_start;  // per ordered chunk, size chunks+1
+    std::vector<int64_t> pix_chunk_label, vis_chunk_label;  // ordered chunk -> Algorithm 2 label
+    std::vector<NufftBlock> blocks;
+    std::vector<DirectRect> rects;
+    double direct_pairs = 0, nufft_points = 0, nufft_cells = 0, max_grid_bytes = 0;
+    double model_seconds = 0;
+};
+
+struct PlanInputs {
+    const double *pix;     // host (n_pix, 3)
+    const double *uvw;     // host (n_vis, 3)
+    int64_t n_pix, n_vis;
+    double sigma;
+    ESKernel es;
+    int prec;              // 1 fp32, 2 fp64
+    int mode;
+    bool plain;
+    double budget;         // 0 -> search
+    double direct_threshold;
+    int elem_bytes;
+};
+
+PartitionResult make_partition(const PlanInputs &in);
+
+// ------------------------------------------------------------------ device buffers
+
+struct DevBuf {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+    void alloc(size_t n);
+    void free_();
+    ~DevBuf() { free_(); }
+    DevBuf() = default;
+    DevBuf(const DevBuf &) = delete;
+    DevBuf &operator=(const DevBuf &) = delete;
+    template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
+};
+
+// Device-side description of a NUFFT block (mirrors NufftBlock, POD for kernels).
+struct DevBlock {
+    int64_t p0, np, v0, nv;
+    int32_t n1[3], n2[3];
+    int64_t psi_off, prec_off, vrec_off;
+};
+
+// Per-(point, block) grid record: window start (integer cell) and offset in the cell.
+template <typename T> struct alignas(16) GridRec {
+    int32_t i0[3];
+    int32_t pad;
+    T fr[3];
+    T pad2;
+};
+
+struct Plan {
+    // configuration
+    int64_t n_pix = 0, n_vis = 0;
+    double eps = 0;
+    int isign = -1;
+    int prec = 1;          // 1 fp32, 2 fp64
+    int mode = 0;
+    bool plain = false;
+    int ntrans = 1;
+    double sigma = 2.0;
+    double budget_opt = 0.0;       // chunk_budget_bytes option (0 -> cost-model search)
+    double direct_threshold = 0.0; // direct_threshold option
+    ESKernel es;
+    bool has_weight = false;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+
+    PartitionResult part;
+    double plan_seconds = 0;
+
+    // chunk-ordered geometry
+    DevBuf pix_perm, vis_perm;          // int32 position -> original index
+    DevBuf weight;                      // double[n_pix] chunk order (or empty)
+    DevBuf pix_xyz, vis_xyz;            // double SoA [3][n] chunk order
+    DevBuf pix_hi, pix_lo, vis_hi, vis_lo;  // float4 splits of the FP64 coordinates
+
+    // direct work lists
+    DevBuf items_s2v, items_v2s;
+    int64_t n_items_s2v = 0, n_items_v2s = 0;
+
+    // NUFFT tables
+    DevBuf blocks_dev;                  // DevBlock[]
+    DevBuf inv_psi;                     // T per (block, dim, l)
+    DevBuf pix_rec, vis_rec;            // GridRec<T>
+    DevBuf pix_phase, vis_phase;        // complex<T>: prephase (pixels), postphase/phihat (baselines)
+    int64_t n_pix_rec = 0, n_vis_rec = 0;
+    DevBuf grid1, grid2;                // largest spread grid and FFT grid
+    std::map<std::tuple<int64_t, int64_t, int64_t>, cufftHandle> fft_plans;
+    DevBuf fft_work;
+    std::vector<DevBlock> dblocks;      // host copy of the block descriptors (launch order)
+    std::vector<cufftHandle> block_fft; // FFT plan of each block
+    DevBuf cis_tab;                     // exp(j 2 pi m / 256) as float pairs (double-float path)
+
+    // per-call buffers (chunk order)
+    DevBuf src, acc;                    // source values, accumulated outputs
+    DevBuf io_in, io_out;               // staging for host-pointer calls
+    DevBuf err_word;                    // device error flag
+
+    double workspace_bytes = 0;
+    ~Plan();
+};
+
+// ------------------------------------------------------------------ kernel launchers
+
+// Split FP64 (n, 3) coordinates into hi/lo float4 arrays and an FP64 SoA copy, in chunk
+// order given perm (position -> original index).
+void launch_prepare_points(const double *xyz_orig_dev, const int32_t *perm, int64_t n, double *soa,
+                           float4 *hi, float4 *lo, cudaStream_t s);
+void launch_gather_weight(const double *w_orig_dev, const int32_t *perm, int64_t n, double *w_perm,
+                          cudaStream_t s);
+
+// Direct kernels (k_direct.cu). Owner tile = direct_tile() points per work item.
+int direct_tile();
+void launch_direct_s2v_f32(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+                           const float4 *rl, const float *c, float2 *acc, int isign, cudaStream_t s);
+void launch_direct_s2v_df(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+                          const float4 *rl, const double *c, double2 *acc, const float4 *tab, int isign,
+                          cudaStream_t s);
+void launch_direct_s2v_f64(const WorkItem *items, int64_t n, const double *vxyz, int64_t nv, const double *pxyz,
+                           int64_t np, const double *c, double2 *acc, int isign, cudaStream_t s);
+void launch_direct_v2s_f32(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+                           const float4 *vl, const float2 *V, float *acc, int isign, cudaStream_t s);
+void launch_direct_v2s_df(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+                          const float4 *vl, const double2 *V, double *acc, const float4 *tab, int isign,
+                          cudaStream_t s);
+void launch_direct_v2s_f64(const WorkItem *items, int64_t n, const double *pxyz, int64_t np, const double *vxyz,
+                           int64_t nv, const double2 *V, double *acc, int isign, cudaStream_t s);
+
+// NUFFT sub-problems (k_nufft.cu).
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+
+template <typename T>
+void nufft_block_s2v(const DevBlock &b, int w, double beta, const T *c, const GridRec<T> *prec,
+                     const typename CplxOf<T>::type *pph, const GridRec<T> *vrec, const typename CplxOf<T>::type *vq,
+                     const T *ipsi, typename CplxOf<T>::type *G1, typename CplxOf<T>::type *G2, cufftHandle plan,
+                     int isign, typename CplxOf<T>::type *acc, cudaStream_t s);
+template <typename T>
+void nufft_block_v2s(const DevBlock &b, int w, double beta, const typename CplxOf<T>::type *V, const GridRec<T> *prec,
+                     const typename CplxOf<T>::type *pph, const GridRec<T> *vrec, const typename CplxOf<T>::type *vq,
+                     const T *ipsi, typename CplxOf<T>::type *G1, typename CplxOf<T>::type *G2, cufftHandle plan,
+                     int isign, T *acc, cudaStream_t s);
+template <typename T>
+void nufft_tables(const NufftBlock &b, const double *pix_soa, int64_t n_pix, const double *vis_soa, int64_t n_vis,
+                  int w, int isign, const double *qz, const double *qf, int nq, GridRec<T> *prec,
+                  typename CplxOf<T>::type *pph, GridRec<T> *vrec, typename CplxOf<T>::type *vq, int *err,
+                  cudaStream_t s);
+
+// Permutations between the caller's order and chunk order (k_misc.cu).
+void launch_s2v_in(int prec, const void *I, const int32_t *perm, const double *w, int64_t n, void *src, cudaStream_t s);
+void launch_s2v_out(int prec, const void *acc, const int32_t *perm, int64_t n, void *V, cudaStream_t s);
+void launch_v2s_in(int prec, const void *V, const int32_t *perm, int64_t n, void *src, cudaStream_t s);
+void launch_v2s_out(int prec, const void *acc, const int32_t *perm, const double *w, int64_t n, void *I, cudaStream_t s);
+
+// Transforms.
+void run_synthesize(Plan &p, const void *I_dev, void *V_dev);
+void run_analyze(Plan &p, const void *V_dev, void *I_dev);
+
+}  // namespace hvox

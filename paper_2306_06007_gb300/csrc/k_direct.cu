@@ -1,0 +1,613 @@
+// Direct evaluation of sub-problems (Sect. 3.1: blocks below a size threshold are
+// summed directly, O(n_pix n_vis), Sect. 2) and the point preparation kernels.
+//
+//   sky -> vis:  V_k += sum_n c_n exp(+isign j 2 pi <p_k, r_n>),  c_n = a_n I_n
+//   vis -> sky:  I_n += Re sum_k V_k exp(-isign j 2 pi <p_k, r_n>)
+//
+// The phase <p, r> reaches ~1e5 turns, so it is never formed in plain FP32. Every
+// coordinate is stored as a pair of floats hi + lo (hi = fl32(x), lo = fl32(x - hi)).
+// Per pair the main products hi(p) hi(r) are split exactly (TwoProduct by fma), their
+// integer turns dropped exactly, and only the fraction of a turn is carried on:
+//  * FP32 path (eps >= 1e-6): fraction in FP32 (abs error ~1e-7 turn), hardware
+//    sin/cos approximations, FP32 accumulation;
+//  * double-float path (eps < 1e-6): fraction as an unevaluated float pair, sin/cos
+//    from a 256-entry table of exp(j 2 pi m / 256) (float pairs) times a short series,
+//    products and sums in double-float arithmetic (Dekker 1971), ~1e-11 absolute;
+//  * plain path: everything in FP64 (the reference form the optimised paths replace).
+#include <cstdint>
+
+#include "hvox_internal.h"
+
+namespace hvox {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kPerThread = 2;
+constexpr int kTile = kThreads * kPerThread;  // owner points per work item
+
+// ------------------------------------------------------------- point preparation
+
+__global__ void prepare_points_kernel(const double *__restrict__ xyz, const int32_t *__restrict__ perm, int64_t n,
+                                      double *__restrict__ soa, float4 *__restrict__ hi, float4 *__restrict__ lo) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int64_t src = perm[i];
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+        double x = xyz[3 * src + d];
+        soa[d * n + i] = x;
+        h[d] = (float)x;
+        l[d] = (float)(x - (double)h[d]);
+    }
+    hi[i] = make_float4(h[0], h[1], h[2], 0.f);
+    lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+__global__ void gather_weight_kernel(const double *__restrict__ w, const int32_t *__restrict__ perm, int64_t n,
+                                     double *__restrict__ out) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n) out[i] = w[perm[i]];
+}
+
+// ------------------------------------------------------------- float helpers
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// Fraction of <p, r> in turns, FP32 (|error| ~ 1e-7 turn), result in [-0.5, 0.5].
+__device__ __forceinline__ float phase_f32(const float3 &ph, const float3 &pl, const float4 &rh, const float4 &rl) {
+    float a0, b0, a1, b1, a2, b2;
+    two_prod(ph.x, rh.x, a0, b0);
+    two_prod(ph.y, rh.y, a1, b1);
+    two_prod(ph.z, rh.z, a2, b2);
+    a0 = __fsub_rn(a0, rintf(a0));
+    a1 = __fsub_rn(a1, rintf(a1));
+    a2 = __fsub_rn(a2, rintf(a2));
+    float cross = __fmaf_rn(ph.x, rl.x, __fmul_rn(pl.x, rh.x));
+    cross = __fmaf_rn(ph.y, rl.y, __fmaf_rn(pl.y, rh.y, cross));
+    cross = __fmaf_rn(ph.z, rl.z, __fmaf_rn(pl.z, rh.z, cross));
+    float small = __fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, cross));
+    float f = __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, small));
+    return __fsub_rn(f, rintf(f));
+}
+
+// Fraction of <p, r> in turns as a float pair (fh + fl), |error| ~ 1e-12 turn * |p|/1e5.
+__device__ __forceinline__ void phase_df(const float3 &ph, const float3 &pl, const float4 &rh, const float4 &rl,
+                                         float &fh, float &fl) {
+    float a0, b0, a1, b1, a2, b2;
+    two_prod(ph.x, rh.x, a0, b0);
+    two_prod(ph.y, rh.y, a1, b1);
+    two_prod(ph.z, rh.z, a2, b2);
+    a0 = __fsub_rn(a0, rintf(a0));
+    a1 = __fsub_rn(a1, rintf(a1));
+    a2 = __fsub_rn(a2, rintf(a2));
+    float s1, e1, s2, e2;
+    two_sum(a0, a1, s1, e1);
+    two_sum(s1, a2, s2, e2);
+    s2 = __fsub_rn(s2, rintf(s2));
+    float cross = __fmaf_rn(ph.x, rl.x, __fmul_rn(pl.x, rh.x));
+    cross = __fmaf_rn(ph.y, rl.y, __fmaf_rn(pl.y, rh.y, cross));
+    cross = __fmaf_rn(ph.z, rl.z, __fmaf_rn(pl.z, rh.z, cross));
+    float small = __fadd_rn(__fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, e1)), __fadd_rn(e2, cross));
+    fast_two_sum(s2, small, fh, fl);
+    fh = __fsub_rn(fh, rintf(fh));  // exact; fh in [-0.5, 0.5] for the table lookup
+}
+
+constexpr int kTab = 256;      // table entries per turn
+constexpr int kTabOff = 128;   // index offset: m = rint(256 f) in [-128, 128] for |f| <= 0.5
+constexpr int kTabLen = 257;
+
+// exp(j 2 pi f) for f = fh + fl (turns), as float pairs (re_h, re_l, im_h, im_l).
+// T holds (cos_h, cos_l, sin_h, sin_l) of 2 pi m / 256 for m = idx - kTabOff.
+__device__ __forceinline__ void cis_df(float fh, float fl, const float4 *__restrict__ T, float &reh, float &rel,
+                                       float &imh, float &iml) {
+    const float TWO_PI_H = 6.28318548202514648f;        // fl32(2 pi)
+    const float TWO_PI_L = -1.74845553146951427e-07f;   // fl32(2 pi - TWO_PI_H)
+    float m = rintf(__fmul_rn(fh, (float)kTab));
+    float d = __fmaf_rn(m, -1.0f / kTab, fh);            // exact
+    float xh, xe;
+    two_prod(d, TWO_PI_H, xh, xe);
+    float xl = __fadd_rn(xe, __fmaf_rn(d, TWO_PI_L, __fmul_rn(fl, TWO_PI_H)));
+    float x2 = __fmul_rn(xh, xh);
+    // sin x = x - x^3/6 + x^5/120 (|x| <= 0.013: truncation < 1e-15)
+    float sc = __fmul_rn(__fmul_rn(xh, x2), __fmaf_rn(x2, 1.0f / 120.0f, -1.0f / 6.0f));
+    // cos x - 1 = -x^2/2 + x^4/24 - x^6/720
+    float cm = __fmul_rn(x2, __fmaf_rn(x2, __fmaf_rn(x2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f));
+    float4 t = T[(int)m + kTabOff];
+    float u = __fadd_rn(xl, sc);  // sin x = xh + u
+    float p1, p1e, p2, p2e;
+    two_prod(t.z, xh, p1, p1e);   // sin_h * xh
+    two_prod(t.x, xh, p2, p2e);   // cos_h * xh
+    float rs, re;
+    two_sum(t.x, -p1, rs, re);
+    float rlo = __fadd_rn(__fadd_rn(re, __fmaf_rn(t.x, cm, t.y)),
+                          -__fadd_rn(p1e, __fmaf_rn(t.z, u, __fmul_rn(t.w, xh))));
+    float is, ie;
+    two_sum(t.z, p2, is, ie);
+    float ilo = __fadd_rn(__fadd_rn(ie, __fmaf_rn(t.z, cm, t.w)),
+                          __fadd_rn(p2e, __fmaf_rn(t.x, u, __fmul_rn(t.y, xh))));
+    fast_two_sum(rs, rlo, reh, rel);
+    fast_two_sum(is, ilo, imh, iml);
+}
+
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
+    float p, e;
+    two_prod(ah, bh, p, e);
+    e = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, e));
+    ph = p;
+    pl = e;
+}
+
+// Lazy double-float accumulation: hi carries an exact TwoSum, lo collects the errors.
+__device__ __forceinline__ void df_acc(float &acc_h, float &acc_l, float th, float tl) {
+    float s, e;
+    two_sum(acc_h, th, s, e);
+    acc_h = s;
+    acc_l = __fadd_rn(acc_l, __fadd_rn(e, tl));
+}
+
+__device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ gT) {
+    for (int i = threadIdx.x; i < kTabLen; i += blockDim.x) sT[i] = gT[i];
+}
+
+// ------------------------------------------------------------- sky -> vis
+
+// FP32: owner = baselines, streamed = pixels (c real, chunk order).
+__global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__restrict__ items, int n_items,
+                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
+                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
+                                                           const float *__restrict__ c, float2 *__restrict__ acc,
+                                                           float sgn) {
+    __shared__ float4 sh[kThreads];
+    __shared__ float4 sl[kThreads];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        float3 ph[kPerThread], pl[kPerThread];
+        float are[kPerThread], aim[kPerThread];
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int k = w.o0 + threadIdx.x + v * kThreads;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (k < w.o1) {
+                a = vh[k];
+                b = vl[k];
+            }
+            ph[v] = make_float3(a.x, a.y, a.z);
+            pl[v] = make_float3(b.x, b.y, b.z);
+            are[v] = 0.f;
+            aim[v] = 0.f;
+        }
+        for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
+            __syncthreads();
+            int n = s0 + threadIdx.x;
+            if (n < w.s1) {
+                float4 a = rh_g[n];
+                a.w = c[n];
+                sh[threadIdx.x] = a;
+                sl[threadIdx.x] = rl_g[n];
+            } else {
+                sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            const int cnt = min(kThreads, w.s1 - s0);
+#pragma unroll 4
+            for (int q = 0; q < cnt; ++q) {
+                const float4 rh = sh[q], rl = sl[q];
+#pragma unroll
+                for (int v = 0; v < kPerThread; ++v) {
+                    float f = phase_f32(ph[v], pl[v], rh, rl);
+                    float sn, cs;
+                    __sincosf(6.28318530717958648f * f, &sn, &cs);
+                    are[v] = __fmaf_rn(rh.w, cs, are[v]);
+                    aim[v] = __fmaf_rn(rh.w, sn, aim[v]);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int k = w.o0 + threadIdx.x + v * kThreads;
+            if (k < w.o1) {
+                atomicAdd(&acc[k].x, are[v]);
+                atomicAdd(&acc[k].y, sgn * aim[v]);
+            }
+        }
+    }
+}
+
+// Double-float: c given in FP64, accumulation returned in FP64.
+__global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__restrict__ items, int n_items,
+                                                          const float4 *__restrict__ vh, const float4 *__restrict__ vl,
+                                                          const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
+                                                          const double *__restrict__ c, double2 *__restrict__ acc,
+                                                          const float4 *__restrict__ gT, float sgn) {
+    __shared__ float4 sh[kThreads];
+    __shared__ float4 sl[kThreads];
+    __shared__ float2 sc[kThreads];
+    __shared__ float4 sT[kTabLen];
+    load_tab(sT, gT);
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        float3 ph[kPerThread], pl[kPerThread];
+        float arh[kPerThread], arl[kPerThread], aih[kPerThread], ail[kPerThread];
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int k = w.o0 + threadIdx.x + v * kThreads;
+            float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+            if (k < w.o1) {
+                a = vh[k];
+                b = vl[k];
+            }
+            ph[v] = make_float3(a.x, a.y, a.z);
+            pl[v] = make_float3(b.x, b.y, b.z);
+            arh[v] = arl[v] = aih[v] = ail[v] = 0.f;
+        }
+        for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
+            __syncthreads();
+            int n = s0 + threadIdx.x;
+            if (n < w.s1) {
+                sh[threadIdx.x] = rh_g[n];
+                sl[threadIdx.x] = rl_g[n];
+                double cv = c[n];
+                float chi = (float)cv;
+                sc[threadIdx.x] = make_float2(chi, (float)(cv - (double)chi));
+            } else {
+                sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sc[threadIdx.x] = make_float2(0.f, 0.f);
+            }
+            __syncthreads();
+            const int cnt = min(kThreads, w.s1 - s0);
+#pragma unroll 2
+            for (int q = 0; q < cnt; ++q) {
+                const float4 rh = sh[q], rl = sl[q];
+                const float2 cv = sc[q];
+#pragma unroll
+                for (int v = 0; v < kPerThread; ++v) {
+                    float fh, fl, reh, rel, imh, iml;
+                    phase_df(ph[v], pl[v], rh, rl, fh, fl);
+                    cis_df(fh, fl, sT, reh, rel, imh, iml);
+                    float th, tl;
+                    df_mul(cv.x, cv.y, reh, rel, th, tl);
+                    df_acc(arh[v], arl[v], th, tl);
+                    df_mul(cv.x, cv.y, imh, iml, th, tl);
+                    df_acc(aih[v], ail[v], th, tl);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int k = w.o0 + threadIdx.x + v * kThreads;
+            if (k < w.o1) {
+                atomicAdd(&acc[k].x, (double)arh[v] + (double)arl[v]);
+                atomicAdd(&acc[k].y, (double)sgn * ((double)aih[v] + (double)ail[v]));
+            }
+        }
+    }
+}
+
+// Plain FP64 reference form.
+__global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__restrict__ items, int n_items,
+                                                           const double *__restrict__ vxyz, int64_t nv_all,
+                                                           const double *__restrict__ pxyz, int64_t np_all,
+                                                           const double *__restrict__ c, double2 *__restrict__ acc,
+                                                           double sgn) {
+    __shared__ double sx[kThreads], sy[kThreads], sz[kThreads], sw[kThreads];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        double px[kPerThread], py[kPerThread], pz[kPerThread], are[kPerThread], aim[kPerThread];
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int k = w.o0 + threadIdx.x + v * kThreads;
+            bool ok = k < w.o1;
+            px[v] = ok ? vxyz[k] : 0.0;
+            py[v] = ok ? vxyz[nv_all + k] : 0.0;
+            pz[v] = ok ? vxyz[2 * nv_all + k] : 0.0;
+            are[v] = aim[v] = 0.0;
+        }
+        for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
+            __syncthreads();
+            int n = s0 + threadIdx.x;
+            bool ok = n < w.s1;
+            sx[threadIdx.x] = ok ? pxyz[n] : 0.0;
+            sy[threadIdx.x] = ok ? pxyz[np_all + n] : 0.0;
+            sz[threadIdx.x] = ok ? pxyz[2 * np_all + n] : 0.0;
+            sw[threadIdx.x] = ok ? c[n] : 0.0;
+            __syncthreads();
+            const int cnt = min(kThreads, w.s1 - s0);
+            for (int q = 0; q < cnt; ++q) {
+#pragma unroll
+                for (int v = 0; v < kPerThread; ++v) {
+                    double t = fma(px[v], sx[q], fma(py[v], sy[q], pz[v] * sz[q]));
+                    t -= rint(t);
+                    double sn, cs;
+                    sincospi(2.0 * t, &sn, &cs);
+                    are[v] = fma(sw[q], cs, are[v]);
+                    aim[v] = fma(sw[q], sn, aim[v]);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int k = w.o0 + threadIdx.x + v * kThreads;
+            if (k < w.o1) {
+                atomicAdd(&acc[k].x, are[v]);
+                atomicAdd(&acc[k].y, sgn * aim[v]);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------- vis -> sky
+
+// FP32: owner = pixels, streamed = baselines (V complex, chunk order). Output real.
+__global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__restrict__ items, int n_items,
+                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
+                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
+                                                           const float2 *__restrict__ V, float *__restrict__ acc,
+                                                           float sgn) {
+    __shared__ float4 sh[kThreads];
+    __shared__ float4 sl[kThreads];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        float3 rh[kPerThread], rl[kPerThread];
+        float a[kPerThread];
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int n = w.o0 + threadIdx.x + v * kThreads;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+            if (n < w.o1) {
+                x = rh_g[n];
+                y = rl_g[n];
+            }
+            rh[v] = make_float3(x.x, x.y, x.z);
+            rl[v] = make_float3(y.x, y.y, y.z);
+            a[v] = 0.f;
+        }
+        for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
+            __syncthreads();
+            int k = s0 + threadIdx.x;
+            if (k < w.s1) {
+                float4 p = vh[k], q = vl[k];
+                float2 val = V[k];
+                p.w = val.x;
+                q.w = sgn * val.y;
+                sh[threadIdx.x] = p;
+                sl[threadIdx.x] = q;
+            } else {
+                sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            const int cnt = min(kThreads, w.s1 - s0);
+#pragma unroll 4
+            for (int q = 0; q < cnt; ++q) {
+                const float4 ph4 = sh[q], pl4 = sl[q];
+                const float3 ph = make_float3(ph4.x, ph4.y, ph4.z), pl = make_float3(pl4.x, pl4.y, pl4.z);
+#pragma unroll
+                for (int v = 0; v < kPerThread; ++v) {
+                    float4 r4h = make_float4(rh[v].x, rh[v].y, rh[v].z, 0.f);
+                    float4 r4l = make_float4(rl[v].x, rl[v].y, rl[v].z, 0.f);
+                    float f = phase_f32(ph, pl, r4h, r4l);
+                    float sn, cs;
+                    __sincosf(6.28318530717958648f * f, &sn, &cs);
+                    // Re(V e^{-isign j 2 pi t}) = Vr cos + isign Vi sin
+                    a[v] = __fmaf_rn(ph4.w, cs, __fmaf_rn(pl4.w, sn, a[v]));
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int n = w.o0 + threadIdx.x + v * kThreads;
+            if (n < w.o1) atomicAdd(&acc[n], a[v]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__restrict__ items, int n_items,
+                                                          const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
+                                                          const float4 *__restrict__ vh, const float4 *__restrict__ vl,
+                                                          const double2 *__restrict__ V, double *__restrict__ acc,
+                                                          const float4 *__restrict__ gT, float sgn) {
+    __shared__ float4 sh[kThreads];
+    __shared__ float4 sl[kThreads];
+    __shared__ float4 sv[kThreads];
+    __shared__ float4 sT[kTabLen];
+    load_tab(sT, gT);
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        float4 rh[kPerThread], rl[kPerThread];
+        float ah[kPerThread], al[kPerThread];
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int n = w.o0 + threadIdx.x + v * kThreads;
+            float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
+            if (n < w.o1) {
+                x = rh_g[n];
+                y = rl_g[n];
+            }
+            rh[v] = x;
+            rl[v] = y;
+            ah[v] = al[v] = 0.f;
+        }
+        for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
+            __syncthreads();
+            int k = s0 + threadIdx.x;
+            if (k < w.s1) {
+                sh[threadIdx.x] = vh[k];
+                sl[threadIdx.x] = vl[k];
+                double2 val = V[k];
+                double vi = (double)sgn * val.y;
+                float rh_ = (float)val.x, ih_ = (float)vi;
+                sv[threadIdx.x] = make_float4(rh_, (float)(val.x - (double)rh_), ih_, (float)(vi - (double)ih_));
+            } else {
+                sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+                sv[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncthreads();
+            const int cnt = min(kThreads, w.s1 - s0);
+#pragma unroll 2
+            for (int q = 0; q < cnt; ++q) {
+                const float4 ph4 = sh[q], pl4 = sl[q], val = sv[q];
+                const float3 ph = make_float3(ph4.x, ph4.y, ph4.z), pl = make_float3(pl4.x, pl4.y, pl4.z);
+#pragma unroll
+                for (int v = 0; v < kPerThread; ++v) {
+                    float fh, fl, reh, rel, imh, iml;
+                    phase_df(ph, pl, rh[v], rl[v], fh, fl);
+                    cis_df(fh, fl, sT, reh, rel, imh, iml);
+                    float th, tl;
+                    df_mul(val.x, val.y, reh, rel, th, tl);
+                    df_acc(ah[v], al[v], th, tl);
+                    df_mul(val.z, val.w, imh, iml, th, tl);
+                    df_acc(ah[v], al[v], th, tl);
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int n = w.o0 + threadIdx.x + v * kThreads;
+            if (n < w.o1) atomicAdd(&acc[n], (double)ah[v] + (double)al[v]);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) direct_v2s_f64(const WorkItem *__restrict__ items, int n_items,
+                                                           const double *__restrict__ pxyz, int64_t np_all,
+                                                           const double *__restrict__ vxyz, int64_t nv_all,
+                                                           const double2 *__restrict__ V, double *__restrict__ acc,
+                                                           double sgn) {
+    __shared__ double sx[kThreads], sy[kThreads], sz[kThreads], sr[kThreads], si[kThreads];
+    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+        const WorkItem w = items[it];
+        double rx[kPerThread], ry[kPerThread], rz[kPerThread], a[kPerThread];
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int n = w.o0 + threadIdx.x + v * kThreads;
+            bool ok = n < w.o1;
+            rx[v] = ok ? pxyz[n] : 0.0;
+            ry[v] = ok ? pxyz[np_all + n] : 0.0;
+            rz[v] = ok ? pxyz[2 * np_all + n] : 0.0;
+            a[v] = 0.0;
+        }
+        for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
+            __syncthreads();
+            int k = s0 + threadIdx.x;
+            bool ok = k < w.s1;
+            sx[threadIdx.x] = ok ? vxyz[k] : 0.0;
+            sy[threadIdx.x] = ok ? vxyz[nv_all + k] : 0.0;
+            sz[threadIdx.x] = ok ? vxyz[2 * nv_all + k] : 0.0;
+            double2 val = ok ? V[k] : make_double2(0.0, 0.0);
+            sr[threadIdx.x] = val.x;
+            si[threadIdx.x] = sgn * val.y;
+            __syncthreads();
+            const int cnt = min(kThreads, w.s1 - s0);
+            for (int q = 0; q < cnt; ++q) {
+#pragma unroll
+                for (int v = 0; v < kPerThread; ++v) {
+                    double t = fma(sx[q], rx[v], fma(sy[q], ry[v], sz[q] * rz[v]));
+                    t -= rint(t);
+                    double sn, cs;
+                    sincospi(2.0 * t, &sn, &cs);
+                    a[v] = fma(sr[q], cs, fma(si[q], sn, a[v]));
+                }
+            }
+        }
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            int n = w.o0 + threadIdx.x + v * kThreads;
+            if (n < w.o1) atomicAdd(&acc[n], a[v]);
+        }
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- launchers
+
+void launch_prepare_points(const double *xyz, const int32_t *perm, int64_t n, double *soa, float4 *hi, float4 *lo,
+                           cudaStream_t s) {
+    if (n <= 0) return;
+    prepare_points_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(xyz, perm, n, soa, hi, lo);
+    check_cuda(cudaGetLastError(), "prepare_points");
+}
+
+void launch_gather_weight(const double *w, const int32_t *perm, int64_t n, double *out, cudaStream_t s) {
+    if (n <= 0) return;
+    gather_weight_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(w, perm, n, out);
+    check_cuda(cudaGetLastError(), "gather_weight");
+}
+
+int direct_tile() { return kTile; }
+
+static unsigned grid_for(int64_t n_items) {
+    static int sms = 0;
+    if (sms == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0) sms = 152;
+    }
+    int64_t g = std::min<int64_t>(n_items, (int64_t)sms * 4);
+    return (unsigned)std::max<int64_t>(g, 1);
+}
+
+void launch_direct_s2v_f32(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+                           const float4 *rl, const float *c, float2 *acc, int isign, cudaStream_t s) {
+    if (n <= 0) return;
+    direct_s2v_f32<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, (float)isign);
+    check_cuda(cudaGetLastError(), "direct_s2v_f32");
+}
+
+void launch_direct_s2v_df(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+                          const float4 *rl, const double *c, double2 *acc, const float4 *tab, int isign,
+                          cudaStream_t s) {
+    if (n <= 0) return;
+    direct_s2v_df<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, tab, (float)isign);
+    check_cuda(cudaGetLastError(), "direct_s2v_df");
+}
+
+void launch_direct_s2v_f64(const WorkItem *items, int64_t n, const double *vxyz, int64_t nv, const double *pxyz,
+                           int64_t np, const double *c, double2 *acc, int isign, cudaStream_t s) {
+    if (n <= 0) return;
+    direct_s2v_f64<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vxyz, nv, pxyz, np, c, acc, (double)isign);
+    check_cuda(cudaGetLastError(), "direct_s2v_f64");
+}
+
+void launch_direct_v2s_f32(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+                           const float4 *vl, const float2 *V, float *acc, int isign, cudaStream_t s) {
+    if (n <= 0) return;
+    direct_v2s_f32<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, (float)isign);
+    check_cuda(cudaGetLastError(), "direct_v2s_f32");
+}
+
+void launch_direct_v2s_df(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+                          const float4 *vl, const double2 *V, double *acc, const float4 *tab, int isign,
+                          cudaStream_t s) {
+    if (n <= 0) return;
+    direct_v2s_df<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, tab, (float)isign);
+    check_cuda(cudaGetLastError(), "direct_v2s_df");
+}
+
+void launch_direct_v2s_f64(const WorkItem *items, int64_t n, const double *pxyz, int64_t np, const double *vxyz,
+                           int64_t nv, const double2 *V, double *acc, int isign, cudaStream_t s) {
+    if (n <= 0) return;
+    direct_v2s_f64<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, pxyz, np, vxyz, nv, V, acc, (double)isign);
+    check_cuda(cudaGetLastError(), "direct_v2s_f64");
+}
+
+}  // namespace hvox

@@ -1,0 +1,451 @@
+// Host planner: Algorithm 1 (maximum Heisenberg dimensions), Algorithm 2 (chunking),
+// the per-sub-problem choice between type-3 NUFFT and direct evaluation (Sect. 3.1,
+// last benefit of chunking), the chunk-order permutation (Sect. 4) and the work
+// decomposition executed by the kernels.
+//
+// Readings where the paper is silent:
+//  * Algorithm 1 is solved at its isotropic optimum h = t B, eta = t P (optimal for
+//    any alpha >= 1, unique at alpha = 1), with the memory budget applied to the
+//    padded spread and FFT grids a full-size sub-problem allocates (bisection on t).
+//  * Algorithm 2 fusion: lattice cells in lexicographic order; each unassigned
+//    occupied cell seeds a chunk and absorbs, in lexicographic offset order, the
+//    unassigned occupied cells of the 2x2x2 window at its minimum corner while the
+//    chunk's point bounding box stays within h in every dimension.
+#include <algorithm>
+#include <cmath>
+#include <numeric>
+
+#include "hvox_internal.h"
+
+namespace hvox {
+
+int64_t smooth_even(int64_t n) {
+    int64_t m = std::max<int64_t>(2, n);
+    if (m % 2) ++m;
+    for (;; m += 2) {
+        int64_t r = m;
+        for (int64_t f : {2, 3, 5, 7})
+            while (r % f == 0) r /= f;
+        if (r == 1) return m;
+    }
+}
+
+void grid_sizes(double extent_pix, double extent_vis, double sigma, int w, int64_t &n1, int64_t &n2) {
+    double need = sigma * extent_pix * extent_vis + (double)w + 2.0;
+    n1 = 2 * (int64_t)std::ceil(need / 2.0);
+    n2 = smooth_even(std::max<int64_t>((int64_t)std::ceil(sigma * (double)n1), 2 * (int64_t)w));
+}
+
+double grid_bytes(const double P[3], const double B[3], double sigma, int w, int elem_bytes) {
+    double n1p = 1, n2p = 1;
+    for (int d = 0; d < 3; ++d) {
+        int64_t n1, n2;
+        grid_sizes(P[d], B[d], sigma, w, n1, n2);
+        n1p *= (double)n1;
+        n2p *= (double)n2;
+    }
+    return (double)elem_bytes * (n1p + n2p);
+}
+
+double box_dims(const double P[3], const double B[3], double budget, double sigma, int w, int elem_bytes,
+                double eta[3], double h[3]) {
+    double t;
+    if (grid_bytes(P, B, sigma, w, elem_bytes) <= budget) {
+        t = 1.0;
+    } else {
+        double lo = 0.0, hi = 1.0;
+        for (int it = 0; it < 64; ++it) {
+            double mid = 0.5 * (lo + hi);
+            double Pm[3], Bm[3];
+            for (int d = 0; d < 3; ++d) {
+                Pm[d] = mid * P[d];
+                Bm[d] = mid * B[d];
+            }
+            if (grid_bytes(Pm, Bm, sigma, w, elem_bytes) <= budget)
+                lo = mid;
+            else
+                hi = mid;
+        }
+        t = lo;
+    }
+    for (int d = 0; d < 3; ++d) {
+        eta[d] = t * P[d];
+        h[d] = t * B[d];
+    }
+    return t;
+}
+
+namespace {
+
+struct Key {
+    int64_t x, y, z;
+    bool operator<(const Key &o) const {
+        if (x != o.x) return x < o.x;
+        if (y != o.y) return y < o.y;
+        return z < o.z;
+    }
+    bool operator==(const Key &o) const { return x == o.x && y == o.y && z == o.z; }
+};
+
+}  // namespace
+
+int64_t chunk_points(const double *xyz, int64_t n, const double h[3], std::vector<int64_t> &labels) {
+    labels.assign(n, 0);
+    if (n == 0) return 0;
+    double lo[3] = {xyz[0], xyz[1], xyz[2]};
+    for (int64_t i = 1; i < n; ++i)
+        for (int d = 0; d < 3; ++d) lo[d] = std::min(lo[d], xyz[3 * i + d]);
+    std::vector<std::pair<Key, int64_t>> kp(n);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c[3] = {0, 0, 0};
+        for (int d = 0; d < 3; ++d)
+            if (h[d] > 0.0 && std::isfinite(h[d])) c[d] = (int64_t)std::floor((xyz[3 * i + d] - lo[d]) / h[d]);
+        kp[i] = {Key{c[0], c[1], c[2]}, i};
+    }
+    std::sort(kp.begin(), kp.end(), [](const auto &a, const auto &b) {
+        if (a.first == b.first) return a.second < b.second;
+        return a.first < b.first;
+    });
+    // Occupied cells (step 3) with their point bounding boxes.
+    std::vector<Key> cells;
+    std::vector<int64_t> cstart;
+    std::vector<double> cbox;  // 6 per cell: lo xyz, hi xyz
+    for (int64_t i = 0; i < n; ++i) {
+        const double *p = xyz + 3 * kp[i].second;
+        if (i == 0 || !(kp[i].first == kp[i - 1].first)) {
+            cells.push_back(kp[i].first);
+            cstart.push_back(i);
+            for (int d = 0; d < 3; ++d) cbox.push_back(p[d]);
+            for (int d = 0; d < 3; ++d) cbox.push_back(p[d]);
+        } else {
+            double *b = &cbox[cbox.size() - 6];
+            for (int d = 0; d < 3; ++d) {
+                b[d] = std::min(b[d], p[d]);
+                b[3 + d] = std::max(b[3 + d], p[d]);
+            }
+        }
+    }
+    cstart.push_back(n);
+    const int64_t nc = (int64_t)cells.size();
+    std::vector<int64_t> owner(nc, -1);
+    static const int off[7][3] = {{0, 0, 1}, {0, 1, 0}, {0, 1, 1}, {1, 0, 0}, {1, 0, 1}, {1, 1, 0}, {1, 1, 1}};
+    int64_t n_chunks = 0;
+    for (int64_t c = 0; c < nc; ++c) {
+        if (owner[c] >= 0) continue;
+        const int64_t cid = n_chunks++;
+        owner[c] = cid;
+        double blo[3], bhi[3];
+        for (int d = 0; d < 3; ++d) {
+            blo[d] = cbox[6 * c + d];
+            bhi[d] = cbox[6 * c + 3 + d];
+        }
+        for (int o = 0; o < 7; ++o) {
+            Key nb{cells[c].x + off[o][0], cells[c].y + off[o][1], cells[c].z + off[o][2]};
+            auto it = std::lower_bound(cells.begin(), cells.end(), nb);
+            if (it == cells.end() || !(*it == nb)) continue;
+            int64_t j = it - cells.begin();
+            if (owner[j] >= 0) continue;
+            double jlo[3], jhi[3];
+            bool ok = true;
+            for (int d = 0; d < 3; ++d) {
+                jlo[d] = std::min(blo[d], cbox[6 * j + d]);
+                jhi[d] = std::max(bhi[d], cbox[6 * j + 3 + d]);
+                if (!(jhi[d] - jlo[d] <= h[d])) ok = false;
+            }
+            if (ok) {
+                for (int d = 0; d < 3; ++d) {
+                    blo[d] = jlo[d];
+                    bhi[d] = jhi[d];
+                }
+                owner[j] = cid;
+            }
+        }
+    }
+    for (int64_t c = 0; c < nc; ++c)
+        for (int64_t i = cstart[c]; i < cstart[c + 1]; ++i) labels[kp[i].second] = owner[c];
+    return n_chunks;
+}
+
+CostModel default_cost_model(int prec, bool plain, int w) {
+    // Seconds per unit of work on one GB300, from the throughput of the kernels that do
+    // the work (direct pair rates of the FP32 / double-float / FP64 kernels, tap rates of
+    // the spread and interpolation kernels, FFT and grid passes at HBM speed).
+    (void)w;
+    CostModel m;
+    if (plain) {
+        m.direct_pair = 1.0 / 1.2e10;
+        m.spread_tap = 1.0 / 1.5e11;
+        m.fft_cell = 6e-12;
+        m.grid_cell = 1e-11;
+        m.block_fixed = 60e-6;
+    } else if (prec == 1) {
+        m.direct_pair = 1.0 / 1.0e12;
+        m.spread_tap = 1.0 / 1.5e12;
+        m.fft_cell = 5e-13;
+        m.grid_cell = 4e-12;
+        m.block_fixed = 25e-6;
+    } else {
+        m.direct_pair = 1.0 / 2.5e11;
+        m.spread_tap = 1.0 / 1.5e11;
+        m.fft_cell = 6e-12;
+        m.grid_cell = 8e-12;
+        m.block_fixed = 40e-6;
+    }
+    return m;
+}
+
+namespace {
+
+struct ChunkStats {
+    std::vector<int64_t> count;
+    std::vector<double> lo, hi;  // 3 per chunk
+};
+
+ChunkStats stats_of(const double *xyz, int64_t n, const std::vector<int64_t> &labels, int64_t nc) {
+    ChunkStats s;
+    s.count.assign(nc, 0);
+    s.lo.assign(3 * nc, INFINITY);
+    s.hi.assign(3 * nc, -INFINITY);
+    for (int64_t i = 0; i < n; ++i) {
+        int64_t c = labels[i];
+        s.count[c]++;
+        for (int d = 0; d < 3; ++d) {
+            s.lo[3 * c + d] = std::min(s.lo[3 * c + d], xyz[3 * i + d]);
+            s.hi[3 * c + d] = std::max(s.hi[3 * c + d], xyz[3 * i + d]);
+        }
+    }
+    return s;
+}
+
+struct Evaluated {
+    double t, h[3], eta[3], budget;
+    std::vector<int64_t> pl, vl;
+    int64_t npc, nvc;
+    ChunkStats ps, vs;
+    std::vector<std::pair<int64_t, int64_t>> nufft_pairs;  // (pix chunk, vis chunk)
+    double cost;
+};
+
+double nufft_cost(const CostModel &m, const ESKernel &es, double sigma, int64_t np, int64_t nv, const double *pext,
+                  const double *vext, double *cells_out) {
+    double m1 = 1, m2 = 1;
+    for (int d = 0; d < 3; ++d) {
+        int64_t n1, n2;
+        grid_sizes(pext[d], vext[d], sigma, es.w, n1, n2);
+        m1 *= (double)n1;
+        m2 *= (double)n2;
+    }
+    if (cells_out) *cells_out = m2;
+    double w3 = (double)es.w * es.w * es.w;
+    return m.spread_tap * w3 * (double)(np + nv) + m.fft_cell * m2 * std::log2(std::max(2.0, m2)) +
+           m.grid_cell * (2.0 * m1 + 2.0 * m2) + m.block_fixed;
+}
+
+Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, const double P[3], const double B[3]) {
+    Evaluated e;
+    e.budget = budget;
+    e.t = box_dims(P, B, budget, in.sigma, in.es.w, in.elem_bytes, e.eta, e.h);
+    e.npc = chunk_points(in.pix, in.n_pix, e.eta, e.pl);
+    e.nvc = chunk_points(in.uvw, in.n_vis, e.h, e.vl);
+    e.ps = stats_of(in.pix, in.n_pix, e.pl, e.npc);
+    e.vs = stats_of(in.uvw, in.n_vis, e.vl, e.nvc);
+    const double w3 = (double)in.es.w * in.es.w * in.es.w;
+    double total = 0.0;
+    double direct_pairs = (double)in.n_pix * (double)in.n_vis;
+    if (in.mode == HVOX_MODE_DIRECT) {
+        e.cost = m.direct_pair * direct_pairs;
+        return e;
+    }
+    // Chunks too small to ever win as NUFFT (tap cost alone exceeds the direct cost).
+    double min_pts = (in.mode == HVOX_MODE_NUFFT || in.direct_threshold > 0) ? 0.0 : m.spread_tap * w3 / m.direct_pair;
+    std::vector<int64_t> bigp, bigv;
+    for (int64_t i = 0; i < e.npc; ++i)
+        if ((double)e.ps.count[i] > min_pts) bigp.push_back(i);
+    for (int64_t j = 0; j < e.nvc; ++j)
+        if ((double)e.vs.count[j] > min_pts) bigv.push_back(j);
+    for (int64_t i : bigp) {
+        double pext[3];
+        for (int d = 0; d < 3; ++d) pext[d] = e.ps.hi[3 * i + d] - e.ps.lo[3 * i + d];
+        for (int64_t j : bigv) {
+            double vext[3];
+            for (int d = 0; d < 3; ++d) vext[d] = e.vs.hi[3 * j + d] - e.vs.lo[3 * j + d];
+            int64_t np = e.ps.count[i], nv = e.vs.count[j];
+            double pairs = (double)np * (double)nv;
+            bool use_nufft;
+            double cn = 0.0;
+            if (in.mode == HVOX_MODE_NUFFT) {
+                use_nufft = true;
+                cn = nufft_cost(m, in.es, in.sigma, np, nv, pext, vext, nullptr);
+            } else if (in.direct_threshold > 0) {
+                use_nufft = pairs > in.direct_threshold;
+                if (use_nufft) cn = nufft_cost(m, in.es, in.sigma, np, nv, pext, vext, nullptr);
+            } else {
+                cn = nufft_cost(m, in.es, in.sigma, np, nv, pext, vext, nullptr);
+                use_nufft = cn < m.direct_pair * pairs;
+            }
+            if (use_nufft) {
+                e.nufft_pairs.push_back({i, j});
+                total += cn;
+                direct_pairs -= pairs;
+            }
+        }
+    }
+    total += m.direct_pair * direct_pairs;
+    e.cost = total;
+    return e;
+}
+
+}  // namespace
+
+PartitionResult make_partition(const PlanInputs &in) {
+    PartitionResult r;
+    CostModel m = default_cost_model(in.prec, in.plain, in.es.w);
+    double P[3], B[3];
+    for (int d = 0; d < 3; ++d) {
+        double lo = INFINITY, hi = -INFINITY;
+        for (int64_t i = 0; i < in.n_pix; ++i) {
+            lo = std::min(lo, in.pix[3 * i + d]);
+            hi = std::max(hi, in.pix[3 * i + d]);
+        }
+        P[d] = hi - lo;
+        lo = INFINITY;
+        hi = -INFINITY;
+        for (int64_t i = 0; i < in.n_vis; ++i) {
+            lo = std::min(lo, in.uvw[3 * i + d]);
+            hi = std::max(hi, in.uvw[3 * i + d]);
+        }
+        B[d] = hi - lo;
+    }
+    Evaluated best;
+    if (in.budget > 0) {
+        best = evaluate(in, m, in.budget, P, B);
+    } else if (in.mode == HVOX_MODE_DIRECT) {
+        best = evaluate(in, m, 1e30, P, B);
+    } else {
+        bool have = false;
+        // Budget search: 256 KiB .. 4 GiB in factors of 4 (the cost model picks B).
+        for (double b = 256.0 * 1024.0; b <= 4.3e9; b *= 4.0) {
+            Evaluated e = evaluate(in, m, b, P, B);
+            if (!have || e.cost < best.cost) {
+                best = std::move(e);
+                have = true;
+            }
+        }
+    }
+    r.t = best.t;
+    r.budget = best.budget;
+    for (int d = 0; d < 3; ++d) {
+        r.h[d] = best.h[d];
+        r.eta[d] = best.eta[d];
+    }
+    r.model_seconds = best.cost;
+    r.pix_label = best.pl;
+    r.vis_label = best.vl;
+    r.n_pix_chunks = best.npc;
+    r.n_vis_chunks = best.nvc;
+
+    // Chunk order: chunks that take part in a NUFFT sub-problem first, then the rest,
+    // each group in Algorithm 2 numbering. Points keep their original order inside a chunk.
+    std::vector<char> pin(best.npc, 0), vin(best.nvc, 0);
+    for (auto &pr : best.nufft_pairs) {
+        pin[pr.first] = 1;
+        vin[pr.second] = 1;
+    }
+    auto order_chunks = [](const std::vector<char> &flag) {
+        std::vector<int64_t> ord;
+        for (int64_t c = 0; c < (int64_t)flag.size(); ++c)
+            if (flag[c]) ord.push_back(c);
+        for (int64_t c = 0; c < (int64_t)flag.size(); ++c)
+            if (!flag[c]) ord.push_back(c);
+        return ord;
+    };
+    r.pix_chunk_label = order_chunks(pin);
+    r.vis_chunk_label = order_chunks(vin);
+    auto build_perm = [](const std::vector<int64_t> &labels, int64_t nc, const std::vector<int64_t> &ord,
+                         std::vector<int64_t> &perm, std::vector<int64_t> &start) {
+        std::vector<int64_t> rank(nc);
+        for (int64_t k = 0; k < nc; ++k) rank[ord[k]] = k;
+        std::vector<int64_t> cnt(nc + 1, 0);
+        for (int64_t l : labels) cnt[rank[l] + 1]++;
+        for (int64_t k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
+        start = cnt;
+        perm.assign(labels.size(), 0);
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t i = 0; i < (int64_t)labels.size(); ++i) perm[pos[rank[labels[i]]]++] = i;
+        return rank;
+    };
+    std::vector<int64_t> prank = build_perm(best.pl, best.npc, r.pix_chunk_label, r.pix_perm, r.pix_chunk_start);
+    std::vector<int64_t> vrank = build_perm(best.vl, best.nvc, r.vis_chunk_label, r.vis_perm, r.vis_chunk_start);
+
+    // NUFFT blocks with their geometry.
+    const double sigma = in.sigma;
+    const int w = in.es.w;
+    std::vector<std::vector<char>> is_nufft_for_vchunk;  // per ordered NUFFT vis chunk: flags over ordered pix chunks
+    int64_t n_pin = 0, n_vin = 0;
+    for (char f : pin) n_pin += f;
+    for (char f : vin) n_vin += f;
+    std::vector<std::vector<int64_t>> nufft_pix_of_v(n_vin);
+    for (auto &pr : best.nufft_pairs) {
+        int64_t i = pr.first, j = pr.second;
+        NufftBlock b;
+        b.pix_chunk = i;
+        b.vis_chunk = j;
+        int64_t pi = prank[i], vj = vrank[j];
+        b.p0 = r.pix_chunk_start[pi];
+        b.p1 = r.pix_chunk_start[pi + 1];
+        b.v0 = r.vis_chunk_start[vj];
+        b.v1 = r.vis_chunk_start[vj + 1];
+        for (int d = 0; d < 3; ++d) {
+            double plo = best.ps.lo[3 * i + d], phi = best.ps.hi[3 * i + d];
+            double vlo = best.vs.lo[3 * j + d], vhi = best.vs.hi[3 * j + d];
+            b.C[d] = 0.5 * (plo + phi);
+            b.D[d] = 0.5 * (vlo + vhi);
+            double X = 0.5 * (phi - plo), Bh = 0.5 * (vhi - vlo);
+            grid_sizes(phi - plo, vhi - vlo, sigma, w, b.n1[d], b.n2[d]);
+            if (X > 0.0)
+                b.a[d] = (double)(b.n1[d] - w - 2) / (2.0 * X);
+            else
+                b.a[d] = 2.0 * sigma * Bh;
+        }
+        double pext[3], vext[3];
+        for (int d = 0; d < 3; ++d) {
+            pext[d] = best.ps.hi[3 * i + d] - best.ps.lo[3 * i + d];
+            vext[d] = best.vs.hi[3 * j + d] - best.vs.lo[3 * j + d];
+        }
+        double cells = 0;
+        b.cost = nufft_cost(m, in.es, sigma, b.p1 - b.p0, b.v1 - b.v0, pext, vext, &cells);
+        double m1 = (double)(b.n1[0] * b.n1[1] * b.n1[2]), m2 = (double)(b.n2[0] * b.n2[1] * b.n2[2]);
+        r.max_grid_bytes = std::max(r.max_grid_bytes, (double)in.elem_bytes * (m1 + m2));
+        r.nufft_cells += cells;
+        r.nufft_points += (double)(b.p1 - b.p0 + b.v1 - b.v0);
+        r.blocks.push_back(b);
+        nufft_pix_of_v[vj].push_back(pi);
+    }
+    // Largest-first ordering of NUFFT blocks (better overlap when several run at once).
+    std::stable_sort(r.blocks.begin(), r.blocks.end(),
+                     [](const NufftBlock &a, const NufftBlock &b) { return a.cost > b.cost; });
+
+    // Direct rectangles.
+    const int64_t p_split = r.pix_chunk_start[n_pin];
+    const int64_t v_split = r.vis_chunk_start[n_vin];
+    if (v_split < in.n_vis) r.rects.push_back({0, in.n_pix, v_split, in.n_vis});
+    if (p_split < in.n_pix && v_split > 0) r.rects.push_back({p_split, in.n_pix, 0, v_split});
+    for (int64_t vj = 0; vj < n_vin; ++vj) {
+        std::vector<char> used(n_pin, 0);
+        for (int64_t pi : nufft_pix_of_v[vj]) used[pi] = 1;
+        int64_t v0 = r.vis_chunk_start[vj], v1 = r.vis_chunk_start[vj + 1];
+        int64_t run = -1;
+        for (int64_t pi = 0; pi <= n_pin; ++pi) {
+            bool direct = pi < n_pin && !used[pi];
+            if (direct && run < 0) run = pi;
+            if (!direct && run >= 0) {
+                r.rects.push_back({r.pix_chunk_start[run], r.pix_chunk_start[pi], v0, v1});
+                run = -1;
+            }
+        }
+    }
+    for (auto &rc : r.rects) r.direct_pairs += (double)(rc.p1 - rc.p0) * (double)(rc.v1 - rc.v0);
+    return r;
+}
+
+}  // namespace hvox

@@ -1,0 +1,111 @@
+"""CPU checks of the C ABI: the library loads, exports every function include/hvox.h
+declares, and its host-only planning primitives agree with the oracle: Algorithm 2
+chunk labels bit for bit, Algorithm 1 box dimensions, and the ES-kernel Fourier
+transform against SciPy quadrature."""
+import ctypes
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_2306_06007_gb300 as hvox
+from oracle import partition
+from hvox_inputs import configs
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "hvox.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(hvox_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    hvox.build()
+    return hvox.load()
+
+
+def test_exports_every_declared_function(lib):
+    names = declared_functions()
+    assert len(names) >= 16
+    for n in names:
+        assert hasattr(lib, n), n
+    assert "hvox" in hvox.version()
+
+
+def test_es_params_rule(lib):
+    # Width grows by about one cell per digit at sigma = 2, and beta scales with w.
+    ws = [hvox.es_params(e)[0] for e in (1e-4, 1e-5, 1e-6, 1e-9)]
+    assert ws == sorted(ws) and ws[-1] - ws[0] in (4, 5, 6)
+    w, b = hvox.es_params(1e-6, 2.0)
+    assert abs(b / w - 0.97 * math.pi * 0.75) < 1e-12
+    assert hvox.es_params(1e-9, 1.25)[0] > hvox.es_params(1e-9, 2.0)[0]
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-9])
+def test_es_ft_against_quadrature(lib, eps):
+    from scipy.integrate import quad
+    w, beta = hvox.es_params(eps)
+    xi = np.array([0.0, 0.3, 1.0, 2.2, math.pi / 2, 3.0, math.pi])
+    got = hvox.es_ft(w, beta, xi)
+
+    def phi(z):
+        q = 1.0 - (2.0 * z / w) ** 2
+        return math.exp(beta * (math.sqrt(q) - 1.0)) if q > 0 else 0.0
+
+    # Adaptive quadrature straight on phi(z) cos(xi z) (the definition), split at the
+    # kernel edges where phi has its square-root behaviour.
+    for x, g in zip(xi, got):
+        ref = quad(lambda z: phi(z) * math.cos(x * z), -w / 2, w / 2, limit=800, epsabs=1e-15, epsrel=1e-14,
+                   points=[-w / 2 * 0.99, 0.0, w / 2 * 0.99])[0]
+        assert abs(g - ref) <= 2e-13 * max(1.0, abs(ref)) + 1e-11 * math.exp(-beta) * beta, (x, g, ref)
+
+
+def test_box_dims_matches_oracle(lib):
+    cases = [([1.0, 1.0, 0.134], [2.0e5, 1.9e5, 4.5e4], 16e6, 2.0, 10, 16),
+             ([1.4, 1.4, 0.29], [1900.0, 1900.0, 51.0], 5e8, 2.0, 7, 8),
+             ([0.5, 0.6, 0.0], [300.0, 200.0, 0.0], 1e6, 1.25, 9, 8)]
+    for P, B, budget, sigma, w, eb in cases:
+        eta, h, t = hvox.box_dims(P, B, budget, sigma, w, eb)
+        eta_o, h_o, t_o = partition.box_dims(P, B, budget, sigma, w, eb)
+        assert t == t_o
+        assert np.array_equal(eta, eta_o) and np.array_equal(h, h_o)
+
+
+def _label_parity(pts, h):
+    lab, nc = hvox.chunk_points(pts, h)
+    lab_o, nc_o = partition.chunk(pts, h)
+    assert nc == nc_o
+    assert np.array_equal(lab, lab_o)
+    return nc
+
+
+def test_chunk_points_bit_exact_random(lib):
+    rng = np.random.default_rng(17)
+    pts = np.concatenate([rng.normal(0, 1, (3000, 3)), rng.normal(0, 20, (500, 3)) * [1, 1, 0.05]])
+    for h in ([0.5, 0.5, 0.5], [2.0, 1.0, 0.25], [0.1, 0.1, 10.0], [1.0, 1.0, 0.0]):
+        _label_parity(pts, h)
+
+
+def test_chunk_points_bit_exact_workload_geometry(lib):
+    # Pixels of a HEALPix cap and earth-rotation baselines, at the box dimensions
+    # Algorithm 1 gives for a 4 MB budget.
+    w = configs.small_case(seed=2, n_pix=5000, n_vis=20000, cap_deg=40.0, radius_m=3000.0)
+    P = w.pix.max(0) - w.pix.min(0)
+    B = w.uvw.max(0) - w.uvw.min(0)
+    eta, h, t = hvox.box_dims(P, B, 4e6, 2.0, 7, 8)
+    assert t < 1.0
+    assert _label_parity(w.pix, eta) > 1
+    assert _label_parity(w.uvw, h) > 1
+
+
+def test_chunk_points_rejects_bad_input(lib):
+    pts = np.zeros((4, 3))
+    pts[2, 1] = np.nan
+    with pytest.raises(hvox.HvoxError) as e:
+        hvox.chunk_points(pts, [1.0, 1.0, 1.0])
+    assert e.value.code == 1

@@ -1,0 +1,179 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 direct-sum oracle
+(Eq. 2 / Eq. 3), relative l2 <= 10 eps (the tolerance the transform promises).
+
+Sizes span several 512-point tiles with ragged tails; every block kind (direct,
+NUFFT) and both directions are exercised."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from hvox_inputs import configs
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(hvox, w, eps, isign=-1, weight=None, **kw):
+    plan = hvox.Plan(w.pix, w.uvw, eps, isign=isign, weight=weight, **kw)
+    I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
+    V = plan.synthesize(I)
+    rng = np.random.default_rng(5)
+    y = rng.normal(size=w.n_vis) + 1j * rng.normal(size=w.n_vis)
+    Y = torch.as_tensor(y, dtype=plan.complex_dtype, device="cuda")
+    img = plan.analyze(Y)
+    torch.cuda.synchronize()
+    info = plan.info()
+    plan.close()
+    return V.cpu().numpy(), y, img.cpu().numpy(), info
+
+
+@pytest.fixture(scope="module")
+def small():
+    return configs.small_case(seed=3, n_pix=1333, n_vis=2777, cap_deg=35.0, radius_m=400.0)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-9])
+@pytest.mark.parametrize("mode", ["auto", "nufft", "direct"])
+def test_small_parity(gpu_lib, small, eps, mode):
+    w = small
+    V, y, img, info = _run(gpu_lib, w, eps, mode=mode)
+    ref_v = oracle.sky2vis(w.pix, w.uvw, w.sky, isign=-1)
+    ref_i = oracle.vis2sky(w.pix, w.uvw, y, isign=-1)
+    e_v = oracle.rel_l2(V, ref_v)
+    e_i = oracle.rel_l2(img, ref_i)
+    if mode == "nufft":
+        assert info["n_nufft_blocks"] >= 1
+    if mode == "direct":
+        assert info["n_nufft_blocks"] == 0
+    assert e_v <= 10 * eps, (e_v, info)
+    assert e_i <= 10 * eps, (e_i, info)
+
+
+@pytest.mark.parametrize("isign", [1, -1])
+def test_weights_and_isign(gpu_lib, small, isign):
+    w = small
+    wt = np.random.default_rng(9).uniform(0.5, 2.0, w.n_pix)
+    for mode in ("nufft", "direct"):
+        V, y, img, _ = _run(gpu_lib, w, 1e-9, isign=isign, weight=wt, mode=mode)
+        assert oracle.rel_l2(V, oracle.sky2vis(w.pix, w.uvw, w.sky, weight=wt, isign=isign)) <= 1e-8
+        assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y, weight=wt, isign=isign)) <= 1e-8
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_adjoint_pair_to_rounding(gpu_lib, small, eps):
+    # The vis->sky pipeline is the exact transpose of sky->vis (same grids, records and
+    # kernels), so Re<A x, y> = <x, A^H y> holds to rounding, not merely to eps.
+    w = small
+    for mode in ("nufft", "direct"):
+        V, y, img, _ = _run(gpu_lib, w, eps, mode=mode)
+        lhs = np.real(np.vdot(y, V))
+        rhs = float(np.dot(w.sky, img))
+        scale = np.linalg.norm(V) * np.linalg.norm(y)
+        tol = 1e-12 if eps < 1e-6 else 2e-5
+        assert abs(lhs - rhs) <= tol * scale, (mode, lhs, rhs)
+
+
+def test_partition_invariance(gpu_lib, small):
+    # Eq. 8: any partition gives the same transform (within eps).
+    w = small
+    outs = []
+    for kw in ({"mode": "direct"}, {"mode": "nufft"}, {"mode": "nufft", "chunk_budget_bytes": 4e6},
+               {"mode": "auto"}):
+        V, _, _, info = _run(gpu_lib, w, 1e-9, **kw)
+        outs.append(V)
+    for V in outs[1:]:
+        assert oracle.rel_l2(V, outs[0]) <= 1e-8
+
+
+def test_plan_chunks_match_oracle_partition(gpu_lib, small):
+    from oracle import partition
+    w = small
+    plan = gpu_lib.Plan(w.pix, w.uvw, 1e-6, mode="nufft", chunk_budget_bytes=2e6)
+    info = plan.info()
+    pc, vc = plan.chunks()
+    plan.close()
+    lp, npc = partition.chunk(w.pix, info["eta"])
+    lv, nvc = partition.chunk(w.uvw, info["h"])
+    assert npc == info["n_pix_chunks"] and nvc == info["n_vis_chunks"]
+    assert np.array_equal(pc, lp) and np.array_equal(vc, lv)
+
+
+def test_host_pointer_path_matches_device(gpu_lib, small):
+    w = small
+    plan = gpu_lib.Plan(w.pix, w.uvw, 1e-6)
+    I_dev = torch.as_tensor(w.sky, dtype=torch.float32, device="cuda")
+    V_dev = plan.synthesize(I_dev).cpu()
+    V_host = plan.synthesize(torch.as_tensor(w.sky, dtype=torch.float32))  # host buffers
+    assert V_host.device.type == "cpu"
+    assert torch.allclose(V_host, V_dev, rtol=0, atol=1e-4 * float(V_dev.abs().max()))
+    plan.close()
+
+
+def test_degenerate_geometries(gpu_lib):
+    rng = np.random.default_rng(11)
+    # One pixel, one baseline.
+    pix = np.array([[0.1, 0.2, math.sqrt(1 - 0.05)]])
+    uvw = np.array([[123.4, -56.7, 8.9]])
+    sky = np.array([2.0])
+    for mode in ("auto", "nufft"):
+        plan = gpu_lib.Plan(pix, uvw, 1e-9, mode=mode)
+        V = plan.synthesize(torch.tensor(sky, device="cuda")).cpu().numpy()
+        plan.close()
+        assert abs(V[0] - oracle.sky2vis(pix, uvw, sky)[0]) < 1e-8 * 2.0
+    # Coplanar baselines (w = 0) and pixels on one ring (z constant).
+    w = configs.small_case(seed=4, n_pix=600, n_vis=800)
+    uvw = w.uvw.copy()
+    uvw[:, 2] = 0.0
+    pix = w.pix.copy()
+    for mode in ("nufft", "auto"):
+        plan = gpu_lib.Plan(pix, uvw, 1e-9, mode=mode)
+        V = plan.synthesize(torch.as_tensor(w.sky, device="cuda")).cpu().numpy()
+        plan.close()
+        assert oracle.rel_l2(V, oracle.sky2vis(pix, uvw, w.sky)) <= 1e-8
+    # All baselines identical.
+    uvw = np.repeat(rng.uniform(-50, 50, (1, 3)), 300, axis=0)
+    plan = gpu_lib.Plan(w.pix, uvw, 1e-6, mode="nufft")
+    V = plan.synthesize(torch.as_tensor(w.sky, dtype=torch.float32, device="cuda")).cpu().numpy()
+    plan.close()
+    assert oracle.rel_l2(V, oracle.sky2vis(w.pix, uvw, w.sky)) <= 1e-5
+
+
+def test_bad_arguments(gpu_lib, small):
+    w = small
+    with pytest.raises(gpu_lib.HvoxError) as e:
+        gpu_lib.Plan(w.pix, w.uvw, -1.0)
+    assert e.value.code == 1
+    with pytest.raises(gpu_lib.HvoxError):
+        gpu_lib.Plan(w.pix, w.uvw, 1e-6, isign=2)
+    bad = w.pix.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(gpu_lib.HvoxError):
+        gpu_lib.Plan(bad, w.uvw, 1e-6)
+
+
+def test_config1_full(gpu_lib):
+    w = configs.config1()
+    ref_v = oracle.sky2vis(w.pix, w.uvw, w.sky)
+    for eps in (1e-9, 1e-6):
+        V, y, img, info = _run(gpu_lib, w, eps)
+        assert oracle.rel_l2(V, ref_v) <= 10 * eps
+        assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 10 * eps
+
+
+@pytest.mark.parametrize("eps", [1e-9, 1e-5])
+def test_config2_full_size_sampled(gpu_lib, eps):
+    # Full LOFAR-like workload (52,812 pixels x 1,435,200 baselines) in the launch
+    # configuration of the benchmark; the oracle checks 2,000 seeded outputs each way.
+    w = configs.config2()
+    plan = gpu_lib.Plan(w.pix, w.uvw, eps)
+    I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
+    V = plan.synthesize(I).cpu().numpy()
+    vis = configs.visibilities_cn(2, w.n_vis)
+    img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
+    plan.close()
+    kv = configs.sample_indices(2, w.n_vis, 2000)
+    kp = configs.sample_indices(2, w.n_pix, 2000, purpose_offset=1)
+    assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
+    assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
