@@ -1,0 +1,317 @@
+"""Benchmark of the HVOX transform pair on one GB300 (or N replicas under torchrun).
+
+A step is one sky->vis and one vis->sky transform of the LOFAR-like workload
+(HEALPix nside=256, 30 deg cap: 52,812 pixels; 300 antennas, 4 earth-rotation steps,
+8 channels: 1,435,200 baselines) at eps = 1e-9 (FP64-accuracy path). The metric is
+(N_pix + N_vis) per transform, two transforms per step, divided by the step time.
+
+value:   device-resident inputs, CUDA events per step on the plan's stream, L2 flushed
+         (256 MiB write) before every step outside the timed window.
+e2e:     the same step through the C ABI with pinned HOST buffers (the library copies
+         host->device and device->host inside the call), wall clock.
+roofline: the dominant kernel's live CUDA-event time over the timed region.
+cpu_baseline: the FP64 oracle on this host's cores, on a bounded sample of outputs.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--eps E]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "3D NUFFT-3 (pix+vis)/s at ε=1e-6/1e-9, served vs plain; p50/p99 ms"
+UNIT = "(pix+vis)/s"
+WORKLOAD = ("LOFAR-like: HEALPix nside=256 30deg cap (52,812 px) x 300 antennas log-radial 50 m-100 km, "
+            "4 hour angles x 8 channels (1,435,200 baselines); step = sky->vis + vis->sky")
+FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9  # FP32 FMA pipes x 2 flops x max SM clock
+FLOPS_PER_PAIR = 16.0                      # algorithmic flops per (pixel, baseline) pair
+
+
+def dist_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
+
+
+def load_workload(n_vis=None):
+    from hvox_inputs import configs
+    w = configs.config2()
+    if n_vis:  # leading baselines only (smaller case for profiler captures)
+        w.uvw = w.uvw[:n_vis].copy()
+    return w
+
+
+# ---------------------------------------------------------------------------- CPU oracle
+
+def oracle_rate(w, target_s: float, seed: int = 0):
+    """Time the oracle on a seeded sample of outputs; returns (pairs/s, seconds, sample text)."""
+    import numpy as np
+    import oracle
+    from hvox_inputs import configs
+    vis = configs.visibilities_cn(2, w.n_vis)
+    rng = np.random.default_rng(1234 + seed)
+    # calibration
+    kv = np.sort(rng.choice(w.n_vis, 16, replace=False))
+    kp = np.sort(rng.choice(w.n_pix, 2, replace=False))
+    t0 = time.perf_counter()
+    oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)
+    oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)
+    dt = max(time.perf_counter() - t0, 1e-3)
+    rate0 = (len(kv) * w.n_pix + len(kp) * w.n_vis) / dt
+    pairs_target = rate0 * target_s
+    n_v = int(max(16, min(w.n_vis, pairs_target / 2 / w.n_pix)))
+    n_p = int(max(2, min(w.n_pix, pairs_target / 2 / w.n_vis)))
+    kv = np.sort(rng.choice(w.n_vis, n_v, replace=False))
+    kp = np.sort(rng.choice(w.n_pix, n_p, replace=False))
+    t0 = time.perf_counter()
+    oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)
+    oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)
+    dt = time.perf_counter() - t0
+    pairs = n_v * w.n_pix + n_p * w.n_vis
+    sample = (f"{n_v} baselines (each summed over all {w.n_pix} pixels) + {n_p} pixels (each over all "
+              f"{w.n_vis} baselines), FP64 direct sums; extrapolated to the full step by pair count")
+    return pairs / dt, dt, sample
+
+
+def cpu_baseline(w, target_s: float = 12.0):
+    import oracle
+    rate, dt, sample = oracle_rate(w, target_s)
+    step_s = 2.0 * w.n_pix * w.n_vis / rate
+    return {"value": 2.0 * (w.n_pix + w.n_vis) / step_s, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": sample, "sample_seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    w = load_workload()
+    import oracle
+    per_step = []
+    sample = ""
+    for i in range(args.warmup + args.steps):
+        rate, dt, sample = oracle_rate(w, 4.0, seed=i)
+        if i >= args.warmup:
+            per_step.append(2.0 * w.n_pix * w.n_vis / rate)
+    step_s = statistics.mean(per_step)
+    value = 2.0 * (w.n_pix + w.n_vis) / step_s
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ---------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"hvox_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+def time_steps(plan, I, V, steps, flush):
+    import torch
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        plan.synthesize(I)
+        plan.analyze(V)
+        e.record()
+        times.append((s, e))
+    torch.cuda.synchronize()
+    return [s.elapsed_time(e) for s, e in times]
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    import paper_2306_06007_gb300 as hvox
+    from hvox_inputs import configs
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    w = load_workload(args.n_vis)
+    units_per_step = 2.0 * (w.n_pix + w.n_vis)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
+    vis = configs.visibilities_cn(2, len(configs.config2().uvw))[:w.n_vis]
+
+    def measure(eps, with_e2e):
+        plan = hvox.Plan(w.pix, w.uvw, eps)
+        info = plan.info()
+        I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
+        V = torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")
+        time_steps(plan, I, V, args.warmup, flush)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        clocks = ClockSampler(local)
+        clocks.start()
+        plan.profile(True)
+        ms = time_steps(plan, I, V, args.steps, flush)
+        st = plan.stats()
+        clk = clocks.stop()
+        if world > 1:
+            dist.barrier()
+        total_ms = sum(ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        out = {"plan": plan, "info": info, "ms_per_step": total_ms / args.steps,
+               "value": world * units_per_step * args.steps / (total_ms * 1e-3), "stats": st, "clocks": clk}
+        if with_e2e:
+            Ih = torch.as_tensor(w.sky, dtype=plan.real_dtype).pin_memory()
+            Vh = torch.as_tensor(vis, dtype=plan.complex_dtype).pin_memory()
+            Vo = torch.empty(w.n_vis, dtype=plan.complex_dtype).pin_memory()
+            Io = torch.empty(w.n_pix, dtype=plan.real_dtype).pin_memory()
+            for _ in range(max(1, args.warmup)):
+                plan.synthesize(Ih, out=Vo)
+                plan.analyze(Vh, out=Io)
+            if world > 1:
+                dist.barrier()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                plan.synthesize(Ih, out=Vo)   # host I in, host V out
+                plan.analyze(Vh, out=Io)      # host V in, host I out
+            el = time.perf_counter() - t0
+            if world > 1:
+                t = torch.tensor([el], device="cuda", dtype=torch.float64)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                el = float(t.item())
+            rb = Ih.element_size()
+            out["e2e"] = {"value": world * units_per_step * args.steps / el, "unit": UNIT,
+                          "h2d_bytes_per_step": w.n_pix * rb + w.n_vis * 2 * rb,
+                          "d2h_bytes_per_step": w.n_vis * 2 * rb + w.n_pix * rb,
+                          "ms_per_step": el * 1e3 / args.steps}
+        return out
+
+    main = measure(args.eps, not args.no_e2e)
+    secondary = measure(1e-5, False) if not args.no_secondary else None
+
+    st = main["stats"]
+    stage_ms = st["ms"]
+    dom = max(("direct", "spread", "interp", "fft", "deconv", "permute"), key=lambda k: stage_ms[k])
+    launches = max(1, st["launches"][dom])
+    avg_s = stage_ms[dom] * 1e-3 / launches
+    info = main["info"]
+    roofline = None
+    if dom == "direct":
+        pairs_per_launch = info["direct_pairs"]
+        achieved = pairs_per_launch * FLOPS_PER_PAIR / avg_s
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_FLOPS, "traffic": None,
+                    "kernel": "direct_s2v_df + direct_v2s_df (one launch each per step)",
+                    "pairs_per_launch": pairs_per_launch, "avg_launch_ms": avg_s * 1e3,
+                    "pairs_per_s": pairs_per_launch / avg_s,
+                    "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
+    own = sum(st["launches"][k] for k in ("permute", "direct", "spread", "deconv", "interp"))
+
+    line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded HEALPix + layout)",
+            "config": {"workload": WORKLOAD, "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
+                       "l2": "flushed before each step (256 MiB write, outside the timed window)",
+                       "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
+                       "direct_pairs": info["direct_pairs"], "w": info["w"]},
+            "e2e": main.get("e2e"), "roofline": roofline, "gpu_launches": own,
+            "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "clocks": main["clocks"]}
+    if secondary is not None:
+        line["secondary"] = {"eps": 1e-5, "dtype": "f32", "value": secondary["value"],
+                             "ms_per_step": secondary["ms_per_step"], "clocks": secondary["clocks"],
+                             "stage_ms_per_step": {k: v / args.steps for k, v in secondary["stats"]["ms"].items()}}
+    main["plan"].close()
+    if secondary is not None:
+        secondary["plan"].close()
+    if rank == 0 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="hvox", choices=["hvox", "reference"])
+    ap.add_argument("--eps", type=float, default=1e-9)
+    ap.add_argument("--no-secondary", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--n-vis", type=int, default=0, help="use the first N baselines (profiler captures)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

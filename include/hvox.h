@@ -156,8 +156,41 @@ hvox_status hvox_plan_info(hvox_plan_t plan, hvox_info *info);
  * either may be NULL. Chunks are numbered as Algorithm 2 creates them. */
 hvox_status hvox_plan_chunks(hvox_plan_t plan, int64_t *pix_chunk, int64_t *vis_chunk);
 
+/* Stages of a transform, for hvox_get_stats. */
+enum {
+    HVOX_STAGE_PERMUTE = 0,  /* caller order <-> chunk order, weights (Sect. 4) */
+    HVOX_STAGE_DIRECT = 1,   /* direct sub-problems (Sect. 3.1 fallback) */
+    HVOX_STAGE_SPREAD = 2,   /* NUFFT spreading (step 1 of the type-3 transform) */
+    HVOX_STAGE_DECONV = 3,   /* deconvolve + zero-pad / crop (taper of step 1) */
+    HVOX_STAGE_FFT = 4,      /* uniform 3-D FFT (cuFFT, step 2) */
+    HVOX_STAGE_INTERP = 5,   /* NUFFT interpolation with taper (steps 3-4) */
+    HVOX_STAGE_ZERO = 6,     /* clearing accumulators and grids */
+    HVOX_NUM_STAGES = 8
+};
+
+typedef struct {
+    double ms[HVOX_NUM_STAGES];        /* device time per stage: CUDA events recorded on the
+                                          plan's stream around each stage (0 unless profiling) */
+    int64_t launches[HVOX_NUM_STAGES]; /* kernel launches of this library per stage (FFT: cuFFT
+                                          executions; ZERO: memsets) */
+    int64_t transforms;                /* transforms run since the last reset */
+} hvox_stats;
+
+/* Reset the statistics and turn event timing on (enable = 1) or off (0). Launch counts
+ * are always collected. */
+hvox_status hvox_profile(hvox_plan_t plan, int enable);
+
+/* Statistics since the last hvox_profile call (waits for the plan's stream). */
+hvox_status hvox_get_stats(hvox_plan_t plan, hvox_stats *out);
+
 /* Wait for the plan's stream and report any device-side error. */
 hvox_status hvox_sync(hvox_plan_t plan);
+
+/* Host-only dry run of hvox_plan: the partition, the per-sub-problem choices and the
+ * cost-model estimate, without touching a GPU (host pointers only). Fills the plan
+ * fields of *info (workspace_bytes is an estimate; plan_seconds is the planning time). */
+hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis, double eps,
+                          const hvox_opts *opts, hvox_info *info);
 
 /* Device memory a plan with these sizes would own (admission control); 0 on error. */
 double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_opts *opts);

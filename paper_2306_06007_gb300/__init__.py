@@ -53,6 +53,12 @@ class Info(ctypes.Structure):
                 ("model_seconds", ctypes.c_double)]
 
 
+class Stats(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 8), ("launches", ctypes.c_int64 * 8), ("transforms", ctypes.c_int64)]
+
+
+STAGES = ("permute", "direct", "spread", "deconv", "fft", "interp", "zero", "unused")
+
 _lib = None
 LIB_PATH = _build.LIB
 
@@ -81,10 +87,13 @@ def load():
         "hvox_sync": [P],
         "hvox_plan_info": [P, ctypes.POINTER(Info)],
         "hvox_plan_chunks": [P, PI64, PI64],
+        "hvox_profile": [P, ctypes.c_int],
+        "hvox_get_stats": [P, ctypes.POINTER(Stats)],
         "hvox_es_params": [ctypes.c_double, ctypes.c_double, ctypes.POINTER(I32), D],
         "hvox_es_ft": [I32, ctypes.c_double, D, I64, D],
         "hvox_box_dims": [D, D, ctypes.c_double, ctypes.c_double, I32, I32, D, D, D],
         "hvox_chunk_points": [D, I64, D, PI64, PI64],
+        "hvox_plan_dry": [D, I64, D, I64, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(Info)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -153,6 +162,26 @@ def chunk_points(xyz, h):
     _check(load().hvox_chunk_points(_dptr(xyz), len(xyz), _dptr(h),
                                     labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(nc)))
     return labels, nc.value
+
+
+def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: float = 0.0,
+             chunk_budget_bytes: float = 0.0, direct_threshold: float = 0.0, plain: bool = False) -> dict:
+    """Host-only planning (no GPU): partition, block choices and cost-model estimate."""
+    np = _np()
+    pix = np.ascontiguousarray(pix, dtype=np.float64)
+    uvw = np.ascontiguousarray(uvw, dtype=np.float64)
+    o = Opts()
+    o.precision = _PREC[precision]
+    o.mode = _MODE[mode]
+    o.upsampfac = upsampfac
+    o.chunk_budget_bytes = chunk_budget_bytes
+    o.direct_threshold = direct_threshold
+    o.plain = 1 if plain else 0
+    inf = Info()
+    _check(load().hvox_plan_dry(_dptr(pix), len(pix), _dptr(uvw), len(uvw), float(eps), ctypes.byref(o),
+                                ctypes.byref(inf)))
+    return {name: (list(getattr(inf, name)) if name in ("h", "eta") else getattr(inf, name))
+            for name, _ in Info._fields_}
 
 
 # ------------------------------------------------------------------ plans
@@ -293,6 +322,18 @@ class Plan:
 
     def sync(self):
         _check(load().hvox_sync(self._handle))
+
+    def profile(self, enable: bool = True):
+        """Reset statistics; time every stage with CUDA events while enabled."""
+        _check(load().hvox_profile(self._handle, 1 if enable else 0))
+
+    def stats(self) -> dict:
+        """Per-stage device milliseconds and launch counts since the last profile() call."""
+        st = Stats()
+        _check(load().hvox_get_stats(self._handle, ctypes.byref(st)))
+        return {"ms": {n: st.ms[i] for i, n in enumerate(STAGES[:7])},
+                "launches": {n: st.launches[i] for i, n in enumerate(STAGES[:7])},
+                "transforms": st.transforms}
 
     def close(self):
         if getattr(self, "_handle", None) and self._handle.value:

@@ -57,8 +57,13 @@ void DevBuf::free_() {
 }
 
 Plan::~Plan() {
-    if (stream) cudaStreamSynchronize(stream);
+    cudaStreamSynchronize(stream);
     for (auto &kv : fft_plans) cufftDestroy(kv.second);
+    for (auto &q : pending) {
+        cudaEventDestroy(q.a);
+        cudaEventDestroy(q.b);
+    }
+    for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
 }
 
 namespace {
@@ -318,6 +323,66 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// Checks the options and fills the configuration fields of a plan.
+void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, const hvox_opts *opts) {
+    hvox_opts o;
+    std::memset(&o, 0, sizeof(o));
+    if (opts) o = *opts;
+    if (o.precision < 0 || o.precision > 2) fail(HVOX_EINVAL, "hvox_plan: bad precision");
+    if (o.mode < 0 || o.mode > 2) fail(HVOX_EINVAL, "hvox_plan: bad mode");
+    if (!(o.upsampfac == 0.0 || (o.upsampfac >= 1.25 && o.upsampfac <= 4.0)))
+        fail(HVOX_EINVAL, "hvox_plan: upsampfac must be 0 or in [1.25, 4]");
+    if (!(o.chunk_budget_bytes >= 0.0) || !std::isfinite(o.chunk_budget_bytes))
+        fail(HVOX_EINVAL, "hvox_plan: bad chunk_budget_bytes");
+    if (!(o.anisotropy == 0.0 || o.anisotropy >= 1.0)) fail(HVOX_EINVAL, "hvox_plan: anisotropy must be >= 1");
+    if (o.ntrans < 0) fail(HVOX_EINVAL, "hvox_plan: ntrans must be >= 0");
+    if (!std::isfinite(o.direct_threshold)) fail(HVOX_EINVAL, "hvox_plan: bad direct_threshold");
+    p.n_pix = n_pix;
+    p.n_vis = n_vis;
+    p.eps = eps;
+    p.isign = isign;
+    p.plain = o.plain != 0;
+    p.mode = eps == 0.0 ? HVOX_MODE_DIRECT : o.mode;
+    p.prec = p.plain ? 2 : (o.precision == HVOX_PREC_AUTO ? (eps >= 1e-6 ? 1 : 2) : o.precision);
+    p.ntrans = o.ntrans > 0 ? o.ntrans : 1;
+    p.sigma = o.upsampfac > 0 ? o.upsampfac : 2.0;
+    p.stream = (cudaStream_t)o.stream;
+    p.budget_opt = o.chunk_budget_bytes;
+    p.direct_threshold = o.direct_threshold;
+    double e = eps > 0 ? eps : 1e-6;
+    if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
+    p.es = es_params(e * kEpsMargin, p.sigma);
+}
+
+void fill_info(const Plan &p, hvox_info *info) {
+    std::memset(info, 0, sizeof(*info));
+    info->n_pix = p.n_pix;
+    info->n_vis = p.n_vis;
+    info->precision = p.prec;
+    info->isign = p.isign;
+    info->eps = p.eps;
+    info->w = p.es.w;
+    info->beta = p.es.beta;
+    info->upsampfac = p.sigma;
+    info->budget_bytes = p.part.budget;
+    info->t = p.part.t;
+    for (int d = 0; d < 3; ++d) {
+        info->h[d] = p.part.h[d];
+        info->eta[d] = p.part.eta[d];
+    }
+    info->n_pix_chunks = p.part.n_pix_chunks;
+    info->n_vis_chunks = p.part.n_vis_chunks;
+    info->n_nufft_blocks = (int64_t)p.part.blocks.size();
+    info->n_direct_rects = (int64_t)p.part.rects.size();
+    info->direct_pairs = p.part.direct_pairs;
+    info->nufft_points = p.part.nufft_points;
+    info->nufft_cells = p.part.nufft_cells;
+    info->max_grid_bytes = p.part.max_grid_bytes;
+    info->workspace_bytes = p.workspace_bytes;
+    info->plan_seconds = p.plan_seconds;
+    info->model_seconds = p.part.model_seconds;
+}
+
 void transform(Plan &p, const void *in, void *out, bool s2v) {
     check_cuda(cudaSetDevice(p.device), "cudaSetDevice");
     const size_t re = p.prec == 1 ? 4 : 8;
@@ -374,38 +439,11 @@ hvox_status hvox_plan(const double *pix_xyz, int64_t n_pix, const double *uvw, i
         if (n_pix > INT32_MAX - 1024 || n_vis > INT32_MAX - 1024) fail(HVOX_EINVAL, "hvox_plan: too many points");
         if (!std::isfinite(eps) || eps < 0.0) fail(HVOX_EINVAL, "hvox_plan: eps must be finite and >= 0");
         if (isign != 1 && isign != -1) fail(HVOX_EINVAL, "hvox_plan: isign must be +1 or -1");
-        hvox_opts o;
-        std::memset(&o, 0, sizeof(o));
-        if (opts) o = *opts;
-        if (o.precision < 0 || o.precision > 2) fail(HVOX_EINVAL, "hvox_plan: bad precision");
-        if (o.mode < 0 || o.mode > 2) fail(HVOX_EINVAL, "hvox_plan: bad mode");
-        if (!(o.upsampfac == 0.0 || (o.upsampfac >= 1.25 && o.upsampfac <= 4.0)))
-            fail(HVOX_EINVAL, "hvox_plan: upsampfac must be 0 or in [1.25, 4]");
-        if (!(o.chunk_budget_bytes >= 0.0) || !std::isfinite(o.chunk_budget_bytes))
-            fail(HVOX_EINVAL, "hvox_plan: bad chunk_budget_bytes");
-        if (!(o.anisotropy == 0.0 || o.anisotropy >= 1.0)) fail(HVOX_EINVAL, "hvox_plan: anisotropy must be >= 1");
-        if (o.ntrans < 0) fail(HVOX_EINVAL, "hvox_plan: ntrans must be >= 0");
-        if (!std::isfinite(o.direct_threshold)) fail(HVOX_EINVAL, "hvox_plan: bad direct_threshold");
         auto *h = new hvox_plan_s();
         try {
             Plan &p = h->p;
             check_cuda(cudaGetDevice(&p.device), "cudaGetDevice");
-            p.n_pix = n_pix;
-            p.n_vis = n_vis;
-            p.eps = eps;
-            p.isign = isign;
-            p.plain = o.plain != 0;
-            p.mode = eps == 0.0 ? HVOX_MODE_DIRECT : o.mode;
-            p.prec = p.plain ? 2 : (o.precision == HVOX_PREC_AUTO ? (eps >= 1e-6 || eps == 0.0 ? 1 : 2) : o.precision);
-            if (eps == 0.0 && o.precision == HVOX_PREC_AUTO) p.prec = 2;
-            p.ntrans = o.ntrans > 0 ? o.ntrans : 1;
-            p.sigma = o.upsampfac > 0 ? o.upsampfac : 2.0;
-            p.stream = (cudaStream_t)o.stream;
-            p.budget_opt = o.chunk_budget_bytes;
-            p.direct_threshold = o.direct_threshold;
-            double e = eps > 0 ? eps : 1e-6;
-            if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
-            p.es = es_params(e * kEpsMargin, p.sigma);
+            configure(p, n_pix, n_vis, eps, isign, opts);
             build_plan(p, pix_xyz, uvw, pix_weight);
         } catch (...) {
             delete h;
@@ -445,36 +483,65 @@ hvox_status hvox_sync(hvox_plan_t plan) {
     });
 }
 
+hvox_status hvox_profile(hvox_plan_t plan, int enable) {
+    return guard([&] {
+        if (!plan) fail(HVOX_EINVAL, "hvox_profile: NULL plan");
+        Plan &p = plan->p;
+        check_cuda(cudaSetDevice(p.device), "cudaSetDevice");
+        collect_stats(p);
+        for (int i = 0; i < HVOX_NUM_STAGES; ++i) {
+            p.stage_ms[i] = 0.0;
+            p.stage_launches[i] = 0;
+        }
+        p.transforms = 0;
+        p.profiling = enable != 0;
+    });
+}
+
+hvox_status hvox_get_stats(hvox_plan_t plan, hvox_stats *out) {
+    return guard([&] {
+        if (!plan || !out) fail(HVOX_EINVAL, "hvox_get_stats: NULL argument");
+        Plan &p = plan->p;
+        check_cuda(cudaSetDevice(p.device), "cudaSetDevice");
+        collect_stats(p);
+        for (int i = 0; i < HVOX_NUM_STAGES; ++i) {
+            out->ms[i] = p.stage_ms[i];
+            out->launches[i] = p.stage_launches[i];
+        }
+        out->transforms = p.transforms;
+    });
+}
+
 hvox_status hvox_plan_info(hvox_plan_t plan, hvox_info *info) {
     return guard([&] {
         if (!plan || !info) fail(HVOX_EINVAL, "hvox_plan_info: NULL argument");
-        const Plan &p = plan->p;
-        std::memset(info, 0, sizeof(*info));
-        info->n_pix = p.n_pix;
-        info->n_vis = p.n_vis;
-        info->precision = p.prec;
-        info->isign = p.isign;
-        info->eps = p.eps;
-        info->w = p.es.w;
-        info->beta = p.es.beta;
-        info->upsampfac = p.sigma;
-        info->budget_bytes = p.part.budget;
-        info->t = p.part.t;
-        for (int d = 0; d < 3; ++d) {
-            info->h[d] = p.part.h[d];
-            info->eta[d] = p.part.eta[d];
-        }
-        info->n_pix_chunks = p.part.n_pix_chunks;
-        info->n_vis_chunks = p.part.n_vis_chunks;
-        info->n_nufft_blocks = (int64_t)p.part.blocks.size();
-        info->n_direct_rects = (int64_t)p.part.rects.size();
-        info->direct_pairs = p.part.direct_pairs;
-        info->nufft_points = p.part.nufft_points;
-        info->nufft_cells = p.part.nufft_cells;
-        info->max_grid_bytes = p.part.max_grid_bytes;
-        info->workspace_bytes = p.workspace_bytes;
-        info->plan_seconds = p.plan_seconds;
-        info->model_seconds = p.part.model_seconds;
+        fill_info(plan->p, info);
+    });
+}
+
+hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis, double eps,
+                          const hvox_opts *opts, hvox_info *info) {
+    return guard([&] {
+        if (!pix_xyz || !uvw || !info) fail(HVOX_EINVAL, "hvox_plan_dry: NULL argument");
+        if (n_pix < 1 || n_vis < 1) fail(HVOX_EINVAL, "hvox_plan_dry: need n_pix >= 1 and n_vis >= 1");
+        if (!std::isfinite(eps) || eps < 0.0) fail(HVOX_EINVAL, "hvox_plan_dry: eps must be finite and >= 0");
+        for (int64_t i = 0; i < 3 * n_pix; ++i)
+            if (!std::isfinite(pix_xyz[i])) fail(HVOX_EINVAL, "hvox_plan_dry: non-finite pixel coordinate");
+        for (int64_t i = 0; i < 3 * n_vis; ++i)
+            if (!std::isfinite(uvw[i])) fail(HVOX_EINVAL, "hvox_plan_dry: non-finite baseline coordinate");
+        auto t0 = std::chrono::steady_clock::now();
+        Plan p;
+        configure(p, n_pix, n_vis, eps, -1, opts);
+        const int elem = p.prec == 1 ? 8 : 16;
+        PlanInputs in{pix_xyz, uvw, n_pix, n_vis, p.sigma, p.es, p.prec, p.mode, p.plain,
+                      p.budget_opt, p.direct_threshold, elem};
+        p.part = make_partition(in);
+        const double re = p.prec == 1 ? 4.0 : 8.0;
+        double recs = p.part.nufft_points * (p.prec == 1 ? 48.0 : 64.0);
+        p.workspace_bytes = (double)(n_pix + n_vis) * 60.0 + recs + p.part.max_grid_bytes +
+                            4.0 * re * (double)std::max(n_pix, 2 * n_vis);
+        p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        fill_info(p, info);
     });
 }
 

@@ -148,7 +148,26 @@ template <typename T> struct alignas(16) GridRec {
     T pad2;
 };
 
+// Stage boundaries reported by the kernel launchers to the executor's profiler.
+struct StageHook {
+    virtual void begin(int stage) = 0;
+    virtual void end(int stage, int launches) = 0;
+    virtual ~StageHook() = default;
+};
+
 struct Plan {
+    // statistics
+    bool profiling = false;
+    double stage_ms[HVOX_NUM_STAGES] = {0};
+    int64_t stage_launches[HVOX_NUM_STAGES] = {0};
+    int64_t transforms = 0;
+    struct Pending {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> pending;
+    std::vector<cudaEvent_t> event_pool;
+
     // configuration
     int64_t n_pix = 0, n_vis = 0;
     double eps = 0;
@@ -235,12 +254,12 @@ template <typename T>
 void nufft_block_s2v(const DevBlock &b, int w, double beta, const T *c, const GridRec<T> *prec,
                      const typename CplxOf<T>::type *pph, const GridRec<T> *vrec, const typename CplxOf<T>::type *vq,
                      const T *ipsi, typename CplxOf<T>::type *G1, typename CplxOf<T>::type *G2, cufftHandle plan,
-                     int isign, typename CplxOf<T>::type *acc, cudaStream_t s);
+                     int isign, typename CplxOf<T>::type *acc, cudaStream_t s, StageHook &hook);
 template <typename T>
 void nufft_block_v2s(const DevBlock &b, int w, double beta, const typename CplxOf<T>::type *V, const GridRec<T> *prec,
                      const typename CplxOf<T>::type *pph, const GridRec<T> *vrec, const typename CplxOf<T>::type *vq,
                      const T *ipsi, typename CplxOf<T>::type *G1, typename CplxOf<T>::type *G2, cufftHandle plan,
-                     int isign, T *acc, cudaStream_t s);
+                     int isign, T *acc, cudaStream_t s, StageHook &hook);
 template <typename T>
 void nufft_tables(const NufftBlock &b, const double *pix_soa, int64_t n_pix, const double *vis_soa, int64_t n_vis,
                   int w, int isign, const double *qz, const double *qf, int nq, GridRec<T> *prec,
@@ -256,5 +275,6 @@ void launch_v2s_out(int prec, const void *acc, const int32_t *perm, const double
 // Transforms.
 void run_synthesize(Plan &p, const void *I_dev, void *V_dev);
 void run_analyze(Plan &p, const void *V_dev, void *I_dev);
+void collect_stats(Plan &p);
 
 }  // namespace hvox

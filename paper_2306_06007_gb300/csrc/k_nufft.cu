@@ -338,75 +338,95 @@ inline unsigned grid_stride_blocks(int64_t n) {
 template <typename T>
 void nufft_block_s2v(const DevBlock &b, int w, double beta, const T *c, const GridRec<T> *prec,
                      const cplx_t<T> *pph, const GridRec<T> *vrec, const cplx_t<T> *vq, const T *ipsi, cplx_t<T> *G1,
-                     cplx_t<T> *G2, cufftHandle plan, int isign, cplx_t<T> *acc, cudaStream_t s) {
+                     cplx_t<T> *G2, cufftHandle plan, int isign, cplx_t<T> *acc, cudaStream_t s, StageHook &hook) {
     const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
+    hook.begin(HVOX_STAGE_ZERO);
     check_cuda(cudaMemsetAsync(G1, 0, sizeof(cplx_t<T>) * m1, s), "memset G1");
+    hook.end(HVOX_STAGE_ZERO, 1);
     const T bt = (T)beta;
     if (b.np > 0) {
+        hook.begin(HVOX_STAGE_SPREAD);
 #define CALL(W) spread_pix_kernel<T, W><<<blocks_for(b.np, 128), 128, 0, s>>>(b, c, prec, pph, G1, bt)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_pix");
+        hook.end(HVOX_STAGE_SPREAD, 1);
     }
     const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
+    hook.begin(HVOX_STAGE_DECONV);
     deconv_pad_kernel<T><<<grid_stride_blocks(m2), 256, 0, s>>>(b, G1, ipsi, G2);
     check_cuda(cudaGetLastError(), "deconv_pad");
+    hook.end(HVOX_STAGE_DECONV, 1);
+    hook.begin(HVOX_STAGE_FFT);
     check_cufft(cufftSetStream(plan, s), "cufftSetStream");
     const int dir = isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
     if constexpr (sizeof(T) == 4)
         check_cufft(cufftExecC2C(plan, (cufftComplex *)G2, (cufftComplex *)G2, dir), "cufftExecC2C");
     else
         check_cufft(cufftExecZ2Z(plan, (cufftDoubleComplex *)G2, (cufftDoubleComplex *)G2, dir), "cufftExecZ2Z");
+    hook.end(HVOX_STAGE_FFT, 1);
     if (b.nv > 0) {
+        hook.begin(HVOX_STAGE_INTERP);
 #define CALL(W) interp_vis_kernel<T, W><<<blocks_for(b.nv, 128), 128, 0, s>>>(b, G2, vrec, vq, acc, bt)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "interp_vis");
+        hook.end(HVOX_STAGE_INTERP, 1);
     }
 }
 
 template <typename T>
 void nufft_block_v2s(const DevBlock &b, int w, double beta, const cplx_t<T> *V, const GridRec<T> *prec,
                      const cplx_t<T> *pph, const GridRec<T> *vrec, const cplx_t<T> *vq, const T *ipsi, cplx_t<T> *G1,
-                     cplx_t<T> *G2, cufftHandle plan, int isign, T *acc, cudaStream_t s) {
+                     cplx_t<T> *G2, cufftHandle plan, int isign, T *acc, cudaStream_t s, StageHook &hook) {
     const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
+    hook.begin(HVOX_STAGE_ZERO);
     check_cuda(cudaMemsetAsync(G2, 0, sizeof(cplx_t<T>) * m2, s), "memset G2");
+    hook.end(HVOX_STAGE_ZERO, 1);
     const T bt = (T)beta;
     if (b.nv > 0) {
+        hook.begin(HVOX_STAGE_SPREAD);
 #define CALL(W) spread_vis_kernel<T, W><<<blocks_for(b.nv, 128), 128, 0, s>>>(b, V, vrec, vq, G2, bt)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_vis");
+        hook.end(HVOX_STAGE_SPREAD, 1);
     }
+    hook.begin(HVOX_STAGE_FFT);
     check_cufft(cufftSetStream(plan, s), "cufftSetStream");
     const int dir = isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD;  // transpose: opposite sign
     if constexpr (sizeof(T) == 4)
         check_cufft(cufftExecC2C(plan, (cufftComplex *)G2, (cufftComplex *)G2, dir), "cufftExecC2C");
     else
         check_cufft(cufftExecZ2Z(plan, (cufftDoubleComplex *)G2, (cufftDoubleComplex *)G2, dir), "cufftExecZ2Z");
+    hook.end(HVOX_STAGE_FFT, 1);
     const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
+    hook.begin(HVOX_STAGE_DECONV);
     crop_deconv_kernel<T><<<grid_stride_blocks(m1), 256, 0, s>>>(b, G2, ipsi, G1);
     check_cuda(cudaGetLastError(), "crop_deconv");
+    hook.end(HVOX_STAGE_DECONV, 1);
     if (b.np > 0) {
+        hook.begin(HVOX_STAGE_INTERP);
 #define CALL(W) interp_pix_kernel<T, W><<<blocks_for(b.np, 128), 128, 0, s>>>(b, G1, prec, pph, acc, bt)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "interp_pix");
+        hook.end(HVOX_STAGE_INTERP, 1);
     }
 }
 
 template void nufft_block_s2v<float>(const DevBlock &, int, double, const float *, const GridRec<float> *,
                                      const float2 *, const GridRec<float> *, const float2 *, const float *, float2 *,
-                                     float2 *, cufftHandle, int, float2 *, cudaStream_t);
+                                     float2 *, cufftHandle, int, float2 *, cudaStream_t, StageHook &);
 template void nufft_block_s2v<double>(const DevBlock &, int, double, const double *, const GridRec<double> *,
                                       const double2 *, const GridRec<double> *, const double2 *, const double *,
-                                      double2 *, double2 *, cufftHandle, int, double2 *, cudaStream_t);
+                                      double2 *, double2 *, cufftHandle, int, double2 *, cudaStream_t, StageHook &);
 template void nufft_block_v2s<float>(const DevBlock &, int, double, const float2 *, const GridRec<float> *,
                                      const float2 *, const GridRec<float> *, const float2 *, const float *, float2 *,
-                                     float2 *, cufftHandle, int, float *, cudaStream_t);
+                                     float2 *, cufftHandle, int, float *, cudaStream_t, StageHook &);
 template void nufft_block_v2s<double>(const DevBlock &, int, double, const double2 *, const GridRec<double> *,
                                       const double2 *, const GridRec<double> *, const double2 *, const double *,
-                                      double2 *, double2 *, cufftHandle, int, double *, cudaStream_t);
+                                      double2 *, double2 *, cufftHandle, int, double *, cudaStream_t, StageHook &);
 
 template <typename T>
 void nufft_tables(const NufftBlock &b, const double *pix_soa, int64_t n_pix, const double *vis_soa, int64_t n_vis,
