@@ -202,6 +202,32 @@ const char *hvox_last_error(void);
 const char *hvox_version(void);
 
 /* ---------------------------------------------------------------------------
+ * Direct sky -> vis evaluation that allocates nothing (no counterpart in the paper).
+ *
+ * For callers that cannot call cudaMalloc: code running inside another framework that has
+ * reserved the device's memory for its own pool, and per-iteration loops (for example a
+ * calibration solver predicting visibilities from a sky model every step) where an
+ * allocation, and the device synchronisation that freeing brings, is not allowed.
+ *
+ * Computes V_k = sum_n I_n exp(+isign j 2 pi <p_k, r_n>) by direct summation in FP32
+ * (phase fractions from exact hi/lo products, as in the planned FP32 path; relative l2
+ * error ~1e-6), without weights, in the caller's point order.
+ *   pix_xyz (n_pix, 3) FP64, uvw (n_vis, 3) FP64 wavelengths, I float[n_pix],
+ *   V interleaved complex float[2 n_vis] (overwritten): all DEVICE pointers (host
+ *   pointers are rejected with HVOX_EINVAL). stream: cudaStream_t or NULL.
+ * Limit: n_pix + n_vis <= 524,288 (HVOX_EINVAL beyond, nothing enqueued). The working
+ * memory is one static device array of 16 MiB (coordinate splits) that every GPU which
+ * loads the library reserves until the process exits; the call itself calls no
+ * cudaMalloc, cudaFree or allocating library routine. The first call on a device looks
+ * up that array's device address (cudaGetSymbolAddress) with the device current; make
+ * that first call before any stream capture. All calls share the array and it keeps
+ * the last call's contents, so calls whose work overlaps on the GPU (different streams,
+ * or different host threads) race: serialise them. Asynchronous on `stream`.
+ */
+hvox_status hvox_direct_synthesize_noalloc(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis,
+                                           const float *I, float *V, int isign, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Host-only planning primitives (no GPU needed), exposed for testing and for
  * callers that want to inspect a partition before planning.
  * --------------------------------------------------------------------------- */

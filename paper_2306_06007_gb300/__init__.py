@@ -94,6 +94,7 @@ def load():
         "hvox_box_dims": [D, D, ctypes.c_double, ctypes.c_double, I32, I32, D, D, D],
         "hvox_chunk_points": [D, I64, D, PI64, PI64],
         "hvox_plan_dry": [D, I64, D, I64, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(Info)],
+        "hvox_direct_synthesize_noalloc": [V, I64, V, I64, V, V, ctypes.c_int, V],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -182,6 +183,27 @@ def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: flo
                                 ctypes.byref(inf)))
     return {name: (list(getattr(inf, name)) if name in ("h", "eta") else getattr(inf, name))
             for name, _ in Info._fields_}
+
+
+def direct_synthesize_noalloc(pix, uvw, I, V, isign: int = -1, stream=None):
+    """sky -> vis by direct FP32 summation without any allocation (hvox_direct_synthesize_noalloc).
+
+    For callers that cannot allocate device memory (a framework owning the device's memory
+    pool, or a per-iteration loop where allocation is not allowed). pix (N, 3) and uvw
+    (K, 3) float64, I float32 (N,), V complex64 (K,): all CUDA tensors, V overwritten.
+    n_pix + n_vis <= 524,288. Calls that overlap on the GPU share one static scratch array
+    and race; run them one after another.
+    """
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    for t, dt in ((pix, torch.float64), (uvw, torch.float64), (I, torch.float32), (V, torch.complex64)):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == dt and t.is_contiguous()):
+            raise TypeError(f"expected a contiguous CUDA tensor of {dt}")
+    _check(load().hvox_direct_synthesize_noalloc(pix.data_ptr(), pix.shape[0], uvw.data_ptr(), uvw.shape[0],
+                                                 I.data_ptr(), V.data_ptr(), int(isign),
+                                                 ctypes.c_void_p(stream.cuda_stream)))
+    return V
 
 
 # ------------------------------------------------------------------ plans

@@ -15,6 +15,8 @@
 //    products and sums in double-float arithmetic (Dekker 1971), ~1e-11 absolute;
 //  * plain path: everything in FP64 (the reference form the optimised paths replace).
 #include <cstdint>
+#include <mutex>
+#include <string>
 
 #include "hvox_internal.h"
 
@@ -611,3 +613,169 @@ void launch_direct_v2s_f64(const WorkItem *items, int64_t n, const double *pxyz,
 }
 
 }  // namespace hvox
+
+// ============================================================================
+// Direct sky -> vis evaluation that allocates nothing.
+//
+// For callers that cannot call cudaMalloc: code that runs inside another framework
+// which has reserved the device's memory for its own pool (a cudaMalloc there fails or
+// fragments that pool), and iteration loops such as calibration solvers that predict
+// visibilities from a sky model every step, where an allocation (and the device
+// synchronisation cudaFree brings) is not allowed. The caller passes device pointers
+// for everything; the only working memory is the static array below, reserved once
+// per device when the library is loaded and kept until the process exits.
+// ============================================================================
+
+namespace hvox {
+
+namespace {
+
+constexpr int64_t kNoAllocMaxPoints = int64_t(1) << 19;  // n_pix + n_vis <= 524,288
+
+// hi and lo float splits of the pixel and baseline coordinates: 2 * 524,288 float4 = 16 MiB.
+__device__ __align__(256) float4 g_noalloc_scratch[2 * kNoAllocMaxPoints];
+
+__global__ void noalloc_split_kernel(const double *__restrict__ xyz, int64_t n, float4 *__restrict__ hi,
+                                     float4 *__restrict__ lo) {
+    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float h[3], l[3];
+    for (int d = 0; d < 3; ++d) {
+        double x = xyz[3 * i + d];
+        h[d] = (float)x;
+        l[d] = (float)(x - (double)h[d]);
+    }
+    hi[i] = make_float4(h[0], h[1], h[2], 0.f);
+    lo[i] = make_float4(l[0], l[1], l[2], 0.f);
+}
+
+// Same arithmetic as direct_s2v_f32; the tile (baselines) comes from blockIdx.x and
+// the pixel segment from blockIdx.y instead of a work list.
+__global__ void __launch_bounds__(kThreads) direct_s2v_f32_noalloc(
+    const float4 *__restrict__ vh, const float4 *__restrict__ vl, int n_vis, const float4 *__restrict__ rh_g,
+    const float4 *__restrict__ rl_g, const float *__restrict__ c, int n_pix, int seg, float2 *__restrict__ V,
+    float sgn) {
+    __shared__ float4 sh[kThreads];
+    __shared__ float4 sl[kThreads];
+    const int o0 = blockIdx.x * kTile, o1 = min(o0 + kTile, n_vis);
+    const int s_begin = blockIdx.y * seg, s_end = min(s_begin + seg, n_pix);
+    float3 ph[kPerThread], pl[kPerThread];
+    float are[kPerThread], aim[kPerThread];
+#pragma unroll
+    for (int v = 0; v < kPerThread; ++v) {
+        int k = o0 + threadIdx.x + v * kThreads;
+        float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
+        if (k < o1) {
+            a = vh[k];
+            b = vl[k];
+        }
+        ph[v] = make_float3(a.x, a.y, a.z);
+        pl[v] = make_float3(b.x, b.y, b.z);
+        are[v] = 0.f;
+        aim[v] = 0.f;
+    }
+    for (int s0 = s_begin; s0 < s_end; s0 += kThreads) {
+        __syncthreads();
+        int n = s0 + threadIdx.x;
+        if (n < s_end) {
+            float4 a = rh_g[n];
+            a.w = c[n];
+            sh[threadIdx.x] = a;
+            sl[threadIdx.x] = rl_g[n];
+        } else {
+            sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+            sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        const int cnt = min(kThreads, s_end - s0);
+#pragma unroll 4
+        for (int q = 0; q < cnt; ++q) {
+            const float4 rh = sh[q], rl = sl[q];
+#pragma unroll
+            for (int v = 0; v < kPerThread; ++v) {
+                float f = phase_f32(ph[v], pl[v], rh, rl);
+                float sn, cs;
+                __sincosf(6.28318530717958648f * f, &sn, &cs);
+                are[v] = __fmaf_rn(rh.w, cs, are[v]);
+                aim[v] = __fmaf_rn(rh.w, sn, aim[v]);
+            }
+        }
+    }
+#pragma unroll
+    for (int v = 0; v < kPerThread; ++v) {
+        int k = o0 + threadIdx.x + v * kThreads;
+        if (k < o1) {
+            atomicAdd(&V[k].x, are[v]);
+            atomicAdd(&V[k].y, sgn * aim[v]);
+        }
+    }
+}
+
+std::mutex g_noalloc_mu;
+void *g_noalloc_ptr[256] = {nullptr};
+
+// Device address of the static scratch for the current device. The first call on a
+// device looks it up (cudaGetSymbolAddress, no allocation) with that device current.
+float4 *noalloc_scratch_for_current_device() {
+    int dev = 0;
+    check_cuda(cudaGetDevice(&dev), "cudaGetDevice");
+    if (dev < 0 || dev >= 256) fail(HVOX_EUNSUPPORTED, "hvox_direct_synthesize_noalloc: device index out of range");
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *ptr = nullptr;
+        check_cuda(cudaGetSymbolAddress(&ptr, g_noalloc_scratch), "cudaGetSymbolAddress");
+        g_noalloc_ptr[dev] = ptr;
+    }
+    return static_cast<float4 *>(g_noalloc_ptr[dev]);
+}
+
+bool on_device(const void *p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
+}  // namespace hvox
+
+extern "C" hvox_status hvox_direct_synthesize_noalloc(const double *pix_xyz, int64_t n_pix, const double *uvw,
+                                                      int64_t n_vis, const float *I, float *V, int isign,
+                                                      void *stream) {
+    using namespace hvox;
+    try {
+        if (!pix_xyz || !uvw || !I || !V) fail(HVOX_EINVAL, "hvox_direct_synthesize_noalloc: NULL pointer");
+        if (n_pix < 1 || n_vis < 1) fail(HVOX_EINVAL, "hvox_direct_synthesize_noalloc: need n_pix, n_vis >= 1");
+        if (n_pix + n_vis > kNoAllocMaxPoints)
+            fail(HVOX_EINVAL, "hvox_direct_synthesize_noalloc: n_pix + n_vis = " + std::to_string(n_pix + n_vis) +
+                                  " exceeds the static limit of " + std::to_string(kNoAllocMaxPoints) + " points");
+        if (isign != 1 && isign != -1) fail(HVOX_EINVAL, "hvox_direct_synthesize_noalloc: isign must be +1 or -1");
+        if (!on_device(pix_xyz) || !on_device(uvw) || !on_device(I) || !on_device(V))
+            fail(HVOX_EINVAL, "hvox_direct_synthesize_noalloc: every pointer must be device memory");
+        cudaStream_t s = (cudaStream_t)stream;
+        float4 *scratch = noalloc_scratch_for_current_device();
+        float4 *rh = scratch, *rl = scratch + n_pix;
+        float4 *vh = scratch + 2 * n_pix, *vl = vh + n_vis;
+        noalloc_split_kernel<<<(unsigned)((n_pix + 255) / 256), 256, 0, s>>>(pix_xyz, n_pix, rh, rl);
+        check_cuda(cudaGetLastError(), "noalloc_split pixels");
+        noalloc_split_kernel<<<(unsigned)((n_vis + 255) / 256), 256, 0, s>>>(uvw, n_vis, vh, vl);
+        check_cuda(cudaGetLastError(), "noalloc_split baselines");
+        check_cuda(cudaMemsetAsync(V, 0, sizeof(float) * 2 * (size_t)n_vis, s), "clear V");
+        const int seg = 4096;
+        dim3 grid((unsigned)((n_vis + kTile - 1) / kTile), (unsigned)((n_pix + seg - 1) / seg));
+        direct_s2v_f32_noalloc<<<grid, kThreads, 0, s>>>(vh, vl, (int)n_vis, rh, rl, I, (int)n_pix, seg,
+                                                          reinterpret_cast<float2 *>(V), (float)isign);
+        check_cuda(cudaGetLastError(), "direct_s2v_f32_noalloc");
+        set_error("");
+        return HVOX_OK;
+    } catch (const Error &e) {
+        set_error(e.msg);
+        return e.code;
+    } catch (const std::exception &e) {
+        set_error(std::string("internal error: ") + e.what());
+        return HVOX_EINTERNAL;
+    }
+}
