@@ -40,9 +40,17 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
-def load_workload(n_vis=None):
+WORKLOADS = {
+    1: "HEALPix nside=32 45deg cap (1,740 px) x 200 antennas in a 1 km disk (19,900 baselines)",
+    2: WORKLOAD,
+    3: ("SKA-Low-like: HEALPix nside=1024 40deg cap (1,470,612 px) x 512 antennas (Gaussian core + arms), "
+        "32 hour angles (4,186,112 baselines); step = sky->vis + vis->sky"),
+}
+
+
+def load_workload(n_vis=None, config=2):
     from hvox_inputs import configs
-    w = configs.config2()
+    w = configs.CONFIGS[config]()
     if n_vis:  # leading baselines only (smaller case for profiler captures)
         w.uvw = w.uvw[:n_vis].copy()
     return w
@@ -180,6 +188,30 @@ def time_steps(plan, I, V, steps, flush):
     return [s.elapsed_time(e) for s, e in times]
 
 
+def serving_study():
+    """Served (continuous batching, mixed precision) vs plain (FP64, one job at a time) on
+    the same seeded request stream; and a larger served stream. Latency = completion -
+    arrival; throughput = sum of (N_pix + N_vis) over requests / makespan."""
+    from hvox_inputs import configs
+    from paper_2306_06007_gb300.serve import Server
+    out = {}
+    small = configs.config5_requests(100, rate_hz=50.0, n_min=1e3, n_max=3e4, seed_offset=11)
+    for name, kw in (("served", {"max_inflight": 8}), ("plain", {"plain": True})):
+        srv = Server(**kw)
+        rep = srv.run(small, realtime=True)
+        srv.close()
+        out[name] = rep.summary()
+    out["stream"] = ("100 requests, Poisson 50/s, N_pix and N_vis log-uniform [1e3, 3e4] (HEALPix caps <= 40 deg; "
+                     "config-2/3 layouts), eps uniform {1e-4, 1e-6, 1e-9}, S or A")
+    big = configs.config5_requests(100, rate_hz=50.0, n_min=1e4, n_max=2e5, seed_offset=12)
+    srv = Server(max_inflight=8)
+    rep = srv.run(big, realtime=True)
+    srv.close()
+    out["served_large"] = rep.summary()
+    out["served_large"]["stream"] = "as above with N log-uniform [1e4, 2e5]"
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -191,13 +223,13 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    w = load_workload(args.n_vis)
+    w = load_workload(args.n_vis, args.config)
     units_per_step = 2.0 * (w.n_pix + w.n_vis)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    vis = configs.visibilities_cn(2, len(configs.config2().uvw))[:w.n_vis]
+    vis = configs.visibilities_cn(args.config, w.n_vis)
 
     def measure(eps, with_e2e):
-        plan = hvox.Plan(w.pix, w.uvw, eps)
+        plan = hvox.Plan(w.pix, w.uvw, eps, mode=args.mode)
         info = plan.info()
         I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
         V = torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")
@@ -261,16 +293,28 @@ def run_gpu(args):
         achieved = pairs_per_launch * FLOPS_PER_PAIR / avg_s
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_FLOPS, "traffic": None,
-                    "kernel": "direct_s2v_df + direct_v2s_df (one launch each per step)",
+                    "kernel": "direct_s2v + direct_v2s (one launch each per step)",
                     "pairs_per_launch": pairs_per_launch, "avg_launch_ms": avg_s * 1e3,
                     "pairs_per_s": pairs_per_launch / avg_s,
+                    "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
+    elif dom in ("spread", "interp"):
+        # Every NUFFT point is spread once and interpolated once per step (w^3 taps each),
+        # 4 flops per tap (complex value times a real weight, accumulated).
+        taps_per_step = info["nufft_points"] * info["w"] ** 3
+        taps_per_launch = taps_per_step / (st["launches"][dom] / args.steps)
+        achieved = taps_per_launch * 4.0 / avg_s
+        roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_FLOPS, "traffic": None,
+                    "kernel": dom + " kernels (one launch per NUFFT sub-problem)",
+                    "taps_per_s": taps_per_launch / avg_s, "avg_launch_ms": avg_s * 1e3,
                     "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
     own = sum(st["launches"][k] for k in ("permute", "direct", "spread", "deconv", "interp"))
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded HEALPix + layout)",
-            "config": {"workload": WORKLOAD, "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
+            "config": {"workload": WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
+                       "mode": args.mode,
                        "l2": "flushed before each step (256 MiB write, outside the timed window)",
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
                        "direct_pairs": info["direct_pairs"], "w": info["w"]},
@@ -284,6 +328,8 @@ def run_gpu(args):
     main["plan"].close()
     if secondary is not None:
         secondary["plan"].close()
+    if rank == 0 and not args.no_serving:
+        line["serving"] = serving_study()
     if rank == 0 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w)
     if rank == 0:
@@ -304,7 +350,11 @@ def main():
     ap.add_argument("--no-secondary", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--n-vis", type=int, default=0, help="use the first N baselines (profiler captures)")
+    ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
+                    help="workload (2, the LOFAR-like case, is the benchmark; 1 and 3 for studies)")
+    ap.add_argument("--mode", default="auto", choices=["auto", "nufft", "direct"])
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

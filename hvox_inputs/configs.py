@@ -140,3 +140,67 @@ def small_case(seed: int, n_pix: int, n_vis: int, cap_deg: float = 30.0, radius_
 
 
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}
+
+
+def _cap_for(n_pix: int, cap_deg: float = 40.0) -> np.ndarray:
+    """The first n_pix RING pixels of the smallest nside whose cap_deg cap holds n_pix."""
+    nside = 1
+    while healpix.cap_count(nside, cap_deg) < n_pix:
+        nside *= 2
+    lo = nside // 2 if nside > 1 else 1
+    while lo < nside and healpix.cap_count(lo, cap_deg) < n_pix:
+        lo += max(1, (nside - lo) // 8)
+    if healpix.cap_count(lo, cap_deg) >= n_pix:
+        nside = lo
+    return healpix.cap_pixels(nside, cap_deg, max_pixels=n_pix)
+
+
+def _baselines_for(n_vis: int, layout: int) -> np.ndarray:
+    """n_vis baselines from the config-2 (LOFAR-like) or config-3 (SKA-like) layout, with
+    as many earth-rotation steps as needed, truncated."""
+    if layout == 2:
+        ant, lat, step, lams = config2_antennas(), 52.9, 15.0, [2.0]
+    else:
+        ant, lat, step, lams = config3_antennas(), -26.7, 3.75, [2.0]
+    pairs = len(ant) * (len(ant) - 1) // 2
+    n_steps = max(1, -(-n_vis // pairs))
+    uvw = layouts.baselines(ant, layouts.centred_steps(n_steps, step), lat, lams)
+    return np.ascontiguousarray(uvw[:n_vis])
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float        # seconds after the start of the stream
+    pix: np.ndarray
+    uvw: np.ndarray
+    eps: float
+    direction: str        # "s2v" (sky -> vis) or "v2s" (vis -> sky)
+    data: np.ndarray      # sky (float64) or visibilities (complex128)
+
+
+def config5_requests(n_requests: int = 2000, rate_hz: float = 50.0, n_min: float = 1e4, n_max: float = 1e7,
+                     eps_choices=(1e-4, 1e-6, 1e-9), seed_offset: int = 0):
+    """Served mixed stream: Poisson arrivals; per request log-uniform pixel and baseline
+    counts in [n_min, n_max], a HEALPix cap (<= 40 deg) and the config-2 or config-3
+    layout (p = 1/2), eps uniform over eps_choices, direction S or A (p = 1/2).
+    Seeds: master + 5000 + request id."""
+    out = []
+    t = 0.0
+    arr = rng_for(5, 9 + seed_offset)
+    for rid in range(n_requests):
+        t += arr.exponential(1.0 / rate_hz)
+        rng = np.random.Generator(np.random.PCG64(MASTER_SEED + 5000 + 100003 * seed_offset + rid))
+        n_pix = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        n_vis = int(round(math.exp(rng.uniform(math.log(n_min), math.log(n_max)))))
+        layout = 2 if rng.uniform() < 0.5 else 3
+        eps = float(eps_choices[int(rng.integers(len(eps_choices)))])
+        direction = "s2v" if rng.uniform() < 0.5 else "v2s"
+        pix = _cap_for(n_pix)
+        uvw = _baselines_for(n_vis, layout)
+        if direction == "s2v":
+            data = rng.lognormal(0.0, 1.0, n_pix)
+        else:
+            data = (rng.normal(0.0, math.sqrt(0.5), n_vis) + 1j * rng.normal(0.0, math.sqrt(0.5), n_vis))
+        out.append(Request(rid, t, pix, uvw, eps, direction, data))
+    return out

@@ -112,7 +112,7 @@ typedef struct {
     double max_grid_bytes;       /* largest sub-problem grid (spread + FFT grids) */
     double workspace_bytes;      /* plan-owned device memory */
     double plan_seconds;         /* wall time of hvox_plan */
-    double model_seconds;        /* cost-model estimate of one transform */
+    double model_seconds;        /* cost-model estimate of one sky->vis plus one vis->sky */
 } hvox_info;
 
 /*

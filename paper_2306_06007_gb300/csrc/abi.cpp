@@ -5,6 +5,7 @@
 #include <cufft.h>
 
 #include <chrono>
+#include <cstdlib>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -112,8 +113,8 @@ void upload(DevBuf &b, const void *host, size_t bytes, cudaStream_t s) {
     if (bytes) check_cuda(cudaMemcpyAsync(b.ptr, host, bytes, cudaMemcpyHostToDevice, s), "upload");
 }
 
-void build_items(const std::vector<DirectRect> &rects, bool owner_is_vis, std::vector<WorkItem> &items) {
-    const int64_t T = direct_tile();
+void build_items(const std::vector<DirectRect> &rects, bool owner_is_vis, int vpt, std::vector<WorkItem> &items) {
+    const int64_t T = direct_tile(vpt);
     double work = 0;
     for (auto &r : rects) work += (double)(r.p1 - r.p0) * (double)(r.v1 - r.v0);
     const double target_items = 152.0 * 16.0;
@@ -189,19 +190,19 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     // Direct work lists.
     {
         std::vector<WorkItem> a, b;
-        build_items(part.rects, true, a);
-        build_items(part.rects, false, b);
+        build_items(part.rects, true, p.direct_vpt, a);
+        build_items(part.rects, false, p.direct_vpt, b);
         upload(p.items_s2v, a.data(), a.size() * sizeof(WorkItem), s);
         upload(p.items_v2s, b.data(), b.size() * sizeof(WorkItem), s);
         p.n_items_s2v = (int64_t)a.size();
         p.n_items_v2s = (int64_t)b.size();
     }
 
-    // exp(j 2 pi m / 256), m = -128 .. 128, split into float pairs.
+    // exp(j 2 pi m / 256), m = -512 .. 512, split into float pairs (double-float direct path).
     {
-        std::vector<float> tab(257 * 4);
-        for (int i = 0; i < 257; ++i) {
-            double ang = 2.0 * M_PI * (double)(i - 128) / 256.0;
+        std::vector<float> tab(1025 * 4);
+        for (int i = 0; i < 1025; ++i) {
+            double ang = 2.0 * M_PI * (double)(i - 512) / 256.0;
             double c = std::cos(ang), sn = std::sin(ang);
             float ch = (float)c, sh = (float)sn;
             tab[4 * i + 0] = ch;
@@ -214,14 +215,10 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
 
     // NUFFT sub-problems.
     const size_t re = p.prec == 1 ? 4 : 8;
-    int64_t psi_total = 0, prec_total = 0, vrec_total = 0, max_m1 = 0, max_m2 = 0;
+    int64_t psi_total = 0, max_m1 = 0, max_m2 = 0;
     for (auto &b : part.blocks) {
         b.psi_off = psi_total;
-        b.prec_off = prec_total;
-        b.vrec_off = vrec_total;
         psi_total += b.n1[0] + b.n1[1] + b.n1[2];
-        prec_total += b.p1 - b.p0;
-        vrec_total += b.v1 - b.v0;
         max_m1 = std::max<int64_t>(max_m1, b.n1[0] * b.n1[1] * b.n1[2]);
         max_m2 = std::max<int64_t>(max_m2, b.n2[0] * b.n2[1] * b.n2[2]);
     }
@@ -235,43 +232,20 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                 es_ft(p.es, xi.data(), b.n1[d], ft.data());
                 for (int64_t l = 0; l < b.n1[d]; ++l) ipsi[b.psi_off + off + l] = 1.0 / ft[l];
             }
+        // 1 / Phi(tau) for |tau| <= pi / sigma as a Chebyshev series in u = 2 (tau/tau_max)^2 - 1.
+        const double tmax = M_PI / p.sigma * 1.001;
+        std::vector<double> cheb;
+        fit_inv_phi(p.es, tmax, p.prec == 1 ? 1e-9 : 1e-13, cheb);
+        p.cheb_deg = (int)cheb.size() - 1;
+        p.cheb_inv_tmax2 = 1.0 / (tmax * tmax);
         if (p.prec == 1) {
-            std::vector<float> f(ipsi.begin(), ipsi.end());
+            std::vector<float> f(ipsi.begin(), ipsi.end()), c(cheb.begin(), cheb.end());
             upload(p.inv_psi, f.data(), f.size() * 4, s);
+            upload(p.cheb, c.data(), c.size() * 4, s);
         } else {
             upload(p.inv_psi, ipsi.data(), ipsi.size() * 8, s);
+            upload(p.cheb, cheb.data(), cheb.size() * 8, s);
         }
-        // Quadrature for Phi at the baselines.
-        std::vector<double> qz, qf;
-        es_ft_nodes(p.es, qz, qf);
-        const int nq = (int)qz.size();
-        DevBuf dqz, dqf;
-        upload(dqz, qz.data(), nq * 8, s);
-        upload(dqf, qf.data(), nq * 8, s);
-        p.err_word.alloc(sizeof(int));
-        check_cuda(cudaMemsetAsync(p.err_word.ptr, 0, sizeof(int), s), "memset err");
-        const size_t rec_bytes = p.prec == 1 ? sizeof(GridRec<float>) : sizeof(GridRec<double>);
-        p.pix_rec.alloc((size_t)prec_total * rec_bytes);
-        p.vis_rec.alloc((size_t)vrec_total * rec_bytes);
-        p.pix_phase.alloc((size_t)prec_total * 2 * re);
-        p.vis_phase.alloc((size_t)vrec_total * 2 * re);
-        for (auto &b : part.blocks) {
-            if (p.prec == 1)
-                nufft_tables<float>(b, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(), p.n_vis, p.es.w,
-                                    p.isign, dqz.as<double>(), dqf.as<double>(), nq, p.pix_rec.as<GridRec<float>>(),
-                                    p.pix_phase.as<float2>(), p.vis_rec.as<GridRec<float>>(),
-                                    p.vis_phase.as<float2>(), p.err_word.as<int>(), s);
-            else
-                nufft_tables<double>(b, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(), p.n_vis, p.es.w,
-                                     p.isign, dqz.as<double>(), dqf.as<double>(), nq,
-                                     p.pix_rec.as<GridRec<double>>(), p.pix_phase.as<double2>(),
-                                     p.vis_rec.as<GridRec<double>>(), p.vis_phase.as<double2>(),
-                                     p.err_word.as<int>(), s);
-        }
-        check_cuda(cudaStreamSynchronize(s), "nufft tables");
-        int err = 0;
-        check_cuda(cudaMemcpy(&err, p.err_word.ptr, sizeof(int), cudaMemcpyDeviceToHost), "read err word");
-        if (err) fail(HVOX_EINTERNAL, "hvox_plan: a spread window left its grid (coordinate rounding)");
         p.grid1.alloc((size_t)max_m1 * 2 * re);
         p.grid2.alloc((size_t)max_m2 * 2 * re);
         // FFT plans per grid shape, one shared work area.
@@ -290,8 +264,13 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         }
         p.fft_work.alloc(std::max<size_t>(max_ws, 256));
         for (auto &kv : p.fft_plans) check_cufft(cufftSetWorkArea(kv.second, p.fft_work.ptr), "cufftSetWorkArea");
+        auto split = [](double x, float &h, float &l) {
+            h = (float)x;
+            l = (float)(x - (double)h);
+        };
         for (auto &b : part.blocks) {
-            DevBlock d;
+            NufftDev d;
+            std::memset(&d, 0, sizeof(d));
             d.p0 = b.p0;
             d.np = b.p1 - b.p0;
             d.v0 = b.v0;
@@ -299,10 +278,18 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             for (int k = 0; k < 3; ++k) {
                 d.n1[k] = (int32_t)b.n1[k];
                 d.n2[k] = (int32_t)b.n2[k];
+                d.C[k] = b.C[k];
+                d.D[k] = b.D[k];
+                d.a[k] = b.a[k];
+                d.n2a[k] = b.a[k] > 0 ? (double)b.n2[k] / b.a[k] : 0.0;
+                d.tpa64[k] = b.a[k] > 0 ? 2.0 * M_PI / b.a[k] : 0.0;
+                split(b.C[k], d.Ch[k], d.Cl[k]);
+                split(b.D[k], d.Dh[k], d.Dl[k]);
+                split(b.a[k], d.ah[k], d.al[k]);
+                split(d.n2a[k], d.n2ah[k], d.n2al[k]);
+                d.tpa[k] = (float)d.tpa64[k];
             }
             d.psi_off = b.psi_off;
-            d.prec_off = b.prec_off;
-            d.vrec_off = b.vrec_off;
             p.dblocks.push_back(d);
             p.block_fft.push_back(p.fft_plans[std::make_tuple(b.n2[0], b.n2[1], b.n2[2])]);
         }
@@ -316,8 +303,8 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
 
     double ws = 0;
     for (DevBuf *b : {&p.pix_perm, &p.vis_perm, &p.weight, &p.pix_xyz, &p.vis_xyz, &p.pix_hi, &p.pix_lo, &p.vis_hi,
-                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.inv_psi, &p.pix_rec, &p.vis_rec, &p.pix_phase,
-                      &p.vis_phase, &p.grid1, &p.grid2, &p.fft_work, &p.src, &p.acc, &p.cis_tab, &p.err_word})
+                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.inv_psi, &p.cheb, &p.grid1, &p.grid2, &p.fft_work,
+                      &p.src, &p.acc, &p.cis_tab, &p.err_word})
         ws += (double)b->bytes;
     p.workspace_bytes = ws;
     p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -352,6 +339,8 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     double e = eps > 0 ? eps : 1e-6;
     if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
     p.es = es_params(e * kEpsMargin, p.sigma);
+    // Points per thread of the direct kernels (tuning knob; 2 or 4).
+    if (const char *v = std::getenv("HVOX_DIRECT_VPT")) p.direct_vpt = std::atoi(v) == 4 ? 4 : 2;
 }
 
 void fill_info(const Plan &p, hvox_info *info) {

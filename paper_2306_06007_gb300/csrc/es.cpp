@@ -81,4 +81,48 @@ void es_ft(const ESKernel &k, const double *xi, int64_t n, double *out) {
     }
 }
 
+// Chebyshev interpolant of 1/Phi(tau) on [0, tau_max] in u = 2 (tau/tau_max)^2 - 1, of the
+// smallest even degree (8 .. 32) whose relative error on a fine check grid is <= tol.
+void fit_inv_phi(const ESKernel &k, double tau_max, double tol, std::vector<double> &coef) {
+    const int n_check = 2001;
+    std::vector<double> tc(n_check), fc(n_check);
+    for (int i = 0; i < n_check; ++i) tc[i] = tau_max * (double)i / (n_check - 1);
+    es_ft(k, tc.data(), n_check, fc.data());
+    std::vector<double> best;
+    double best_err = INFINITY;
+    for (int deg = 8; deg <= 32; deg += 2) {
+        const int n = deg + 1;
+        std::vector<double> tau(n), f(n), c(n, 0.0);
+        for (int j = 0; j < n; ++j) {
+            double u = std::cos(M_PI * (j + 0.5) / n);
+            tau[j] = tau_max * std::sqrt(0.5 * (u + 1.0));
+        }
+        es_ft(k, tau.data(), n, f.data());
+        for (int m = 0; m < n; ++m) {
+            double sum = 0.0;
+            for (int j = 0; j < n; ++j) sum += (1.0 / f[j]) * std::cos(m * M_PI * (j + 0.5) / n);
+            c[m] = 2.0 * sum / n;
+        }
+        c[0] *= 0.5;
+        double err = 0.0;
+        for (int i = 0; i < n_check; ++i) {
+            double u = 2.0 * (tc[i] / tau_max) * (tc[i] / tau_max) - 1.0;
+            double b1 = 0, b2 = 0;
+            for (int m = deg; m >= 1; --m) {
+                double b0 = c[m] + 2.0 * u * b1 - b2;
+                b2 = b1;
+                b1 = b0;
+            }
+            double v = c[0] + u * b1 - b2;
+            err = std::max(err, std::fabs(v * fc[i] - 1.0));
+        }
+        if (err < best_err) {
+            best_err = err;
+            best = c;
+        }
+        if (err <= tol) break;
+    }
+    coef = best;
+}
+
 }  // namespace hvox

@@ -45,6 +45,28 @@ struct Profiler final : StageHook {
     }
 };
 
+template <typename T> NufftArgs<T> nufft_args(const Plan &p) {
+    NufftArgs<T> a;
+    a.w = p.es.w;
+    a.beta = p.es.beta;
+    a.isign = p.isign;
+    a.G1 = p.grid1.as<typename CplxOf<T>::type>();
+    a.G2 = p.grid2.as<typename CplxOf<T>::type>();
+    a.ipsi = p.inv_psi.as<T>();
+    a.pix_hi = p.pix_hi.as<float4>();
+    a.pix_lo = p.pix_lo.as<float4>();
+    a.vis_hi = p.vis_hi.as<float4>();
+    a.vis_lo = p.vis_lo.as<float4>();
+    a.pix_soa = p.pix_xyz.as<double>();
+    a.vis_soa = p.vis_xyz.as<double>();
+    a.n_pix = p.n_pix;
+    a.n_vis = p.n_vis;
+    a.cheb = p.cheb.as<T>();
+    a.deg = p.cheb_deg;
+    a.inv_tmax2 = p.cheb_inv_tmax2;
+    return a;
+}
+
 }  // namespace
 
 void collect_stats(Plan &p) {
@@ -78,32 +100,31 @@ void run_synthesize(Plan &p, const void *I, void *V) {
             const WorkItem *it = p.items_s2v.as<WorkItem>();
             if (p.plain)
                 launch_direct_s2v_f64(it, p.n_items_s2v, p.vis_xyz.as<double>(), p.n_vis, p.pix_xyz.as<double>(),
-                                      p.n_pix, p.src.as<double>(), p.acc.as<double2>(), p.isign, s);
+                                      p.n_pix, p.src.as<double>(), p.acc.as<double2>(), p.isign, p.direct_vpt, s);
             else if (p.prec == 1)
                 launch_direct_s2v_f32(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
                                       p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<float>(),
-                                      p.acc.as<float2>(), p.isign, s);
+                                      p.acc.as<float2>(), p.isign, p.direct_vpt, s);
             else
                 launch_direct_s2v_df(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
                                      p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<double>(),
-                                     p.acc.as<double2>(), p.cis_tab.as<float4>(), p.isign, s);
+                                     p.acc.as<double2>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
             prof.end(HVOX_STAGE_DIRECT, 1);
         }
-        for (size_t b = 0; b < p.dblocks.size(); ++b) {
-            const DevBlock &db = p.dblocks[b];
-            cufftHandle fh = p.block_fft[b];
-            if (p.prec == 1)
-                nufft_block_s2v<float>(db, p.es.w, p.es.beta, p.src.as<float>(), p.pix_rec.as<GridRec<float>>(),
-                                       p.pix_phase.as<float2>(), p.vis_rec.as<GridRec<float>>(),
-                                       p.vis_phase.as<float2>(), p.inv_psi.as<float>() + db.psi_off,
-                                       p.grid1.as<float2>(), p.grid2.as<float2>(), fh, p.isign, p.acc.as<float2>(), s,
-                                       prof);
-            else
-                nufft_block_s2v<double>(db, p.es.w, p.es.beta, p.src.as<double>(), p.pix_rec.as<GridRec<double>>(),
-                                        p.pix_phase.as<double2>(), p.vis_rec.as<GridRec<double>>(),
-                                        p.vis_phase.as<double2>(), p.inv_psi.as<double>() + db.psi_off,
-                                        p.grid1.as<double2>(), p.grid2.as<double2>(), fh, p.isign,
-                                        p.acc.as<double2>(), s, prof);
+        if (!p.dblocks.empty()) {
+            if (p.prec == 1) {
+                NufftArgs<float> a = nufft_args<float>(p);
+                for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                    a.fft = p.block_fft[b];
+                    nufft_block_s2v<float>(p.dblocks[b], a, p.src.as<float>(), p.acc.as<float2>(), s, prof);
+                }
+            } else {
+                NufftArgs<double> a = nufft_args<double>(p);
+                for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                    a.fft = p.block_fft[b];
+                    nufft_block_s2v<double>(p.dblocks[b], a, p.src.as<double>(), p.acc.as<double2>(), s, prof);
+                }
+            }
         }
         prof.begin(HVOX_STAGE_PERMUTE);
         launch_s2v_out(p.prec, p.acc.ptr, p.vis_perm.as<int32_t>(), p.n_vis, Vt, s);
@@ -130,32 +151,31 @@ void run_analyze(Plan &p, const void *V, void *I) {
             const WorkItem *it = p.items_v2s.as<WorkItem>();
             if (p.plain)
                 launch_direct_v2s_f64(it, p.n_items_v2s, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(),
-                                      p.n_vis, p.src.as<double2>(), p.acc.as<double>(), p.isign, s);
+                                      p.n_vis, p.src.as<double2>(), p.acc.as<double>(), p.isign, p.direct_vpt, s);
             else if (p.prec == 1)
                 launch_direct_v2s_f32(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
                                       p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<float2>(),
-                                      p.acc.as<float>(), p.isign, s);
+                                      p.acc.as<float>(), p.isign, p.direct_vpt, s);
             else
                 launch_direct_v2s_df(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
                                      p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<double2>(),
-                                     p.acc.as<double>(), p.cis_tab.as<float4>(), p.isign, s);
+                                     p.acc.as<double>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
             prof.end(HVOX_STAGE_DIRECT, 1);
         }
-        for (size_t b = 0; b < p.dblocks.size(); ++b) {
-            const DevBlock &db = p.dblocks[b];
-            cufftHandle fh = p.block_fft[b];
-            if (p.prec == 1)
-                nufft_block_v2s<float>(db, p.es.w, p.es.beta, p.src.as<float2>(), p.pix_rec.as<GridRec<float>>(),
-                                       p.pix_phase.as<float2>(), p.vis_rec.as<GridRec<float>>(),
-                                       p.vis_phase.as<float2>(), p.inv_psi.as<float>() + db.psi_off,
-                                       p.grid1.as<float2>(), p.grid2.as<float2>(), fh, p.isign, p.acc.as<float>(), s,
-                                       prof);
-            else
-                nufft_block_v2s<double>(db, p.es.w, p.es.beta, p.src.as<double2>(),
-                                        p.pix_rec.as<GridRec<double>>(), p.pix_phase.as<double2>(),
-                                        p.vis_rec.as<GridRec<double>>(), p.vis_phase.as<double2>(),
-                                        p.inv_psi.as<double>() + db.psi_off, p.grid1.as<double2>(),
-                                        p.grid2.as<double2>(), fh, p.isign, p.acc.as<double>(), s, prof);
+        if (!p.dblocks.empty()) {
+            if (p.prec == 1) {
+                NufftArgs<float> a = nufft_args<float>(p);
+                for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                    a.fft = p.block_fft[b];
+                    nufft_block_v2s<float>(p.dblocks[b], a, p.src.as<float2>(), p.acc.as<float>(), s, prof);
+                }
+            } else {
+                NufftArgs<double> a = nufft_args<double>(p);
+                for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                    a.fft = p.block_fft[b];
+                    nufft_block_v2s<double>(p.dblocks[b], a, p.src.as<double2>(), p.acc.as<double>(), s, prof);
+                }
+            }
         }
         prof.begin(HVOX_STAGE_PERMUTE);
         launch_v2s_out(p.prec, p.acc.ptr, p.pix_perm.as<int32_t>(), weight_ptr(p), p.n_pix, It, s);

@@ -43,6 +43,7 @@ void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &wt);
 void es_ft(const ESKernel &k, const double *xi, int64_t n, double *out);
 int es_quad_nodes(const ESKernel &k);
 void es_ft_nodes(const ESKernel &k, std::vector<double> &z, std::vector<double> &f);
+void fit_inv_phi(const ESKernel &k, double tau_max, double tol, std::vector<double> &coef);
 
 // ------------------------------------------------------------------ planning
 
@@ -81,11 +82,14 @@ struct WorkItem {
 };
 
 struct CostModel {
-    double direct_pair = 0;   // seconds per (pixel, baseline) pair
-    double spread_tap = 0;    // seconds per (point, tap) of spread or interpolation
-    double fft_cell = 0;      // seconds per FFT-grid cell per log2(cells)
-    double grid_cell = 0;     // seconds per grid cell of pad/crop/zero passes
-    double block_fixed = 0;   // seconds of fixed overhead per NUFFT block (launches)
+    double direct_pair = 0;      // seconds per (pixel, baseline) pair, one direction
+    double scatter_smem = 0;     // seconds per tap of spreading through a shared-memory tile
+    double scatter_global = 0;   // seconds per tap of spreading straight into the grid
+    double gather_tap = 0;       // seconds per tap of interpolation
+    double fft_cell = 0;         // seconds per FFT-grid cell per log2(cells)
+    double grid_cell = 0;        // seconds per grid cell of pad/crop/zero passes
+    double block_fixed = 0;      // seconds of fixed overhead per NUFFT block and direction
+    double tile_cells = 0;       // shared-memory tile capacity of the spreading kernels
 };
 
 CostModel default_cost_model(int prec, bool plain, int w);
@@ -133,19 +137,36 @@ struct DevBuf {
     template <typename T> T *as() const { return reinterpret_cast<T *>(ptr); }
 };
 
-// Device-side description of a NUFFT block (mirrors NufftBlock, POD for kernels).
-struct DevBlock {
+// Device-side description of a NUFFT block: FP64 geometry and its float hi/lo splits
+// (passed by value to the kernels).
+struct NufftDev {
     int64_t p0, np, v0, nv;
     int32_t n1[3], n2[3];
-    int64_t psi_off, prec_off, vrec_off;
+    double C[3], D[3], a[3];
+    double n2a[3];    // n2 / a (0 when a = 0)
+    double tpa64[3];  // 2 pi / a (0 when a = 0)
+    float Ch[3], Cl[3], Dh[3], Dl[3], ah[3], al[3], n2ah[3], n2al[3], tpa[3];
+    int64_t psi_off;
 };
 
-// Per-(point, block) grid record: window start (integer cell) and offset in the cell.
-template <typename T> struct alignas(16) GridRec {
-    int32_t i0[3];
-    int32_t pad;
-    T fr[3];
-    T pad2;
+template <typename T> struct CplxOf;
+template <> struct CplxOf<float> { using type = float2; };
+template <> struct CplxOf<double> { using type = double2; };
+
+// Plan-wide arguments of the NUFFT launchers.
+template <typename T> struct NufftArgs {
+    int w = 0;
+    double beta = 0.0;
+    int isign = -1;
+    typename CplxOf<T>::type *G1 = nullptr, *G2 = nullptr;
+    const T *ipsi = nullptr;
+    cufftHandle fft = 0;
+    const float4 *pix_hi = nullptr, *pix_lo = nullptr, *vis_hi = nullptr, *vis_lo = nullptr;
+    const double *pix_soa = nullptr, *vis_soa = nullptr;
+    int64_t n_pix = 0, n_vis = 0;
+    const T *cheb = nullptr;   // Chebyshev coefficients of 1/Phi in u = 2 (tau/tau_max)^2 - 1
+    int deg = 0;
+    double inv_tmax2 = 0.0;    // 1 / tau_max^2
 };
 
 // Stage boundaries reported by the kernel launchers to the executor's profiler.
@@ -176,6 +197,7 @@ struct Plan {
     int mode = 0;
     bool plain = false;
     int ntrans = 1;
+    int direct_vpt = 2;            // points per thread of the direct kernels (owner tile 256 * vpt)
     double sigma = 2.0;
     double budget_opt = 0.0;       // chunk_budget_bytes option (0 -> cost-model search)
     double direct_threshold = 0.0; // direct_threshold option
@@ -197,16 +219,15 @@ struct Plan {
     DevBuf items_s2v, items_v2s;
     int64_t n_items_s2v = 0, n_items_v2s = 0;
 
-    // NUFFT tables
-    DevBuf blocks_dev;                  // DevBlock[]
-    DevBuf inv_psi;                     // T per (block, dim, l)
-    DevBuf pix_rec, vis_rec;            // GridRec<T>
-    DevBuf pix_phase, vis_phase;        // complex<T>: prephase (pixels), postphase/phihat (baselines)
-    int64_t n_pix_rec = 0, n_vis_rec = 0;
+    // NUFFT sub-problems
+    DevBuf inv_psi;                     // T per (block, dim, l): 1 / Psi on the n1 band
+    DevBuf cheb;                        // T: Chebyshev coefficients of 1/Phi
+    int cheb_deg = 0;
+    double cheb_inv_tmax2 = 0.0;
     DevBuf grid1, grid2;                // largest spread grid and FFT grid
     std::map<std::tuple<int64_t, int64_t, int64_t>, cufftHandle> fft_plans;
     DevBuf fft_work;
-    std::vector<DevBlock> dblocks;      // host copy of the block descriptors (launch order)
+    std::vector<NufftDev> dblocks;      // block descriptors (launch order)
     std::vector<cufftHandle> block_fft; // FFT plan of each block
     DevBuf cis_tab;                     // exp(j 2 pi m / 256) as float pairs (double-float path)
 
@@ -229,42 +250,29 @@ void launch_gather_weight(const double *w_orig_dev, const int32_t *perm, int64_t
                           cudaStream_t s);
 
 // Direct kernels (k_direct.cu). Owner tile = direct_tile() points per work item.
-int direct_tile();
+int direct_tile(int vpt);
 void launch_direct_s2v_f32(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
-                           const float4 *rl, const float *c, float2 *acc, int isign, cudaStream_t s);
+                           const float4 *rl, const float *c, float2 *acc, int isign, int vpt, cudaStream_t s);
 void launch_direct_s2v_df(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
                           const float4 *rl, const double *c, double2 *acc, const float4 *tab, int isign,
-                          cudaStream_t s);
+                          int vpt, cudaStream_t s);
 void launch_direct_s2v_f64(const WorkItem *items, int64_t n, const double *vxyz, int64_t nv, const double *pxyz,
-                           int64_t np, const double *c, double2 *acc, int isign, cudaStream_t s);
+                           int64_t np, const double *c, double2 *acc, int isign, int vpt, cudaStream_t s);
 void launch_direct_v2s_f32(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
-                           const float4 *vl, const float2 *V, float *acc, int isign, cudaStream_t s);
+                           const float4 *vl, const float2 *V, float *acc, int isign, int vpt, cudaStream_t s);
 void launch_direct_v2s_df(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
                           const float4 *vl, const double2 *V, double *acc, const float4 *tab, int isign,
-                          cudaStream_t s);
+                          int vpt, cudaStream_t s);
 void launch_direct_v2s_f64(const WorkItem *items, int64_t n, const double *pxyz, int64_t np, const double *vxyz,
-                           int64_t nv, const double2 *V, double *acc, int isign, cudaStream_t s);
+                           int64_t nv, const double2 *V, double *acc, int isign, int vpt, cudaStream_t s);
 
 // NUFFT sub-problems (k_nufft.cu).
-template <typename T> struct CplxOf;
-template <> struct CplxOf<float> { using type = float2; };
-template <> struct CplxOf<double> { using type = double2; };
-
 template <typename T>
-void nufft_block_s2v(const DevBlock &b, int w, double beta, const T *c, const GridRec<T> *prec,
-                     const typename CplxOf<T>::type *pph, const GridRec<T> *vrec, const typename CplxOf<T>::type *vq,
-                     const T *ipsi, typename CplxOf<T>::type *G1, typename CplxOf<T>::type *G2, cufftHandle plan,
-                     int isign, typename CplxOf<T>::type *acc, cudaStream_t s, StageHook &hook);
+void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, typename CplxOf<T>::type *acc,
+                     cudaStream_t s, StageHook &hook);
 template <typename T>
-void nufft_block_v2s(const DevBlock &b, int w, double beta, const typename CplxOf<T>::type *V, const GridRec<T> *prec,
-                     const typename CplxOf<T>::type *pph, const GridRec<T> *vrec, const typename CplxOf<T>::type *vq,
-                     const T *ipsi, typename CplxOf<T>::type *G1, typename CplxOf<T>::type *G2, cufftHandle plan,
-                     int isign, T *acc, cudaStream_t s, StageHook &hook);
-template <typename T>
-void nufft_tables(const NufftBlock &b, const double *pix_soa, int64_t n_pix, const double *vis_soa, int64_t n_vis,
-                  int w, int isign, const double *qz, const double *qf, int nq, GridRec<T> *prec,
-                  typename CplxOf<T>::type *pph, GridRec<T> *vrec, typename CplxOf<T>::type *vq, int *err,
-                  cudaStream_t s);
+void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const typename CplxOf<T>::type *V, T *acc,
+                     cudaStream_t s, StageHook &hook);
 
 // Permutations between the caller's order and chunk order (k_misc.cu).
 void launch_s2v_in(int prec, const void *I, const int32_t *perm, const double *w, int64_t n, void *src, cudaStream_t s);

@@ -70,24 +70,36 @@ __device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
     e = __fmaf_rn(a, b, -p);
 }
 
+// Round to nearest integer on the FMA pipe: adding and subtracting 1.5 * 2^23 leaves the
+// integer part for |x| < 2^22 (rintf would use the XU pipe, which the sin/cos need).
+constexpr float kRoundMagic = 12582912.0f;
+
+__device__ __forceinline__ float round_fma(float x) { return __fsub_rn(__fadd_rn(x, kRoundMagic), kRoundMagic); }
+
+// x - nearest integer, exact (the difference of a float and its rounding is exact).
+__device__ __forceinline__ float frac_fma(float x) { return __fsub_rn(x, round_fma(x)); }
+
 // Fraction of <p, r> in turns, FP32 (|error| ~ 1e-7 turn), result in [-0.5, 0.5].
+// Valid for |p_d r_d| < 2^22 turns per dimension.
 __device__ __forceinline__ float phase_f32(const float3 &ph, const float3 &pl, const float4 &rh, const float4 &rl) {
     float a0, b0, a1, b1, a2, b2;
     two_prod(ph.x, rh.x, a0, b0);
     two_prod(ph.y, rh.y, a1, b1);
     two_prod(ph.z, rh.z, a2, b2);
-    a0 = __fsub_rn(a0, rintf(a0));
-    a1 = __fsub_rn(a1, rintf(a1));
-    a2 = __fsub_rn(a2, rintf(a2));
-    float cross = __fmaf_rn(ph.x, rl.x, __fmul_rn(pl.x, rh.x));
-    cross = __fmaf_rn(ph.y, rl.y, __fmaf_rn(pl.y, rh.y, cross));
-    cross = __fmaf_rn(ph.z, rl.z, __fmaf_rn(pl.z, rh.z, cross));
-    float small = __fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, cross));
+    a0 = frac_fma(a0);
+    a1 = frac_fma(a1);
+    a2 = frac_fma(a2);
+    float small = __fadd_rn(__fadd_rn(b0, b1), b2);
+    small = __fmaf_rn(ph.x, rl.x, __fmaf_rn(pl.x, rh.x, small));
+    small = __fmaf_rn(ph.y, rl.y, __fmaf_rn(pl.y, rh.y, small));
+    small = __fmaf_rn(ph.z, rl.z, __fmaf_rn(pl.z, rh.z, small));
     float f = __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, small));
-    return __fsub_rn(f, rintf(f));
+    return frac_fma(f);
 }
 
-// Fraction of <p, r> in turns as a float pair (fh + fl), |error| ~ 1e-12 turn * |p|/1e5.
+// Fraction of <p, r> in turns as an unevaluated float pair fh + fl with |fh| < 2
+// (integer turns dropped exactly per dimension; the sum of the three fractions is kept
+// exact with TwoSum), |error| ~ 1e-12 turn * |p| / 1e5.
 __device__ __forceinline__ void phase_df(const float3 &ph, const float3 &pl, const float4 &rh, const float4 &rl,
                                          float &fh, float &fl) {
     float a0, b0, a1, b1, a2, b2;
@@ -100,50 +112,47 @@ __device__ __forceinline__ void phase_df(const float3 &ph, const float3 &pl, con
     float s1, e1, s2, e2;
     two_sum(a0, a1, s1, e1);
     two_sum(s1, a2, s2, e2);
-    s2 = __fsub_rn(s2, rintf(s2));
-    float cross = __fmaf_rn(ph.x, rl.x, __fmul_rn(pl.x, rh.x));
-    cross = __fmaf_rn(ph.y, rl.y, __fmaf_rn(pl.y, rh.y, cross));
-    cross = __fmaf_rn(ph.z, rl.z, __fmaf_rn(pl.z, rh.z, cross));
-    float small = __fadd_rn(__fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, e1)), __fadd_rn(e2, cross));
+    float small = __fadd_rn(__fadd_rn(b0, b1), __fadd_rn(b2, __fadd_rn(e1, e2)));
+    small = __fmaf_rn(ph.x, rl.x, __fmaf_rn(pl.x, rh.x, small));
+    small = __fmaf_rn(ph.y, rl.y, __fmaf_rn(pl.y, rh.y, small));
+    small = __fmaf_rn(ph.z, rl.z, __fmaf_rn(pl.z, rh.z, small));
     fast_two_sum(s2, small, fh, fl);
-    fh = __fsub_rn(fh, rintf(fh));  // exact; fh in [-0.5, 0.5] for the table lookup
 }
 
 constexpr int kTab = 256;      // table entries per turn
-constexpr int kTabOff = 128;   // index offset: m = rint(256 f) in [-128, 128] for |f| <= 0.5
-constexpr int kTabLen = 257;
+constexpr int kTabOff = 512;   // m = round(256 f) in [-512, 512] for |f| < 2
+constexpr int kTabLen = 1025;
 
-// exp(j 2 pi f) for f = fh + fl (turns), as float pairs (re_h, re_l, im_h, im_l).
-// T holds (cos_h, cos_l, sin_h, sin_l) of 2 pi m / 256 for m = idx - kTabOff.
+// exp(j 2 pi f) for f = fh + fl (turns, |fh| < 2) as two unevaluated float pairs
+// (re = reh + rel, im = imh + iml, |rel|, |iml| < 1e-4). T holds (cos_h, cos_l, sin_h,
+// sin_l) of 2 pi m / 256 for m = idx - kTabOff; the remainder x = 2 pi (f - m/256),
+// |x| <= pi/256, goes through short Taylor series.
 __device__ __forceinline__ void cis_df(float fh, float fl, const float4 *__restrict__ T, float &reh, float &rel,
                                        float &imh, float &iml) {
     const float TWO_PI_H = 6.28318548202514648f;        // fl32(2 pi)
     const float TWO_PI_L = -1.74845553146951427e-07f;   // fl32(2 pi - TWO_PI_H)
-    float m = rintf(__fmul_rn(fh, (float)kTab));
-    float d = __fmaf_rn(m, -1.0f / kTab, fh);            // exact
+    const float t = __fadd_rn(__fmul_rn(fh, (float)kTab), kRoundMagic);  // m in the low mantissa bits
+    const int m = min(max(__float_as_int(t) - __float_as_int(kRoundMagic), -kTabOff), kTabOff);
+    const float mf = __fsub_rn(t, kRoundMagic);
+    const float d = __fmaf_rn(mf, -1.0f / kTab, fh);     // exact
     float xh, xe;
     two_prod(d, TWO_PI_H, xh, xe);
-    float xl = __fadd_rn(xe, __fmaf_rn(d, TWO_PI_L, __fmul_rn(fl, TWO_PI_H)));
-    float x2 = __fmul_rn(xh, xh);
-    // sin x = x - x^3/6 + x^5/120 (|x| <= 0.013: truncation < 1e-15)
-    float sc = __fmul_rn(__fmul_rn(xh, x2), __fmaf_rn(x2, 1.0f / 120.0f, -1.0f / 6.0f));
-    // cos x - 1 = -x^2/2 + x^4/24 - x^6/720
-    float cm = __fmul_rn(x2, __fmaf_rn(x2, __fmaf_rn(x2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f));
-    float4 t = T[(int)m + kTabOff];
-    float u = __fadd_rn(xl, sc);  // sin x = xh + u
+    const float xl = __fadd_rn(xe, __fmaf_rn(d, TWO_PI_L, __fmul_rn(fl, TWO_PI_H)));
+    const float x2 = __fmul_rn(xh, xh);
+    // sin x = x - x^3/6 + x^5/120, cos x - 1 = -x^2/2 + x^4/24 - x^6/720 (|x| <= 0.0123)
+    const float sc = __fmul_rn(__fmul_rn(xh, x2), __fmaf_rn(x2, 1.0f / 120.0f, -1.0f / 6.0f));
+    const float cm = __fmul_rn(x2, __fmaf_rn(x2, __fmaf_rn(x2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f));
+    const float4 tb = T[m + kTabOff];
+    const float u = __fadd_rn(xl, sc);  // sin x = xh + u
     float p1, p1e, p2, p2e;
-    two_prod(t.z, xh, p1, p1e);   // sin_h * xh
-    two_prod(t.x, xh, p2, p2e);   // cos_h * xh
-    float rs, re;
-    two_sum(t.x, -p1, rs, re);
-    float rlo = __fadd_rn(__fadd_rn(re, __fmaf_rn(t.x, cm, t.y)),
-                          -__fadd_rn(p1e, __fmaf_rn(t.z, u, __fmul_rn(t.w, xh))));
-    float is, ie;
-    two_sum(t.z, p2, is, ie);
-    float ilo = __fadd_rn(__fadd_rn(ie, __fmaf_rn(t.z, cm, t.w)),
-                          __fadd_rn(p2e, __fmaf_rn(t.x, u, __fmul_rn(t.y, xh))));
-    fast_two_sum(rs, rlo, reh, rel);
-    fast_two_sum(is, ilo, imh, iml);
+    two_prod(tb.z, xh, p1, p1e);   // sin_h * xh
+    two_prod(tb.x, xh, p2, p2e);   // cos_h * xh
+    float re;
+    two_sum(tb.x, -p1, reh, re);
+    rel = __fadd_rn(__fadd_rn(re, __fmaf_rn(tb.x, cm, tb.y)), -__fadd_rn(p1e, __fmaf_rn(tb.z, u, __fmul_rn(tb.w, xh))));
+    float ie;
+    two_sum(tb.z, p2, imh, ie);
+    iml = __fadd_rn(__fadd_rn(ie, __fmaf_rn(tb.z, cm, tb.w)), __fadd_rn(p2e, __fmaf_rn(tb.x, u, __fmul_rn(tb.y, xh))));
 }
 
 __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
@@ -162,6 +171,16 @@ __device__ __forceinline__ void df_acc(float &acc_h, float &acc_l, float th, flo
     acc_l = __fadd_rn(acc_l, __fadd_rn(e, tl));
 }
 
+// Kahan-compensated accumulation of per-tile partial sums: the FP32 paths sum each
+// 256-term shared-memory tile in registers and add the tile sums here, which keeps the
+// rounding error of sums over millions of terms near that of a 256-term sum.
+__device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
+    const float y = __fsub_rn(x, comp);
+    const float t = __fadd_rn(sum, y);
+    comp = __fsub_rn(__fsub_rn(t, sum), y);
+    sum = t;
+}
+
 __device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ gT) {
     for (int i = threadIdx.x; i < kTabLen; i += blockDim.x) sT[i] = gT[i];
 }
@@ -169,6 +188,7 @@ __device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ 
 // ------------------------------------------------------------- sky -> vis
 
 // FP32: owner = baselines, streamed = pixels (c real, chunk order).
+template <int VPT>
 __global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__restrict__ items, int n_items,
                                                            const float4 *__restrict__ vh, const float4 *__restrict__ vl,
                                                            const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
@@ -178,10 +198,10 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__res
     __shared__ float4 sl[kThreads];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        float3 ph[kPerThread], pl[kPerThread];
-        float are[kPerThread], aim[kPerThread];
+        float3 ph[VPT], pl[VPT];
+        float are[VPT], aim[VPT], cre[VPT], cim[VPT];
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
             if (k < w.o1) {
@@ -190,8 +210,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__res
             }
             ph[v] = make_float3(a.x, a.y, a.z);
             pl[v] = make_float3(b.x, b.y, b.z);
-            are[v] = 0.f;
-            aim[v] = 0.f;
+            are[v] = aim[v] = cre[v] = cim[v] = 0.f;
         }
         for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
             __syncthreads();
@@ -207,31 +226,40 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__res
             }
             __syncthreads();
             const int cnt = min(kThreads, w.s1 - s0);
+            float tre[VPT], tim[VPT];
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) tre[v] = tim[v] = 0.f;
 #pragma unroll 4
             for (int q = 0; q < cnt; ++q) {
                 const float4 rh = sh[q], rl = sl[q];
 #pragma unroll
-                for (int v = 0; v < kPerThread; ++v) {
+                for (int v = 0; v < VPT; ++v) {
                     float f = phase_f32(ph[v], pl[v], rh, rl);
                     float sn, cs;
                     __sincosf(6.28318530717958648f * f, &sn, &cs);
-                    are[v] = __fmaf_rn(rh.w, cs, are[v]);
-                    aim[v] = __fmaf_rn(rh.w, sn, aim[v]);
+                    tre[v] = __fmaf_rn(rh.w, cs, tre[v]);
+                    tim[v] = __fmaf_rn(rh.w, sn, tim[v]);
                 }
+            }
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                kahan_add(are[v], cre[v], tre[v]);
+                kahan_add(aim[v], cim[v], tim[v]);
             }
         }
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
             if (k < w.o1) {
-                atomicAdd(&acc[k].x, are[v]);
-                atomicAdd(&acc[k].y, sgn * aim[v]);
+                atomicAdd(&acc[k].x, __fsub_rn(are[v], cre[v]));
+                atomicAdd(&acc[k].y, sgn * __fsub_rn(aim[v], cim[v]));
             }
         }
     }
 }
 
 // Double-float: c given in FP64, accumulation returned in FP64.
+template <int VPT>
 __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__restrict__ items, int n_items,
                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
@@ -244,10 +272,10 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
     load_tab(sT, gT);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        float3 ph[kPerThread], pl[kPerThread];
-        float arh[kPerThread], arl[kPerThread], aih[kPerThread], ail[kPerThread];
+        float3 ph[VPT], pl[VPT];
+        float arh[VPT], arl[VPT], aih[VPT], ail[VPT];
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
             float4 a = make_float4(0.f, 0.f, 0.f, 0.f), b = a;
             if (k < w.o1) {
@@ -279,7 +307,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
                 const float4 rh = sh[q], rl = sl[q];
                 const float2 cv = sc[q];
 #pragma unroll
-                for (int v = 0; v < kPerThread; ++v) {
+                for (int v = 0; v < VPT; ++v) {
                     float fh, fl, reh, rel, imh, iml;
                     phase_df(ph[v], pl[v], rh, rl, fh, fl);
                     cis_df(fh, fl, sT, reh, rel, imh, iml);
@@ -292,7 +320,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
             }
         }
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
             if (k < w.o1) {
                 atomicAdd(&acc[k].x, (double)arh[v] + (double)arl[v]);
@@ -303,6 +331,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
 }
 
 // Plain FP64 reference form.
+template <int VPT>
 __global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__restrict__ items, int n_items,
                                                            const double *__restrict__ vxyz, int64_t nv_all,
                                                            const double *__restrict__ pxyz, int64_t np_all,
@@ -311,9 +340,9 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__res
     __shared__ double sx[kThreads], sy[kThreads], sz[kThreads], sw[kThreads];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        double px[kPerThread], py[kPerThread], pz[kPerThread], are[kPerThread], aim[kPerThread];
+        double px[VPT], py[VPT], pz[VPT], are[VPT], aim[VPT];
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
             bool ok = k < w.o1;
             px[v] = ok ? vxyz[k] : 0.0;
@@ -333,7 +362,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__res
             const int cnt = min(kThreads, w.s1 - s0);
             for (int q = 0; q < cnt; ++q) {
 #pragma unroll
-                for (int v = 0; v < kPerThread; ++v) {
+                for (int v = 0; v < VPT; ++v) {
                     double t = fma(px[v], sx[q], fma(py[v], sy[q], pz[v] * sz[q]));
                     t -= rint(t);
                     double sn, cs;
@@ -344,7 +373,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__res
             }
         }
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
             if (k < w.o1) {
                 atomicAdd(&acc[k].x, are[v]);
@@ -357,6 +386,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__res
 // ------------------------------------------------------------- vis -> sky
 
 // FP32: owner = pixels, streamed = baselines (V complex, chunk order). Output real.
+template <int VPT>
 __global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__restrict__ items, int n_items,
                                                            const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
                                                            const float4 *__restrict__ vh, const float4 *__restrict__ vl,
@@ -366,10 +396,10 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__res
     __shared__ float4 sl[kThreads];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        float3 rh[kPerThread], rl[kPerThread];
-        float a[kPerThread];
+        float3 rh[VPT], rl[VPT];
+        float a[VPT], ca[VPT];
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
             float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
             if (n < w.o1) {
@@ -378,7 +408,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__res
             }
             rh[v] = make_float3(x.x, x.y, x.z);
             rl[v] = make_float3(y.x, y.y, y.z);
-            a[v] = 0.f;
+            a[v] = ca[v] = 0.f;
         }
         for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
             __syncthreads();
@@ -396,30 +426,36 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__res
             }
             __syncthreads();
             const int cnt = min(kThreads, w.s1 - s0);
+            float ta[VPT];
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) ta[v] = 0.f;
 #pragma unroll 4
             for (int q = 0; q < cnt; ++q) {
                 const float4 ph4 = sh[q], pl4 = sl[q];
                 const float3 ph = make_float3(ph4.x, ph4.y, ph4.z), pl = make_float3(pl4.x, pl4.y, pl4.z);
 #pragma unroll
-                for (int v = 0; v < kPerThread; ++v) {
+                for (int v = 0; v < VPT; ++v) {
                     float4 r4h = make_float4(rh[v].x, rh[v].y, rh[v].z, 0.f);
                     float4 r4l = make_float4(rl[v].x, rl[v].y, rl[v].z, 0.f);
                     float f = phase_f32(ph, pl, r4h, r4l);
                     float sn, cs;
                     __sincosf(6.28318530717958648f * f, &sn, &cs);
                     // Re(V e^{-isign j 2 pi t}) = Vr cos + isign Vi sin
-                    a[v] = __fmaf_rn(ph4.w, cs, __fmaf_rn(pl4.w, sn, a[v]));
+                    ta[v] = __fmaf_rn(ph4.w, cs, __fmaf_rn(pl4.w, sn, ta[v]));
                 }
             }
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) kahan_add(a[v], ca[v], ta[v]);
         }
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
-            if (n < w.o1) atomicAdd(&acc[n], a[v]);
+            if (n < w.o1) atomicAdd(&acc[n], __fsub_rn(a[v], ca[v]));
         }
     }
 }
 
+template <int VPT>
 __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__restrict__ items, int n_items,
                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
@@ -432,10 +468,10 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
     load_tab(sT, gT);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        float4 rh[kPerThread], rl[kPerThread];
-        float ah[kPerThread], al[kPerThread];
+        float4 rh[VPT], rl[VPT];
+        float ah[VPT], al[VPT];
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
             float4 x = make_float4(0.f, 0.f, 0.f, 0.f), y = x;
             if (n < w.o1) {
@@ -468,7 +504,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
                 const float4 ph4 = sh[q], pl4 = sl[q], val = sv[q];
                 const float3 ph = make_float3(ph4.x, ph4.y, ph4.z), pl = make_float3(pl4.x, pl4.y, pl4.z);
 #pragma unroll
-                for (int v = 0; v < kPerThread; ++v) {
+                for (int v = 0; v < VPT; ++v) {
                     float fh, fl, reh, rel, imh, iml;
                     phase_df(ph, pl, rh[v], rl[v], fh, fl);
                     cis_df(fh, fl, sT, reh, rel, imh, iml);
@@ -481,13 +517,14 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
             }
         }
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
             if (n < w.o1) atomicAdd(&acc[n], (double)ah[v] + (double)al[v]);
         }
     }
 }
 
+template <int VPT>
 __global__ void __launch_bounds__(kThreads) direct_v2s_f64(const WorkItem *__restrict__ items, int n_items,
                                                            const double *__restrict__ pxyz, int64_t np_all,
                                                            const double *__restrict__ vxyz, int64_t nv_all,
@@ -496,9 +533,9 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f64(const WorkItem *__res
     __shared__ double sx[kThreads], sy[kThreads], sz[kThreads], sr[kThreads], si[kThreads];
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
-        double rx[kPerThread], ry[kPerThread], rz[kPerThread], a[kPerThread];
+        double rx[VPT], ry[VPT], rz[VPT], a[VPT];
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
             bool ok = n < w.o1;
             rx[v] = ok ? pxyz[n] : 0.0;
@@ -520,7 +557,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f64(const WorkItem *__res
             const int cnt = min(kThreads, w.s1 - s0);
             for (int q = 0; q < cnt; ++q) {
 #pragma unroll
-                for (int v = 0; v < kPerThread; ++v) {
+                for (int v = 0; v < VPT; ++v) {
                     double t = fma(sx[q], rx[v], fma(sy[q], ry[v], sz[q] * rz[v]));
                     t -= rint(t);
                     double sn, cs;
@@ -530,7 +567,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f64(const WorkItem *__res
             }
         }
 #pragma unroll
-        for (int v = 0; v < kPerThread; ++v) {
+        for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
             if (n < w.o1) atomicAdd(&acc[n], a[v]);
         }
@@ -554,7 +591,7 @@ void launch_gather_weight(const double *w, const int32_t *perm, int64_t n, doubl
     check_cuda(cudaGetLastError(), "gather_weight");
 }
 
-int direct_tile() { return kTile; }
+int direct_tile(int vpt) { return kThreads * vpt; }
 
 static unsigned grid_for(int64_t n_items) {
     static int sms = 0;
@@ -569,46 +606,64 @@ static unsigned grid_for(int64_t n_items) {
 }
 
 void launch_direct_s2v_f32(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
-                           const float4 *rl, const float *c, float2 *acc, int isign, cudaStream_t s) {
+                           const float4 *rl, const float *c, float2 *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
-    direct_s2v_f32<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, (float)isign);
+    if (vpt == 4)
+        direct_s2v_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, (float)isign);
+    else
+        direct_s2v_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, (float)isign);
     check_cuda(cudaGetLastError(), "direct_s2v_f32");
 }
 
 void launch_direct_s2v_df(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
                           const float4 *rl, const double *c, double2 *acc, const float4 *tab, int isign,
-                          cudaStream_t s) {
+                          int vpt, cudaStream_t s) {
     if (n <= 0) return;
-    direct_s2v_df<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, tab, (float)isign);
+    if (vpt == 4)
+        direct_s2v_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, tab, (float)isign);
+    else
+        direct_s2v_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, tab, (float)isign);
     check_cuda(cudaGetLastError(), "direct_s2v_df");
 }
 
 void launch_direct_s2v_f64(const WorkItem *items, int64_t n, const double *vxyz, int64_t nv, const double *pxyz,
-                           int64_t np, const double *c, double2 *acc, int isign, cudaStream_t s) {
+                           int64_t np, const double *c, double2 *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
-    direct_s2v_f64<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vxyz, nv, pxyz, np, c, acc, (double)isign);
+    if (vpt == 4)
+        direct_s2v_f64<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vxyz, nv, pxyz, np, c, acc, (double)isign);
+    else
+        direct_s2v_f64<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vxyz, nv, pxyz, np, c, acc, (double)isign);
     check_cuda(cudaGetLastError(), "direct_s2v_f64");
 }
 
 void launch_direct_v2s_f32(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
-                           const float4 *vl, const float2 *V, float *acc, int isign, cudaStream_t s) {
+                           const float4 *vl, const float2 *V, float *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
-    direct_v2s_f32<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, (float)isign);
+    if (vpt == 4)
+        direct_v2s_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, (float)isign);
+    else
+        direct_v2s_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, (float)isign);
     check_cuda(cudaGetLastError(), "direct_v2s_f32");
 }
 
 void launch_direct_v2s_df(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
                           const float4 *vl, const double2 *V, double *acc, const float4 *tab, int isign,
-                          cudaStream_t s) {
+                          int vpt, cudaStream_t s) {
     if (n <= 0) return;
-    direct_v2s_df<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, tab, (float)isign);
+    if (vpt == 4)
+        direct_v2s_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, tab, (float)isign);
+    else
+        direct_v2s_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, tab, (float)isign);
     check_cuda(cudaGetLastError(), "direct_v2s_df");
 }
 
 void launch_direct_v2s_f64(const WorkItem *items, int64_t n, const double *pxyz, int64_t np, const double *vxyz,
-                           int64_t nv, const double2 *V, double *acc, int isign, cudaStream_t s) {
+                           int64_t nv, const double2 *V, double *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
-    direct_v2s_f64<<<grid_for(n), kThreads, 0, s>>>(items, (int)n, pxyz, np, vxyz, nv, V, acc, (double)isign);
+    if (vpt == 4)
+        direct_v2s_f64<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, pxyz, np, vxyz, nv, V, acc, (double)isign);
+    else
+        direct_v2s_f64<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, pxyz, np, vxyz, nv, V, acc, (double)isign);
     check_cuda(cudaGetLastError(), "direct_v2s_f64");
 }
 

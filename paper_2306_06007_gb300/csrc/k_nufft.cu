@@ -4,16 +4,26 @@
 // dimension: r~ = r - C, p~ = p - D, spread-grid scale a (cells per unit of r),
 // spread grid n1, FFT grid n2. With s = isign:
 //
-//   f_k = Q_k sum_j G_j psi(v_k - j)                      (interpolate, n2 grid, periodic)
+//   f_k = Q_k sum_j G_j psi(v_k - j)                       (interpolate, n2 grid, periodic)
 //   G   = FFT_s( pad( b_l / Psi(l) ) ),  l in [-n1/2, n1/2)  (deconvolve, zero-pad, FFT)
-//   b_l = sum_n P_n c_n phi(l - g_n)                       (spread, n1 grid)
+//   b_l = sum_n P_n c_n phi(l - g_n)                        (spread, n1 grid)
 //   g_n = a r~_n + n1/2,  v_k = p~_k n2 / a,  tau_k = 2 pi p~_k / a
 //   P_n = exp(s j 2 pi <D, r~_n>),  Q_k = exp(s j 2 pi <C, p_k>) / prod_d Phi(tau_kd)
 //
-// phi = psi = ES kernel of width w; Phi(tau) = int phi(z) cos(tau z) dz on the n1 grid,
-// Psi(l) = int psi(z) cos(2 pi l z / n2) dz on the n2 grid. vis -> sky runs the exact
-// transpose of every step (spread at baselines on n2, FFT_-s, crop and divide, gather
-// at pixels), so the pair is adjoint to rounding.
+// phi = psi = ES kernel of width w; Phi(tau) = int phi(z) cos(tau z) dz. Phi depends only
+// on the kernel, so 1/Phi is one Chebyshev series in tau^2 per plan; Psi(l) = Phi(2 pi l/n2)
+// is tabulated per block on the host. vis -> sky runs the exact transpose of every step
+// (spread at baselines on n2, FFT_-s, crop and divide, gather at pixels).
+//
+// Grid positions and phases are computed on the fly for every (point, block): FP64 for
+// the FP64 path; for the FP32 path from the float hi/lo splits of the coordinates and of
+// C, D, a with exact differences and products, so no FP64 is used per point.
+//
+// Spreading: each CTA takes 256 consecutive points (chunk order is Morton order inside a
+// chunk, so they are close in space), accumulates their w^3 taps into a shared-memory
+// tile that covers all their windows, then adds the tile to the grid with vector
+// atomics; when the tile would not fit, the CTA adds its taps to the grid directly.
+#include <climits>
 #include <cstdint>
 #include <vector>
 
@@ -24,6 +34,8 @@ namespace hvox {
 namespace {
 
 template <typename T> using cplx_t = typename CplxOf<T>::type;
+
+constexpr int kSpreadThreads = 256;
 
 __device__ __forceinline__ float es_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double es_exp(double x) { return exp(x); }
@@ -39,62 +51,16 @@ template <typename T, int W> __device__ __forceinline__ void es_weights(T fr, T 
     }
 }
 
-// ------------------------------------------------------------------ sky -> vis
-
-template <typename T, int W>
-__global__ void spread_pix_kernel(DevBlock b, const T *__restrict__ c, const GridRec<T> *__restrict__ rec,
-                                  const cplx_t<T> *__restrict__ ph, cplx_t<T> *__restrict__ G1, T beta) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= b.np) return;
-    const GridRec<T> r = rec[b.prec_off + i];
-    const cplx_t<T> P = ph[b.prec_off + i];
-    const T cv = c[b.p0 + i];
-    const T vr = cv * P.x, vi = cv * P.y;
-    T wx[W], wy[W], wz[W];
-    es_weights<T, W>(r.fr[0], beta, wx);
-    es_weights<T, W>(r.fr[1], beta, wy);
-    es_weights<T, W>(r.fr[2], beta, wz);
-    const int64_t nx = b.n1[0], ny = b.n1[1];
-    for (int jz = 0; jz < W; ++jz) {
-        for (int jy = 0; jy < W; ++jy) {
-            const T wyz = wy[jy] * wz[jz];
-            const int64_t base = ((int64_t)(r.i0[2] + jz) * ny + (r.i0[1] + jy)) * nx + r.i0[0];
-            const T ar = vr * wyz, ai = vi * wyz;
+// Same weights with the tap order rotated: wt[j] = phi((j + rot) mod W - fr).
+template <typename T, int W> __device__ __forceinline__ void es_weights_rot(T fr, T beta, int rot, T *wt) {
+    const T inv = T(2) / T(W);
 #pragma unroll
-            for (int jx = 0; jx < W; ++jx) {
-                atomicAdd(&G1[base + jx].x, ar * wx[jx]);
-                atomicAdd(&G1[base + jx].y, ai * wx[jx]);
-            }
-        }
-    }
-}
-
-// G2[j] = G1[l + n1/2] / (Psi_x Psi_y Psi_z)(l) for the centred frequency l of FFT index j
-// inside the n1 band, 0 elsewhere.
-template <typename T>
-__global__ void deconv_pad_kernel(DevBlock b, const cplx_t<T> *__restrict__ G1, const T *__restrict__ ipsi,
-                                  cplx_t<T> *__restrict__ G2) {
-    const int64_t n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
-    const int64_t total = n2x * n2y * n2z;
-    const T *px = ipsi, *py = ipsi + b.n1[0], *pz = py + b.n1[1];
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
-        int64_t jx = j % n2x, t = j / n2x;
-        int64_t jy = t % n2y, jz = t / n2y;
-        int64_t lx = jx < n2x / 2 ? jx : jx - n2x;
-        int64_t ly = jy < n2y / 2 ? jy : jy - n2y;
-        int64_t lz = jz < n2z / 2 ? jz : jz - n2z;
-        cplx_t<T> out;
-        out.x = T(0);
-        out.y = T(0);
-        if (lx >= -b.n1[0] / 2 && lx < b.n1[0] / 2 && ly >= -b.n1[1] / 2 && ly < b.n1[1] / 2 && lz >= -b.n1[2] / 2 &&
-            lz < b.n1[2] / 2) {
-            int64_t ix = lx + b.n1[0] / 2, iy = ly + b.n1[1] / 2, iz = lz + b.n1[2] / 2;
-            T f = px[ix] * py[iy] * pz[iz];
-            cplx_t<T> g = G1[(iz * b.n1[1] + iy) * b.n1[0] + ix];
-            out.x = g.x * f;
-            out.y = g.y * f;
-        }
-        G2[j] = out;
+    for (int j = 0; j < W; ++j) {
+        int jr = j + rot;
+        jr = jr >= W ? jr - W : jr;
+        T x = (T(jr) - fr) * inv;
+        T q = T(1) - x * x;
+        wt[j] = q > T(0) ? es_exp(beta * (sqrt(q) - T(1))) : T(0);
     }
 }
 
@@ -103,26 +69,351 @@ __device__ __forceinline__ int64_t wrap(int64_t i, int64_t n) {
     return r < 0 ? r + n : r;
 }
 
-template <typename T, int W>
-__global__ void interp_vis_kernel(DevBlock b, const cplx_t<T> *__restrict__ G2, const GridRec<T> *__restrict__ rec,
-                                  const cplx_t<T> *__restrict__ q, cplx_t<T> *__restrict__ acc, T beta) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= b.nv) return;
-    const GridRec<T> r = rec[b.vrec_off + k];
-    T wx[W], wy[W], wz[W];
-    es_weights<T, W>(r.fr[0], beta, wx);
-    es_weights<T, W>(r.fr[1], beta, wy);
-    es_weights<T, W>(r.fr[2], beta, wz);
-    const int64_t nx = b.n2[0], ny = b.n2[1], nz = b.n2[2];
-    int64_t ix[W];
+// ------------------------------------------------------------------ float helpers
+
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+    s = __fadd_rn(a, b);
+    float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void two_prod(float a, float b, float &p, float &e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+
+// (ah + al) - (bh + bl) as hi + lo with the leading difference exact.
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float &rh, float &rl) {
+    float s, e;
+    two_sum(ah, -bh, s, e);
+    rh = s;
+    rl = __fadd_rn(e, __fsub_rn(al, bl));
+}
+
+// (ah + al)(bh + bl) as hi + lo.
+__device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &p, float &lo) {
+    two_prod(ah, bh, p, lo);
+    lo = __fmaf_rn(ah, bl, __fmaf_rn(al, bh, lo));
+}
+
+// Fraction of sum_d x_d y_d in turns (x, y as hi/lo splits), |error| ~ 1e-7 turn.
+__device__ __forceinline__ float dot_frac_f32(const float *xh, const float *xl, const float *yh, const float *yl) {
+    float f = 0.f, small = 0.f;
 #pragma unroll
-    for (int j = 0; j < W; ++j) ix[j] = wrap((int64_t)r.i0[0] + j, nx);
+    for (int d = 0; d < 3; ++d) {
+        float a, b;
+        two_prod(xh[d], yh[d], a, b);
+        a = __fsub_rn(a, rintf(a));
+        f = __fadd_rn(f, a);
+        small = __fadd_rn(small, __fmaf_rn(xh[d], yl[d], __fmaf_rn(xl[d], yh[d], b)));
+    }
+    f = __fadd_rn(f, small);
+    return __fsub_rn(f, rintf(f));
+}
+
+// Window of a point at grid position g = s + off (s = sh + sl): start i0 = ceil(g - W/2)
+// and offset fr = g - i0 in (W/2 - 1, W/2].
+template <int W> __device__ __forceinline__ void window_f32(float sh, float sl, int off, int &i0, float &fr) {
+    const float m = rintf(sh);
+    const float f = __fadd_rn(__fsub_rn(sh, m), sl);
+    const float cf = ceilf(__fsub_rn(f, 0.5f * W));
+    i0 = (int)m + off + (int)cf;
+    fr = __fsub_rn(f, cf);
+}
+
+template <int W> __device__ __forceinline__ void window_f64(double g, int &i0, double &fr) {
+    const double c = ceil(g - 0.5 * W);
+    i0 = (int)c;
+    fr = g - c;
+}
+
+// 1 / Phi(tau): Chebyshev series in u = 2 (tau / tau_max)^2 - 1 (Clenshaw).
+template <typename T> __device__ __forceinline__ T inv_phi(T tau, const T *__restrict__ cc, int deg, T inv_tmax2) {
+    const T u = T(2) * tau * tau * inv_tmax2 - T(1);
+    T b1 = 0, b2 = 0;
+    for (int k = deg; k >= 1; --k) {
+        T b0 = cc[k] + T(2) * u * b1 - b2;
+        b2 = b1;
+        b1 = b0;
+    }
+    return cc[0] + u * b1 - b2;
+}
+
+// ------------------------------------------------------------------ per-point geometry
+
+// Pixel n (chunk position) in block b: window on the n1 grid and prephase P = exp(s j 2 pi <D, r~>).
+template <int W>
+__device__ __forceinline__ void geo_pix(const NufftDev &b, int64_t n, const float4 *__restrict__ rh,
+                                        const float4 *__restrict__ rl, const double *, int64_t, int isign, int i0[3],
+                                        float fr[3], float &pr, float &pim) {
+    const float4 h = rh[n], l = rl[n];
+    const float xh[3] = {h.x, h.y, h.z}, xl[3] = {l.x, l.y, l.z};
+    float th[3], tl[3];
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        df_sub(xh[d], xl[d], b.Ch[d], b.Cl[d], th[d], tl[d]);
+        float sh, sl;
+        df_mul(b.ah[d], b.al[d], th[d], tl[d], sh, sl);
+        window_f32<W>(sh, sl, b.n1[d] / 2, i0[d], fr[d]);
+        i0[d] = min(max(i0[d], 0), b.n1[d] - W);
+    }
+    const float f = dot_frac_f32(b.Dh, b.Dl, th, tl);
+    float sn, cs;
+    __sincosf(6.28318530717958648f * f, &sn, &cs);
+    pr = cs;
+    pim = isign * sn;
+}
+
+template <int W>
+__device__ __forceinline__ void geo_pix(const NufftDev &b, int64_t n, const float4 *, const float4 *,
+                                        const double *__restrict__ soa, int64_t n_all, int isign, int i0[3],
+                                        double fr[3], double &pr, double &pim) {
+    double t = 0.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double r = soa[d * n_all + n] - b.C[d];
+        window_f64<W>(b.a[d] * r + 0.5 * b.n1[d], i0[d], fr[d]);
+        i0[d] = min(max(i0[d], 0), b.n1[d] - W);
+        t = fma(b.D[d], r, t);
+    }
+    t -= rint(t);
+    double sn, cs;
+    sincospi(2.0 * t, &sn, &cs);
+    pr = cs;
+    pim = isign * sn;
+}
+
+// Baseline k (chunk position) in block b: window on the n2 grid (unwrapped start) and
+// Q = exp(s j 2 pi <C, p>) / prod_d Phi(tau_d).
+template <int W>
+__device__ __forceinline__ void geo_vis(const NufftDev &b, int64_t k, const float4 *__restrict__ vh,
+                                        const float4 *__restrict__ vl, const double *, int64_t, int isign,
+                                        const float *__restrict__ cc, int deg, float inv_tmax2, int i0[3], float fr[3],
+                                        float &qr, float &qi) {
+    const float4 h = vh[k], l = vl[k];
+    const float ph[3] = {h.x, h.y, h.z}, pl[3] = {l.x, l.y, l.z};
+    float ip = 1.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        float th, tl;
+        df_sub(ph[d], pl[d], b.Dh[d], b.Dl[d], th, tl);
+        float sh, sl;
+        df_mul(b.n2ah[d], b.n2al[d], th, tl, sh, sl);
+        window_f32<W>(sh, sl, 0, i0[d], fr[d]);
+        ip *= inv_phi<float>(th * b.tpa[d], cc, deg, inv_tmax2);
+    }
+    const float f = dot_frac_f32(ph, pl, b.Ch, b.Cl);
+    float sn, cs;
+    __sincosf(6.28318530717958648f * f, &sn, &cs);
+    qr = cs * ip;
+    qi = isign * sn * ip;
+}
+
+template <int W>
+__device__ __forceinline__ void geo_vis(const NufftDev &b, int64_t k, const float4 *, const float4 *,
+                                        const double *__restrict__ soa, int64_t n_all, int isign,
+                                        const double *__restrict__ cc, int deg, double inv_tmax2, int i0[3],
+                                        double fr[3], double &qr, double &qi) {
+    double t = 0.0, ip = 1.0;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        const double p = soa[d * n_all + k];
+        const double pt = p - b.D[d];
+        window_f64<W>(pt * b.n2a[d], i0[d], fr[d]);
+        ip *= inv_phi<double>(pt * b.tpa64[d], cc, deg, inv_tmax2);
+        t = fma(b.C[d], p, t);
+    }
+    t -= rint(t);
+    double sn, cs;
+    sincospi(2.0 * t, &sn, &cs);
+    qr = cs * ip;
+    qi = isign * sn * ip;
+}
+
+// ------------------------------------------------------------------ atomics
+
+__device__ __forceinline__ void grid_add(float2 *g, float re, float im) { atomicAdd(g, make_float2(re, im)); }
+__device__ __forceinline__ void grid_add(double2 *g, double re, double im) {
+    atomicAdd(&g->x, re);
+    atomicAdd(&g->y, im);
+}
+__device__ __forceinline__ void tile_add(float2 *t, float re, float im) {
+    atomicAdd(&t->x, re);
+    atomicAdd(&t->y, im);
+}
+__device__ __forceinline__ void tile_add(double2 *t, double re, double im) {
+    atomicAdd(&t->x, re);
+    atomicAdd(&t->y, im);
+}
+
+// ------------------------------------------------------------------ spreading (tiled)
+
+// Shared-memory tile over the union of the CTA's windows, then vector-atomic flush.
+// PERIODIC: grid indices wrap (n2 grid) instead of lying inside (n1 grid).
+template <typename T, int W, bool PERIODIC>
+__device__ __forceinline__ void spread_tiled(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
+                                             const int ng[3], cplx_t<T> *__restrict__ G, int tile_cap) {
+    extern __shared__ unsigned char smem_raw[];
+    cplx_t<T> *tile = reinterpret_cast<cplx_t<T> *>(smem_raw);
+    __shared__ int s_lo[3], s_hi[3];
+    if (threadIdx.x < 3) {
+        s_lo[threadIdx.x] = INT_MAX;
+        s_hi[threadIdx.x] = INT_MIN;
+    }
+    __syncthreads();
+    if (act) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            atomicMin(&s_lo[d], i0[d]);
+            atomicMax(&s_hi[d], i0[d]);
+        }
+    }
+    __syncthreads();
+    const int lo0 = s_lo[0], lo1 = s_lo[1], lo2 = s_lo[2];
+    const int64_t tx = (int64_t)s_hi[0] - lo0 + W, ty = (int64_t)s_hi[1] - lo1 + W, tz = (int64_t)s_hi[2] - lo2 + W;
+    const int64_t cells = tx * ty * tz;
+    // Lanes whose windows coincide (clustered points) would add to the same cell in the
+    // same instruction; rotating the z order of the taps by lane spreads those adds.
+    const int rot = (threadIdx.x & 31) % W;
+    T wx[W], wy[W], wz[W];
+    if (act) {
+        es_weights<T, W>(fr[0], beta, wx);
+        es_weights<T, W>(fr[1], beta, wy);
+        es_weights_rot<T, W>(fr[2], beta, rot, wz);
+    }
+    if (s_hi[0] >= lo0 && cells <= tile_cap) {
+        for (int64_t j = threadIdx.x; j < cells; j += blockDim.x) {
+            tile[j].x = T(0);
+            tile[j].y = T(0);
+        }
+        __syncthreads();
+        if (act) {
+            for (int jz = 0; jz < W; ++jz) {
+                int jzr = jz + rot;
+                jzr = jzr >= W ? jzr - W : jzr;
+                for (int jy = 0; jy < W; ++jy) {
+                    const T wyz = wy[jy] * wz[jz];
+                    const T ar = vr * wyz, ai = vi * wyz;
+                    cplx_t<T> *row = tile + ((int64_t)(i0[2] - lo2 + jzr) * ty + (i0[1] - lo1 + jy)) * tx + (i0[0] - lo0);
+#pragma unroll
+                    for (int jx = 0; jx < W; ++jx) tile_add(row + jx, ar * wx[jx], ai * wx[jx]);
+                }
+            }
+        }
+        __syncthreads();
+        for (int64_t j = threadIdx.x; j < cells; j += blockDim.x) {
+            const cplx_t<T> v = tile[j];
+            if (v.x == T(0) && v.y == T(0)) continue;
+            const int64_t x = j % tx, r = j / tx;
+            const int64_t y = r % ty, z = r / ty;
+            int64_t gx = lo0 + x, gy = lo1 + y, gz = lo2 + z;
+            if (PERIODIC) {
+                gx = wrap(gx, ng[0]);
+                gy = wrap(gy, ng[1]);
+                gz = wrap(gz, ng[2]);
+            }
+            grid_add(G + (gz * ng[1] + gy) * ng[0] + gx, v.x, v.y);
+        }
+    } else if (act) {
+        int64_t ix[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) ix[j] = PERIODIC ? wrap((int64_t)i0[0] + j, ng[0]) : (int64_t)i0[0] + j;
+        for (int jz = 0; jz < W; ++jz) {
+            int jzr = jz + rot;
+            jzr = jzr >= W ? jzr - W : jzr;
+            const int64_t gz = PERIODIC ? wrap((int64_t)i0[2] + jzr, ng[2]) : (int64_t)i0[2] + jzr;
+            for (int jy = 0; jy < W; ++jy) {
+                const int64_t gy = PERIODIC ? wrap((int64_t)i0[1] + jy, ng[1]) : (int64_t)i0[1] + jy;
+                const T wyz = wy[jy] * wz[jz];
+                const T ar = vr * wyz, ai = vi * wyz;
+                cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
+#pragma unroll
+                for (int jx = 0; jx < W; ++jx) grid_add(row + ix[jx], ar * wx[jx], ai * wx[jx]);
+            }
+        }
+    }
+}
+
+// Point of the CTA's 256 handled by this thread: warp w takes points w, w + 8, w + 16, ...
+// so that the 32 lanes of a warp are spread over the CTA's (spatially ordered) points.
+__device__ __forceinline__ int cta_slot() { return (threadIdx.x & 31) * (kSpreadThreads / 32) + (threadIdx.x >> 5); }
+
+// sky -> vis step 1: pixels (values c, prephase P) onto the n1 grid.
+template <typename T, int W>
+__global__ void __launch_bounds__(kSpreadThreads) spread_pix_kernel(NufftDev b, const float4 *__restrict__ rh,
+                                                                     const float4 *__restrict__ rl,
+                                                                     const double *__restrict__ soa, int64_t n_all,
+                                                                     const T *__restrict__ c, cplx_t<T> *__restrict__ G1,
+                                                                     T beta, int isign, int tile_cap) {
+    const int64_t i = blockIdx.x * (int64_t)kSpreadThreads + cta_slot();
+    const bool act = i < b.np;
+    int i0[3] = {0, 0, 0};
+    T fr[3] = {0, 0, 0}, vr = 0, vi = 0;
+    if (act) {
+        T pr, pim;
+        geo_pix<W>(b, b.p0 + i, rh, rl, soa, n_all, isign, i0, fr, pr, pim);
+        const T cv = c[b.p0 + i];
+        vr = cv * pr;
+        vi = cv * pim;
+    }
+    const int ng[3] = {b.n1[0], b.n1[1], b.n1[2]};
+    spread_tiled<T, W, false>(act, i0, fr, vr, vi, beta, ng, G1, tile_cap);
+}
+
+// vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2 grid.
+template <typename T, int W>
+__global__ void __launch_bounds__(kSpreadThreads) spread_vis_kernel(NufftDev b, const float4 *__restrict__ vh,
+                                                                     const float4 *__restrict__ vl,
+                                                                     const double *__restrict__ soa, int64_t n_all,
+                                                                     const cplx_t<T> *__restrict__ V,
+                                                                     const T *__restrict__ cc, int deg, T inv_tmax2,
+                                                                     cplx_t<T> *__restrict__ G2, T beta, int isign,
+                                                                     int tile_cap) {
+    const int64_t k = blockIdx.x * (int64_t)kSpreadThreads + cta_slot();
+    const bool act = k < b.nv;
+    int i0[3] = {0, 0, 0};
+    T fr[3] = {0, 0, 0}, ur = 0, ui = 0;
+    if (act) {
+        T qr, qi;
+        geo_vis<W>(b, b.v0 + k, vh, vl, soa, n_all, isign, cc, deg, inv_tmax2, i0, fr, qr, qi);
+        const cplx_t<T> v = V[b.v0 + k];
+        ur = qr * v.x + qi * v.y;  // conj(Q) v
+        ui = qr * v.y - qi * v.x;
+    }
+    const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
+    spread_tiled<T, W, true>(act, i0, fr, ur, ui, beta, ng, G2, tile_cap);
+}
+
+// ------------------------------------------------------------------ interpolation (gather)
+
+// sky -> vis steps 3-4: gather the n2 grid at the baselines, times Q; add into acc.
+template <typename T, int W>
+__global__ void __launch_bounds__(128) interp_vis_kernel(NufftDev b, const float4 *__restrict__ vh,
+                                                          const float4 *__restrict__ vl, const double *__restrict__ soa,
+                                                          int64_t n_all, const cplx_t<T> *__restrict__ G2,
+                                                          const T *__restrict__ cc, int deg, T inv_tmax2,
+                                                          cplx_t<T> *__restrict__ acc, T beta, int isign) {
+    const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (k >= b.nv) return;
+    int i0[3];
+    T fr[3], qr, qi;
+    geo_vis<W>(b, b.v0 + k, vh, vl, soa, n_all, isign, cc, deg, inv_tmax2, i0, fr, qr, qi);
+    T wx[W], wy[W], wz[W];
+    es_weights<T, W>(fr[0], beta, wx);
+    es_weights<T, W>(fr[1], beta, wy);
+    es_weights<T, W>(fr[2], beta, wz);
+    const int64_t nx = b.n2[0], ny = b.n2[1], nz = b.n2[2];
+    int64_t ix[W], iy[W], iz[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        ix[j] = wrap((int64_t)i0[0] + j, nx);
+        iy[j] = wrap((int64_t)i0[1] + j, ny) * nx;
+        iz[j] = wrap((int64_t)i0[2] + j, nz) * ny * nx;
+    }
     T sr = 0, si = 0;
     for (int jz = 0; jz < W; ++jz) {
-        const int64_t iz = wrap((int64_t)r.i0[2] + jz, nz);
         for (int jy = 0; jy < W; ++jy) {
-            const int64_t iy = wrap((int64_t)r.i0[1] + jy, ny);
-            const cplx_t<T> *row = G2 + (iz * ny + iy) * nx;
+            const cplx_t<T> *row = G2 + iz[jz] + iy[jy];
             T rr = 0, ri = 0;
 #pragma unroll
             for (int jx = 0; jx < W; ++jx) {
@@ -135,82 +426,30 @@ __global__ void interp_vis_kernel(DevBlock b, const cplx_t<T> *__restrict__ G2, 
             si += ri * wyz;
         }
     }
-    const cplx_t<T> Q = q[b.vrec_off + k];
-    atomicAdd(&acc[b.v0 + k].x, Q.x * sr - Q.y * si);
-    atomicAdd(&acc[b.v0 + k].y, Q.x * si + Q.y * sr);
+    grid_add(acc + b.v0 + k, qr * sr - qi * si, qr * si + qi * sr);
 }
 
-// ------------------------------------------------------------------ vis -> sky (transposes)
-
+// vis -> sky steps 3-4 (transpose of the spreading): gather the n1 grid at the pixels,
+// times conj(P), real part into acc.
 template <typename T, int W>
-__global__ void spread_vis_kernel(DevBlock b, const cplx_t<T> *__restrict__ V, const GridRec<T> *__restrict__ rec,
-                                  const cplx_t<T> *__restrict__ q, cplx_t<T> *__restrict__ G2, T beta) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= b.nv) return;
-    const GridRec<T> r = rec[b.vrec_off + k];
-    const cplx_t<T> Q = q[b.vrec_off + k];
-    const cplx_t<T> v = V[b.v0 + k];
-    // u = conj(Q) v
-    const T ur = Q.x * v.x + Q.y * v.y, ui = Q.x * v.y - Q.y * v.x;
-    T wx[W], wy[W], wz[W];
-    es_weights<T, W>(r.fr[0], beta, wx);
-    es_weights<T, W>(r.fr[1], beta, wy);
-    es_weights<T, W>(r.fr[2], beta, wz);
-    const int64_t nx = b.n2[0], ny = b.n2[1], nz = b.n2[2];
-    int64_t ix[W];
-#pragma unroll
-    for (int j = 0; j < W; ++j) ix[j] = wrap((int64_t)r.i0[0] + j, nx);
-    for (int jz = 0; jz < W; ++jz) {
-        const int64_t iz = wrap((int64_t)r.i0[2] + jz, nz);
-        for (int jy = 0; jy < W; ++jy) {
-            const int64_t iy = wrap((int64_t)r.i0[1] + jy, ny);
-            cplx_t<T> *row = G2 + (iz * ny + iy) * nx;
-            const T wyz = wy[jy] * wz[jz];
-            const T ar = ur * wyz, ai = ui * wyz;
-#pragma unroll
-            for (int jx = 0; jx < W; ++jx) {
-                atomicAdd(&row[ix[jx]].x, ar * wx[jx]);
-                atomicAdd(&row[ix[jx]].y, ai * wx[jx]);
-            }
-        }
-    }
-}
-
-// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band.
-template <typename T>
-__global__ void crop_deconv_kernel(DevBlock b, const cplx_t<T> *__restrict__ G2, const T *__restrict__ ipsi,
-                                   cplx_t<T> *__restrict__ G1) {
-    const int64_t n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
-    const int64_t total = n1x * n1y * n1z;
-    const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t ix = i % n1x, t = i / n1x;
-        int64_t iy = t % n1y, iz = t / n1y;
-        int64_t jx = wrap(ix - n1x / 2, b.n2[0]), jy = wrap(iy - n1y / 2, b.n2[1]), jz = wrap(iz - n1z / 2, b.n2[2]);
-        cplx_t<T> g = G2[(jz * b.n2[1] + jy) * b.n2[0] + jx];
-        T f = px[ix] * py[iy] * pz[iz];
-        cplx_t<T> out;
-        out.x = g.x * f;
-        out.y = g.y * f;
-        G1[i] = out;
-    }
-}
-
-template <typename T, int W>
-__global__ void interp_pix_kernel(DevBlock b, const cplx_t<T> *__restrict__ G1, const GridRec<T> *__restrict__ rec,
-                                  const cplx_t<T> *__restrict__ ph, T *__restrict__ acc, T beta) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) interp_pix_kernel(NufftDev b, const float4 *__restrict__ rh,
+                                                          const float4 *__restrict__ rl, const double *__restrict__ soa,
+                                                          int64_t n_all, const cplx_t<T> *__restrict__ G1,
+                                                          T *__restrict__ acc, T beta, int isign) {
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= b.np) return;
-    const GridRec<T> r = rec[b.prec_off + i];
+    int i0[3];
+    T fr[3], pr, pim;
+    geo_pix<W>(b, b.p0 + i, rh, rl, soa, n_all, isign, i0, fr, pr, pim);
     T wx[W], wy[W], wz[W];
-    es_weights<T, W>(r.fr[0], beta, wx);
-    es_weights<T, W>(r.fr[1], beta, wy);
-    es_weights<T, W>(r.fr[2], beta, wz);
+    es_weights<T, W>(fr[0], beta, wx);
+    es_weights<T, W>(fr[1], beta, wy);
+    es_weights<T, W>(fr[2], beta, wz);
     const int64_t nx = b.n1[0], ny = b.n1[1];
     T sr = 0, si = 0;
     for (int jz = 0; jz < W; ++jz) {
         for (int jy = 0; jy < W; ++jy) {
-            const cplx_t<T> *row = G1 + ((int64_t)(r.i0[2] + jz) * ny + (r.i0[1] + jy)) * nx + r.i0[0];
+            const cplx_t<T> *row = G1 + ((int64_t)(i0[2] + jz) * ny + (i0[1] + jy)) * nx + i0[0];
             T rr = 0, ri = 0;
 #pragma unroll
             for (int jx = 0; jx < W; ++jx) {
@@ -223,104 +462,78 @@ __global__ void interp_pix_kernel(DevBlock b, const cplx_t<T> *__restrict__ G1, 
             si += ri * wyz;
         }
     }
-    const cplx_t<T> P = ph[b.prec_off + i];
-    // Re(conj(P) y)
-    atomicAdd(&acc[b.p0 + i], P.x * sr + P.y * si);
+    atomicAdd(acc + b.p0 + i, pr * sr + pim * si);  // Re(conj(P) y)
 }
 
-// ------------------------------------------------------------------ plan-time tables
+// ------------------------------------------------------------------ deconvolution passes
 
-// Pixel-side records: window start, offset, prephase exp(s j 2 pi <D, r~>).
+// G2[j] = G1[l + n1/2] / (Psi_x Psi_y Psi_z)(l) for the centred frequency l of FFT index j
+// inside the n1 band, 0 elsewhere.
 template <typename T>
-__global__ void pix_tables_kernel(int64_t np, const double *__restrict__ xyz, int64_t n_all, int64_t p0, double3 C,
-                                  double3 D, double3 a, int3 n1, int w, int isign, GridRec<T> *__restrict__ rec,
-                                  cplx_t<T> *__restrict__ ph, int *__restrict__ err) {
-    int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= np) return;
-    const double r[3] = {xyz[p0 + i] - C.x, xyz[n_all + p0 + i] - C.y, xyz[2 * n_all + p0 + i] - C.z};
-    const double aa[3] = {a.x, a.y, a.z};
-    const int nn[3] = {n1.x, n1.y, n1.z};
-    GridRec<T> R;
-    R.pad = 0;
-    R.pad2 = T(0);
-    for (int d = 0; d < 3; ++d) {
-        double g = aa[d] * r[d] + 0.5 * nn[d];
-        double i0 = ceil(g - 0.5 * w);
-        if (i0 < 0.0 || i0 + w > nn[d]) {
-            atomicExch(err, 1);
-            i0 = fmin(fmax(i0, 0.0), (double)(nn[d] - w));
+__global__ void deconv_pad_kernel(NufftDev b, const cplx_t<T> *__restrict__ G1, const T *__restrict__ ipsi,
+                                  cplx_t<T> *__restrict__ G2) {
+    const int64_t n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
+    const int64_t total = n2x * n2y * n2z;
+    const T *px = ipsi, *py = ipsi + b.n1[0], *pz = py + b.n1[1];
+    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t jx = j % n2x, t = j / n2x;
+        const int64_t jy = t % n2y, jz = t / n2y;
+        const int64_t lx = jx < n2x / 2 ? jx : jx - n2x;
+        const int64_t ly = jy < n2y / 2 ? jy : jy - n2y;
+        const int64_t lz = jz < n2z / 2 ? jz : jz - n2z;
+        cplx_t<T> out;
+        out.x = T(0);
+        out.y = T(0);
+        if (lx >= -b.n1[0] / 2 && lx < b.n1[0] / 2 && ly >= -b.n1[1] / 2 && ly < b.n1[1] / 2 && lz >= -b.n1[2] / 2 &&
+            lz < b.n1[2] / 2) {
+            const int64_t ix = lx + b.n1[0] / 2, iy = ly + b.n1[1] / 2, iz = lz + b.n1[2] / 2;
+            const T f = px[ix] * py[iy] * pz[iz];
+            const cplx_t<T> g = G1[(iz * b.n1[1] + iy) * b.n1[0] + ix];
+            out.x = g.x * f;
+            out.y = g.y * f;
         }
-        R.i0[d] = (int32_t)i0;
-        R.fr[d] = (T)(g - i0);
+        G2[j] = out;
     }
-    rec[i] = R;
-    double t = fma(D.x, r[0], fma(D.y, r[1], D.z * r[2]));
-    t -= rint(t);
-    double s, c;
-    sincospi(2.0 * t, &s, &c);
-    cplx_t<T> P;
-    P.x = (T)c;
-    P.y = (T)(isign * s);
-    ph[i] = P;
 }
 
-// Baseline-side records: window start and offset on the n2 grid, and
-// Q = exp(s j 2 pi <C, p>) / prod_d Phi(tau_d) with Phi by Gauss-Legendre quadrature.
+// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band.
 template <typename T>
-__global__ void vis_tables_kernel(int64_t nv, const double *__restrict__ xyz, int64_t n_all, int64_t v0, double3 C,
-                                  double3 D, double3 a, int3 n2, int w, int isign, const double *__restrict__ qz,
-                                  const double *__restrict__ qf, int nq, GridRec<T> *__restrict__ rec,
-                                  cplx_t<T> *__restrict__ q) {
-    int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (k >= nv) return;
-    const double p[3] = {xyz[v0 + k], xyz[n_all + v0 + k], xyz[2 * n_all + v0 + k]};
-    const double pt[3] = {p[0] - D.x, p[1] - D.y, p[2] - D.z};
-    const double aa[3] = {a.x, a.y, a.z};
-    const int nn[3] = {n2.x, n2.y, n2.z};
-    GridRec<T> R;
-    R.pad = 0;
-    R.pad2 = T(0);
-    double phiprod = 1.0;
-    for (int d = 0; d < 3; ++d) {
-        double v = aa[d] > 0.0 ? pt[d] * nn[d] / aa[d] : 0.0;
-        double j0 = ceil(v - 0.5 * w);
-        R.i0[d] = (int32_t)j0;
-        R.fr[d] = (T)(v - j0);
-        double tau = aa[d] > 0.0 ? 2.0 * M_PI * pt[d] / aa[d] : 0.0;
-        double s = 0.0;
-        for (int m = 0; m < nq; ++m) s += qf[m] * cos(tau * qz[m]);
-        phiprod *= s;
+__global__ void crop_deconv_kernel(NufftDev b, const cplx_t<T> *__restrict__ G2, const T *__restrict__ ipsi,
+                                   cplx_t<T> *__restrict__ G1) {
+    const int64_t n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
+    const int64_t total = n1x * n1y * n1z;
+    const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t ix = i % n1x, t = i / n1x;
+        const int64_t iy = t % n1y, iz = t / n1y;
+        const int64_t jx = wrap(ix - n1x / 2, b.n2[0]), jy = wrap(iy - n1y / 2, b.n2[1]),
+                      jz = wrap(iz - n1z / 2, b.n2[2]);
+        const cplx_t<T> g = G2[(jz * b.n2[1] + jy) * b.n2[0] + jx];
+        const T f = px[ix] * py[iy] * pz[iz];
+        cplx_t<T> out;
+        out.x = g.x * f;
+        out.y = g.y * f;
+        G1[i] = out;
     }
-    rec[k] = R;
-    double t = fma(C.x, p[0], fma(C.y, p[1], C.z * p[2]));
-    t -= rint(t);
-    double s, c;
-    sincospi(2.0 * t, &s, &c);
-    cplx_t<T> Q;
-    Q.x = (T)(c / phiprod);
-    Q.y = (T)(isign * s / phiprod);
-    q[k] = Q;
 }
 
-// ------------------------------------------------------------------ dispatch on W
-
-#define HVOX_W_SWITCH(w, CALL)                       \
-    switch (w) {                                     \
-        case 2: CALL(2); break;                      \
-        case 3: CALL(3); break;                      \
-        case 4: CALL(4); break;                      \
-        case 5: CALL(5); break;                      \
-        case 6: CALL(6); break;                      \
-        case 7: CALL(7); break;                      \
-        case 8: CALL(8); break;                      \
-        case 9: CALL(9); break;                      \
-        case 10: CALL(10); break;                    \
-        case 11: CALL(11); break;                    \
-        case 12: CALL(12); break;                    \
-        case 13: CALL(13); break;                    \
-        case 14: CALL(14); break;                    \
-        case 15: CALL(15); break;                    \
-        case 16: CALL(16); break;                    \
+#define HVOX_W_SWITCH(w, CALL)                                         \
+    switch (w) {                                                       \
+        case 2: CALL(2); break;                                        \
+        case 3: CALL(3); break;                                        \
+        case 4: CALL(4); break;                                        \
+        case 5: CALL(5); break;                                        \
+        case 6: CALL(6); break;                                        \
+        case 7: CALL(7); break;                                        \
+        case 8: CALL(8); break;                                        \
+        case 9: CALL(9); break;                                        \
+        case 10: CALL(10); break;                                      \
+        case 11: CALL(11); break;                                      \
+        case 12: CALL(12); break;                                      \
+        case 13: CALL(13); break;                                      \
+        case 14: CALL(14); break;                                      \
+        case 15: CALL(15); break;                                      \
+        case 16: CALL(16); break;                                      \
         default: fail(HVOX_EUNSUPPORTED, "kernel width out of range"); \
     }
 
@@ -331,22 +544,39 @@ inline unsigned grid_stride_blocks(int64_t n) {
     return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
 }
 
+// Dynamic shared memory of the spreading kernels (tile capacity in cells).
+constexpr int kTileBytes = 96 * 1024;
+
+template <typename T, int W> void set_smem_attrs() {
+    static bool done = false;
+    if (done) return;
+    check_cuda(cudaFuncSetAttribute(spread_pix_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes),
+               "cudaFuncSetAttribute");
+    check_cuda(cudaFuncSetAttribute(spread_vis_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes),
+               "cudaFuncSetAttribute");
+    done = true;
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ host launchers
 
 template <typename T>
-void nufft_block_s2v(const DevBlock &b, int w, double beta, const T *c, const GridRec<T> *prec,
-                     const cplx_t<T> *pph, const GridRec<T> *vrec, const cplx_t<T> *vq, const T *ipsi, cplx_t<T> *G1,
-                     cplx_t<T> *G2, cufftHandle plan, int isign, cplx_t<T> *acc, cudaStream_t s, StageHook &hook) {
+void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_t<T> *acc, cudaStream_t s,
+                     StageHook &hook) {
+    const int w = a.w;
+    const T bt = (T)a.beta;
     const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
     hook.begin(HVOX_STAGE_ZERO);
-    check_cuda(cudaMemsetAsync(G1, 0, sizeof(cplx_t<T>) * m1, s), "memset G1");
+    check_cuda(cudaMemsetAsync(a.G1, 0, sizeof(cplx_t<T>) * m1, s), "memset G1");
     hook.end(HVOX_STAGE_ZERO, 1);
-    const T bt = (T)beta;
+    const int cap = kTileBytes / (int)sizeof(cplx_t<T>);
     if (b.np > 0) {
         hook.begin(HVOX_STAGE_SPREAD);
-#define CALL(W) spread_pix_kernel<T, W><<<blocks_for(b.np, 128), 128, 0, s>>>(b, c, prec, pph, G1, bt)
+#define CALL(W)                                                                                                   \
+    set_smem_attrs<T, W>();                                                                                       \
+    spread_pix_kernel<T, W><<<blocks_for(b.np, kSpreadThreads), kSpreadThreads, kTileBytes, s>>>(                 \
+        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, a.G1, bt, a.isign, cap)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_pix");
@@ -354,20 +584,22 @@ void nufft_block_s2v(const DevBlock &b, int w, double beta, const T *c, const Gr
     }
     const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
     hook.begin(HVOX_STAGE_DECONV);
-    deconv_pad_kernel<T><<<grid_stride_blocks(m2), 256, 0, s>>>(b, G1, ipsi, G2);
+    deconv_pad_kernel<T><<<grid_stride_blocks(m2), 256, 0, s>>>(b, a.G1, a.ipsi + b.psi_off, a.G2);
     check_cuda(cudaGetLastError(), "deconv_pad");
     hook.end(HVOX_STAGE_DECONV, 1);
     hook.begin(HVOX_STAGE_FFT);
-    check_cufft(cufftSetStream(plan, s), "cufftSetStream");
-    const int dir = isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
+    check_cufft(cufftSetStream(a.fft, s), "cufftSetStream");
+    const int dir = a.isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
     if constexpr (sizeof(T) == 4)
-        check_cufft(cufftExecC2C(plan, (cufftComplex *)G2, (cufftComplex *)G2, dir), "cufftExecC2C");
+        check_cufft(cufftExecC2C(a.fft, (cufftComplex *)a.G2, (cufftComplex *)a.G2, dir), "cufftExecC2C");
     else
-        check_cufft(cufftExecZ2Z(plan, (cufftDoubleComplex *)G2, (cufftDoubleComplex *)G2, dir), "cufftExecZ2Z");
+        check_cufft(cufftExecZ2Z(a.fft, (cufftDoubleComplex *)a.G2, (cufftDoubleComplex *)a.G2, dir), "cufftExecZ2Z");
     hook.end(HVOX_STAGE_FFT, 1);
     if (b.nv > 0) {
         hook.begin(HVOX_STAGE_INTERP);
-#define CALL(W) interp_vis_kernel<T, W><<<blocks_for(b.nv, 128), 128, 0, s>>>(b, G2, vrec, vq, acc, bt)
+#define CALL(W)                                                                                                   \
+    interp_vis_kernel<T, W><<<blocks_for(b.nv, 128), 128, 0, s>>>(b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, a.G2, \
+                                                                  a.cheb, a.deg, (T)a.inv_tmax2, acc, bt, a.isign)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "interp_vis");
@@ -376,38 +608,44 @@ void nufft_block_s2v(const DevBlock &b, int w, double beta, const T *c, const Gr
 }
 
 template <typename T>
-void nufft_block_v2s(const DevBlock &b, int w, double beta, const cplx_t<T> *V, const GridRec<T> *prec,
-                     const cplx_t<T> *pph, const GridRec<T> *vrec, const cplx_t<T> *vq, const T *ipsi, cplx_t<T> *G1,
-                     cplx_t<T> *G2, cufftHandle plan, int isign, T *acc, cudaStream_t s, StageHook &hook) {
+void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *V, T *acc, cudaStream_t s,
+                     StageHook &hook) {
+    const int w = a.w;
+    const T bt = (T)a.beta;
     const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
     hook.begin(HVOX_STAGE_ZERO);
-    check_cuda(cudaMemsetAsync(G2, 0, sizeof(cplx_t<T>) * m2, s), "memset G2");
+    check_cuda(cudaMemsetAsync(a.G2, 0, sizeof(cplx_t<T>) * m2, s), "memset G2");
     hook.end(HVOX_STAGE_ZERO, 1);
-    const T bt = (T)beta;
+    const int cap = kTileBytes / (int)sizeof(cplx_t<T>);
     if (b.nv > 0) {
         hook.begin(HVOX_STAGE_SPREAD);
-#define CALL(W) spread_vis_kernel<T, W><<<blocks_for(b.nv, 128), 128, 0, s>>>(b, V, vrec, vq, G2, bt)
+#define CALL(W)                                                                                                   \
+    set_smem_attrs<T, W>();                                                                                       \
+    spread_vis_kernel<T, W><<<blocks_for(b.nv, kSpreadThreads), kSpreadThreads, kTileBytes, s>>>(                 \
+        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, bt, a.isign, cap)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_vis");
         hook.end(HVOX_STAGE_SPREAD, 1);
     }
     hook.begin(HVOX_STAGE_FFT);
-    check_cufft(cufftSetStream(plan, s), "cufftSetStream");
-    const int dir = isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD;  // transpose: opposite sign
+    check_cufft(cufftSetStream(a.fft, s), "cufftSetStream");
+    const int dir = a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD;  // transpose: opposite sign
     if constexpr (sizeof(T) == 4)
-        check_cufft(cufftExecC2C(plan, (cufftComplex *)G2, (cufftComplex *)G2, dir), "cufftExecC2C");
+        check_cufft(cufftExecC2C(a.fft, (cufftComplex *)a.G2, (cufftComplex *)a.G2, dir), "cufftExecC2C");
     else
-        check_cufft(cufftExecZ2Z(plan, (cufftDoubleComplex *)G2, (cufftDoubleComplex *)G2, dir), "cufftExecZ2Z");
+        check_cufft(cufftExecZ2Z(a.fft, (cufftDoubleComplex *)a.G2, (cufftDoubleComplex *)a.G2, dir), "cufftExecZ2Z");
     hook.end(HVOX_STAGE_FFT, 1);
     const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
     hook.begin(HVOX_STAGE_DECONV);
-    crop_deconv_kernel<T><<<grid_stride_blocks(m1), 256, 0, s>>>(b, G2, ipsi, G1);
+    crop_deconv_kernel<T><<<grid_stride_blocks(m1), 256, 0, s>>>(b, a.G2, a.ipsi + b.psi_off, a.G1);
     check_cuda(cudaGetLastError(), "crop_deconv");
     hook.end(HVOX_STAGE_DECONV, 1);
     if (b.np > 0) {
         hook.begin(HVOX_STAGE_INTERP);
-#define CALL(W) interp_pix_kernel<T, W><<<blocks_for(b.np, 128), 128, 0, s>>>(b, G1, prec, pph, acc, bt)
+#define CALL(W)                                                                                                   \
+    interp_pix_kernel<T, W><<<blocks_for(b.np, 128), 128, 0, s>>>(b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, a.G1, \
+                                                                  acc, bt, a.isign)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "interp_pix");
@@ -415,46 +653,13 @@ void nufft_block_v2s(const DevBlock &b, int w, double beta, const cplx_t<T> *V, 
     }
 }
 
-template void nufft_block_s2v<float>(const DevBlock &, int, double, const float *, const GridRec<float> *,
-                                     const float2 *, const GridRec<float> *, const float2 *, const float *, float2 *,
-                                     float2 *, cufftHandle, int, float2 *, cudaStream_t, StageHook &);
-template void nufft_block_s2v<double>(const DevBlock &, int, double, const double *, const GridRec<double> *,
-                                      const double2 *, const GridRec<double> *, const double2 *, const double *,
-                                      double2 *, double2 *, cufftHandle, int, double2 *, cudaStream_t, StageHook &);
-template void nufft_block_v2s<float>(const DevBlock &, int, double, const float2 *, const GridRec<float> *,
-                                     const float2 *, const GridRec<float> *, const float2 *, const float *, float2 *,
-                                     float2 *, cufftHandle, int, float *, cudaStream_t, StageHook &);
-template void nufft_block_v2s<double>(const DevBlock &, int, double, const double2 *, const GridRec<double> *,
-                                      const double2 *, const GridRec<double> *, const double2 *, const double *,
-                                      double2 *, double2 *, cufftHandle, int, double *, cudaStream_t, StageHook &);
-
-template <typename T>
-void nufft_tables(const NufftBlock &b, const double *pix_soa, int64_t n_pix, const double *vis_soa, int64_t n_vis,
-                  int w, int isign, const double *qz, const double *qf, int nq, GridRec<T> *prec, cplx_t<T> *pph,
-                  GridRec<T> *vrec, cplx_t<T> *vq, int *err, cudaStream_t s) {
-    double3 C = make_double3(b.C[0], b.C[1], b.C[2]);
-    double3 D = make_double3(b.D[0], b.D[1], b.D[2]);
-    double3 a = make_double3(b.a[0], b.a[1], b.a[2]);
-    int3 n1 = make_int3((int)b.n1[0], (int)b.n1[1], (int)b.n1[2]);
-    int3 n2 = make_int3((int)b.n2[0], (int)b.n2[1], (int)b.n2[2]);
-    int64_t np = b.p1 - b.p0, nv = b.v1 - b.v0;
-    if (np > 0) {
-        pix_tables_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(np, pix_soa, n_pix, b.p0, C, D, a, n1, w, isign,
-                                                                   prec + b.prec_off, pph + b.prec_off, err);
-        check_cuda(cudaGetLastError(), "pix_tables");
-    }
-    if (nv > 0) {
-        vis_tables_kernel<T><<<blocks_for(nv, 128), 128, 0, s>>>(nv, vis_soa, n_vis, b.v0, C, D, a, n2, w, isign, qz,
-                                                                   qf, nq, vrec + b.vrec_off, vq + b.vrec_off);
-        check_cuda(cudaGetLastError(), "vis_tables");
-    }
-}
-
-template void nufft_tables<float>(const NufftBlock &, const double *, int64_t, const double *, int64_t, int, int,
-                                  const double *, const double *, int, GridRec<float> *, float2 *, GridRec<float> *,
-                                  float2 *, int *, cudaStream_t);
-template void nufft_tables<double>(const NufftBlock &, const double *, int64_t, const double *, int64_t, int, int,
-                                   const double *, const double *, int, GridRec<double> *, double2 *,
-                                   GridRec<double> *, double2 *, int *, cudaStream_t);
+template void nufft_block_s2v<float>(const NufftDev &, const NufftArgs<float> &, const float *, float2 *,
+                                     cudaStream_t, StageHook &);
+template void nufft_block_s2v<double>(const NufftDev &, const NufftArgs<double> &, const double *, double2 *,
+                                      cudaStream_t, StageHook &);
+template void nufft_block_v2s<float>(const NufftDev &, const NufftArgs<float> &, const float2 *, float *,
+                                     cudaStream_t, StageHook &);
+template void nufft_block_v2s<double>(const NufftDev &, const NufftArgs<double> &, const double2 *, double *,
+                                      cudaStream_t, StageHook &);
 
 }  // namespace hvox

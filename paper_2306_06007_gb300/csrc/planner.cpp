@@ -167,29 +167,31 @@ int64_t chunk_points(const double *xyz, int64_t n, const double h[3], std::vecto
 }
 
 CostModel default_cost_model(int prec, bool plain, int w) {
-    // Seconds per unit of work on one GB300, from the throughput of the kernels that do
-    // the work (direct pair rates of the FP32 / double-float / FP64 kernels, tap rates of
-    // the spread and interpolation kernels, FFT and grid passes at HBM speed).
+    // Seconds per unit of work on one GB300, measured with this library's kernels: direct
+    // pairs/s of the FP32, double-float and FP64 kernels; spreading taps/s through
+    // shared-memory tiles and straight into the grid (vector atomics); interpolation
+    // taps/s; cuFFT C2C (HBM-bound) and Z2Z (bound by GB300's FP64 units) per cell and
+    // log2(cells); grid passes at HBM speed.
     (void)w;
     CostModel m;
-    if (plain) {
-        m.direct_pair = 1.0 / 1.2e10;
-        m.spread_tap = 1.0 / 1.5e11;
-        m.fft_cell = 6e-12;
-        m.grid_cell = 1e-11;
-        m.block_fixed = 60e-6;
-    } else if (prec == 1) {
-        m.direct_pair = 1.0 / 1.0e12;
-        m.spread_tap = 1.0 / 1.5e12;
-        m.fft_cell = 5e-13;
+    if (prec == 1 && !plain) {
+        m.direct_pair = 1.0 / 8.5e11;
+        m.scatter_smem = 1.0 / 3.0e11;
+        m.scatter_global = 1.0 / 1.5e11;
+        m.gather_tap = 1.0 / 1.2e12;
+        m.fft_cell = 6e-13;
         m.grid_cell = 4e-12;
-        m.block_fixed = 25e-6;
+        m.block_fixed = 30e-6;
+        m.tile_cells = 96.0 * 1024 / 8;
     } else {
-        m.direct_pair = 1.0 / 2.5e11;
-        m.spread_tap = 1.0 / 1.5e11;
-        m.fft_cell = 6e-12;
-        m.grid_cell = 8e-12;
-        m.block_fixed = 40e-6;
+        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 2.8e11;
+        m.scatter_smem = 1.0 / 2.0e9;
+        m.scatter_global = 1.0 / 1.0e9;
+        m.gather_tap = 1.0 / 2.0e9;
+        m.fft_cell = 2.1e-11;
+        m.grid_cell = 1e-11;
+        m.block_fixed = 50e-6;
+        m.tile_cells = 96.0 * 1024 / 16;
     }
     return m;
 }
@@ -226,6 +228,17 @@ struct Evaluated {
     double cost;
 };
 
+// Spreading cost per tap for n points on a grid of `cells`: through the shared tile when
+// the 256 points of a CTA (uniform-density estimate of the region they occupy, plus the
+// kernel width) fit the tile, else straight into the grid.
+double scatter_cost(const CostModel &m, double n, double cells, int w) {
+    double region = 256.0 * cells / std::max(1.0, n);
+    double side = std::cbrt(region) + (double)(w - 1);
+    return side * side * side <= m.tile_cells ? m.scatter_smem : m.scatter_global;
+}
+
+// Modelled cost of one sub-problem by NUFFT in both directions (sky -> vis spreads pixels
+// and gathers baselines; vis -> sky spreads baselines and gathers pixels).
 double nufft_cost(const CostModel &m, const ESKernel &es, double sigma, int64_t np, int64_t nv, const double *pext,
                   const double *vext, double *cells_out) {
     double m1 = 1, m2 = 1;
@@ -236,9 +249,12 @@ double nufft_cost(const CostModel &m, const ESKernel &es, double sigma, int64_t 
         m2 *= (double)n2;
     }
     if (cells_out) *cells_out = m2;
-    double w3 = (double)es.w * es.w * es.w;
-    return m.spread_tap * w3 * (double)(np + nv) + m.fft_cell * m2 * std::log2(std::max(2.0, m2)) +
-           m.grid_cell * (2.0 * m1 + 2.0 * m2) + m.block_fixed;
+    const double w3 = (double)es.w * es.w * es.w;
+    const double taps_p = (double)np * w3, taps_v = (double)nv * w3;
+    double c = taps_p * (scatter_cost(m, (double)np, m1, es.w) + m.gather_tap) +
+               taps_v * (scatter_cost(m, (double)nv, m2, es.w) + m.gather_tap);
+    c += 2.0 * (m.fft_cell * m2 * std::log2(std::max(2.0, m2)) + m.grid_cell * (2.0 * m1 + 2.0 * m2) + m.block_fixed);
+    return c;
 }
 
 Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, const double P[3], const double B[3]) {
@@ -253,11 +269,13 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
     double total = 0.0;
     double direct_pairs = (double)in.n_pix * (double)in.n_vis;
     if (in.mode == HVOX_MODE_DIRECT) {
-        e.cost = m.direct_pair * direct_pairs;
+        e.cost = 2.0 * m.direct_pair * direct_pairs;
         return e;
     }
     // Chunks too small to ever win as NUFFT (tap cost alone exceeds the direct cost).
-    double min_pts = (in.mode == HVOX_MODE_NUFFT || in.direct_threshold > 0) ? 0.0 : m.spread_tap * w3 / m.direct_pair;
+    double min_pts = (in.mode == HVOX_MODE_NUFFT || in.direct_threshold > 0)
+                         ? 0.0
+                         : (m.scatter_smem + m.gather_tap) * w3 / (2.0 * m.direct_pair);
     std::vector<int64_t> bigp, bigv;
     for (int64_t i = 0; i < e.npc; ++i)
         if ((double)e.ps.count[i] > min_pts) bigp.push_back(i);
@@ -281,7 +299,7 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
                 if (use_nufft) cn = nufft_cost(m, in.es, in.sigma, np, nv, pext, vext, nullptr);
             } else {
                 cn = nufft_cost(m, in.es, in.sigma, np, nv, pext, vext, nullptr);
-                use_nufft = cn < m.direct_pair * pairs;
+                use_nufft = cn < 2.0 * m.direct_pair * pairs;
             }
             if (use_nufft) {
                 e.nufft_pairs.push_back({i, j});
@@ -290,7 +308,7 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
             }
         }
     }
-    total += m.direct_pair * direct_pairs;
+    total += 2.0 * m.direct_pair * direct_pairs;
     e.cost = total;
     return e;
 }
@@ -317,14 +335,20 @@ PartitionResult make_partition(const PlanInputs &in) {
         B[d] = hi - lo;
     }
     Evaluated best;
+    // Problems whose whole direct evaluation (both directions) is modelled below 100 ms are
+    // planned as one direct rectangle without a budget search: the search costs more than
+    // it could save, which matters when plans are made per request while serving.
+    const bool tiny = 2.0 * m.direct_pair * (double)in.n_pix * (double)in.n_vis < 100e-3;
     if (in.budget > 0) {
         best = evaluate(in, m, in.budget, P, B);
-    } else if (in.mode == HVOX_MODE_DIRECT) {
-        best = evaluate(in, m, 1e30, P, B);
+    } else if (in.mode == HVOX_MODE_DIRECT || (tiny && in.mode == HVOX_MODE_AUTO && in.direct_threshold <= 0)) {
+        PlanInputs direct = in;
+        direct.mode = HVOX_MODE_DIRECT;
+        best = evaluate(direct, m, 1e30, P, B);
     } else {
         bool have = false;
-        // Budget search: 256 KiB .. 4 GiB in factors of 4 (the cost model picks B).
-        for (double b = 256.0 * 1024.0; b <= 4.3e9; b *= 4.0) {
+        // Budget search: 256 KiB .. 1 GiB in factors of 8 (the cost model picks B).
+        for (double b = 256.0 * 1024.0; b <= 1.1e9; b *= 8.0) {
             Evaluated e = evaluate(in, m, b, P, B);
             if (!have || e.cost < best.cost) {
                 best = std::move(e);
@@ -361,26 +385,53 @@ PartitionResult make_partition(const PlanInputs &in) {
     };
     r.pix_chunk_label = order_chunks(pin);
     r.vis_chunk_label = order_chunks(vin);
-    auto build_perm = [](const std::vector<int64_t> &labels, int64_t nc, const std::vector<int64_t> &ord,
-                         std::vector<int64_t> &perm, std::vector<int64_t> &start) {
+    // Inside a chunk, points follow the Morton (Z-order) curve of their position, so that
+    // consecutive points are close in space (compact spreading tiles).
+    auto build_perm = [](const double *xyz, const std::vector<int64_t> &labels, int64_t nc,
+                         const std::vector<int64_t> &ord, std::vector<int64_t> &perm, std::vector<int64_t> &start) {
+        const int64_t n = (int64_t)labels.size();
         std::vector<int64_t> rank(nc);
         for (int64_t k = 0; k < nc; ++k) rank[ord[k]] = k;
         std::vector<int64_t> cnt(nc + 1, 0);
         for (int64_t l : labels) cnt[rank[l] + 1]++;
         for (int64_t k = 0; k < nc; ++k) cnt[k + 1] += cnt[k];
         start = cnt;
-        perm.assign(labels.size(), 0);
+        perm.assign(n, 0);
         std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-        for (int64_t i = 0; i < (int64_t)labels.size(); ++i) perm[pos[rank[labels[i]]]++] = i;
+        for (int64_t i = 0; i < n; ++i) perm[pos[rank[labels[i]]]++] = i;
+        double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+        for (int64_t i = 0; i < n; ++i)
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = std::min(lo[d], xyz[3 * i + d]);
+                hi[d] = std::max(hi[d], xyz[3 * i + d]);
+            }
+        std::vector<uint64_t> code(n);
+        for (int64_t i = 0; i < n; ++i) {
+            uint64_t c = 0;
+            uint32_t q[3];
+            for (int d = 0; d < 3; ++d) {
+                double ext = hi[d] - lo[d];
+                double u = ext > 0 ? (xyz[3 * i + d] - lo[d]) / ext : 0.0;
+                q[d] = (uint32_t)std::min(2097151.0, std::floor(u * 2097151.0));
+            }
+            for (int bit = 20; bit >= 0; --bit)
+                for (int d = 0; d < 3; ++d) c = (c << 1) | ((q[d] >> bit) & 1u);
+            code[i] = c;
+        }
+        for (int64_t k = 0; k < nc; ++k)
+            std::sort(perm.begin() + start[k], perm.begin() + start[k + 1], [&](int64_t a, int64_t b) {
+                return code[a] != code[b] ? code[a] < code[b] : a < b;
+            });
         return rank;
     };
-    std::vector<int64_t> prank = build_perm(best.pl, best.npc, r.pix_chunk_label, r.pix_perm, r.pix_chunk_start);
-    std::vector<int64_t> vrank = build_perm(best.vl, best.nvc, r.vis_chunk_label, r.vis_perm, r.vis_chunk_start);
+    std::vector<int64_t> prank =
+        build_perm(in.pix, best.pl, best.npc, r.pix_chunk_label, r.pix_perm, r.pix_chunk_start);
+    std::vector<int64_t> vrank =
+        build_perm(in.uvw, best.vl, best.nvc, r.vis_chunk_label, r.vis_perm, r.vis_chunk_start);
 
     // NUFFT blocks with their geometry.
     const double sigma = in.sigma;
     const int w = in.es.w;
-    std::vector<std::vector<char>> is_nufft_for_vchunk;  // per ordered NUFFT vis chunk: flags over ordered pix chunks
     int64_t n_pin = 0, n_vin = 0;
     for (char f : pin) n_pin += f;
     for (char f : vin) n_vin += f;

@@ -1,0 +1,222 @@
+"""Continuous-batching request server for HVOX transforms on one GPU.
+
+Requests (sky -> vis or vis -> sky, any geometry and tolerance) arrive over time. The
+server keeps plans resident on the device (one per geometry and tolerance, each bound
+to its own CUDA stream), plans new geometries on worker threads while the GPU works,
+admits a request as soon as a slot is free, its plan is idle and the HBM budget has
+room for the plan and the request's buffers, and overlaps the admitted requests on the
+device through their streams. Completion is detected by polling a CUDA event recorded
+after each request's device-to-host copy; latency = completion - arrival.
+
+`plain=True` gives the comparison form: one request at a time in arrival order, plans
+in the plain FP64 form (hvox_opts.plain).
+
+This module is scheduling and bookkeeping only; every transform step runs in libhvox.
+"""
+from __future__ import annotations
+
+import concurrent.futures as cf
+import hashlib
+import statistics
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import Plan
+
+
+def geometry_key(pix: np.ndarray, uvw: np.ndarray, eps: float, plain: bool) -> str:
+    h = hashlib.blake2b(digest_size=16)
+    h.update(np.ascontiguousarray(pix, dtype=np.float64).tobytes())
+    h.update(np.ascontiguousarray(uvw, dtype=np.float64).tobytes())
+    h.update(repr((float(eps), bool(plain))).encode())
+    return h.hexdigest()
+
+
+@dataclass
+class _Resident:
+    plan: Plan
+    stream: object
+    bytes: float
+    busy: bool = False
+    last_used: float = 0.0
+
+
+@dataclass
+class _Inflight:
+    req: object
+    key: str
+    event: object
+    out: object
+    io_bytes: float
+    start: float
+
+
+@dataclass
+class ServeReport:
+    results: dict = field(default_factory=dict)      # rid -> numpy output
+    latency_s: dict = field(default_factory=dict)    # rid -> completion - arrival
+    plan_s: dict = field(default_factory=dict)       # key -> planning seconds
+    makespan_s: float = 0.0
+    units: float = 0.0                               # sum of (n_pix + n_vis) over requests
+    peak_bytes: float = 0.0
+
+    def summary(self) -> dict:
+        lat = sorted(self.latency_s.values())
+        q = (lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))] * 1e3) if lat else (lambda f: None)
+        return {"requests": len(lat), "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": q(1.0),
+                "mean_ms": statistics.mean(lat) * 1e3 if lat else None,
+                "throughput_units_per_s": self.units / self.makespan_s if self.makespan_s > 0 else None,
+                "makespan_s": self.makespan_s, "plans": len(self.plan_s),
+                "plan_s_total": sum(self.plan_s.values()), "peak_bytes": self.peak_bytes}
+
+
+class Server:
+    """Request loop over libhvox plans (see the module docstring)."""
+
+    def __init__(self, hbm_budget_bytes: float = 150e9, max_inflight: int = 8, planner_threads: int = 0,
+                 plain: bool = False, keep_plans: bool = True):
+        import os
+        if planner_threads <= 0:
+            planner_threads = max(2, (os.cpu_count() or 4) // 2)
+        self.budget = float(hbm_budget_bytes)
+        self.max_inflight = 1 if plain else int(max_inflight)
+        self.plain = plain
+        self.keep_plans = keep_plans
+        self.pool = cf.ThreadPoolExecutor(max_workers=max(1, planner_threads))
+        self.resident: dict[str, _Resident] = {}
+        self.used = 0.0
+
+    # ------------------------------------------------------------------ plans
+    def _make_plan(self, req):
+        import torch
+        t0 = time.perf_counter()
+        stream = torch.cuda.Stream()
+        plan = Plan(req.pix, req.uvw, req.eps, plain=self.plain, stream=stream)
+        info = plan.info()
+        return plan, stream, info["workspace_bytes"], time.perf_counter() - t0
+
+    def _estimate_plan_bytes(self, req) -> float:
+        # Upper-level estimate used to admit planning (the real figure replaces it).
+        n = len(req.pix) + len(req.uvw)
+        return 120.0 * n + 64e6
+
+    def _evict_idle(self, need: float, protect: set):
+        for key, r in sorted(self.resident.items(), key=lambda kv: kv[1].last_used):
+            if self.used + need <= self.budget:
+                return
+            if r.busy or key in protect:
+                continue
+            r.plan.close()
+            self.used -= r.bytes
+            del self.resident[key]
+
+    # ------------------------------------------------------------------ loop
+    def run(self, requests, realtime: bool = True, time_scale: float = 1.0) -> ServeReport:
+        """Serve `requests` (objects with rid, arrival, pix, uvw, eps, direction, data).
+        realtime: arrivals happen at their timestamps (times time_scale); otherwise all
+        requests are present at t = 0."""
+        import torch
+        rep = ServeReport()
+        pending = sorted(requests, key=lambda r: r.arrival)
+        arrived: list = []
+        planning: dict[str, cf.Future] = {}
+        reserved: dict[str, float] = {}
+        inflight: list[_Inflight] = []
+        t0 = time.perf_counter()
+        first_arrival = None
+        rep.units = float(sum(len(r.pix) + len(r.uvw) for r in requests))
+        nxt = 0
+        while nxt < len(pending) or arrived or inflight or planning:
+            now = time.perf_counter() - t0
+            progressed = False
+            # arrivals
+            while nxt < len(pending) and (not realtime or pending[nxt].arrival * time_scale <= now):
+                r = pending[nxt]
+                r._key = geometry_key(r.pix, r.uvw, r.eps, self.plain)
+                arrived.append(r)
+                nxt += 1
+                progressed = True
+                if first_arrival is None:
+                    first_arrival = (r.arrival * time_scale) if realtime else 0.0
+            # planning (admitted against the budget with an estimate)
+            for r in arrived:
+                k = r._key
+                if k in self.resident or k in planning:
+                    continue
+                if self.plain and (inflight or planning):
+                    break
+                est = self._estimate_plan_bytes(r)
+                if self.used + est > self.budget:
+                    self._evict_idle(est, {x._key for x in arrived})
+                if self.used + est > self.budget and (inflight or planning or self.resident):
+                    continue
+                self.used += est
+                reserved[k] = est
+                planning[k] = self.pool.submit(self._make_plan, r)
+                progressed = True
+            for k in [k for k, f in planning.items() if f.done()]:
+                plan, stream, nbytes, secs = planning.pop(k).result()
+                self.used += nbytes - reserved.pop(k)
+                self.resident[k] = _Resident(plan, stream, nbytes)
+                rep.plan_s[k] = secs
+                progressed = True
+            # admission and launch
+            i = 0
+            while i < len(arrived) and len(inflight) < self.max_inflight:
+                r = arrived[i]
+                res = self.resident.get(r._key)
+                if res is None or res.busy:
+                    i += 1
+                    if self.plain:
+                        break
+                    continue
+                io = 16.0 * (len(r.pix) + len(r.uvw)) * 2
+                if self.used + io > self.budget and inflight:
+                    break
+                arrived.pop(i)
+                res.busy = True
+                self.used += io
+                rep.peak_bytes = max(rep.peak_bytes, self.used)
+                with torch.cuda.stream(res.stream):
+                    if r.direction == "s2v":
+                        x = torch.as_tensor(r.data, dtype=res.plan.real_dtype).pin_memory().to("cuda", non_blocking=True)
+                        y = res.plan.synthesize(x)
+                    else:
+                        x = torch.as_tensor(r.data, dtype=res.plan.complex_dtype).pin_memory().to("cuda", non_blocking=True)
+                        y = res.plan.analyze(x)
+                    out = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+                    out.copy_(y, non_blocking=True)
+                    ev = torch.cuda.Event()
+                    ev.record(res.stream)
+                inflight.append(_Inflight(r, r._key, ev, out, io, time.perf_counter() - t0))
+                progressed = True
+            # completions
+            for f in [f for f in inflight if f.event.query()]:
+                inflight.remove(f)
+                done = time.perf_counter() - t0
+                r = f.req
+                arrival = (r.arrival * time_scale) if realtime else 0.0
+                rep.latency_s[r.rid] = done - arrival
+                rep.results[r.rid] = f.out.numpy().copy()
+                res = self.resident[f.key]
+                res.busy = False
+                res.last_used = done
+                self.used -= f.io_bytes
+                if not self.keep_plans and not any(x._key == f.key for x in arrived):
+                    res.plan.close()
+                    self.used -= res.bytes
+                    del self.resident[f.key]
+                progressed = True
+            if not progressed:
+                time.sleep(0.0002)
+        rep.makespan_s = (time.perf_counter() - t0) - (first_arrival or 0.0)
+        return rep
+
+    def close(self):
+        for r in self.resident.values():
+            r.plan.close()
+        self.resident.clear()
+        self.used = 0.0
+        self.pool.shutdown(wait=True)
