@@ -48,9 +48,12 @@ WORKLOADS = {
 }
 
 
-def load_workload(n_vis=None, config=2):
+def load_workload(n_vis=None, config=2, core_radius=0.0):
+    import numpy as np
     from hvox_inputs import configs
     w = configs.CONFIGS[config]()
+    if core_radius > 0:  # dense core only: baselines with |(u, v)| <= core_radius wavelengths
+        w.uvw = np.ascontiguousarray(w.uvw[np.hypot(w.uvw[:, 0], w.uvw[:, 1]) <= core_radius])
     if n_vis:  # leading baselines only (smaller case for profiler captures)
         w.uvw = w.uvw[:n_vis].copy()
     return w
@@ -223,7 +226,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    w = load_workload(args.n_vis, args.config)
+    w = load_workload(args.n_vis, args.config, args.core_radius)
     units_per_step = 2.0 * (w.n_pix + w.n_vis)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     vis = configs.visibilities_cn(args.config, w.n_vis)
@@ -314,7 +317,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded HEALPix + layout)",
             "config": {"workload": WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
-                       "mode": args.mode,
+                       "mode": args.mode, "core_radius": args.core_radius or None,
                        "l2": "flushed before each step (256 MiB write, outside the timed window)",
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
                        "direct_pairs": info["direct_pairs"], "w": info["w"]},
@@ -355,6 +358,8 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
                     help="workload (2, the LOFAR-like case, is the benchmark; 1 and 3 for studies)")
     ap.add_argument("--mode", default="auto", choices=["auto", "nufft", "direct"])
+    ap.add_argument("--core-radius", type=float, default=0.0,
+                    help="keep only baselines with |(u, v)| <= R wavelengths (dense-core study)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -147,10 +147,19 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     }
 
     const int elem = p.prec == 1 ? 8 : 16;
-    PlanInputs in{pix.data(), uvw.data(), p.n_pix, p.n_vis, p.sigma, p.es, p.prec, p.mode, p.plain,
-                  p.budget_opt, p.direct_threshold, elem};
+    PlanInputs in{pix.data(), uvw.data(), p.n_pix, p.n_vis, p.sigma, p.es};
+    in.prec = p.prec;
+    in.mode = p.mode;
+    in.plain = p.plain;
+    in.budget = p.budget_opt;
+    in.direct_threshold = p.direct_threshold;
+    in.elem_bytes = elem;
+    in.sigma_auto = p.sigma_auto;
+    in.eps_es = p.eps_es;
     p.part = make_partition(in);
     PartitionResult &part = p.part;
+    p.sigma = part.sigma;
+    p.es = part.es;
 
     // Chunk-ordered geometry.
     std::vector<int32_t> pp(p.n_pix), vp(p.n_vis);
@@ -333,12 +342,14 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.prec = p.plain ? 2 : (o.precision == HVOX_PREC_AUTO ? (eps >= 1e-6 ? 1 : 2) : o.precision);
     p.ntrans = o.ntrans > 0 ? o.ntrans : 1;
     p.sigma = o.upsampfac > 0 ? o.upsampfac : 2.0;
+    p.sigma_auto = !(o.upsampfac > 0);
     p.stream = (cudaStream_t)o.stream;
     p.budget_opt = o.chunk_budget_bytes;
     p.direct_threshold = o.direct_threshold;
     double e = eps > 0 ? eps : 1e-6;
     if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
-    p.es = es_params(e * kEpsMargin, p.sigma);
+    p.eps_es = e * kEpsMargin;
+    p.es = es_params(p.eps_es, p.sigma);
     // Points per thread of the direct kernels (tuning knob; 2 or 4).
     if (const char *v = std::getenv("HVOX_DIRECT_VPT")) p.direct_vpt = std::atoi(v) == 4 ? 4 : 2;
 }
@@ -522,9 +533,18 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         Plan p;
         configure(p, n_pix, n_vis, eps, -1, opts);
         const int elem = p.prec == 1 ? 8 : 16;
-        PlanInputs in{pix_xyz, uvw, n_pix, n_vis, p.sigma, p.es, p.prec, p.mode, p.plain,
-                      p.budget_opt, p.direct_threshold, elem};
+        PlanInputs in{pix_xyz, uvw, n_pix, n_vis, p.sigma, p.es};
+        in.prec = p.prec;
+        in.mode = p.mode;
+        in.plain = p.plain;
+        in.budget = p.budget_opt;
+        in.direct_threshold = p.direct_threshold;
+        in.elem_bytes = elem;
+        in.sigma_auto = p.sigma_auto;
+        in.eps_es = p.eps_es;
         p.part = make_partition(in);
+        p.sigma = p.part.sigma;
+        p.es = p.part.es;
         const double re = p.prec == 1 ? 4.0 : 8.0;
         double recs = p.part.nufft_points * (p.prec == 1 ? 48.0 : 64.0);
         p.workspace_bytes = (double)(n_pix + n_vis) * 60.0 + recs + p.part.max_grid_bytes +

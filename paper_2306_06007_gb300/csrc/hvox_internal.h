@@ -96,6 +96,8 @@ CostModel default_cost_model(int prec, bool plain, int w);
 
 struct PartitionResult {
     double t = 1.0, h[3] = {0, 0, 0}, eta[3] = {0, 0, 0}, budget = 0;
+    double sigma = 2.0;       // upsampling chosen for the NUFFT sub-problems
+    ESKernel es;              // kernel for that upsampling
     std::vector<int64_t> pix_label, vis_label;  // original index -> chunk label
     int64_t n_pix_chunks = 0, n_vis_chunks = 0;
     std::vector<int64_t> pix_perm, vis_perm;    // chunk-order position -> original index
@@ -111,8 +113,10 @@ struct PlanInputs {
     const double *pix;     // host (n_pix, 3)
     const double *uvw;     // host (n_vis, 3)
     int64_t n_pix, n_vis;
-    double sigma;
+    double sigma;          // upsampling (used when sigma_auto is false)
     ESKernel es;
+    bool sigma_auto = false;  // choose sigma in {2, 1.5} by the cost model
+    double eps_es = 1e-6;     // tolerance given to the kernel-width rule
     int prec;              // 1 fp32, 2 fp64
     int mode;
     bool plain;
@@ -200,6 +204,8 @@ struct Plan {
     int direct_vpt = 2;            // points per thread of the direct kernels (owner tile 256 * vpt)
     double sigma = 2.0;
     double budget_opt = 0.0;       // chunk_budget_bytes option (0 -> cost-model search)
+    bool sigma_auto = true;        // upsampling chosen by the planner
+    double eps_es = 1e-6;          // tolerance given to the kernel-width rule
     double direct_threshold = 0.0; // direct_threshold option
     ESKernel es;
     bool has_weight = false;

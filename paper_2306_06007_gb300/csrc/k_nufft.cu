@@ -468,53 +468,53 @@ __global__ void __launch_bounds__(128) interp_pix_kernel(NufftDev b, const float
 // ------------------------------------------------------------------ deconvolution passes
 
 // G2[j] = G1[l + n1/2] / (Psi_x Psi_y Psi_z)(l) for the centred frequency l of FFT index j
-// inside the n1 band, 0 elsewhere.
+// inside the n1 band, 0 elsewhere. One thread per x index of a (y, z) row: coalesced rows,
+// no integer division.
 template <typename T>
 __global__ void deconv_pad_kernel(NufftDev b, const cplx_t<T> *__restrict__ G1, const T *__restrict__ ipsi,
                                   cplx_t<T> *__restrict__ G2) {
-    const int64_t n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
-    const int64_t total = n2x * n2y * n2z;
-    const T *px = ipsi, *py = ipsi + b.n1[0], *pz = py + b.n1[1];
-    for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < total; j += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t jx = j % n2x, t = j / n2x;
-        const int64_t jy = t % n2y, jz = t / n2y;
-        const int64_t lx = jx < n2x / 2 ? jx : jx - n2x;
-        const int64_t ly = jy < n2y / 2 ? jy : jy - n2y;
-        const int64_t lz = jz < n2z / 2 ? jz : jz - n2z;
-        cplx_t<T> out;
-        out.x = T(0);
-        out.y = T(0);
-        if (lx >= -b.n1[0] / 2 && lx < b.n1[0] / 2 && ly >= -b.n1[1] / 2 && ly < b.n1[1] / 2 && lz >= -b.n1[2] / 2 &&
-            lz < b.n1[2] / 2) {
-            const int64_t ix = lx + b.n1[0] / 2, iy = ly + b.n1[1] / 2, iz = lz + b.n1[2] / 2;
-            const T f = px[ix] * py[iy] * pz[iz];
-            const cplx_t<T> g = G1[(iz * b.n1[1] + iy) * b.n1[0] + ix];
-            out.x = g.x * f;
-            out.y = g.y * f;
-        }
-        G2[j] = out;
+    const int jx = blockIdx.x * blockDim.x + threadIdx.x;
+    const int jy = blockIdx.y, jz = blockIdx.z;
+    const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
+    if (jx >= n2x) return;
+    const int h1x = b.n1[0] / 2, h1y = b.n1[1] / 2, h1z = b.n1[2] / 2;
+    const int lx = jx < n2x / 2 ? jx : jx - n2x;
+    const int ly = jy < n2y / 2 ? jy : jy - n2y;
+    const int lz = jz < n2z / 2 ? jz : jz - n2z;
+    cplx_t<T> out;
+    out.x = T(0);
+    out.y = T(0);
+    if (lx >= -h1x && lx < h1x && ly >= -h1y && ly < h1y && lz >= -h1z && lz < h1z) {
+        const int ix = lx + h1x, iy = ly + h1y, iz = lz + h1z;
+        const T *px = ipsi, *py = ipsi + b.n1[0], *pz = py + b.n1[1];
+        const T f = px[ix] * py[iy] * pz[iz];
+        const cplx_t<T> g = G1[((int64_t)iz * b.n1[1] + iy) * b.n1[0] + ix];
+        out.x = g.x * f;
+        out.y = g.y * f;
     }
+    G2[((int64_t)jz * n2y + jy) * n2x + jx] = out;
 }
 
-// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band.
+// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band (row-wise, as above).
 template <typename T>
 __global__ void crop_deconv_kernel(NufftDev b, const cplx_t<T> *__restrict__ G2, const T *__restrict__ ipsi,
                                    cplx_t<T> *__restrict__ G1) {
-    const int64_t n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
-    const int64_t total = n1x * n1y * n1z;
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y, iz = blockIdx.z;
+    const int n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
+    if (ix >= n1x) return;
+    const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
+    int jx = ix - n1x / 2, jy = iy - n1y / 2, jz = iz - n1z / 2;
+    jx += jx < 0 ? n2x : 0;
+    jy += jy < 0 ? n2y : 0;
+    jz += jz < 0 ? n2z : 0;
+    const cplx_t<T> g = G2[((int64_t)jz * n2y + jy) * n2x + jx];
     const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
-    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t ix = i % n1x, t = i / n1x;
-        const int64_t iy = t % n1y, iz = t / n1y;
-        const int64_t jx = wrap(ix - n1x / 2, b.n2[0]), jy = wrap(iy - n1y / 2, b.n2[1]),
-                      jz = wrap(iz - n1z / 2, b.n2[2]);
-        const cplx_t<T> g = G2[(jz * b.n2[1] + jy) * b.n2[0] + jx];
-        const T f = px[ix] * py[iy] * pz[iz];
-        cplx_t<T> out;
-        out.x = g.x * f;
-        out.y = g.y * f;
-        G1[i] = out;
-    }
+    const T f = px[ix] * py[iy] * pz[iz];
+    cplx_t<T> out;
+    out.x = g.x * f;
+    out.y = g.y * f;
+    G1[((int64_t)iz * n1y + iy) * n1x + ix] = out;
 }
 
 #define HVOX_W_SWITCH(w, CALL)                                         \
@@ -539,10 +539,6 @@ __global__ void crop_deconv_kernel(NufftDev b, const cplx_t<T> *__restrict__ G2,
 
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
-inline unsigned grid_stride_blocks(int64_t n) {
-    int64_t b = (n + 255) / 256;
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(b, 152 * 32));
-}
 
 // Dynamic shared memory of the spreading kernels (tile capacity in cells).
 constexpr int kTileBytes = 96 * 1024;
@@ -584,7 +580,8 @@ void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_
     }
     const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
     hook.begin(HVOX_STAGE_DECONV);
-    deconv_pad_kernel<T><<<grid_stride_blocks(m2), 256, 0, s>>>(b, a.G1, a.ipsi + b.psi_off, a.G2);
+    deconv_pad_kernel<T><<<dim3((unsigned)((b.n2[0] + 127) / 128), (unsigned)b.n2[1], (unsigned)b.n2[2]), 128, 0, s>>>(
+        b, a.G1, a.ipsi + b.psi_off, a.G2);
     check_cuda(cudaGetLastError(), "deconv_pad");
     hook.end(HVOX_STAGE_DECONV, 1);
     hook.begin(HVOX_STAGE_FFT);
@@ -638,7 +635,8 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
     hook.end(HVOX_STAGE_FFT, 1);
     const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
     hook.begin(HVOX_STAGE_DECONV);
-    crop_deconv_kernel<T><<<grid_stride_blocks(m1), 256, 0, s>>>(b, a.G2, a.ipsi + b.psi_off, a.G1);
+    crop_deconv_kernel<T><<<dim3((unsigned)((b.n1[0] + 127) / 128), (unsigned)b.n1[1], (unsigned)b.n1[2]), 128, 0, s>>>(
+        b, a.G2, a.ipsi + b.psi_off, a.G1);
     check_cuda(cudaGetLastError(), "crop_deconv");
     hook.end(HVOX_STAGE_DECONV, 1);
     if (b.np > 0) {

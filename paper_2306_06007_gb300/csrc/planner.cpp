@@ -302,6 +302,13 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
                 use_nufft = cn < 2.0 * m.direct_pair * pairs;
             }
             if (use_nufft) {
+                for (int d = 0; d < 3 && use_nufft; ++d) {
+                    int64_t n1, n2;
+                    grid_sizes(pext[d], vext[d], in.sigma, in.es.w, n1, n2);
+                    if (n2 > 65535 || n1 > 65535) use_nufft = false;  // launch-grid limit
+                }
+            }
+            if (use_nufft) {
                 e.nufft_pairs.push_back({i, j});
                 total += cn;
                 direct_pairs -= pairs;
@@ -335,6 +342,8 @@ PartitionResult make_partition(const PlanInputs &in) {
         B[d] = hi - lo;
     }
     Evaluated best;
+    double best_sigma = in.sigma;
+    ESKernel best_es = in.es;
     // Problems whose whole direct evaluation (both directions) is modelled below 100 ms are
     // planned as one direct rectangle without a budget search: the search costs more than
     // it could save, which matters when plans are made per request while serving.
@@ -347,15 +356,26 @@ PartitionResult make_partition(const PlanInputs &in) {
         best = evaluate(direct, m, 1e30, P, B);
     } else {
         bool have = false;
-        // Budget search: 256 KiB .. 1 GiB in factors of 8 (the cost model picks B).
-        for (double b = 256.0 * 1024.0; b <= 1.1e9; b *= 8.0) {
-            Evaluated e = evaluate(in, m, b, P, B);
-            if (!have || e.cost < best.cost) {
-                best = std::move(e);
-                have = true;
+        // Upsampling search (sigma trades FFT cells, ~sigma^6, against kernel width) and
+        // budget search: 256 KiB .. 1 GiB in factors of 8 (the cost model picks both).
+        std::vector<double> sigmas = in.sigma_auto ? std::vector<double>{2.0, 1.5} : std::vector<double>{in.sigma};
+        for (double sg : sigmas) {
+            PlanInputs cand = in;
+            cand.sigma = sg;
+            if (in.sigma_auto) cand.es = es_params(in.eps_es, sg);
+            for (double b = 256.0 * 1024.0; b <= 1.1e9; b *= 8.0) {
+                Evaluated e = evaluate(cand, m, b, P, B);
+                if (!have || e.cost < best.cost) {
+                    best = std::move(e);
+                    best_sigma = sg;
+                    best_es = cand.es;
+                    have = true;
+                }
             }
         }
     }
+    r.sigma = best_sigma;
+    r.es = best_es;
     r.t = best.t;
     r.budget = best.budget;
     for (int d = 0; d < 3; ++d) {
@@ -430,8 +450,8 @@ PartitionResult make_partition(const PlanInputs &in) {
         build_perm(in.uvw, best.vl, best.nvc, r.vis_chunk_label, r.vis_perm, r.vis_chunk_start);
 
     // NUFFT blocks with their geometry.
-    const double sigma = in.sigma;
-    const int w = in.es.w;
+    const double sigma = best_sigma;
+    const int w = best_es.w;
     int64_t n_pin = 0, n_vin = 0;
     for (char f : pin) n_pin += f;
     for (char f : vin) n_vin += f;
@@ -464,7 +484,7 @@ PartitionResult make_partition(const PlanInputs &in) {
             vext[d] = best.vs.hi[3 * j + d] - best.vs.lo[3 * j + d];
         }
         double cells = 0;
-        b.cost = nufft_cost(m, in.es, sigma, b.p1 - b.p0, b.v1 - b.v0, pext, vext, &cells);
+        b.cost = nufft_cost(m, best_es, sigma, b.p1 - b.p0, b.v1 - b.v0, pext, vext, &cells);
         double m1 = (double)(b.n1[0] * b.n1[1] * b.n1[2]), m2 = (double)(b.n2[0] * b.n2[1] * b.n2[2]);
         r.max_grid_bytes = std::max(r.max_grid_bytes, (double)in.elem_bytes * (m1 + m2));
         r.nufft_cells += cells;

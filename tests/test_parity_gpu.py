@@ -177,3 +177,24 @@ def test_config2_full_size_sampled(gpu_lib, eps):
     kp = configs.sample_indices(2, w.n_pix, 2000, purpose_offset=1)
     assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
     assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
+
+
+def test_config3_dense_core_nufft_sampled(gpu_lib):
+    # SKA-Low-like sky (1,470,612 pixels) x the dense core of its baselines (|uv| <= 500
+    # wavelengths, ~1.08M): most pairs go through NUFFT sub-problems. 300 seeded outputs
+    # per direction are checked against the oracle.
+    w = configs.config3()
+    w.uvw = np.ascontiguousarray(w.uvw[np.hypot(w.uvw[:, 0], w.uvw[:, 1]) <= 500.0])
+    eps = 1e-6
+    plan = gpu_lib.Plan(w.pix, w.uvw, eps)
+    info = plan.info()
+    assert info["n_nufft_blocks"] > 0 and info["nufft_points"] > 0
+    I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
+    V = plan.synthesize(I).cpu().numpy()
+    vis = configs.visibilities_cn(3, w.n_vis)
+    img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
+    plan.close()
+    kv = configs.sample_indices(3, w.n_vis, 300)
+    kp = configs.sample_indices(3, w.n_pix, 300, purpose_offset=1)
+    assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
+    assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
