@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <cufft.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cstdlib>
 #include <cmath>
@@ -57,9 +58,17 @@ void DevBuf::free_() {
     bytes = 0;
 }
 
+Lane::~Lane() {
+    if (stream) cudaStreamSynchronize(stream);
+    for (auto &kv : fft) cufftDestroy(kv.second);
+    if (done) cudaEventDestroy(done);
+    if (stream) cudaStreamDestroy(stream);
+}
+
 Plan::~Plan() {
     cudaStreamSynchronize(stream);
-    for (auto &kv : fft_plans) cufftDestroy(kv.second);
+    lanes.clear();
+    if (fork_event) cudaEventDestroy(fork_event);
     for (auto &q : pending) {
         cudaEventDestroy(q.a);
         cudaEventDestroy(q.b);
@@ -103,6 +112,9 @@ void to_host(const double *src, size_t n, std::vector<double> &dst) {
     else
         std::memcpy(dst.data(), src, n * sizeof(double));
 }
+
+// Concurrent execution lanes for NUFFT sub-problems.
+constexpr int kMaxLanes = 4;
 
 // Tolerance given to the kernel-width rule: the type-3 transform chains two
 // approximations (spread on n1, interpolate on n2), each held to eps.
@@ -255,24 +267,51 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             upload(p.inv_psi, ipsi.data(), ipsi.size() * 8, s);
             upload(p.cheb, cheb.data(), cheb.size() * 8, s);
         }
-        p.grid1.alloc((size_t)max_m1 * 2 * re);
-        p.grid2.alloc((size_t)max_m2 * 2 * re);
-        // FFT plans per grid shape, one shared work area.
-        size_t max_ws = 0;
-        const cufftType type = p.prec == 1 ? CUFFT_C2C : CUFFT_Z2Z;
+        // Execution lanes: sub-problems assigned longest-first to the least-loaded lane.
+        int n_lanes = (int)std::min<size_t>(kMaxLanes, part.blocks.size());
+        if (const char *v = std::getenv("HVOX_NUFFT_LANES")) n_lanes = std::max(1, std::min(n_lanes, std::atoi(v)));
+        std::vector<double> load(n_lanes, 0.0);
+        std::vector<int64_t> lane_m1(n_lanes, 0), lane_m2(n_lanes, 0);
         for (auto &b : part.blocks) {
-            auto key = std::make_tuple(b.n2[0], b.n2[1], b.n2[2]);
-            if (p.fft_plans.count(key)) continue;
-            cufftHandle h;
-            check_cufft(cufftCreate(&h), "cufftCreate");
-            p.fft_plans[key] = h;
-            check_cufft(cufftSetAutoAllocation(h, 0), "cufftSetAutoAllocation");
-            size_t ws = 0;
-            check_cufft(cufftMakePlan3d(h, (int)b.n2[2], (int)b.n2[1], (int)b.n2[0], type, &ws), "cufftMakePlan3d");
-            max_ws = std::max(max_ws, ws);
+            int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+            load[l] += b.cost;
+            p.block_lane.push_back(l);
+            lane_m1[l] = std::max<int64_t>(lane_m1[l], b.n1[0] * b.n1[1] * b.n1[2]);
+            lane_m2[l] = std::max<int64_t>(lane_m2[l], b.n2[0] * b.n2[1] * b.n2[2]);
         }
-        p.fft_work.alloc(std::max<size_t>(max_ws, 256));
-        for (auto &kv : p.fft_plans) check_cufft(cufftSetWorkArea(kv.second, p.fft_work.ptr), "cufftSetWorkArea");
+        check_cuda(cudaEventCreateWithFlags(&p.fork_event, cudaEventDisableTiming), "cudaEventCreate");
+        const cufftType type = p.prec == 1 ? CUFFT_C2C : CUFFT_Z2Z;
+        for (int l = 0; l < n_lanes; ++l) {
+            auto lane = std::make_unique<Lane>();
+            check_cuda(cudaStreamCreateWithFlags(&lane->stream, cudaStreamNonBlocking), "cudaStreamCreate");
+            check_cuda(cudaEventCreateWithFlags(&lane->done, cudaEventDisableTiming), "cudaEventCreate");
+            lane->g1.alloc((size_t)lane_m1[l] * 2 * re);
+            lane->g2.alloc((size_t)lane_m2[l] * 2 * re);
+            p.lanes.push_back(std::move(lane));
+        }
+        // cuFFT plans per lane and grid shape, one work area per lane.
+        std::vector<size_t> max_ws(n_lanes, 0);
+        for (size_t i = 0; i < part.blocks.size(); ++i) {
+            const auto &b = part.blocks[i];
+            Lane &lane = *p.lanes[p.block_lane[i]];
+            auto key = std::make_tuple(b.n2[0], b.n2[1], b.n2[2]);
+            if (!lane.fft.count(key)) {
+                cufftHandle h;
+                check_cufft(cufftCreate(&h), "cufftCreate");
+                lane.fft[key] = h;
+                check_cufft(cufftSetAutoAllocation(h, 0), "cufftSetAutoAllocation");
+                size_t ws = 0;
+                check_cufft(cufftMakePlan3d(h, (int)b.n2[2], (int)b.n2[1], (int)b.n2[0], type, &ws),
+                            "cufftMakePlan3d");
+                max_ws[p.block_lane[i]] = std::max(max_ws[p.block_lane[i]], ws);
+            }
+            p.block_fft.push_back(lane.fft[key]);
+        }
+        for (int l = 0; l < n_lanes; ++l) {
+            Lane &lane = *p.lanes[l];
+            lane.work.alloc(std::max<size_t>(max_ws[l], 256));
+            for (auto &kv : lane.fft) check_cufft(cufftSetWorkArea(kv.second, lane.work.ptr), "cufftSetWorkArea");
+        }
         auto split = [](double x, float &h, float &l) {
             h = (float)x;
             l = (float)(x - (double)h);
@@ -300,7 +339,6 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             }
             d.psi_off = b.psi_off;
             p.dblocks.push_back(d);
-            p.block_fft.push_back(p.fft_plans[std::make_tuple(b.n2[0], b.n2[1], b.n2[2])]);
         }
     }
 
@@ -312,9 +350,9 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
 
     double ws = 0;
     for (DevBuf *b : {&p.pix_perm, &p.vis_perm, &p.weight, &p.pix_xyz, &p.vis_xyz, &p.pix_hi, &p.pix_lo, &p.vis_hi,
-                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.inv_psi, &p.cheb, &p.grid1, &p.grid2, &p.fft_work,
-                      &p.src, &p.acc, &p.cis_tab, &p.err_word})
+                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.inv_psi, &p.cheb, &p.src, &p.acc, &p.cis_tab})
         ws += (double)b->bytes;
+    for (auto &l : p.lanes) ws += (double)(l->g1.bytes + l->g2.bytes + l->work.bytes);
     p.workspace_bytes = ws;
     p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }

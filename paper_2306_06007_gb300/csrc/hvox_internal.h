@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <map>
+#include <memory>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -175,9 +176,19 @@ template <typename T> struct NufftArgs {
 
 // Stage boundaries reported by the kernel launchers to the executor's profiler.
 struct StageHook {
-    virtual void begin(int stage) = 0;
-    virtual void end(int stage, int launches) = 0;
+    virtual void begin(int stage, cudaStream_t s) = 0;
+    virtual void end(int stage, int launches, cudaStream_t s) = 0;
     virtual ~StageHook() = default;
+};
+
+// An execution lane for NUFFT sub-problems: its own stream, grids, cuFFT plans and
+// cuFFT work area, so that sub-problems on different lanes run concurrently.
+struct Lane {
+    cudaStream_t stream = nullptr;
+    cudaEvent_t done = nullptr;
+    DevBuf g1, g2, work;
+    std::map<std::tuple<int64_t, int64_t, int64_t>, cufftHandle> fft;
+    ~Lane();
 };
 
 struct Plan {
@@ -230,17 +241,16 @@ struct Plan {
     DevBuf cheb;                        // T: Chebyshev coefficients of 1/Phi
     int cheb_deg = 0;
     double cheb_inv_tmax2 = 0.0;
-    DevBuf grid1, grid2;                // largest spread grid and FFT grid
-    std::map<std::tuple<int64_t, int64_t, int64_t>, cufftHandle> fft_plans;
-    DevBuf fft_work;
+    std::vector<std::unique_ptr<Lane>> lanes;  // NUFFT execution lanes
+    cudaEvent_t fork_event = nullptr;   // main stream -> lanes
     std::vector<NufftDev> dblocks;      // block descriptors (launch order)
-    std::vector<cufftHandle> block_fft; // FFT plan of each block
+    std::vector<int> block_lane;        // lane of each block
+    std::vector<cufftHandle> block_fft; // FFT plan of each block (its lane's plan for its shape)
     DevBuf cis_tab;                     // exp(j 2 pi m / 256) as float pairs (double-float path)
 
     // per-call buffers (chunk order)
     DevBuf src, acc;                    // source values, accumulated outputs
     DevBuf io_in, io_out;               // staging for host-pointer calls
-    DevBuf err_word;                    // device error flag
 
     double workspace_bytes = 0;
     ~Plan();

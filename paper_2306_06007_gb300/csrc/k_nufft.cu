@@ -563,12 +563,12 @@ void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_
     const int w = a.w;
     const T bt = (T)a.beta;
     const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
-    hook.begin(HVOX_STAGE_ZERO);
+    hook.begin(HVOX_STAGE_ZERO, s);
     check_cuda(cudaMemsetAsync(a.G1, 0, sizeof(cplx_t<T>) * m1, s), "memset G1");
-    hook.end(HVOX_STAGE_ZERO, 1);
+    hook.end(HVOX_STAGE_ZERO, 1, s);
     const int cap = kTileBytes / (int)sizeof(cplx_t<T>);
     if (b.np > 0) {
-        hook.begin(HVOX_STAGE_SPREAD);
+        hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
     spread_pix_kernel<T, W><<<blocks_for(b.np, kSpreadThreads), kSpreadThreads, kTileBytes, s>>>(                 \
@@ -576,31 +576,31 @@ void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_pix");
-        hook.end(HVOX_STAGE_SPREAD, 1);
+        hook.end(HVOX_STAGE_SPREAD, 1, s);
     }
     const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
-    hook.begin(HVOX_STAGE_DECONV);
+    hook.begin(HVOX_STAGE_DECONV, s);
     deconv_pad_kernel<T><<<dim3((unsigned)((b.n2[0] + 127) / 128), (unsigned)b.n2[1], (unsigned)b.n2[2]), 128, 0, s>>>(
         b, a.G1, a.ipsi + b.psi_off, a.G2);
     check_cuda(cudaGetLastError(), "deconv_pad");
-    hook.end(HVOX_STAGE_DECONV, 1);
-    hook.begin(HVOX_STAGE_FFT);
+    hook.end(HVOX_STAGE_DECONV, 1, s);
+    hook.begin(HVOX_STAGE_FFT, s);
     check_cufft(cufftSetStream(a.fft, s), "cufftSetStream");
     const int dir = a.isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
     if constexpr (sizeof(T) == 4)
         check_cufft(cufftExecC2C(a.fft, (cufftComplex *)a.G2, (cufftComplex *)a.G2, dir), "cufftExecC2C");
     else
         check_cufft(cufftExecZ2Z(a.fft, (cufftDoubleComplex *)a.G2, (cufftDoubleComplex *)a.G2, dir), "cufftExecZ2Z");
-    hook.end(HVOX_STAGE_FFT, 1);
+    hook.end(HVOX_STAGE_FFT, 1, s);
     if (b.nv > 0) {
-        hook.begin(HVOX_STAGE_INTERP);
+        hook.begin(HVOX_STAGE_INTERP, s);
 #define CALL(W)                                                                                                   \
     interp_vis_kernel<T, W><<<blocks_for(b.nv, 128), 128, 0, s>>>(b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, a.G2, \
                                                                   a.cheb, a.deg, (T)a.inv_tmax2, acc, bt, a.isign)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "interp_vis");
-        hook.end(HVOX_STAGE_INTERP, 1);
+        hook.end(HVOX_STAGE_INTERP, 1, s);
     }
 }
 
@@ -610,12 +610,12 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
     const int w = a.w;
     const T bt = (T)a.beta;
     const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
-    hook.begin(HVOX_STAGE_ZERO);
+    hook.begin(HVOX_STAGE_ZERO, s);
     check_cuda(cudaMemsetAsync(a.G2, 0, sizeof(cplx_t<T>) * m2, s), "memset G2");
-    hook.end(HVOX_STAGE_ZERO, 1);
+    hook.end(HVOX_STAGE_ZERO, 1, s);
     const int cap = kTileBytes / (int)sizeof(cplx_t<T>);
     if (b.nv > 0) {
-        hook.begin(HVOX_STAGE_SPREAD);
+        hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
     spread_vis_kernel<T, W><<<blocks_for(b.nv, kSpreadThreads), kSpreadThreads, kTileBytes, s>>>(                 \
@@ -623,31 +623,31 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_vis");
-        hook.end(HVOX_STAGE_SPREAD, 1);
+        hook.end(HVOX_STAGE_SPREAD, 1, s);
     }
-    hook.begin(HVOX_STAGE_FFT);
+    hook.begin(HVOX_STAGE_FFT, s);
     check_cufft(cufftSetStream(a.fft, s), "cufftSetStream");
     const int dir = a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD;  // transpose: opposite sign
     if constexpr (sizeof(T) == 4)
         check_cufft(cufftExecC2C(a.fft, (cufftComplex *)a.G2, (cufftComplex *)a.G2, dir), "cufftExecC2C");
     else
         check_cufft(cufftExecZ2Z(a.fft, (cufftDoubleComplex *)a.G2, (cufftDoubleComplex *)a.G2, dir), "cufftExecZ2Z");
-    hook.end(HVOX_STAGE_FFT, 1);
+    hook.end(HVOX_STAGE_FFT, 1, s);
     const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
-    hook.begin(HVOX_STAGE_DECONV);
+    hook.begin(HVOX_STAGE_DECONV, s);
     crop_deconv_kernel<T><<<dim3((unsigned)((b.n1[0] + 127) / 128), (unsigned)b.n1[1], (unsigned)b.n1[2]), 128, 0, s>>>(
         b, a.G2, a.ipsi + b.psi_off, a.G1);
     check_cuda(cudaGetLastError(), "crop_deconv");
-    hook.end(HVOX_STAGE_DECONV, 1);
+    hook.end(HVOX_STAGE_DECONV, 1, s);
     if (b.np > 0) {
-        hook.begin(HVOX_STAGE_INTERP);
+        hook.begin(HVOX_STAGE_INTERP, s);
 #define CALL(W)                                                                                                   \
     interp_pix_kernel<T, W><<<blocks_for(b.np, 128), 128, 0, s>>>(b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, a.G1, \
                                                                   acc, bt, a.isign)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "interp_pix");
-        hook.end(HVOX_STAGE_INTERP, 1);
+        hook.end(HVOX_STAGE_INTERP, 1, s);
     }
 }
 
