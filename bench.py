@@ -248,10 +248,11 @@ def run_gpu(args):
     vis = configs.visibilities_cn(args.config, w.n_vis)
 
     def measure(eps, with_e2e):
-        plan = hvox.Plan(w.pix, w.uvw, eps, mode=args.mode)
+        plan = hvox.Plan(w.pix, w.uvw, eps, mode=args.mode, graphs=args.graphs)
         info = plan.info()
         I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
         V = torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")
+        plan.profile(True)  # warm-up runs the profiled form too (its graph is captured there)
         time_steps(plan, I, V, args.warmup, flush)
         if world > 1:
             dist.barrier()
@@ -334,7 +335,7 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded HEALPix + layout)",
             "config": {"workload": WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
-                       "mode": args.mode, "core_radius": args.core_radius or None,
+                       "mode": args.mode, "core_radius": args.core_radius or None, "graphs": args.graphs,
                        "l2": "flushed before each step (256 MiB write, outside the timed window)",
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
                        "direct_pairs": info["direct_pairs"], "w": info["w"]},
@@ -375,6 +376,8 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
                     help="workload (2, the LOFAR-like case, is the benchmark; 1 and 3 for studies)")
     ap.add_argument("--mode", default="auto", choices=["auto", "nufft", "direct"])
+    ap.add_argument("--graphs", type=int, default=0, choices=[-1, 0, 1],
+                    help="CUDA graphs: 0 for plans with NUFFT sub-problems, 1 always, -1 never")
     ap.add_argument("--core-radius", type=float, default=0.0,
                     help="keep only baselines with |(u, v)| <= R wavelengths (dense-core study)")
     args = ap.parse_args()

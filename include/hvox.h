@@ -88,6 +88,13 @@ typedef struct {
     int32_t ntrans;              /* number of stacked inputs on one geometry; 0 -> 1 */
     int32_t plain;               /* 1: the plain reference form: FP64 arithmetic in every
                                     kernel, blocks launched one by one, no graph */
+    int32_t graphs;              /* CUDA graphs: 0 -> for plans with NUFFT sub-problems;
+                                    1 -> for every plan; -1 -> never (eager launches).
+                                    The first call of each direction runs eagerly; the
+                                    second captures the work between the permutations
+                                    (zeroing, direct launch, every sub-problem on its lane)
+                                    into one graph, which later calls replay. Ignored by
+                                    the plain form. */
     void *stream;                /* cudaStream_t; NULL = legacy default stream */
 } hvox_opts;
 
@@ -113,6 +120,8 @@ typedef struct {
     double workspace_bytes;      /* plan-owned device memory */
     double plan_seconds;         /* wall time of hvox_plan */
     double model_seconds;        /* cost-model estimate of one sky->vis plus one vis->sky */
+    int32_t graph_state;         /* 0: eager launches so far; 1: a graph has been captured
+                                    and is replayed; -1: capture failed, eager launches */
 } hvox_info;
 
 /*

@@ -37,7 +37,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("upsampfac", ctypes.c_double),
                 ("chunk_budget_bytes", ctypes.c_double), ("anisotropy", ctypes.c_double),
                 ("direct_threshold", ctypes.c_double), ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
-                ("stream", ctypes.c_void_p)]
+                ("graphs", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -50,7 +50,7 @@ class Info(ctypes.Structure):
                 ("direct_pairs", ctypes.c_double), ("nufft_points", ctypes.c_double),
                 ("nufft_cells", ctypes.c_double), ("max_grid_bytes", ctypes.c_double),
                 ("workspace_bytes", ctypes.c_double), ("plan_seconds", ctypes.c_double),
-                ("model_seconds", ctypes.c_double)]
+                ("model_seconds", ctypes.c_double), ("graph_state", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -256,7 +256,8 @@ class Plan:
 
     def __init__(self, pix, uvw, eps: float, isign: int = -1, weight=None, precision="auto", mode="auto",
                  upsampfac: float = 0.0, chunk_budget_bytes: float = 0.0, anisotropy: float = 0.0,
-                 direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, stream=None):
+                 direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, graphs: int = 0,
+                 stream=None):
         import torch
         lib = load()
         self._handle = ctypes.c_void_p()
@@ -272,6 +273,7 @@ class Plan:
         o.direct_threshold = direct_threshold
         o.ntrans = ntrans
         o.plain = 1 if plain else 0
+        o.graphs = int(graphs)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -65,8 +65,17 @@ Lane::~Lane() {
     if (stream) cudaStreamDestroy(stream);
 }
 
+GraphRun::~GraphRun() {
+    if (exec) cudaGraphExecDestroy(exec);
+    for (cudaEvent_t e : owned) cudaEventDestroy(e);
+    if (done) cudaEventDestroy(done);
+}
+
 Plan::~Plan() {
     cudaStreamSynchronize(stream);
+    for (auto &d : graph)
+        for (auto &g : d) g.reset();
+    if (cap) cudaStreamDestroy(cap);
     lanes.clear();
     if (fork_event) cudaEventDestroy(fork_event);
     for (auto &q : pending) {
@@ -376,6 +385,8 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.eps = eps;
     p.isign = isign;
     p.plain = o.plain != 0;
+    if (o.graphs < -1 || o.graphs > 1) fail(HVOX_EINVAL, "hvox_plan: graphs must be -1, 0 or 1");
+    p.graphs_opt = o.graphs;
     p.mode = eps == 0.0 ? HVOX_MODE_DIRECT : o.mode;
     p.prec = p.plain ? 2 : (o.precision == HVOX_PREC_AUTO ? (eps >= 1e-6 ? 1 : 2) : o.precision);
     p.ntrans = o.ntrans > 0 ? o.ntrans : 1;
@@ -419,6 +430,7 @@ void fill_info(const Plan &p, hvox_info *info) {
     info->workspace_bytes = p.workspace_bytes;
     info->plan_seconds = p.plan_seconds;
     info->model_seconds = p.part.model_seconds;
+    info->graph_state = p.graph_state;
 }
 
 void transform(Plan &p, const void *in, void *out, bool s2v) {

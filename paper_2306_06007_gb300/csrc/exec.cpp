@@ -1,6 +1,11 @@
 // Executor: one transform = permute in -> direct rectangles -> NUFFT sub-problems ->
 // permute out, all enqueued on the plan's stream (Fig. 6 flow: inputs to chunk order,
 // sub-transforms, row sums, outputs back to the caller's order).
+//
+// The part between the permutations touches plan-owned buffers only, so after one eager
+// call it is captured once per direction into a CUDA graph (the lanes forked from and
+// joined into the capture stream) and replayed on the plan's stream; the permutations,
+// whose pointers are the caller's, stay ordinary launches around the replay.
 #include <cuda_runtime.h>
 
 #include <map>
@@ -29,24 +34,39 @@ cudaEvent_t take_event(Plan &p) {
 // Counts launches per stage and, when profiling, brackets each stage with events on the
 // stream that runs it (the plan's stream or a NUFFT lane). Stage times are sums of the
 // stages' durations, so stages that overlap on different lanes add up.
+// While a graph is captured (g set), launch counts and stage brackets go to the graph, and
+// the brackets become event-record nodes whose events the graph owns.
 struct Profiler final : StageHook {
     Plan &p;
+    GraphRun *g = nullptr;
     std::map<cudaStream_t, cudaEvent_t> open;
-    explicit Profiler(Plan &plan) : p(plan) {}
+    explicit Profiler(Plan &plan, GraphRun *graph = nullptr) : p(plan), g(graph) {}
+    cudaEvent_t mark(cudaStream_t s) {
+        cudaEvent_t e;
+        if (g) {
+            check_cuda(cudaEventCreate(&e), "cudaEventCreate");
+            g->owned.push_back(e);
+            check_cuda(cudaEventRecordWithFlags(e, s, cudaEventRecordExternal), "cudaEventRecordWithFlags");
+        } else {
+            e = take_event(p);
+            check_cuda(cudaEventRecord(e, s), "cudaEventRecord");
+        }
+        return e;
+    }
     void begin(int, cudaStream_t s) override {
         if (!p.profiling) return;
-        cudaEvent_t e = take_event(p);
-        check_cuda(cudaEventRecord(e, s), "cudaEventRecord");
-        open[s] = e;
+        open[s] = mark(s);
     }
     void end(int stage, int launches, cudaStream_t s) override {
-        p.stage_launches[stage] += launches;
+        (g ? g->launches : p.stage_launches)[stage] += launches;
         if (!p.profiling) return;
         auto it = open.find(s);
         if (it == open.end()) return;
-        cudaEvent_t b = take_event(p);
-        check_cuda(cudaEventRecord(b, s), "cudaEventRecord");
-        p.pending.push_back({stage, it->second, b});
+        cudaEvent_t b = mark(s);
+        if (g)
+            g->brackets.push_back({stage, it->second, b});
+        else
+            p.pending.push_back({stage, it->second, b});
         open.erase(it);
     }
 };
@@ -71,18 +91,18 @@ template <typename T> NufftArgs<T> nufft_args(const Plan &p) {
     return a;
 }
 
-// Lanes start after everything enqueued so far on the plan's stream.
-void fork_lanes(Plan &p) {
+// Lanes start after everything enqueued so far on stream s.
+void fork_lanes(Plan &p, cudaStream_t s) {
     if (p.lanes.empty()) return;
-    check_cuda(cudaEventRecord(p.fork_event, p.stream), "cudaEventRecord");
+    check_cuda(cudaEventRecord(p.fork_event, s), "cudaEventRecord");
     for (auto &l : p.lanes) check_cuda(cudaStreamWaitEvent(l->stream, p.fork_event, 0), "cudaStreamWaitEvent");
 }
 
-// The plan's stream continues after every lane's work.
-void join_lanes(Plan &p) {
+// Stream s continues after every lane's work.
+void join_lanes(Plan &p, cudaStream_t s) {
     for (auto &l : p.lanes) {
         check_cuda(cudaEventRecord(l->done, l->stream), "cudaEventRecord");
-        check_cuda(cudaStreamWaitEvent(p.stream, l->done, 0), "cudaStreamWaitEvent");
+        check_cuda(cudaStreamWaitEvent(s, l->done, 0), "cudaStreamWaitEvent");
     }
 }
 
@@ -93,9 +113,187 @@ template <typename T> void set_lane(NufftArgs<T> &a, const Plan &p, size_t b) {
     a.fft = p.block_fft[b];
 }
 
+// sky -> vis between the permutations: src (chunk-ordered c_n) -> acc (chunk-ordered V).
+void body_s2v(Plan &p, cudaStream_t s, Profiler &prof) {
+    const size_t re = real_bytes(p);
+    prof.begin(HVOX_STAGE_ZERO, s);
+    check_cuda(cudaMemsetAsync(p.acc.ptr, 0, (size_t)p.n_vis * 2 * re, s), "memset acc");
+    prof.end(HVOX_STAGE_ZERO, 1, s);
+    fork_lanes(p, s);
+    if (p.n_items_s2v > 0) {
+        prof.begin(HVOX_STAGE_DIRECT, s);
+        const WorkItem *it = p.items_s2v.as<WorkItem>();
+        if (p.plain)
+            launch_direct_s2v_f64(it, p.n_items_s2v, p.vis_xyz.as<double>(), p.n_vis, p.pix_xyz.as<double>(),
+                                  p.n_pix, p.src.as<double>(), p.acc.as<double2>(), p.isign, p.direct_vpt, s);
+        else if (p.prec == 1)
+            launch_direct_s2v_f32(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
+                                  p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<float>(),
+                                  p.acc.as<float2>(), p.isign, p.direct_vpt, s);
+        else
+            launch_direct_s2v_df(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
+                                 p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<double>(),
+                                 p.acc.as<double2>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
+        prof.end(HVOX_STAGE_DIRECT, 1, s);
+    }
+    if (!p.dblocks.empty()) {
+        if (p.prec == 1) {
+            NufftArgs<float> a = nufft_args<float>(p);
+            for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                set_lane(a, p, b);
+                nufft_block_s2v<float>(p.dblocks[b], a, p.src.as<float>(), p.acc.as<float2>(),
+                                       p.lanes[p.block_lane[b]]->stream, prof);
+            }
+        } else {
+            NufftArgs<double> a = nufft_args<double>(p);
+            for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                set_lane(a, p, b);
+                nufft_block_s2v<double>(p.dblocks[b], a, p.src.as<double>(), p.acc.as<double2>(),
+                                        p.lanes[p.block_lane[b]]->stream, prof);
+            }
+        }
+    }
+    join_lanes(p, s);
+}
+
+// vis -> sky between the permutations: src (chunk-ordered V) -> acc (chunk-ordered I).
+void body_v2s(Plan &p, cudaStream_t s, Profiler &prof) {
+    const size_t re = real_bytes(p);
+    prof.begin(HVOX_STAGE_ZERO, s);
+    check_cuda(cudaMemsetAsync(p.acc.ptr, 0, (size_t)p.n_pix * re, s), "memset acc");
+    prof.end(HVOX_STAGE_ZERO, 1, s);
+    fork_lanes(p, s);
+    if (p.n_items_v2s > 0) {
+        prof.begin(HVOX_STAGE_DIRECT, s);
+        const WorkItem *it = p.items_v2s.as<WorkItem>();
+        if (p.plain)
+            launch_direct_v2s_f64(it, p.n_items_v2s, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(),
+                                  p.n_vis, p.src.as<double2>(), p.acc.as<double>(), p.isign, p.direct_vpt, s);
+        else if (p.prec == 1)
+            launch_direct_v2s_f32(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
+                                  p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<float2>(),
+                                  p.acc.as<float>(), p.isign, p.direct_vpt, s);
+        else
+            launch_direct_v2s_df(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
+                                 p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<double2>(),
+                                 p.acc.as<double>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
+        prof.end(HVOX_STAGE_DIRECT, 1, s);
+    }
+    if (!p.dblocks.empty()) {
+        if (p.prec == 1) {
+            NufftArgs<float> a = nufft_args<float>(p);
+            for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                set_lane(a, p, b);
+                nufft_block_v2s<float>(p.dblocks[b], a, p.src.as<float2>(), p.acc.as<float>(),
+                                       p.lanes[p.block_lane[b]]->stream, prof);
+            }
+        } else {
+            NufftArgs<double> a = nufft_args<double>(p);
+            for (size_t b = 0; b < p.dblocks.size(); ++b) {
+                set_lane(a, p, b);
+                nufft_block_v2s<double>(p.dblocks[b], a, p.src.as<double2>(), p.acc.as<double>(),
+                                        p.lanes[p.block_lane[b]]->stream, prof);
+            }
+        }
+    }
+    join_lanes(p, s);
+}
+
+void body(Plan &p, int dir, cudaStream_t s, Profiler &prof) {
+    if (dir == 0)
+        body_s2v(p, s, prof);
+    else
+        body_v2s(p, s, prof);
+}
+
+bool graphs_wanted(const Plan &p) {
+    if (p.plain || p.graph_state < 0 || p.graphs_opt < 0) return false;
+    return p.graphs_opt > 0 || !p.dblocks.empty();
+}
+
+// Gives up on graphs for this plan after a failed capture: ends the capture, drops the
+// partial graph and the sticky capture error; later calls launch eagerly.
+void abandon_capture(Plan &p) {
+    cudaGraph_t g = nullptr;
+    cudaStreamEndCapture(p.cap, &g);
+    if (g) cudaGraphDestroy(g);
+    (void)cudaGetLastError();
+    p.graph_state = -1;
+}
+
+std::unique_ptr<GraphRun> capture(Plan &p, int dir) {
+    auto g = std::make_unique<GraphRun>();
+    if (!p.cap) check_cuda(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking), "cudaStreamCreate");
+    check_cuda(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming), "cudaEventCreate");
+    check_cuda(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    try {
+        Profiler prof(p, g.get());
+        body(p, dir, p.cap, prof);
+    } catch (const Error &) {
+        abandon_capture(p);
+        return nullptr;
+    }
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamEndCapture(p.cap, &graph) != cudaSuccess || !graph) {
+        if (graph) cudaGraphDestroy(graph);
+        (void)cudaGetLastError();
+        p.graph_state = -1;
+        return nullptr;
+    }
+    const cudaError_t e = cudaGraphInstantiate(&g->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        (void)cudaGetLastError();
+        p.graph_state = -1;
+        return nullptr;
+    }
+    p.graph_state = 1;
+    return g;
+}
+
+// Adds the stage times of a profiled replay to the plan's statistics.
+void harvest(Plan &p, GraphRun &g) {
+    if (!g.outstanding) return;
+    check_cuda(cudaEventSynchronize(g.done), "cudaEventSynchronize");
+    for (auto &b : g.brackets) {
+        float ms = 0.f;
+        check_cuda(cudaEventElapsedTime(&ms, b.a, b.b), "cudaEventElapsedTime");
+        p.stage_ms[b.stage] += ms;
+    }
+    g.outstanding = false;
+}
+
+void execute(Plan &p, int dir) {
+    cudaStream_t s = p.stream;
+    if (!graphs_wanted(p) || p.eager_calls[dir] < 1) {
+        p.eager_calls[dir]++;
+        Profiler prof(p);
+        body(p, dir, s, prof);
+        return;
+    }
+    std::unique_ptr<GraphRun> &slot = p.graph[dir][p.profiling ? 1 : 0];
+    if (!slot) slot = capture(p, dir);
+    if (!slot) {
+        Profiler prof(p);
+        body(p, dir, s, prof);
+        return;
+    }
+    GraphRun &g = *slot;
+    harvest(p, g);
+    check_cuda(cudaGraphLaunch(g.exec, s), "cudaGraphLaunch");
+    for (int i = 0; i < HVOX_NUM_STAGES; ++i) p.stage_launches[i] += g.launches[i];
+    if (p.profiling) {
+        check_cuda(cudaEventRecord(g.done, s), "cudaEventRecord");
+        g.outstanding = true;
+    }
+}
+
 }  // namespace
 
 void collect_stats(Plan &p) {
+    for (auto &d : p.graph)
+        for (auto &g : d)
+            if (g) harvest(p, *g);
     if (p.pending.empty()) return;
     check_cuda(cudaStreamSynchronize(p.stream), "collect_stats");
     for (auto &q : p.pending) {
@@ -118,42 +316,7 @@ void run_synthesize(Plan &p, const void *I, void *V) {
         prof.begin(HVOX_STAGE_PERMUTE, s);
         launch_s2v_in(p.prec, It, p.pix_perm.as<int32_t>(), weight_ptr(p), p.n_pix, p.src.ptr, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
-        prof.begin(HVOX_STAGE_ZERO, s);
-        check_cuda(cudaMemsetAsync(p.acc.ptr, 0, (size_t)p.n_vis * 2 * re, s), "memset acc");
-        prof.end(HVOX_STAGE_ZERO, 1, s);
-        fork_lanes(p);
-        if (p.n_items_s2v > 0) {
-            prof.begin(HVOX_STAGE_DIRECT, s);
-            const WorkItem *it = p.items_s2v.as<WorkItem>();
-            if (p.plain)
-                launch_direct_s2v_f64(it, p.n_items_s2v, p.vis_xyz.as<double>(), p.n_vis, p.pix_xyz.as<double>(),
-                                      p.n_pix, p.src.as<double>(), p.acc.as<double2>(), p.isign, p.direct_vpt, s);
-            else if (p.prec == 1)
-                launch_direct_s2v_f32(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
-                                      p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<float>(),
-                                      p.acc.as<float2>(), p.isign, p.direct_vpt, s);
-            else
-                launch_direct_s2v_df(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
-                                     p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<double>(),
-                                     p.acc.as<double2>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
-            prof.end(HVOX_STAGE_DIRECT, 1, s);
-        }
-        if (!p.dblocks.empty()) {
-            if (p.prec == 1) {
-                NufftArgs<float> a = nufft_args<float>(p);
-                for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                    set_lane(a, p, b);
-                    nufft_block_s2v<float>(p.dblocks[b], a, p.src.as<float>(), p.acc.as<float2>(), p.lanes[p.block_lane[b]]->stream, prof);
-                }
-            } else {
-                NufftArgs<double> a = nufft_args<double>(p);
-                for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                    set_lane(a, p, b);
-                    nufft_block_s2v<double>(p.dblocks[b], a, p.src.as<double>(), p.acc.as<double2>(), p.lanes[p.block_lane[b]]->stream, prof);
-                }
-            }
-        }
-        join_lanes(p);
+        execute(p, 0);
         prof.begin(HVOX_STAGE_PERMUTE, s);
         launch_s2v_out(p.prec, p.acc.ptr, p.vis_perm.as<int32_t>(), p.n_vis, Vt, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
@@ -171,42 +334,7 @@ void run_analyze(Plan &p, const void *V, void *I) {
         prof.begin(HVOX_STAGE_PERMUTE, s);
         launch_v2s_in(p.prec, Vt, p.vis_perm.as<int32_t>(), p.n_vis, p.src.ptr, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
-        prof.begin(HVOX_STAGE_ZERO, s);
-        check_cuda(cudaMemsetAsync(p.acc.ptr, 0, (size_t)p.n_pix * re, s), "memset acc");
-        prof.end(HVOX_STAGE_ZERO, 1, s);
-        fork_lanes(p);
-        if (p.n_items_v2s > 0) {
-            prof.begin(HVOX_STAGE_DIRECT, s);
-            const WorkItem *it = p.items_v2s.as<WorkItem>();
-            if (p.plain)
-                launch_direct_v2s_f64(it, p.n_items_v2s, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(),
-                                      p.n_vis, p.src.as<double2>(), p.acc.as<double>(), p.isign, p.direct_vpt, s);
-            else if (p.prec == 1)
-                launch_direct_v2s_f32(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
-                                      p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<float2>(),
-                                      p.acc.as<float>(), p.isign, p.direct_vpt, s);
-            else
-                launch_direct_v2s_df(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
-                                     p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<double2>(),
-                                     p.acc.as<double>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
-            prof.end(HVOX_STAGE_DIRECT, 1, s);
-        }
-        if (!p.dblocks.empty()) {
-            if (p.prec == 1) {
-                NufftArgs<float> a = nufft_args<float>(p);
-                for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                    set_lane(a, p, b);
-                    nufft_block_v2s<float>(p.dblocks[b], a, p.src.as<float2>(), p.acc.as<float>(), p.lanes[p.block_lane[b]]->stream, prof);
-                }
-            } else {
-                NufftArgs<double> a = nufft_args<double>(p);
-                for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                    set_lane(a, p, b);
-                    nufft_block_v2s<double>(p.dblocks[b], a, p.src.as<double2>(), p.acc.as<double>(), p.lanes[p.block_lane[b]]->stream, prof);
-                }
-            }
-        }
-        join_lanes(p);
+        execute(p, 1);
         prof.begin(HVOX_STAGE_PERMUTE, s);
         launch_v2s_out(p.prec, p.acc.ptr, p.pix_perm.as<int32_t>(), weight_ptr(p), p.n_pix, It, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);

@@ -191,6 +191,22 @@ struct Lane {
     ~Lane();
 };
 
+// One captured CUDA graph of the middle of a transform (everything between the two
+// permutations), for one direction and one profiling state.
+struct GraphRun {
+    struct Bracket {
+        int stage;
+        cudaEvent_t a, b;
+    };
+    cudaGraphExec_t exec = nullptr;
+    int64_t launches[HVOX_NUM_STAGES] = {0};  // kernel launches per replay, by stage
+    std::vector<Bracket> brackets;            // stage brackets (profiled variant: event nodes)
+    std::vector<cudaEvent_t> owned;           // events referenced by the event nodes
+    cudaEvent_t done = nullptr;               // recorded after a profiled replay
+    bool outstanding = false;                 // a profiled replay not yet read back
+    ~GraphRun();
+};
+
 struct Plan {
     // statistics
     bool profiling = false;
@@ -251,6 +267,13 @@ struct Plan {
     // per-call buffers (chunk order)
     DevBuf src, acc;                    // source values, accumulated outputs
     DevBuf io_in, io_out;               // staging for host-pointer calls
+
+    // CUDA graphs (per direction, per profiling state)
+    int graphs_opt = 0;                 // hvox_opts.graphs
+    int graph_state = 0;                // 0 eager so far, 1 captured, -1 capture failed
+    int eager_calls[2] = {0, 0};
+    cudaStream_t cap = nullptr;         // capture stream
+    std::unique_ptr<GraphRun> graph[2][2];
 
     double workspace_bytes = 0;
     ~Plan();

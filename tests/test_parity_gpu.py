@@ -198,3 +198,56 @@ def test_config3_dense_core_nufft_sampled(gpu_lib):
     kp = configs.sample_indices(3, w.n_pix, 300, purpose_offset=1)
     assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
     assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_graph_replay_matches_eager_and_oracle(gpu_lib, small, eps):
+    # The first call of each direction runs eagerly, the second captures a CUDA graph,
+    # later calls replay it; every call's result must agree with the eager plan and the
+    # oracle, and the graph's stage statistics must count the same launches.
+    w = small
+    rng = np.random.default_rng(21)
+    graph = gpu_lib.Plan(w.pix, w.uvw, eps, mode="nufft")
+    eager = gpu_lib.Plan(w.pix, w.uvw, eps, mode="nufft", graphs=-1)
+    tol = 1e-12 if eps < 1e-6 else 2e-6
+    for call in range(4):
+        sky = rng.lognormal(0.0, 1.0, w.n_pix)
+        vis = rng.normal(size=w.n_vis) + 1j * rng.normal(size=w.n_vis)
+        if call == 3:
+            graph.profile(True)
+            eager.profile(True)
+        outs = []
+        for plan in (graph, eager):
+            I = torch.as_tensor(sky, dtype=plan.real_dtype, device="cuda")
+            Y = torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")
+            outs.append((plan.synthesize(I).cpu().numpy(), plan.analyze(Y).cpu().numpy()))
+        (Vg, Ig), (Ve, Ie) = outs
+        assert oracle.rel_l2(Vg, Ve) <= tol and oracle.rel_l2(Ig, Ie) <= tol, call
+        assert oracle.rel_l2(Vg, oracle.sky2vis(w.pix, w.uvw, sky)) <= 10 * eps
+        assert oracle.rel_l2(Ig, oracle.vis2sky(w.pix, w.uvw, vis)) <= 10 * eps
+    assert graph.info()["graph_state"] == 1
+    assert eager.info()["graph_state"] == 0
+    sg, se = graph.stats(), eager.stats()
+    assert sg["launches"] == se["launches"] and sg["transforms"] == se["transforms"] == 2
+    assert sg["ms"]["spread"] > 0 and sg["ms"]["fft"] > 0 and sg["ms"]["interp"] > 0
+    graph.close()
+    eager.close()
+
+
+def test_ntrans_stacked_inputs(gpu_lib, small):
+    # ntrans inputs on one geometry (Stokes-like batching): row t of the output is the
+    # transform of row t of the input.
+    w = small
+    rng = np.random.default_rng(8)
+    nt = 3
+    sky = rng.lognormal(0.0, 1.0, (nt, w.n_pix))
+    vis = rng.normal(size=(nt, w.n_vis)) + 1j * rng.normal(size=(nt, w.n_vis))
+    for mode in ("nufft", "direct"):
+        plan = gpu_lib.Plan(w.pix, w.uvw, 1e-6, mode=mode, ntrans=nt)
+        V = plan.synthesize(torch.as_tensor(sky, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+        img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
+        plan.close()
+        assert V.shape == (nt, w.n_vis) and img.shape == (nt, w.n_pix)
+        for t in range(nt):
+            assert oracle.rel_l2(V[t], oracle.sky2vis(w.pix, w.uvw, sky[t])) <= 1e-5
+            assert oracle.rel_l2(img[t], oracle.vis2sky(w.pix, w.uvw, vis[t])) <= 1e-5
