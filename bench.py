@@ -35,21 +35,23 @@ WORKLOAD = ("LOFAR-like: HEALPix nside=256 30deg cap (52,812 px) x 300 antennas 
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9  # FP32 FMA pipes x 2 flops x max SM clock
 FLOPS_PER_PAIR = 16.0                      # algorithmic flops per (pixel, baseline) pair
 
-# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum, one ncu capture of the
-# full-size launch, mean of the s2v and v2s launches) of the direct kernels on the LOFAR-like
-# workload, keyed by eps and valid only for the kernel source it was taken on.
-DIRECT_TRAFFIC = {1e-9: ("7f4f0480f14dbade7037a41dfe7425566a74fc3e606adc27b6418d123b95b22f", 178229120.0)}
+# From one ncu capture of the direct kernels on the LOFAR-like workload at eps = 1e-9, valid
+# only for the kernel source it was taken on: DRAM bytes per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum of the full-size launches, mean of the s2v and v2s launches) and
+# thread instructions per pair (smsp__inst_executed.sum x 32 / pairs, 100k-baseline case).
+DIRECT_COUNTERS = {1e-9: ("71c72a72750d4bb921bcac36cd22146352882ab164057f2aaca6a7eaa68f93be", 205507840.0, 80.7)}
 
 
-def direct_traffic(eps, config, core_radius, n_vis):
+def direct_counters(eps, config, other_workload, n_vis):
+    """(traffic bytes per launch, instructions per pair) or (None, None)."""
     import hashlib
-    entry = DIRECT_TRAFFIC.get(eps)
-    if entry is None or config != 2 or core_radius or n_vis:
-        return None
+    entry = DIRECT_COUNTERS.get(eps)
+    if entry is None or config != 2 or other_workload or n_vis:
+        return None, None
     path = os.path.join(ROOT, "paper_2306_06007_gb300", "csrc", "k_direct.cu")
     with open(path, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()
-    return entry[1] if digest == entry[0] else None
+    return (entry[1], entry[2]) if digest == entry[0] else (None, None)
 
 
 def dist_env():
@@ -64,9 +66,11 @@ WORKLOADS = {
 }
 
 
-def load_workload(n_vis=None, config=2, core_radius=0.0):
+def load_workload(n_vis=None, config=2, core_radius=0.0, radius_km=0.0, sparse=0):
     import numpy as np
     from hvox_inputs import configs
+    if radius_km > 0:  # telescope-radius sweep (Table 3 setups), optionally a sparse sky
+        return configs.radius_sweep(radius_km, sparse_pixels=sparse)
     w = configs.CONFIGS[config]()
     if core_radius > 0:  # dense core only: baselines with |(u, v)| <= core_radius wavelengths
         w.uvw = np.ascontiguousarray(w.uvw[np.hypot(w.uvw[:, 0], w.uvw[:, 1]) <= core_radius])
@@ -242,7 +246,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    w = load_workload(args.n_vis, args.config, args.core_radius)
+    w = load_workload(args.n_vis, args.config, args.core_radius, args.radius_km, args.sparse)
     units_per_step = 2.0 * (w.n_pix + w.n_vis)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
     vis = configs.visibilities_cn(args.config, w.n_vis)
@@ -311,13 +315,18 @@ def run_gpu(args):
     if dom == "direct":
         pairs_per_launch = info["direct_pairs"]
         achieved = pairs_per_launch * FLOPS_PER_PAIR / avg_s
+        traffic, ipp = direct_counters(args.eps, args.config, args.core_radius or args.radius_km, args.n_vis)
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
-                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_FLOPS,
-                    "traffic": direct_traffic(args.eps, args.config, args.core_radius, args.n_vis),
+                    "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_FLOPS, "traffic": traffic,
                     "kernel": "direct_s2v + direct_v2s (one launch each per step)",
                     "pairs_per_launch": pairs_per_launch, "avg_launch_ms": avg_s * 1e3,
                     "pairs_per_s": pairs_per_launch / avg_s,
                     "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
+        if ipp is not None:
+            # FP32-pipe instruction issue against the same pipes' peak (one instruction per
+            # lane per cycle): how close the kernel runs to the hardware it is bound by.
+            roofline["instr_per_pair"] = ipp
+            roofline["issue_frac"] = ipp * pairs_per_launch / avg_s / (FP32_PEAK_FLOPS / 2.0)
     elif dom in ("spread", "interp"):
         # Every NUFFT point is spread once and interpolated once per step (w^3 taps each),
         # 4 flops per tap (complex value times a real weight, accumulated).
@@ -334,7 +343,8 @@ def run_gpu(args):
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded HEALPix + layout)",
-            "config": {"workload": WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
+            "config": {"workload": w.name + "; step = sky->vis + vis->sky" if args.radius_km > 0
+                       else WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
                        "mode": args.mode, "core_radius": args.core_radius or None, "graphs": args.graphs,
                        "l2": "flushed before each step (256 MiB write, outside the timed window)",
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
@@ -376,6 +386,9 @@ def main():
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
                     help="workload (2, the LOFAR-like case, is the benchmark; 1 and 3 for studies)")
     ap.add_argument("--mode", default="auto", choices=["auto", "nufft", "direct"])
+    ap.add_argument("--radius-km", type=float, default=0.0,
+                    help="study: telescope-radius sweep workload (0.1, 0.3, 1, 3, 10, 30 or 100 km)")
+    ap.add_argument("--sparse", type=int, default=0, help="study: keep this many sky pixels (sparse sky)")
     ap.add_argument("--graphs", type=int, default=0, choices=[-1, 0, 1],
                     help="CUDA graphs: 0 for plans with NUFFT sub-problems, 1 always, -1 never")
     ap.add_argument("--core-radius", type=float, default=0.0,

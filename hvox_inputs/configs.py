@@ -142,6 +142,50 @@ def small_case(seed: int, n_pix: int, n_vis: int, cap_deg: float = 30.0, radius_
 CONFIGS = {1: config1, 2: config2, 3: config3, 4: config4}
 
 
+# Telescope-radius sweep (the paper's Table 3 setups): radius (km) -> (N_vis, N_pix). One
+# SKA-Low-like layout of 888 antennas in annuli whose cumulative counts (24, 162, 437, 545,
+# 690, 826, 888 within 0.1 .. 100 km) give the table's visibility counts as all pairs
+# within the radius; one snapshot at transit, lambda 2 m. The sky is the first N_pix RING
+# pixels around +z at the HEALPix resolution that puts two pixels in the finest fringe
+# (nside = ceil(4.1 R / lambda)), I ~ lognormal(0, 1).
+RADIUS_TABLE = {0.1: (273, 6_400), 0.3: (13_000, 25_600), 1.0: (95_000, 130_000), 3.0: (148_000, 810_000),
+                10.0: (238_000, 10_240_000), 30.0: (341_000, 74_650_000), 100.0: (394_000, 182_250_000)}
+SWEEP_EDGES_KM = (0.0, 0.1, 0.3, 1.0, 3.0, 10.0, 30.0, 100.0)
+SWEEP_COUNTS = (24, 138, 275, 108, 145, 136, 62)
+
+
+def sweep_antennas() -> np.ndarray:
+    return layouts.annuli(rng_for(6, 1), [e * 1e3 for e in SWEEP_EDGES_KM], SWEEP_COUNTS, 5.0)
+
+
+def radius_sweep(radius_km: float, lam: float = 2.0, sparse_pixels: int = 0) -> Workload:
+    """Radius-sweep workload; sparse_pixels > 0 keeps only that many pixels of interest,
+    in 5 compact groups around seeded directions of the field (the sparse-sky setup)."""
+    radius_km = float(radius_km)
+    if radius_km not in RADIUS_TABLE:
+        raise ValueError(f"radius must be one of {sorted(RADIUS_TABLE)} km")
+    ant = sweep_antennas()
+    ant = ant[np.hypot(ant[:, 0], ant[:, 1]) <= radius_km * 1e3]
+    uvw = layouts.baselines(ant, [0.0], -26.7, [lam])
+    n_pix = RADIUS_TABLE[radius_km][1]
+    nside = int(math.ceil(4.1 * radius_km * 1e3 / lam))
+    pix = healpix.cap_pixels(nside, 90.0, max_pixels=n_pix)
+    name = f"radius {radius_km:g} km: {len(ant)} antennas, HEALPix nside={nside} first {len(pix)} RING pixels"
+    if sparse_pixels > 0:
+        rng = rng_for(6, 3)
+        centres = pix[rng.choice(len(pix), 5, replace=False)]
+        per = -(-sparse_pixels // 5)
+        keep = []
+        for c in centres:
+            d = np.einsum("ij,j->i", pix, c)
+            keep.append(np.argpartition(-d, per)[:per])
+        idx = np.unique(np.concatenate(keep))[:sparse_pixels]
+        pix = np.ascontiguousarray(pix[idx])
+        name += f", sparse: {len(pix)} pixels in 5 groups"
+    sky = rng_for(6, 2).lognormal(0.0, 1.0, len(pix))
+    return Workload(name, pix, uvw, sky, (1e-6,))
+
+
 def _cap_for(n_pix: int, cap_deg: float = 40.0) -> np.ndarray:
     """The first n_pix RING pixels of the smallest nside whose cap_deg cap holds n_pix."""
     nside = 1

@@ -38,6 +38,18 @@ def core_plus_arms(rng: np.random.Generator, n: int, core_frac: float, core_sigm
     return np.concatenate([core, outer], axis=0)
 
 
+def annuli(rng: np.random.Generator, edges_m, counts, sigma_z_m: float) -> np.ndarray:
+    """counts[k] antennas uniform in area in the annulus edges_m[k] <= r < edges_m[k + 1]."""
+    parts = []
+    for k, n in enumerate(counts):
+        r0, r1 = edges_m[k], edges_m[k + 1]
+        r = np.sqrt(rng.uniform(r0 * r0, r1 * r1, n))
+        t = rng.uniform(0.0, 2.0 * math.pi, n)
+        z = rng.normal(0.0, sigma_z_m, n)
+        parts.append(np.stack([r * np.cos(t), r * np.sin(t), z], axis=1))
+    return np.concatenate(parts, axis=0)
+
+
 def rotate_about_axis(v: np.ndarray, axis: np.ndarray, angle_rad: float) -> np.ndarray:
     a = axis / np.linalg.norm(axis)
     c, s = math.cos(angle_rad), math.sin(angle_rad)

@@ -177,6 +177,13 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     in.elem_bytes = elem;
     in.sigma_auto = p.sigma_auto;
     in.eps_es = p.eps_es;
+    {
+        // Up to kMaxLanes lanes each hold the grids of their largest sub-problem and a cuFFT
+        // work area of about the same size: keep that within a third of the free memory.
+        size_t free_b = 0, total_b = 0;
+        check_cuda(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+        in.max_budget = (double)free_b / (3.0 * 2.0 * kMaxLanes);
+    }
     p.part = make_partition(in);
     PartitionResult &part = p.part;
     p.sigma = part.sigma;
@@ -228,11 +235,11 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         p.n_items_v2s = (int64_t)b.size();
     }
 
-    // exp(j 2 pi m / 256), m = -512 .. 512, split into float pairs (double-float direct path).
+    // exp(j 2 pi m / 2048), m = 0 .. 2047, split into float pairs (double-float direct path).
     {
-        std::vector<float> tab(1025 * 4);
-        for (int i = 0; i < 1025; ++i) {
-            double ang = 2.0 * M_PI * (double)(i - 512) / 256.0;
+        std::vector<float> tab(2048 * 4);
+        for (int i = 0; i < 2048; ++i) {
+            double ang = 2.0 * M_PI * (double)i / 2048.0;
             double c = std::cos(ang), sn = std::sin(ang);
             float ch = (float)c, sh = (float)sn;
             tab[4 * i + 0] = ch;

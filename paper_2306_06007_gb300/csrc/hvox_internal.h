@@ -122,6 +122,7 @@ struct PlanInputs {
     int mode;
     bool plain;
     double budget;         // 0 -> search
+    double max_budget = 0; // > 0: largest budget the search may pick (device memory)
     double direct_threshold;
     int elem_bytes;
 };
@@ -262,7 +263,7 @@ struct Plan {
     std::vector<NufftDev> dblocks;      // block descriptors (launch order)
     std::vector<int> block_lane;        // lane of each block
     std::vector<cufftHandle> block_fft; // FFT plan of each block (its lane's plan for its shape)
-    DevBuf cis_tab;                     // exp(j 2 pi m / 256) as float pairs (double-float path)
+    DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
 
     // per-call buffers (chunk order)
     DevBuf src, acc;                    // source values, accumulated outputs

@@ -119,40 +119,29 @@ __device__ __forceinline__ void phase_df(const float3 &ph, const float3 &pl, con
     fast_two_sum(s2, small, fh, fl);
 }
 
-constexpr int kTab = 256;      // table entries per turn
-constexpr int kTabOff = 512;   // m = round(256 f) in [-512, 512] for |f| < 2
-constexpr int kTabLen = 1025;
+constexpr int kTabN = 2048;    // table entries per turn; the table is periodic in m
 
-// exp(j 2 pi f) for f = fh + fl (turns, |fh| < 2) as two unevaluated float pairs
-// (re = reh + rel, im = imh + iml, |rel|, |iml| < 1e-4). T holds (cos_h, cos_l, sin_h,
-// sin_l) of 2 pi m / 256 for m = idx - kTabOff; the remainder x = 2 pi (f - m/256),
-// |x| <= pi/256, goes through short Taylor series.
-__device__ __forceinline__ void cis_df(float fh, float fl, const float4 *__restrict__ T, float &reh, float &rel,
-                                       float &imh, float &iml) {
-    const float TWO_PI_H = 6.28318548202514648f;        // fl32(2 pi)
-    const float TWO_PI_L = -1.74845553146951427e-07f;   // fl32(2 pi - TWO_PI_H)
-    const float t = __fadd_rn(__fmul_rn(fh, (float)kTab), kRoundMagic);  // m in the low mantissa bits
-    const int m = min(max(__float_as_int(t) - __float_as_int(kRoundMagic), -kTabOff), kTabOff);
-    const float mf = __fsub_rn(t, kRoundMagic);
-    const float d = __fmaf_rn(mf, -1.0f / kTab, fh);     // exact
-    float xh, xe;
-    two_prod(d, TWO_PI_H, xh, xe);
-    const float xl = __fadd_rn(xe, __fmaf_rn(d, TWO_PI_L, __fmul_rn(fl, TWO_PI_H)));
-    const float x2 = __fmul_rn(xh, xh);
-    // sin x = x - x^3/6 + x^5/120, cos x - 1 = -x^2/2 + x^4/24 - x^6/720 (|x| <= 0.0123)
-    const float sc = __fmul_rn(__fmul_rn(xh, x2), __fmaf_rn(x2, 1.0f / 120.0f, -1.0f / 6.0f));
-    const float cm = __fmul_rn(x2, __fmaf_rn(x2, __fmaf_rn(x2, -1.0f / 720.0f, 1.0f / 24.0f), -0.5f));
-    const float4 tb = T[m + kTabOff];
-    const float u = __fadd_rn(xl, sc);  // sin x = xh + u
-    float p1, p1e, p2, p2e;
-    two_prod(tb.z, xh, p1, p1e);   // sin_h * xh
-    two_prod(tb.x, xh, p2, p2e);   // cos_h * xh
-    float re;
-    two_sum(tb.x, -p1, reh, re);
-    rel = __fadd_rn(__fadd_rn(re, __fmaf_rn(tb.x, cm, tb.y)), -__fadd_rn(p1e, __fmaf_rn(tb.z, u, __fmul_rn(tb.w, xh))));
-    float ie;
-    two_sum(tb.z, p2, imh, ie);
-    iml = __fadd_rn(__fadd_rn(ie, __fmaf_rn(tb.z, cm, tb.w)), __fadd_rn(p2e, __fmaf_rn(tb.x, u, __fmul_rn(tb.y, xh))));
+// exp(j 2 pi f) for f = fh + fl (turns, |fh| < 1024) as re = reh + rel, im = imh + iml.
+// (reh, imh) are the hi parts of cos and sin of 2 pi m / 2048 for m = round(2048 fh), read
+// from T[m mod 2048] = (cos_h, cos_l, sin_h, sin_l). (rel, iml) collect the table's lo
+// parts and the rotation by x = 2 pi (fh - m/2048 + fl), |x| <= pi/2048, through
+// cos x - 1 = -x^2/2 and sin x = x - x^3/6 (dropped terms below 3e-13). Every term of a lo
+// part is below 1.6e-3 in magnitude, so plain float arithmetic keeps the pair within
+// ~2.5e-10 of exp(j 2 pi f); the hi parts need no error-free transformations.
+__device__ __forceinline__ void cis_tab(float fh, float fl, const float4 *__restrict__ T, float &reh, float &rel,
+                                        float &imh, float &iml) {
+    const float t = __fmaf_rn(fh, (float)kTabN, kRoundMagic);  // 1.5 * 2^23 + m
+    const int idx = __float_as_int(t) & (kTabN - 1);           // m mod 2048 (the magic's low bits are 0)
+    const float d = __fmaf_rn(__fsub_rn(t, kRoundMagic), -1.0f / kTabN, fh);  // fh - m/2048, exact
+    const float x = __fmul_rn(__fadd_rn(d, fl), 6.28318530717958648f);
+    const float x2 = __fmul_rn(x, x);
+    const float cm = __fmul_rn(x2, -0.5f);
+    const float sx = __fmaf_rn(__fmul_rn(x2, x), -1.0f / 6.0f, x);
+    const float4 tb = T[idx];
+    reh = tb.x;
+    rel = __fmaf_rn(-tb.z, sx, __fmaf_rn(tb.x, cm, tb.y));
+    imh = tb.z;
+    iml = __fmaf_rn(tb.x, sx, __fmaf_rn(tb.z, cm, tb.w));
 }
 
 __device__ __forceinline__ void df_mul(float ah, float al, float bh, float bl, float &ph, float &pl) {
@@ -182,7 +171,7 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
 }
 
 __device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ gT) {
-    for (int i = threadIdx.x; i < kTabLen; i += blockDim.x) sT[i] = gT[i];
+    for (int i = threadIdx.x; i < kTabN; i += blockDim.x) sT[i] = gT[i];
 }
 
 // ------------------------------------------------------------- sky -> vis
@@ -268,7 +257,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
     __shared__ float2 sc[kThreads];
-    __shared__ float4 sT[kTabLen];
+    __shared__ float4 sT[kTabN];
     load_tab(sT, gT);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
@@ -310,7 +299,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
                 for (int v = 0; v < VPT; ++v) {
                     float fh, fl, reh, rel, imh, iml;
                     phase_df(ph[v], pl[v], rh, rl, fh, fl);
-                    cis_df(fh, fl, sT, reh, rel, imh, iml);
+                    cis_tab(fh, fl, sT, reh, rel, imh, iml);
                     float th, tl;
                     df_mul(cv.x, cv.y, reh, rel, th, tl);
                     df_acc(arh[v], arl[v], th, tl);
@@ -464,7 +453,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
     __shared__ float4 sv[kThreads];
-    __shared__ float4 sT[kTabLen];
+    __shared__ float4 sT[kTabN];
     load_tab(sT, gT);
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
@@ -507,7 +496,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
                 for (int v = 0; v < VPT; ++v) {
                     float fh, fl, reh, rel, imh, iml;
                     phase_df(ph, pl, rh[v], rl[v], fh, fl);
-                    cis_df(fh, fl, sT, reh, rel, imh, iml);
+                    cis_tab(fh, fl, sT, reh, rel, imh, iml);
                     float th, tl;
                     df_mul(val.x, val.y, reh, rel, th, tl);
                     df_acc(ah[v], al[v], th, tl);

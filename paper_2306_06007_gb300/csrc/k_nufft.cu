@@ -64,9 +64,12 @@ template <typename T, int W> __device__ __forceinline__ void es_weights_rot(T fr
     }
 }
 
-__device__ __forceinline__ int64_t wrap(int64_t i, int64_t n) {
-    int64_t r = i % n;
-    return r < 0 ? r + n : r;
+// i mod n for i in [-n, 2n): window cells of points inside a sub-problem's band lie within
+// n2/2 + w of the origin and n2 >= 2w. The clamp keeps any index inside the grid.
+__device__ __forceinline__ int wrap(int i, int n) {
+    i += i < 0 ? n : 0;
+    i -= i >= n ? n : 0;
+    return min(max(i, 0), n - 1);
 }
 
 // ------------------------------------------------------------------ float helpers
@@ -301,29 +304,35 @@ __device__ __forceinline__ void spread_tiled(bool act, const int i0[3], const T 
             }
         }
         __syncthreads();
-        for (int64_t j = threadIdx.x; j < cells; j += blockDim.x) {
-            const cplx_t<T> v = tile[j];
-            if (v.x == T(0) && v.y == T(0)) continue;
-            const int64_t x = j % tx, r = j / tx;
-            const int64_t y = r % ty, z = r / ty;
-            int64_t gx = lo0 + x, gy = lo1 + y, gz = lo2 + z;
+        // Flush: one warp per (y, z) row of the tile, lanes along x (coalesced atomics).
+        const int txi = (int)tx, tyi = (int)ty, rows = (int)(ty * tz);
+        const int lane = threadIdx.x & 31;
+        for (int r = threadIdx.x >> 5; r < rows; r += blockDim.x >> 5) {
+            const int y = r % tyi, z = r / tyi;
+            int gy = lo1 + y, gz = lo2 + z;
             if (PERIODIC) {
-                gx = wrap(gx, ng[0]);
                 gy = wrap(gy, ng[1]);
                 gz = wrap(gz, ng[2]);
             }
-            grid_add(G + (gz * ng[1] + gy) * ng[0] + gx, v.x, v.y);
+            cplx_t<T> *grow = G + ((int64_t)gz * ng[1] + gy) * ng[0];
+            const cplx_t<T> *trow = tile + (int64_t)r * txi;
+            for (int x = lane; x < txi; x += 32) {
+                const cplx_t<T> v = trow[x];
+                if (v.x == T(0) && v.y == T(0)) continue;
+                const int gx = PERIODIC ? wrap(lo0 + x, ng[0]) : lo0 + x;
+                grid_add(grow + gx, v.x, v.y);
+            }
         }
     } else if (act) {
         int64_t ix[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) ix[j] = PERIODIC ? wrap((int64_t)i0[0] + j, ng[0]) : (int64_t)i0[0] + j;
+        for (int j = 0; j < W; ++j) ix[j] = PERIODIC ? wrap(i0[0] + j, ng[0]) : i0[0] + j;
         for (int jz = 0; jz < W; ++jz) {
             int jzr = jz + rot;
             jzr = jzr >= W ? jzr - W : jzr;
-            const int64_t gz = PERIODIC ? wrap((int64_t)i0[2] + jzr, ng[2]) : (int64_t)i0[2] + jzr;
+            const int64_t gz = PERIODIC ? wrap(i0[2] + jzr, ng[2]) : i0[2] + jzr;
             for (int jy = 0; jy < W; ++jy) {
-                const int64_t gy = PERIODIC ? wrap((int64_t)i0[1] + jy, ng[1]) : (int64_t)i0[1] + jy;
+                const int64_t gy = PERIODIC ? wrap(i0[1] + jy, ng[1]) : i0[1] + jy;
                 const T wyz = wy[jy] * wz[jz];
                 const T ar = vr * wyz, ai = vi * wyz;
                 cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
@@ -406,9 +415,9 @@ __global__ void __launch_bounds__(128) interp_vis_kernel(NufftDev b, const float
     int64_t ix[W], iy[W], iz[W];
 #pragma unroll
     for (int j = 0; j < W; ++j) {
-        ix[j] = wrap((int64_t)i0[0] + j, nx);
-        iy[j] = wrap((int64_t)i0[1] + j, ny) * nx;
-        iz[j] = wrap((int64_t)i0[2] + j, nz) * ny * nx;
+        ix[j] = wrap(i0[0] + j, (int)nx);
+        iy[j] = (int64_t)wrap(i0[1] + j, (int)ny) * nx;
+        iz[j] = (int64_t)wrap(i0[2] + j, (int)nz) * ny * nx;
     }
     T sr = 0, si = 0;
     for (int jz = 0; jz < W; ++jz) {

@@ -13,7 +13,9 @@
 //    chunk's point bounding box stays within h in every dimension.
 #include <algorithm>
 #include <cmath>
+#include <future>
 #include <numeric>
+#include <thread>
 
 #include "hvox_internal.h"
 
@@ -355,22 +357,43 @@ PartitionResult make_partition(const PlanInputs &in) {
         direct.mode = HVOX_MODE_DIRECT;
         best = evaluate(direct, m, 1e30, P, B);
     } else {
-        bool have = false;
         // Upsampling search (sigma trades FFT cells, ~sigma^6, against kernel width) and
-        // budget search: 256 KiB .. 1 GiB in factors of 8 (the cost model picks both).
+        // budget search: 256 KiB .. 8 GiB in factors of 8, capped by max_budget (the cost
+        // model picks both). Candidates are evaluated on up to 4 threads; the choice is the
+        // cheapest, the earliest candidate on ties, so it does not depend on the threading.
+        struct Cand {
+            double sigma, budget;
+            ESKernel es;
+        };
+        std::vector<Cand> cands;
         std::vector<double> sigmas = in.sigma_auto ? std::vector<double>{2.0, 1.5} : std::vector<double>{in.sigma};
         for (double sg : sigmas) {
-            PlanInputs cand = in;
-            cand.sigma = sg;
-            if (in.sigma_auto) cand.es = es_params(in.eps_es, sg);
-            for (double b = 256.0 * 1024.0; b <= 1.1e9; b *= 8.0) {
-                Evaluated e = evaluate(cand, m, b, P, B);
-                if (!have || e.cost < best.cost) {
-                    best = std::move(e);
-                    best_sigma = sg;
-                    best_es = cand.es;
-                    have = true;
+            const ESKernel es = in.sigma_auto ? es_params(in.eps_es, sg) : in.es;
+            for (double b = 256.0 * 1024.0; b <= 9.0e9; b *= 8.0) {
+                if (in.max_budget > 0 && b > in.max_budget && b > 256.0 * 1024.0) break;
+                cands.push_back({sg, b, es});
+            }
+        }
+        std::vector<Evaluated> evals(cands.size());
+        const size_t width = std::max<size_t>(1, std::min<size_t>(4, std::thread::hardware_concurrency()));
+        for (size_t c0 = 0; c0 < cands.size(); c0 += width) {
+            std::vector<std::future<void>> jobs;
+            for (size_t c = c0; c < std::min(cands.size(), c0 + width); ++c)
+                jobs.push_back(std::async(std::launch::async, [&, c] {
+                    PlanInputs cand = in;
+                    cand.sigma = cands[c].sigma;
+                    cand.es = cands[c].es;
+                    evals[c] = evaluate(cand, m, cands[c].budget, P, B);
+                }));
+            for (auto &j : jobs) j.get();
+            // keep only the best so far (bounds host memory on large point sets)
+            for (size_t c = c0; c < std::min(cands.size(), c0 + width); ++c) {
+                if (c == 0 || evals[c].cost < best.cost) {
+                    best = std::move(evals[c]);
+                    best_sigma = cands[c].sigma;
+                    best_es = cands[c].es;
                 }
+                evals[c] = Evaluated();
             }
         }
     }

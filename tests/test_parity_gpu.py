@@ -63,15 +63,17 @@ def test_weights_and_isign(gpu_lib, small, isign):
 
 @pytest.mark.parametrize("eps", [1e-6, 1e-9])
 def test_adjoint_pair_to_rounding(gpu_lib, small, eps):
-    # The vis->sky pipeline is the exact transpose of sky->vis (same grids, records and
-    # kernels), so Re<A x, y> = <x, A^H y> holds to rounding, not merely to eps.
+    # The vis->sky pipeline is the exact transpose of sky->vis (same grids, windows, phases
+    # and exponentials per pair), so Re<A x, y> = <x, A^H y> holds to rounding, not merely
+    # to eps. In the double-float direct kernels the lo part of each exponential (up to
+    # 1.6e-3) is multiplied in FP32, which rounds at ~1e-10 of a term.
     w = small
     for mode in ("nufft", "direct"):
         V, y, img, _ = _run(gpu_lib, w, eps, mode=mode)
         lhs = np.real(np.vdot(y, V))
         rhs = float(np.dot(w.sky, img))
         scale = np.linalg.norm(V) * np.linalg.norm(y)
-        tol = 1e-12 if eps < 1e-6 else 2e-5
+        tol = 1e-10 if eps < 1e-6 else 2e-5
         assert abs(lhs - rhs) <= tol * scale, (mode, lhs, rhs)
 
 
