@@ -79,7 +79,8 @@ typedef enum {
 typedef struct {
     int32_t precision;           /* hvox_prec */
     int32_t mode;                /* hvox_mode */
-    double upsampfac;            /* sigma of both NUFFT stages; 0 -> 2.0 (1.25 allowed) */
+    double upsampfac;            /* sigma of both NUFFT stages, in [1.25, 4]; 0 -> chosen by
+                                    the planner among 2, 1.5 and 1.25 */
     double chunk_budget_bytes;   /* FFT-grid budget B of one sub-problem (Algorithm 1);
                                     0 -> chosen by the planner's cost model */
     double anisotropy;           /* Algorithm 1 alpha >= 1; 0 -> 1 (isotropic optimum) */

@@ -116,7 +116,7 @@ struct PlanInputs {
     int64_t n_pix, n_vis;
     double sigma;          // upsampling (used when sigma_auto is false)
     ESKernel es;
-    bool sigma_auto = false;  // choose sigma in {2, 1.5} by the cost model
+    bool sigma_auto = false;  // choose sigma in {2, 1.5, 1.25} by the cost model
     double eps_es = 1e-6;     // tolerance given to the kernel-width rule
     int prec;              // 1 fp32, 2 fp64
     int mode;

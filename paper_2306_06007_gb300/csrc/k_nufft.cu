@@ -19,10 +19,12 @@
 // the FP64 path; for the FP32 path from the float hi/lo splits of the coordinates and of
 // C, D, a with exact differences and products, so no FP64 is used per point.
 //
-// Spreading: each CTA takes 256 consecutive points (chunk order is Morton order inside a
-// chunk, so they are close in space), accumulates their w^3 taps into a shared-memory
+// Spreading: each CTA takes 128 consecutive points (chunk order is Morton order inside a
+// chunk, in grid-cell units, so they are close on the grid), two threads per point each
+// taking half of the window's z planes, accumulates the w^3 taps into a shared-memory
 // tile that covers all their windows, then adds the tile to the grid with vector
 // atomics; when the tile would not fit, the CTA adds its taps to the grid directly.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 #include <vector>
@@ -35,7 +37,8 @@ namespace {
 
 template <typename T> using cplx_t = typename CplxOf<T>::type;
 
-constexpr int kSpreadThreads = 256;
+constexpr int kSpreadThreads = 512;  // 16 warps: latency hiding at two CTAs per SM
+constexpr int kSpreadPoints = 128;  // points per spreading CTA: two threads per point
 
 __device__ __forceinline__ float es_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double es_exp(double x) { return exp(x); }
@@ -46,19 +49,6 @@ template <typename T, int W> __device__ __forceinline__ void es_weights(T fr, T 
 #pragma unroll
     for (int j = 0; j < W; ++j) {
         T x = (T(j) - fr) * inv;
-        T q = T(1) - x * x;
-        wt[j] = q > T(0) ? es_exp(beta * (sqrt(q) - T(1))) : T(0);
-    }
-}
-
-// Same weights with the tap order rotated: wt[j] = phi((j + rot) mod W - fr).
-template <typename T, int W> __device__ __forceinline__ void es_weights_rot(T fr, T beta, int rot, T *wt) {
-    const T inv = T(2) / T(W);
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        int jr = j + rot;
-        jr = jr >= W ? jr - W : jr;
-        T x = (T(jr) - fr) * inv;
         T q = T(1) - x * x;
         wt[j] = q > T(0) ? es_exp(beta * (sqrt(q) - T(1))) : T(0);
     }
@@ -240,122 +230,174 @@ __device__ __forceinline__ void grid_add(double2 *g, double re, double im) {
     atomicAdd(&g->x, re);
     atomicAdd(&g->y, im);
 }
-__device__ __forceinline__ void tile_add(float2 *t, float re, float im) {
-    atomicAdd(&t->x, re);
-    atomicAdd(&t->y, im);
-}
-__device__ __forceinline__ void tile_add(double2 *t, double re, double im) {
-    atomicAdd(&t->x, re);
-    atomicAdd(&t->y, im);
-}
-
 // ------------------------------------------------------------------ spreading (tiled)
 
-// Shared-memory tile over the union of the CTA's windows, then vector-atomic flush.
-// PERIODIC: grid indices wrap (n2 grid) instead of lying inside (n1 grid).
+// A CTA spreads 128 consecutive points (Morton order in grid-cell units, so they are close
+// on the grid). Phase 1: threads 0..127 each take one point, compute its window start,
+// kernel weights and value, stage them in shared memory and extend the CTA's bounding box.
+// Phase 2: each of the 16 warps handles 4 points at a time, 8 lanes per point, lane j along the
+// window's x taps j (and j + 8 when w > 8), looping over the (z, y) taps: a group's 8 adds
+// fall on 8 consecutive cells, so the 4 groups of a warp meet few bank conflicts. The four
+// points a warp takes together are 32 apart in the CTA's order (mostly disjoint windows),
+// and each group starts its z loop at a different plane. The taps go into a shared tile
+// (separate real and imaginary planes) covering the union of the windows, which is then
+// added to the grid with vector atomics, one warp per tile row; when the tile would not
+// fit, the taps go straight to the grid with the same lane layout.
+constexpr int kGroupLanes = 8;
+static_assert(kSpreadPoints * kGroupLanes % kSpreadThreads == 0 && kSpreadThreads % 32 == 0 &&
+                  (kSpreadThreads / 32) * 4 * (kSpreadPoints * kGroupLanes / kSpreadThreads) == kSpreadPoints,
+              "every point of a spreading CTA is taken by exactly one lane group");
+constexpr int kSmemPerCta = 110 * 1024;  // two CTAs per SM
+
+template <typename T, int W> struct SpreadShared {
+    static constexpr int kWStride = 3 * W + 1;  // odd row stride: fewer bank conflicts
+    T w[kSpreadPoints][kWStride];                // x, y, z weights of each point
+    T v[kSpreadPoints][2];                       // complex value
+    int i0[kSpreadPoints][3];                    // window start (i0[.][0] = INT_MIN: no point)
+    int lo[3], hi[3];
+};
+
+template <typename T, int W> __host__ __device__ constexpr int tile_bytes() {
+    return ((kSmemPerCta - (int)sizeof(SpreadShared<T, W>)) / (2 * (int)sizeof(T) * 32)) * (2 * (int)sizeof(T) * 32);
+}
+
 template <typename T, int W, bool PERIODIC>
-__device__ __forceinline__ void spread_tiled(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
-                                             const int ng[3], cplx_t<T> *__restrict__ G, int tile_cap) {
+__device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
+                                           const int ng[3], cplx_t<T> *__restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
-    cplx_t<T> *tile = reinterpret_cast<cplx_t<T> *>(smem_raw);
-    __shared__ int s_lo[3], s_hi[3];
-    if (threadIdx.x < 3) {
-        s_lo[threadIdx.x] = INT_MAX;
-        s_hi[threadIdx.x] = INT_MIN;
+    __shared__ SpreadShared<T, W> sh;
+    constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));
+    T *tre = reinterpret_cast<T *>(smem_raw);
+    T *tim = tre + cap;
+    const int tid = threadIdx.x;
+    if (tid < 3) {
+        sh.lo[tid] = INT_MAX;
+        sh.hi[tid] = INT_MIN;
     }
     __syncthreads();
-    if (act) {
+    if (tid < kSpreadPoints) {
+        if (act) {
+            T wx[W], wy[W], wz[W];
+            es_weights<T, W>(fr[0], beta, wx);
+            es_weights<T, W>(fr[1], beta, wy);
+            es_weights<T, W>(fr[2], beta, wz);
 #pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            atomicMin(&s_lo[d], i0[d]);
-            atomicMax(&s_hi[d], i0[d]);
+            for (int j = 0; j < W; ++j) {
+                sh.w[tid][j] = wx[j];
+                sh.w[tid][W + j] = wy[j];
+                sh.w[tid][2 * W + j] = wz[j];
+            }
+            sh.v[tid][0] = vr;
+            sh.v[tid][1] = vi;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                sh.i0[tid][d] = i0[d];
+                atomicMin(&sh.lo[d], i0[d]);
+                atomicMax(&sh.hi[d], i0[d]);
+            }
+        } else {
+            sh.i0[tid][0] = INT_MIN;
         }
     }
     __syncthreads();
-    const int lo0 = s_lo[0], lo1 = s_lo[1], lo2 = s_lo[2];
-    const int64_t tx = (int64_t)s_hi[0] - lo0 + W, ty = (int64_t)s_hi[1] - lo1 + W, tz = (int64_t)s_hi[2] - lo2 + W;
-    const int64_t cells = tx * ty * tz;
-    // Lanes whose windows coincide (clustered points) would add to the same cell in the
-    // same instruction; rotating the z order of the taps by lane spreads those adds.
-    const int rot = (threadIdx.x & 31) % W;
-    T wx[W], wy[W], wz[W];
-    if (act) {
-        es_weights<T, W>(fr[0], beta, wx);
-        es_weights<T, W>(fr[1], beta, wy);
-        es_weights_rot<T, W>(fr[2], beta, rot, wz);
-    }
-    if (s_hi[0] >= lo0 && cells <= tile_cap) {
-        for (int64_t j = threadIdx.x; j < cells; j += blockDim.x) {
-            tile[j].x = T(0);
-            tile[j].y = T(0);
+    if (sh.hi[0] < sh.lo[0]) return;  // no point in this CTA (uniform across the CTA)
+    const int lo0 = sh.lo[0], lo1 = sh.lo[1], lo2 = sh.lo[2];
+    const int64_t tx = (int64_t)sh.hi[0] - lo0 + W, ty = (int64_t)sh.hi[1] - lo1 + W,
+                  tz = (int64_t)sh.hi[2] - lo2 + W;
+    const bool tiled = tx * ty * tz <= cap;
+    const int txi = (int)tx, tyi = (int)ty;
+    if (tiled) {
+        const int cells = (int)(tx * ty * tz);
+        for (int j = tid; j < cells; j += blockDim.x) {
+            tre[j] = T(0);
+            tim[j] = T(0);
         }
         __syncthreads();
-        if (act) {
-            for (int jz = 0; jz < W; ++jz) {
-                int jzr = jz + rot;
-                jzr = jzr >= W ? jzr - W : jzr;
-                for (int jy = 0; jy < W; ++jy) {
-                    const T wyz = wy[jy] * wz[jz];
-                    const T ar = vr * wyz, ai = vi * wyz;
-                    cplx_t<T> *row = tile + ((int64_t)(i0[2] - lo2 + jzr) * ty + (i0[1] - lo1 + jy)) * tx + (i0[0] - lo0);
+    }
+    const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
+    constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;  // x taps per lane (1 or 2)
+    constexpr int kRounds = kSpreadPoints * kGroupLanes / kSpreadThreads;  // points per group
+    for (int round = 0; round < kRounds; ++round) {
+        const int p = g * 32 + warp * kRounds + round;  // groups of a warp: points 32 apart
+        const int px0 = sh.i0[p][0];
+        if (px0 == INT_MIN) continue;
+        const int py0 = sh.i0[p][1], pz0 = sh.i0[p][2];
+        T ar[kXT], ai[kXT];
+        int cx[kXT];
+        bool on[kXT];
 #pragma unroll
-                    for (int jx = 0; jx < W; ++jx) tile_add(row + jx, ar * wx[jx], ai * wx[jx]);
+        for (int t = 0; t < kXT; ++t) {
+            const int jx = jx0 + t * kGroupLanes;
+            on[t] = jx < W;
+            const T wxv = on[t] ? sh.w[p][jx] : T(0);
+            ar[t] = sh.v[p][0] * wxv;
+            ai[t] = sh.v[p][1] * wxv;
+            cx[t] = tiled ? px0 - lo0 + jx : (PERIODIC ? wrap(px0 + jx, ng[0]) : px0 + jx);
+        }
+        T wy[W];
+#pragma unroll
+        for (int j = 0; j < W; ++j) wy[j] = sh.w[p][W + j];
+        for (int jj = 0; jj < W; ++jj) {
+            const int jz = (jj + 2 * g) % W;
+            const T wz = sh.w[p][2 * W + jz];
+            if (tiled) {
+                const int zrow = (pz0 - lo2 + jz) * tyi + (py0 - lo1);
+#pragma unroll
+                for (int jy = 0; jy < W; ++jy) {
+                    const T c = wy[jy] * wz;
+                    const int base = (zrow + jy) * txi;
+#pragma unroll
+                    for (int t = 0; t < kXT; ++t)
+                        if (on[t]) {
+                            atomicAdd(tre + base + cx[t], ar[t] * c);
+                            atomicAdd(tim + base + cx[t], ai[t] * c);
+                        }
+                }
+            } else {
+                const int64_t gz = PERIODIC ? wrap(pz0 + jz, ng[2]) : pz0 + jz;
+                for (int jy = 0; jy < W; ++jy) {
+                    const T c = wy[jy] * wz;
+                    const int64_t gy = PERIODIC ? wrap(py0 + jy, ng[1]) : py0 + jy;
+                    cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
+#pragma unroll
+                    for (int t = 0; t < kXT; ++t)
+                        if (on[t]) grid_add(row + cx[t], ar[t] * c, ai[t] * c);
                 }
             }
         }
-        __syncthreads();
-        // Flush: one warp per (y, z) row of the tile, lanes along x (coalesced atomics).
-        const int txi = (int)tx, tyi = (int)ty, rows = (int)(ty * tz);
-        const int lane = threadIdx.x & 31;
-        for (int r = threadIdx.x >> 5; r < rows; r += blockDim.x >> 5) {
-            const int y = r % tyi, z = r / tyi;
-            int gy = lo1 + y, gz = lo2 + z;
-            if (PERIODIC) {
-                gy = wrap(gy, ng[1]);
-                gz = wrap(gz, ng[2]);
-            }
-            cplx_t<T> *grow = G + ((int64_t)gz * ng[1] + gy) * ng[0];
-            const cplx_t<T> *trow = tile + (int64_t)r * txi;
-            for (int x = lane; x < txi; x += 32) {
-                const cplx_t<T> v = trow[x];
-                if (v.x == T(0) && v.y == T(0)) continue;
-                const int gx = PERIODIC ? wrap(lo0 + x, ng[0]) : lo0 + x;
-                grid_add(grow + gx, v.x, v.y);
-            }
+    }
+    if (!tiled) return;
+    __syncthreads();
+    // Flush: one warp per (y, z) row of the tile, lanes along x (coalesced vector atomics).
+    const int rows = (int)(ty * tz);
+    for (int r = warp; r < rows; r += blockDim.x >> 5) {
+        const int y = r % tyi, z = r / tyi;
+        int gy = lo1 + y, gz = lo2 + z;
+        if (PERIODIC) {
+            gy = wrap(gy, ng[1]);
+            gz = wrap(gz, ng[2]);
         }
-    } else if (act) {
-        int64_t ix[W];
-#pragma unroll
-        for (int j = 0; j < W; ++j) ix[j] = PERIODIC ? wrap(i0[0] + j, ng[0]) : i0[0] + j;
-        for (int jz = 0; jz < W; ++jz) {
-            int jzr = jz + rot;
-            jzr = jzr >= W ? jzr - W : jzr;
-            const int64_t gz = PERIODIC ? wrap(i0[2] + jzr, ng[2]) : i0[2] + jzr;
-            for (int jy = 0; jy < W; ++jy) {
-                const int64_t gy = PERIODIC ? wrap(i0[1] + jy, ng[1]) : i0[1] + jy;
-                const T wyz = wy[jy] * wz[jz];
-                const T ar = vr * wyz, ai = vi * wyz;
-                cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
-#pragma unroll
-                for (int jx = 0; jx < W; ++jx) grid_add(row + ix[jx], ar * wx[jx], ai * wx[jx]);
-            }
+        cplx_t<T> *grow = G + ((int64_t)gz * ng[1] + gy) * ng[0];
+        const int t0 = r * txi;
+        for (int x = lane; x < txi; x += 32) {
+            const T re = tre[t0 + x], im = tim[t0 + x];
+            if (re == T(0) && im == T(0)) continue;
+            const int gx = PERIODIC ? wrap(lo0 + x, ng[0]) : lo0 + x;
+            grid_add(grow + gx, re, im);
         }
     }
 }
 
-// Point of the CTA's 256 handled by this thread: warp w takes points w, w + 8, w + 16, ...
-// so that the 32 lanes of a warp are spread over the CTA's (spatially ordered) points.
-__device__ __forceinline__ int cta_slot() { return (threadIdx.x & 31) * (kSpreadThreads / 32) + (threadIdx.x >> 5); }
-
-// sky -> vis step 1: pixels (values c, prephase P) onto the n1 grid.
+// sky -> vis step 1: pixels (values c, prephase P) onto the n1 grid. Thread t < 128 takes
+// point blockIdx.x * 128 + t.
 template <typename T, int W>
-__global__ void __launch_bounds__(kSpreadThreads) spread_pix_kernel(NufftDev b, const float4 *__restrict__ rh,
+__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread_pix_kernel(NufftDev b, const float4 *__restrict__ rh,
                                                                      const float4 *__restrict__ rl,
                                                                      const double *__restrict__ soa, int64_t n_all,
                                                                      const T *__restrict__ c, cplx_t<T> *__restrict__ G1,
-                                                                     T beta, int isign, int tile_cap) {
-    const int64_t i = blockIdx.x * (int64_t)kSpreadThreads + cta_slot();
-    const bool act = i < b.np;
+                                                                     T beta, int isign) {
+    const int64_t i = blockIdx.x * (int64_t)kSpreadPoints + threadIdx.x;
+    const bool act = threadIdx.x < kSpreadPoints && i < b.np;
     int i0[3] = {0, 0, 0};
     T fr[3] = {0, 0, 0}, vr = 0, vi = 0;
     if (act) {
@@ -366,20 +408,19 @@ __global__ void __launch_bounds__(kSpreadThreads) spread_pix_kernel(NufftDev b, 
         vi = cv * pim;
     }
     const int ng[3] = {b.n1[0], b.n1[1], b.n1[2]};
-    spread_tiled<T, W, false>(act, i0, fr, vr, vi, beta, ng, G1, tile_cap);
+    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, ng, G1);
 }
 
 // vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2 grid.
 template <typename T, int W>
-__global__ void __launch_bounds__(kSpreadThreads) spread_vis_kernel(NufftDev b, const float4 *__restrict__ vh,
+__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread_vis_kernel(NufftDev b, const float4 *__restrict__ vh,
                                                                      const float4 *__restrict__ vl,
                                                                      const double *__restrict__ soa, int64_t n_all,
                                                                      const cplx_t<T> *__restrict__ V,
                                                                      const T *__restrict__ cc, int deg, T inv_tmax2,
-                                                                     cplx_t<T> *__restrict__ G2, T beta, int isign,
-                                                                     int tile_cap) {
-    const int64_t k = blockIdx.x * (int64_t)kSpreadThreads + cta_slot();
-    const bool act = k < b.nv;
+                                                                     cplx_t<T> *__restrict__ G2, T beta, int isign) {
+    const int64_t k = blockIdx.x * (int64_t)kSpreadPoints + threadIdx.x;
+    const bool act = threadIdx.x < kSpreadPoints && k < b.nv;
     int i0[3] = {0, 0, 0};
     T fr[3] = {0, 0, 0}, ur = 0, ui = 0;
     if (act) {
@@ -390,7 +431,7 @@ __global__ void __launch_bounds__(kSpreadThreads) spread_vis_kernel(NufftDev b, 
         ui = qr * v.y - qi * v.x;
     }
     const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
-    spread_tiled<T, W, true>(act, i0, fr, ur, ui, beta, ng, G2, tile_cap);
+    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, ng, G2);
 }
 
 // ------------------------------------------------------------------ interpolation (gather)
@@ -476,54 +517,124 @@ __global__ void __launch_bounds__(128) interp_pix_kernel(NufftDev b, const float
 
 // ------------------------------------------------------------------ deconvolution passes
 
-// G2[j] = G1[l + n1/2] / (Psi_x Psi_y Psi_z)(l) for the centred frequency l of FFT index j
-// inside the n1 band, 0 elsewhere. One thread per x index of a (y, z) row: coalesced rows,
-// no integer division.
-template <typename T>
-__global__ void deconv_pad_kernel(NufftDev b, const cplx_t<T> *__restrict__ G1, const T *__restrict__ ipsi,
-                                  cplx_t<T> *__restrict__ G2) {
-    const int jx = blockIdx.x * blockDim.x + threadIdx.x;
-    const int jy = blockIdx.y, jz = blockIdx.z;
-    const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
-    if (jx >= n2x) return;
-    const int h1x = b.n1[0] / 2, h1y = b.n1[1] / 2, h1z = b.n1[2] / 2;
-    const int lx = jx < n2x / 2 ? jx : jx - n2x;
-    const int ly = jy < n2y / 2 ? jy : jy - n2y;
-    const int lz = jz < n2z / 2 ? jz : jz - n2z;
-    cplx_t<T> out;
-    out.x = T(0);
-    out.y = T(0);
-    if (lx >= -h1x && lx < h1x && ly >= -h1y && ly < h1y && lz >= -h1z && lz < h1z) {
-        const int ix = lx + h1x, iy = ly + h1y, iz = lz + h1z;
-        const T *px = ipsi, *py = ipsi + b.n1[0], *pz = py + b.n1[1];
-        const T f = px[ix] * py[iy] * pz[iz];
-        const cplx_t<T> g = G1[((int64_t)iz * b.n1[1] + iy) * b.n1[0] + ix];
-        out.x = g.x * f;
-        out.y = g.y * f;
-    }
-    G2[((int64_t)jz * n2y + jy) * n2x + jx] = out;
+// Row-wise passes over (y, z) rows of a grid: each warp takes a contiguous range of rows,
+// its lanes sweep x with four independent elements in flight per lane (enough bytes in
+// flight to keep HBM busy), and the row index advances without division.
+constexpr int kRowThreads = 256;
+constexpr int kRowUnroll = 4;
+
+inline unsigned row_ctas(int64_t rows) {
+    const int64_t warps = (rows + 1) / 2;  // at least two rows per warp
+    const int64_t ctas = (warps + kRowThreads / 32 - 1) / (kRowThreads / 32);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ctas, 152 * 8));
 }
 
-// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band (row-wise, as above).
+// First row and row count of this warp for `rows` rows split over all warps of the grid.
+__device__ __forceinline__ void warp_rows(int64_t rows, int64_t &r0, int64_t &cnt) {
+    const int64_t nw = (int64_t)gridDim.x * (kRowThreads / 32);
+    const int64_t gw = (int64_t)blockIdx.x * (kRowThreads / 32) + (threadIdx.x >> 5);
+    const int64_t per = (rows + nw - 1) / nw;
+    r0 = gw * per;
+    cnt = r0 < rows ? (rows - r0 < per ? rows - r0 : per) : 0;
+}
+
+// G2[j] = G1[l + n1/2] / (Psi_x Psi_y Psi_z)(l) for the centred frequency l of FFT index j
+// inside the n1 band, 0 elsewhere (rows of the n2 grid).
 template <typename T>
-__global__ void crop_deconv_kernel(NufftDev b, const cplx_t<T> *__restrict__ G2, const T *__restrict__ ipsi,
-                                   cplx_t<T> *__restrict__ G1) {
-    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
-    const int iy = blockIdx.y, iz = blockIdx.z;
-    const int n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
-    if (ix >= n1x) return;
+__global__ void __launch_bounds__(kRowThreads) deconv_pad_kernel(NufftDev b, const cplx_t<T> *__restrict__ G1,
+                                                                 const T *__restrict__ ipsi,
+                                                                 cplx_t<T> *__restrict__ G2) {
     const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
-    int jx = ix - n1x / 2, jy = iy - n1y / 2, jz = iz - n1z / 2;
-    jx += jx < 0 ? n2x : 0;
-    jy += jy < 0 ? n2y : 0;
-    jz += jz < 0 ? n2z : 0;
-    const cplx_t<T> g = G2[((int64_t)jz * n2y + jy) * n2x + jx];
+    const int n1x = b.n1[0], n1y = b.n1[1];
+    const int h1x = b.n1[0] / 2, h1y = b.n1[1] / 2, h1z = b.n1[2] / 2;
     const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
-    const T f = px[ix] * py[iy] * pz[iz];
-    cplx_t<T> out;
-    out.x = g.x * f;
-    out.y = g.y * f;
-    G1[((int64_t)iz * n1y + iy) * n1x + ix] = out;
+    int64_t r, cnt;
+    warp_rows((int64_t)n2y * n2z, r, cnt);
+    if (cnt == 0) return;
+    int jy = (int)(r % n2y), jz = (int)(r / n2y);
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = 0; k < cnt; ++k) {
+        cplx_t<T> *out = G2 + ((int64_t)jz * n2y + jy) * n2x;
+        const int ly = jy < n2y / 2 ? jy : jy - n2y;
+        const int lz = jz < n2z / 2 ? jz : jz - n2z;
+        cplx_t<T> zero;
+        zero.x = T(0);
+        zero.y = T(0);
+        if (ly >= -h1y && ly < h1y && lz >= -h1z && lz < h1z) {
+            const int iy = ly + h1y, iz = lz + h1z;
+            const T fyz = py[iy] * pz[iz];
+            const cplx_t<T> *in = G1 + ((int64_t)iz * n1y + iy) * n1x;
+            for (int x0 = lane; x0 < n2x; x0 += 32 * kRowUnroll) {
+                cplx_t<T> v[kRowUnroll];
+#pragma unroll
+                for (int u = 0; u < kRowUnroll; ++u) {
+                    const int jx = x0 + 32 * u;
+                    const int lx = jx < n2x / 2 ? jx : jx - n2x;
+                    v[u] = zero;
+                    if (jx < n2x && lx >= -h1x && lx < h1x) {
+                        const cplx_t<T> g = in[lx + h1x];
+                        const T f = px[lx + h1x] * fyz;
+                        v[u].x = g.x * f;
+                        v[u].y = g.y * f;
+                    }
+                }
+#pragma unroll
+                for (int u = 0; u < kRowUnroll; ++u)
+                    if (x0 + 32 * u < n2x) out[x0 + 32 * u] = v[u];
+            }
+        } else {
+            for (int jx = lane; jx < n2x; jx += 32) out[jx] = zero;
+        }
+        if (++jy == n2y) {
+            jy = 0;
+            ++jz;
+        }
+    }
+}
+
+// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band (rows of the n1 grid).
+template <typename T>
+__global__ void __launch_bounds__(kRowThreads) crop_deconv_kernel(NufftDev b, const cplx_t<T> *__restrict__ G2,
+                                                                  const T *__restrict__ ipsi,
+                                                                  cplx_t<T> *__restrict__ G1) {
+    const int n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
+    const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
+    const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
+    int64_t r, cnt;
+    warp_rows((int64_t)n1y * n1z, r, cnt);
+    if (cnt == 0) return;
+    int iy = (int)(r % n1y), iz = (int)(r / n1y);
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = 0; k < cnt; ++k) {
+        int jy = iy - n1y / 2, jz = iz - n1z / 2;
+        jy += jy < 0 ? n2y : 0;
+        jz += jz < 0 ? n2z : 0;
+        const cplx_t<T> *in = G2 + ((int64_t)jz * n2y + jy) * n2x;
+        cplx_t<T> *out = G1 + ((int64_t)iz * n1y + iy) * n1x;
+        const T fyz = py[iy] * pz[iz];
+        for (int x0 = lane; x0 < n1x; x0 += 32 * kRowUnroll) {
+            cplx_t<T> v[kRowUnroll];
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u) {
+                const int ix = x0 + 32 * u;
+                if (ix < n1x) {
+                    int jx = ix - n1x / 2;
+                    jx += jx < 0 ? n2x : 0;
+                    const cplx_t<T> g = in[jx];
+                    const T f = px[ix] * fyz;
+                    v[u].x = g.x * f;
+                    v[u].y = g.y * f;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u)
+                if (x0 + 32 * u < n1x) out[x0 + 32 * u] = v[u];
+        }
+        if (++iy == n1y) {
+            iy = 0;
+            ++iz;
+        }
+    }
 }
 
 #define HVOX_W_SWITCH(w, CALL)                                         \
@@ -549,15 +660,15 @@ __global__ void crop_deconv_kernel(NufftDev b, const cplx_t<T> *__restrict__ G2,
 inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + threads - 1) / threads); }
 
 
-// Dynamic shared memory of the spreading kernels (tile capacity in cells).
-constexpr int kTileBytes = 96 * 1024;
-
+// Dynamic shared memory of the spreading kernels: the tile (real and imaginary planes).
 template <typename T, int W> void set_smem_attrs() {
     static bool done = false;
     if (done) return;
-    check_cuda(cudaFuncSetAttribute(spread_pix_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes),
+    check_cuda(cudaFuncSetAttribute(spread_pix_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tile_bytes<T, W>()),
                "cudaFuncSetAttribute");
-    check_cuda(cudaFuncSetAttribute(spread_vis_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTileBytes),
+    check_cuda(cudaFuncSetAttribute(spread_vis_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    tile_bytes<T, W>()),
                "cudaFuncSetAttribute");
     done = true;
 }
@@ -575,21 +686,19 @@ void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_
     hook.begin(HVOX_STAGE_ZERO, s);
     check_cuda(cudaMemsetAsync(a.G1, 0, sizeof(cplx_t<T>) * m1, s), "memset G1");
     hook.end(HVOX_STAGE_ZERO, 1, s);
-    const int cap = kTileBytes / (int)sizeof(cplx_t<T>);
     if (b.np > 0) {
         hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_pix_kernel<T, W><<<blocks_for(b.np, kSpreadThreads), kSpreadThreads, kTileBytes, s>>>(                 \
-        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, a.G1, bt, a.isign, cap)
+    spread_pix_kernel<T, W><<<blocks_for(b.np, kSpreadPoints), kSpreadThreads, tile_bytes<T, W>(), s>>>(         \
+        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, a.G1, bt, a.isign)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_pix");
         hook.end(HVOX_STAGE_SPREAD, 1, s);
     }
-    const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
     hook.begin(HVOX_STAGE_DECONV, s);
-    deconv_pad_kernel<T><<<dim3((unsigned)((b.n2[0] + 127) / 128), (unsigned)b.n2[1], (unsigned)b.n2[2]), 128, 0, s>>>(
+    deconv_pad_kernel<T><<<row_ctas((int64_t)b.n2[1] * b.n2[2]), kRowThreads, 0, s>>>(
         b, a.G1, a.ipsi + b.psi_off, a.G2);
     check_cuda(cudaGetLastError(), "deconv_pad");
     hook.end(HVOX_STAGE_DECONV, 1, s);
@@ -622,13 +731,12 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
     hook.begin(HVOX_STAGE_ZERO, s);
     check_cuda(cudaMemsetAsync(a.G2, 0, sizeof(cplx_t<T>) * m2, s), "memset G2");
     hook.end(HVOX_STAGE_ZERO, 1, s);
-    const int cap = kTileBytes / (int)sizeof(cplx_t<T>);
     if (b.nv > 0) {
         hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_vis_kernel<T, W><<<blocks_for(b.nv, kSpreadThreads), kSpreadThreads, kTileBytes, s>>>(                 \
-        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, bt, a.isign, cap)
+    spread_vis_kernel<T, W><<<blocks_for(b.nv, kSpreadPoints), kSpreadThreads, tile_bytes<T, W>(), s>>>(         \
+        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, bt, a.isign)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_vis");
@@ -642,9 +750,8 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
     else
         check_cufft(cufftExecZ2Z(a.fft, (cufftDoubleComplex *)a.G2, (cufftDoubleComplex *)a.G2, dir), "cufftExecZ2Z");
     hook.end(HVOX_STAGE_FFT, 1, s);
-    const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
     hook.begin(HVOX_STAGE_DECONV, s);
-    crop_deconv_kernel<T><<<dim3((unsigned)((b.n1[0] + 127) / 128), (unsigned)b.n1[1], (unsigned)b.n1[2]), 128, 0, s>>>(
+    crop_deconv_kernel<T><<<row_ctas((int64_t)b.n1[1] * b.n1[2]), kRowThreads, 0, s>>>(
         b, a.G2, a.ipsi + b.psi_off, a.G1);
     check_cuda(cudaGetLastError(), "crop_deconv");
     hook.end(HVOX_STAGE_DECONV, 1, s);

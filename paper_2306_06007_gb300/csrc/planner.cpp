@@ -184,16 +184,16 @@ CostModel default_cost_model(int prec, bool plain, int w) {
         m.fft_cell = 6e-13;
         m.grid_cell = 4e-12;
         m.block_fixed = 30e-6;
-        m.tile_cells = 96.0 * 1024 / 8;
+        m.tile_cells = 12000.0;  // shared tile of a spreading CTA (float planes, w <= 8)
     } else {
-        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 2.8e11;
+        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 4.0e11;
         m.scatter_smem = 1.0 / 2.0e9;
         m.scatter_global = 1.0 / 1.0e9;
         m.gather_tap = 1.0 / 2.0e9;
         m.fft_cell = 2.1e-11;
         m.grid_cell = 1e-11;
         m.block_fixed = 50e-6;
-        m.tile_cells = 96.0 * 1024 / 16;
+        m.tile_cells = 4800.0;   // double planes, w ~ 10
     }
     return m;
 }
@@ -231,10 +231,10 @@ struct Evaluated {
 };
 
 // Spreading cost per tap for n points on a grid of `cells`: through the shared tile when
-// the 256 points of a CTA (uniform-density estimate of the region they occupy, plus the
+// the 128 points of a CTA (uniform-density estimate of the region they occupy, plus the
 // kernel width) fit the tile, else straight into the grid.
 double scatter_cost(const CostModel &m, double n, double cells, int w) {
-    double region = 256.0 * cells / std::max(1.0, n);
+    double region = 128.0 * cells / std::max(1.0, n);
     double side = std::cbrt(region) + (double)(w - 1);
     return side * side * side <= m.tile_cells ? m.scatter_smem : m.scatter_global;
 }
@@ -366,9 +366,21 @@ PartitionResult make_partition(const PlanInputs &in) {
             ESKernel es;
         };
         std::vector<Cand> cands;
-        std::vector<double> sigmas = in.sigma_auto ? std::vector<double>{2.0, 1.5} : std::vector<double>{in.sigma};
+        std::vector<double> sigmas = in.sigma_auto ? std::vector<double>{2.0, 1.5, 1.25} : std::vector<double>{in.sigma};
         for (double sg : sigmas) {
             const ESKernel es = in.sigma_auto ? es_params(in.eps_es, sg) : in.es;
+            if (in.sigma_auto && in.prec == 1 && sg != sigmas.front()) {
+                // FP32 grids: rounding errors near the band edge are divided twice by the
+                // kernel transform (1/Psi before the FFT, 1/Phi after the interpolation),
+                // so the error floor is about 2^-24 (Phi(0) / Phi(pi / sigma))^2. Smaller
+                // sigma narrows the margin; keep a candidate only while the floor stays
+                // within half of the 10 eps bound.
+                const double tau[2] = {0.0, M_PI / sg};
+                double ph[2];
+                es_ft(es, tau, 2, ph);
+                const double r = ph[0] / ph[1];
+                if (std::ldexp(1.0, -24) * r * r > 5.0 * in.eps_es) continue;
+            }
             for (double b = 256.0 * 1024.0; b <= 9.0e9; b *= 8.0) {
                 if (in.max_budget > 0 && b > in.max_budget && b > 256.0 * 1024.0) break;
                 cands.push_back({sg, b, es});
@@ -428,10 +440,14 @@ PartitionResult make_partition(const PlanInputs &in) {
     };
     r.pix_chunk_label = order_chunks(pin);
     r.vis_chunk_label = order_chunks(vin);
-    // Inside a chunk, points follow the Morton (Z-order) curve of their position, so that
-    // consecutive points are close in space (compact spreading tiles).
+    // Inside a chunk, points follow the Morton (Z-order) curve of their position in grid-cell
+    // units: a pixel's grid coordinate along d is ~ sigma B_d r_d and a baseline's ~ sigma
+    // P_d p_d, so dimension d is scaled by the other set's extent before quantising. Then
+    // consecutive points are close on the grid (compact spreading tiles) even where one
+    // dimension is thin, such as a sky cap's z.
     auto build_perm = [](const double *xyz, const std::vector<int64_t> &labels, int64_t nc,
-                         const std::vector<int64_t> &ord, std::vector<int64_t> &perm, std::vector<int64_t> &start) {
+                         const std::vector<int64_t> &ord, std::vector<int64_t> &perm, std::vector<int64_t> &start,
+                         const double scale[3]) {
         const int64_t n = (int64_t)labels.size();
         std::vector<int64_t> rank(nc);
         for (int64_t k = 0; k < nc; ++k) rank[ord[k]] = k;
@@ -448,14 +464,15 @@ PartitionResult make_partition(const PlanInputs &in) {
                 lo[d] = std::min(lo[d], xyz[3 * i + d]);
                 hi[d] = std::max(hi[d], xyz[3 * i + d]);
             }
+        double span = 0.0;
+        for (int d = 0; d < 3; ++d) span = std::max(span, (hi[d] - lo[d]) * scale[d]);
         std::vector<uint64_t> code(n);
         for (int64_t i = 0; i < n; ++i) {
             uint64_t c = 0;
             uint32_t q[3];
             for (int d = 0; d < 3; ++d) {
-                double ext = hi[d] - lo[d];
-                double u = ext > 0 ? (xyz[3 * i + d] - lo[d]) / ext : 0.0;
-                q[d] = (uint32_t)std::min(2097151.0, std::floor(u * 2097151.0));
+                double u = span > 0 ? (xyz[3 * i + d] - lo[d]) * scale[d] / span : 0.0;
+                q[d] = (uint32_t)std::min(2097151.0, std::max(0.0, std::floor(u * 2097151.0)));
             }
             for (int bit = 20; bit >= 0; --bit)
                 for (int d = 0; d < 3; ++d) c = (c << 1) | ((q[d] >> bit) & 1u);
@@ -468,9 +485,9 @@ PartitionResult make_partition(const PlanInputs &in) {
         return rank;
     };
     std::vector<int64_t> prank =
-        build_perm(in.pix, best.pl, best.npc, r.pix_chunk_label, r.pix_perm, r.pix_chunk_start);
+        build_perm(in.pix, best.pl, best.npc, r.pix_chunk_label, r.pix_perm, r.pix_chunk_start, B);
     std::vector<int64_t> vrank =
-        build_perm(in.uvw, best.vl, best.nvc, r.vis_chunk_label, r.vis_perm, r.vis_chunk_start);
+        build_perm(in.uvw, best.vl, best.nvc, r.vis_chunk_label, r.vis_perm, r.vis_chunk_start, P);
 
     // NUFFT blocks with their geometry.
     const double sigma = best_sigma;

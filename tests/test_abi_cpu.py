@@ -109,3 +109,19 @@ def test_chunk_points_rejects_bad_input(lib):
     with pytest.raises(hvox.HvoxError) as e:
         hvox.chunk_points(pts, [1.0, 1.0, 1.0])
     assert e.value.code == 1
+
+
+def test_fp32_plans_keep_sigma_above_error_floor():
+    # FP32 NUFFT grids carry a rounding floor of ~2^-24 (Phi(0)/Phi(pi/sigma))^2 (errors
+    # near the band edge are divided by the kernel transform before the FFT and after the
+    # interpolation); the planner must not pick an upsampling whose floor exceeds 5 eps.
+    import math
+    import paper_2306_06007_gb300 as hvox
+    from hvox_inputs import configs
+    w = configs.radius_sweep(3.0)
+    for eps in (1e-5, 1e-6):
+        info = hvox.plan_dry(w.pix, w.uvw, eps)
+        assert info["n_nufft_blocks"] >= 1
+        wd, beta = hvox.es_params(eps, info["upsampfac"])
+        ph = hvox.es_ft(wd, beta, [0.0, math.pi / info["upsampfac"]])
+        assert 2.0 ** -24 * (ph[0] / ph[1]) ** 2 <= 5 * eps, info["upsampfac"]

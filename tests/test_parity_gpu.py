@@ -253,3 +253,15 @@ def test_ntrans_stacked_inputs(gpu_lib, small):
         for t in range(nt):
             assert oracle.rel_l2(V[t], oracle.sky2vis(w.pix, w.uvw, sky[t])) <= 1e-5
             assert oracle.rel_l2(img[t], oracle.vis2sky(w.pix, w.uvw, vis[t])) <= 1e-5
+
+
+@pytest.mark.parametrize("sigma", [1.25, 1.5])
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-9])
+def test_upsampling_factors(gpu_lib, small, sigma, eps):
+    # The planner may choose sigma = 2, 1.5 or 1.25 (kernel width and shape from the same
+    # rules); every choice must meet the tolerance in both directions.
+    w = small
+    V, y, img, info = _run(gpu_lib, w, eps, mode="nufft", upsampfac=sigma)
+    assert abs(info["upsampfac"] - sigma) < 1e-12 and info["n_nufft_blocks"] >= 1
+    assert oracle.rel_l2(V, oracle.sky2vis(w.pix, w.uvw, w.sky)) <= 10 * eps
+    assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 10 * eps
