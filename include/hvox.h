@@ -86,6 +86,11 @@ typedef struct {
     double anisotropy;           /* Algorithm 1 alpha >= 1; 0 -> 1 (isotropic optimum) */
     double direct_threshold;     /* < 0 or 0 -> cost model; > 0: a block with
                                     n_pix_blk * n_vis_blk <= threshold is direct */
+    double search_threshold;     /* seconds; a job whose direct evaluation (both directions)
+                                    is modelled below this is planned as direct sums
+                                    without searching partitions. 0 -> 0.01 s. Callers
+                                    that use a plan once (per-request serving) pass more,
+                                    since the search costs ~1-3 us per point. */
     int32_t ntrans;              /* number of stacked inputs on one geometry; 0 -> 1 */
     int32_t plain;               /* 1: the plain reference form: FP64 arithmetic in every
                                     kernel, blocks launched one by one, no graph */

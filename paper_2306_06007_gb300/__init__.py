@@ -36,7 +36,8 @@ class HvoxError(RuntimeError):
 class Opts(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int32), ("mode", ctypes.c_int32), ("upsampfac", ctypes.c_double),
                 ("chunk_budget_bytes", ctypes.c_double), ("anisotropy", ctypes.c_double),
-                ("direct_threshold", ctypes.c_double), ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
+                ("direct_threshold", ctypes.c_double), ("search_threshold", ctypes.c_double),
+                ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
@@ -166,7 +167,8 @@ def chunk_points(xyz, h):
 
 
 def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: float = 0.0,
-             chunk_budget_bytes: float = 0.0, direct_threshold: float = 0.0, plain: bool = False) -> dict:
+             chunk_budget_bytes: float = 0.0, direct_threshold: float = 0.0, plain: bool = False,
+             search_threshold: float = 0.0) -> dict:
     """Host-only planning (no GPU): partition, block choices and cost-model estimate."""
     np = _np()
     pix = np.ascontiguousarray(pix, dtype=np.float64)
@@ -177,6 +179,7 @@ def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: flo
     o.upsampfac = upsampfac
     o.chunk_budget_bytes = chunk_budget_bytes
     o.direct_threshold = direct_threshold
+    o.search_threshold = search_threshold
     o.plain = 1 if plain else 0
     inf = Info()
     _check(load().hvox_plan_dry(_dptr(pix), len(pix), _dptr(uvw), len(uvw), float(eps), ctypes.byref(o),
@@ -257,7 +260,7 @@ class Plan:
     def __init__(self, pix, uvw, eps: float, isign: int = -1, weight=None, precision="auto", mode="auto",
                  upsampfac: float = 0.0, chunk_budget_bytes: float = 0.0, anisotropy: float = 0.0,
                  direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, graphs: int = 0,
-                 stream=None):
+                 search_threshold: float = 0.0, stream=None):
         import torch
         lib = load()
         self._handle = ctypes.c_void_p()
@@ -271,6 +274,7 @@ class Plan:
         o.chunk_budget_bytes = chunk_budget_bytes
         o.anisotropy = anisotropy
         o.direct_threshold = direct_threshold
+        o.search_threshold = search_threshold
         o.ntrans = ntrans
         o.plain = 1 if plain else 0
         o.graphs = int(graphs)

@@ -174,6 +174,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     in.plain = p.plain;
     in.budget = p.budget_opt;
     in.direct_threshold = p.direct_threshold;
+    in.search_threshold = p.search_threshold;
     in.elem_bytes = elem;
     in.sigma_auto = p.sigma_auto;
     in.eps_es = p.eps_es;
@@ -387,6 +388,8 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     if (!(o.anisotropy == 0.0 || o.anisotropy >= 1.0)) fail(HVOX_EINVAL, "hvox_plan: anisotropy must be >= 1");
     if (o.ntrans < 0) fail(HVOX_EINVAL, "hvox_plan: ntrans must be >= 0");
     if (!std::isfinite(o.direct_threshold)) fail(HVOX_EINVAL, "hvox_plan: bad direct_threshold");
+    if (!(o.search_threshold >= 0.0) || !std::isfinite(o.search_threshold))
+        fail(HVOX_EINVAL, "hvox_plan: bad search_threshold");
     p.n_pix = n_pix;
     p.n_vis = n_vis;
     p.eps = eps;
@@ -402,6 +405,7 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.stream = (cudaStream_t)o.stream;
     p.budget_opt = o.chunk_budget_bytes;
     p.direct_threshold = o.direct_threshold;
+    p.search_threshold = o.search_threshold > 0 ? o.search_threshold : 0.01;
     double e = eps > 0 ? eps : 1e-6;
     if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
     p.eps_es = e * kEpsMargin;
@@ -596,6 +600,7 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         in.plain = p.plain;
         in.budget = p.budget_opt;
         in.direct_threshold = p.direct_threshold;
+        in.search_threshold = p.search_threshold;
         in.elem_bytes = elem;
         in.sigma_auto = p.sigma_auto;
         in.eps_es = p.eps_es;

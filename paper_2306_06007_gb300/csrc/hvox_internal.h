@@ -124,6 +124,7 @@ struct PlanInputs {
     double budget;         // 0 -> search
     double max_budget = 0; // > 0: largest budget the search may pick (device memory)
     double direct_threshold;
+    double search_threshold = 0.01;  // seconds of modelled direct work below which no search
     int elem_bytes;
 };
 
@@ -235,6 +236,7 @@ struct Plan {
     bool sigma_auto = true;        // upsampling chosen by the planner
     double eps_es = 1e-6;          // tolerance given to the kernel-width rule
     double direct_threshold = 0.0; // direct_threshold option
+    double search_threshold = 0.01; // search_threshold option (seconds)
     ESKernel es;
     bool has_weight = false;
     cudaStream_t stream = nullptr;

@@ -346,10 +346,10 @@ PartitionResult make_partition(const PlanInputs &in) {
     Evaluated best;
     double best_sigma = in.sigma;
     ESKernel best_es = in.es;
-    // Problems whose whole direct evaluation (both directions) is modelled below 100 ms are
-    // planned as one direct rectangle without a budget search: the search costs more than
-    // it could save, which matters when plans are made per request while serving.
-    const bool tiny = 2.0 * m.direct_pair * (double)in.n_pix * (double)in.n_vis < 100e-3;
+    // Problems whose whole direct evaluation (both directions) is modelled below the search
+    // threshold are planned as one direct rectangle without a budget search: the search
+    // (~1-3 us per point) would cost more than it could save over the plan's expected use.
+    const bool tiny = 2.0 * m.direct_pair * (double)in.n_pix * (double)in.n_vis < in.search_threshold;
     if (in.budget > 0) {
         best = evaluate(in, m, in.budget, P, B);
     } else if (in.mode == HVOX_MODE_DIRECT || (tiny && in.mode == HVOX_MODE_AUTO && in.direct_threshold <= 0)) {

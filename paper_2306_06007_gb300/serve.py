@@ -76,7 +76,7 @@ class Server:
     """Request loop over libhvox plans (see the module docstring)."""
 
     def __init__(self, hbm_budget_bytes: float = 150e9, max_inflight: int = 8, planner_threads: int = 0,
-                 plain: bool = False, keep_plans: bool = True):
+                 plain: bool = False, keep_plans: bool = True, search_threshold: float = 0.1):
         import os
         if planner_threads <= 0:
             planner_threads = max(2, (os.cpu_count() or 4) // 2)
@@ -84,6 +84,9 @@ class Server:
         self.max_inflight = 1 if plain else int(max_inflight)
         self.plain = plain
         self.keep_plans = keep_plans
+        # A request's plan is usually used once: skip the partition search for jobs whose
+        # direct evaluation is modelled below this many seconds (it costs ~1-3 us a point).
+        self.search_threshold = float(search_threshold)
         self.pool = cf.ThreadPoolExecutor(max_workers=max(1, planner_threads))
         self.resident: dict[str, _Resident] = {}
         self.used = 0.0
@@ -93,7 +96,8 @@ class Server:
         import torch
         t0 = time.perf_counter()
         stream = torch.cuda.Stream()
-        plan = Plan(req.pix, req.uvw, req.eps, plain=self.plain, stream=stream)
+        plan = Plan(req.pix, req.uvw, req.eps, plain=self.plain, stream=stream,
+                    search_threshold=self.search_threshold)
         info = plan.info()
         return plan, stream, info["workspace_bytes"], time.perf_counter() - t0
 
