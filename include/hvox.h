@@ -128,6 +128,12 @@ typedef struct {
     double model_seconds;        /* cost-model estimate of one sky->vis plus one vis->sky */
     int32_t graph_state;         /* 0: eager launches so far; 1: a graph has been captured
                                     and is replayed; -1: capture failed, eager launches */
+    /* Work of one sky->vis (the same again for vis->sky) summed over NUFFT sub-problems,
+       the quantities the cost model charges: */
+    double nufft_pix_points;     /* pixels spread (and, in vis->sky, gathered) */
+    double nufft_vis_points;     /* baselines gathered (and, in vis->sky, spread) */
+    double spread_cells;         /* n1 grid cells (M1) */
+    double fft_work;             /* M2 log2 M2 over the FFT grids */
 } hvox_info;
 
 /*

@@ -1,0 +1,107 @@
+"""Per-stage calibration of the planner's cost model.
+
+The paper fits its CPU build's runtime by regressing measured stage times on stage work
+(spread, FFT, interpolation). This does the same for the GPU stages: each workload runs
+with one NUFFT lane (so stages do not overlap and their CUDA-event times add up to the
+step), every stage is timed by the library's profiler over a few steps, and each rate is
+fitted by least squares through the origin across the workloads:
+
+    spread ms         ~ taps         * c_spread     taps = (pix + vis points) * w^3
+    interp ms         ~ taps         * c_interp
+    fft ms            ~ 2 sum M2 log2 M2 * c_fft    (one FFT per direction)
+    deconv + zero ms  ~ 2 (2 M1 + 2 M2)  * c_grid   (grid passes per direction)
+    direct ms         ~ 2 direct_pairs   * c_direct
+
+The fitted rates are printed beside the model's so that the constants of the planner can
+be replaced by measured ones. Runs on the GPU through the public binding only.
+
+    python -m paper_2306_06007_gb300.calibrate [--eps 1e-6] [--steps 3]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+
+STAGE_WORK = {
+    "spread": lambda i: (i["nufft_pix_points"] + i["nufft_vis_points"]) * i["w"] ** 3,
+    "interp": lambda i: (i["nufft_pix_points"] + i["nufft_vis_points"]) * i["w"] ** 3,
+    "fft": lambda i: 2.0 * i["fft_work"],
+    "grid": lambda i: 2.0 * (2.0 * i["spread_cells"] + 2.0 * i["nufft_cells"]),
+    "direct": lambda i: 2.0 * i["direct_pairs"],
+}
+
+# FP32 rates of the planner's cost model (seconds per unit of work).
+MODEL = {"spread": 1.0 / 3.0e11, "interp": 1.0 / 1.2e12, "fft": 6.0e-13, "grid": 4.0e-12,
+         "direct": 1.0 / 8.5e11}
+
+
+def _workloads():
+    import numpy as np
+
+    from hvox_inputs import configs
+    out = []
+    for r in (1.0, 3.0, 10.0):
+        out.append((f"radius {r:g} km", configs.radius_sweep(r)))
+    w = configs.config3()
+    w.uvw = np.ascontiguousarray(w.uvw[np.hypot(w.uvw[:, 0], w.uvw[:, 1]) <= 500.0])
+    out.append(("config-3 dense core", w))
+    return out
+
+
+def measure(w, eps: float, steps: int):
+    import torch
+
+    from . import Plan
+    plan = Plan(w.pix, w.uvw, eps, graphs=-1)
+    info = plan.info()
+    I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
+    V = torch.zeros(w.n_vis, dtype=plan.complex_dtype, device="cuda")
+    plan.synthesize(I)
+    plan.analyze(V)
+    torch.cuda.synchronize()
+    plan.profile(True)
+    for _ in range(steps):
+        plan.synthesize(I, out=V)
+        plan.analyze(V)
+    st = plan.stats()
+    plan.close()
+    ms = {k: v / steps for k, v in st["ms"].items()}
+    ms["grid"] = ms.pop("deconv") + ms.pop("zero")
+    return info, ms
+
+
+def fit(rows):
+    """Least squares through the origin per stage: rate = sum(x t) / sum(x x)."""
+    rates = {}
+    for stage in STAGE_WORK:
+        xs = [(STAGE_WORK[stage](info), ms[stage] * 1e-3) for info, ms in rows]
+        sxx = sum(x * x for x, _ in xs)
+        sxt = sum(x * t for x, t in xs)
+        rates[stage] = sxt / sxx if sxx > 0 else None
+    return rates
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--eps", type=float, default=1e-6)
+    ap.add_argument("--steps", type=int, default=3)
+    args = ap.parse_args(argv)
+    os.environ["HVOX_NUFFT_LANES"] = "1"  # stages serialised: their times add up
+    rows, report = [], []
+    for name, w in _workloads():
+        info, ms = measure(w, args.eps, args.steps)
+        rows.append((info, ms))
+        report.append({"workload": name, "n_pix": w.n_pix, "n_vis": w.n_vis, "blocks": info["n_nufft_blocks"],
+                       "w": info["w"], "upsampfac": info["upsampfac"], "stage_ms": ms,
+                       "work": {k: f(info) for k, f in STAGE_WORK.items()}})
+    rates = fit(rows)
+    for r, (info, ms) in zip(report, rows):
+        r["model_ms"] = {k: 1e3 * MODEL[k] * f(info) for k, f in STAGE_WORK.items()}
+        r["fitted_ms"] = {k: (1e3 * rates[k] * f(info) if rates[k] else None) for k, f in STAGE_WORK.items()}
+    print(json.dumps({"eps": args.eps, "fitted_seconds_per_unit": rates, "model_seconds_per_unit": MODEL,
+                      "workloads": report}, indent=1))
+
+
+if __name__ == "__main__":
+    main()

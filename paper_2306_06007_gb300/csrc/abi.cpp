@@ -60,7 +60,9 @@ void DevBuf::free_() {
 
 Lane::~Lane() {
     if (stream) cudaStreamSynchronize(stream);
-    for (auto &kv : fft) cufftDestroy(kv.second);
+    for (auto &kv : fft)
+        for (cufftHandle h : {kv.second.full, kv.second.xy, kv.second.z})
+            if (h) cufftDestroy(h);
     if (done) cudaEventDestroy(done);
     if (stream) cudaStreamDestroy(stream);
 }
@@ -306,28 +308,47 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             lane->g2.alloc((size_t)lane_m2[l] * 2 * re);
             p.lanes.push_back(std::move(lane));
         }
-        // cuFFT plans per lane and grid shape, one work area per lane.
+        // cuFFT plans per lane and grid shape, one work area per lane. HVOX_FFT_PRUNE=0
+        // selects the full 3-D plans instead of the pruned pair.
+        bool prune = true;
+        if (const char *v = std::getenv("HVOX_FFT_PRUNE")) prune = std::atoi(v) != 0;
         std::vector<size_t> max_ws(n_lanes, 0);
+        auto make = [&](cufftHandle &h, int rank, long long *n, long long *emb, long long stride, long long dist,
+                        long long batch, size_t &ws) {
+            check_cufft(cufftCreate(&h), "cufftCreate");
+            check_cufft(cufftSetAutoAllocation(h, 0), "cufftSetAutoAllocation");
+            check_cufft(cufftMakePlanMany64(h, rank, n, emb, stride, dist, emb, stride, dist, type, batch, &ws),
+                        "cufftMakePlanMany64");
+        };
         for (size_t i = 0; i < part.blocks.size(); ++i) {
             const auto &b = part.blocks[i];
             Lane &lane = *p.lanes[p.block_lane[i]];
-            auto key = std::make_tuple(b.n2[0], b.n2[1], b.n2[2]);
+            const int64_t half = b.n1[2] / 2;
+            auto key = std::make_tuple(b.n2[0], b.n2[1], b.n2[2], prune ? half : (int64_t)-1);
             if (!lane.fft.count(key)) {
-                cufftHandle h;
-                check_cufft(cufftCreate(&h), "cufftCreate");
-                lane.fft[key] = h;
-                check_cufft(cufftSetAutoAllocation(h, 0), "cufftSetAutoAllocation");
+                FftPlans f;
                 size_t ws = 0;
-                check_cufft(cufftMakePlan3d(h, (int)b.n2[2], (int)b.n2[1], (int)b.n2[0], type, &ws),
-                            "cufftMakePlan3d");
+                if (prune) {
+                    long long nxy[2] = {b.n2[1], b.n2[0]};
+                    make(f.xy, 2, nxy, nullptr, 1, b.n2[0] * b.n2[1], half, ws);
+                    max_ws[p.block_lane[i]] = std::max(max_ws[p.block_lane[i]], ws);
+                    long long nz[1] = {b.n2[2]}, emb[1] = {b.n2[2]};
+                    make(f.z, 1, nz, emb, b.n2[0] * b.n2[1], 1, b.n2[0] * b.n2[1], ws);
+                } else {
+                    long long n3[3] = {b.n2[2], b.n2[1], b.n2[0]};
+                    make(f.full, 3, n3, nullptr, 1, 0, 1, ws);
+                }
                 max_ws[p.block_lane[i]] = std::max(max_ws[p.block_lane[i]], ws);
+                lane.fft[key] = f;
             }
             p.block_fft.push_back(lane.fft[key]);
         }
         for (int l = 0; l < n_lanes; ++l) {
             Lane &lane = *p.lanes[l];
             lane.work.alloc(std::max<size_t>(max_ws[l], 256));
-            for (auto &kv : lane.fft) check_cufft(cufftSetWorkArea(kv.second, lane.work.ptr), "cufftSetWorkArea");
+            for (auto &kv : lane.fft)
+                for (cufftHandle h : {kv.second.full, kv.second.xy, kv.second.z})
+                    if (h) check_cufft(cufftSetWorkArea(h, lane.work.ptr), "cufftSetWorkArea");
         }
         auto split = [](double x, float &h, float &l) {
             h = (float)x;
@@ -442,6 +463,10 @@ void fill_info(const Plan &p, hvox_info *info) {
     info->plan_seconds = p.plan_seconds;
     info->model_seconds = p.part.model_seconds;
     info->graph_state = p.graph_state;
+    info->nufft_pix_points = p.part.nufft_pix_points;
+    info->nufft_vis_points = p.part.nufft_vis_points;
+    info->spread_cells = p.part.spread_cells;
+    info->fft_work = p.part.fft_work;
 }
 
 void transform(Plan &p, const void *in, void *out, bool s2v) {
@@ -607,9 +632,12 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         p.part = make_partition(in);
         p.sigma = p.part.sigma;
         p.es = p.part.es;
+        // Estimate of what hvox_plan would allocate: coordinates and permutations, the
+        // source and accumulator, and per lane the grids and a cuFFT work area of about
+        // the largest sub-problem's size.
         const double re = p.prec == 1 ? 4.0 : 8.0;
-        double recs = p.part.nufft_points * (p.prec == 1 ? 48.0 : 64.0);
-        p.workspace_bytes = (double)(n_pix + n_vis) * 60.0 + recs + p.part.max_grid_bytes +
+        const double lanes = (double)std::min<size_t>(kMaxLanes, p.part.blocks.size());
+        p.workspace_bytes = (double)(n_pix + n_vis) * 60.0 + 2.0 * lanes * p.part.max_grid_bytes +
                             4.0 * re * (double)std::max(n_pix, 2 * n_vis);
         p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         fill_info(p, info);

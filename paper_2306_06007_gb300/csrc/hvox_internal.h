@@ -107,6 +107,7 @@ struct PartitionResult {
     std::vector<NufftBlock> blocks;
     std::vector<DirectRect> rects;
     double direct_pairs = 0, nufft_points = 0, nufft_cells = 0, max_grid_bytes = 0;
+    double nufft_pix_points = 0, nufft_vis_points = 0, spread_cells = 0, fft_work = 0;
     double model_seconds = 0;
 };
 
@@ -160,6 +161,15 @@ template <typename T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
 
+// cuFFT plans of one FFT-grid shape. Pruned form (xy and z set): the 3-D transform as a 2-D
+// transform of the n1 band's z planes (two slabs of n1z/2 planes, at the start and the end
+// of the grid) and a 1-D transform along z of every column; the other z planes hold only
+// zeros before the transform (sky -> vis) or are not read after it (vis -> sky), so their
+// 2-D transforms are skipped. Full form (full set): one 3-D plan.
+struct FftPlans {
+    cufftHandle full = 0, xy = 0, z = 0;
+};
+
 // Plan-wide arguments of the NUFFT launchers.
 template <typename T> struct NufftArgs {
     int w = 0;
@@ -167,7 +177,7 @@ template <typename T> struct NufftArgs {
     int isign = -1;
     typename CplxOf<T>::type *G1 = nullptr, *G2 = nullptr;
     const T *ipsi = nullptr;
-    cufftHandle fft = 0;
+    FftPlans fft;
     const float4 *pix_hi = nullptr, *pix_lo = nullptr, *vis_hi = nullptr, *vis_lo = nullptr;
     const double *pix_soa = nullptr, *vis_soa = nullptr;
     int64_t n_pix = 0, n_vis = 0;
@@ -189,7 +199,7 @@ struct Lane {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     DevBuf g1, g2, work;
-    std::map<std::tuple<int64_t, int64_t, int64_t>, cufftHandle> fft;
+    std::map<std::tuple<int64_t, int64_t, int64_t, int64_t>, FftPlans> fft;
     ~Lane();
 };
 
@@ -264,7 +274,7 @@ struct Plan {
     cudaEvent_t fork_event = nullptr;   // main stream -> lanes
     std::vector<NufftDev> dblocks;      // block descriptors (launch order)
     std::vector<int> block_lane;        // lane of each block
-    std::vector<cufftHandle> block_fft; // FFT plan of each block (its lane's plan for its shape)
+    std::vector<FftPlans> block_fft;    // FFT plans of each block (its lane's plans for its shape)
     DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
 
     // per-call buffers (chunk order)

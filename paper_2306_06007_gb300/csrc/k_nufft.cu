@@ -677,6 +677,35 @@ template <typename T, int W> void set_smem_attrs() {
 
 // ------------------------------------------------------------------ host launchers
 
+// In-place transform of the FFT grid with sign dir. band_input: only the n1 band's z planes
+// are nonzero (sky -> vis: 2-D transforms of those planes, then z); otherwise only those
+// planes are read afterwards (vis -> sky: z first, then 2-D transforms of those planes).
+template <typename T>
+void fft_grid(const NufftDev &b, const NufftArgs<T> &a, int dir, bool band_input, cudaStream_t s) {
+    auto exec = [&](cufftHandle h, typename CplxOf<T>::type *g) {
+        check_cufft(cufftSetStream(h, s), "cufftSetStream");
+        if constexpr (sizeof(T) == 4)
+            check_cufft(cufftExecC2C(h, (cufftComplex *)g, (cufftComplex *)g, dir), "cufftExecC2C");
+        else
+            check_cufft(cufftExecZ2Z(h, (cufftDoubleComplex *)g, (cufftDoubleComplex *)g, dir), "cufftExecZ2Z");
+    };
+    if (a.fft.full) {
+        exec(a.fft.full, a.G2);
+        return;
+    }
+    const int64_t plane = (int64_t)b.n2[0] * b.n2[1];
+    typename CplxOf<T>::type *upper = a.G2 + (int64_t)(b.n2[2] - b.n1[2] / 2) * plane;
+    if (band_input) {
+        exec(a.fft.xy, a.G2);
+        exec(a.fft.xy, upper);
+        exec(a.fft.z, a.G2);
+    } else {
+        exec(a.fft.z, a.G2);
+        exec(a.fft.xy, a.G2);
+        exec(a.fft.xy, upper);
+    }
+}
+
 template <typename T>
 void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_t<T> *acc, cudaStream_t s,
                      StageHook &hook) {
@@ -703,12 +732,7 @@ void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_
     check_cuda(cudaGetLastError(), "deconv_pad");
     hook.end(HVOX_STAGE_DECONV, 1, s);
     hook.begin(HVOX_STAGE_FFT, s);
-    check_cufft(cufftSetStream(a.fft, s), "cufftSetStream");
-    const int dir = a.isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE;
-    if constexpr (sizeof(T) == 4)
-        check_cufft(cufftExecC2C(a.fft, (cufftComplex *)a.G2, (cufftComplex *)a.G2, dir), "cufftExecC2C");
-    else
-        check_cufft(cufftExecZ2Z(a.fft, (cufftDoubleComplex *)a.G2, (cufftDoubleComplex *)a.G2, dir), "cufftExecZ2Z");
+    fft_grid<T>(b, a, a.isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE, true, s);
     hook.end(HVOX_STAGE_FFT, 1, s);
     if (b.nv > 0) {
         hook.begin(HVOX_STAGE_INTERP, s);
@@ -743,12 +767,7 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
         hook.end(HVOX_STAGE_SPREAD, 1, s);
     }
     hook.begin(HVOX_STAGE_FFT, s);
-    check_cufft(cufftSetStream(a.fft, s), "cufftSetStream");
-    const int dir = a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD;  // transpose: opposite sign
-    if constexpr (sizeof(T) == 4)
-        check_cufft(cufftExecC2C(a.fft, (cufftComplex *)a.G2, (cufftComplex *)a.G2, dir), "cufftExecC2C");
-    else
-        check_cufft(cufftExecZ2Z(a.fft, (cufftDoubleComplex *)a.G2, (cufftDoubleComplex *)a.G2, dir), "cufftExecZ2Z");
+    fft_grid<T>(b, a, a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD, false, s);  // transpose: opposite sign
     hook.end(HVOX_STAGE_FFT, 1, s);
     hook.begin(HVOX_STAGE_DECONV, s);
     crop_deconv_kernel<T><<<row_ctas((int64_t)b.n1[1] * b.n1[2]), kRowThreads, 0, s>>>(

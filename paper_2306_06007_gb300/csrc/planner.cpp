@@ -529,6 +529,10 @@ PartitionResult make_partition(const PlanInputs &in) {
         r.max_grid_bytes = std::max(r.max_grid_bytes, (double)in.elem_bytes * (m1 + m2));
         r.nufft_cells += cells;
         r.nufft_points += (double)(b.p1 - b.p0 + b.v1 - b.v0);
+        r.nufft_pix_points += (double)(b.p1 - b.p0);
+        r.nufft_vis_points += (double)(b.v1 - b.v0);
+        r.spread_cells += m1;
+        r.fft_work += m2 * std::log2(std::max(2.0, m2));
         r.blocks.push_back(b);
         nufft_pix_of_v[vj].push_back(pi);
     }

@@ -265,3 +265,22 @@ def test_upsampling_factors(gpu_lib, small, sigma, eps):
     assert abs(info["upsampfac"] - sigma) < 1e-12 and info["n_nufft_blocks"] >= 1
     assert oracle.rel_l2(V, oracle.sky2vis(w.pix, w.uvw, w.sky)) <= 10 * eps
     assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 10 * eps
+
+
+def test_radius_sweep_10km_sampled(gpu_lib):
+    # The paper's 10 km setup at matched resolution (10,240,000 pixels x 237,705
+    # baselines): four large NUFFT sub-problems; 300 seeded outputs per direction are
+    # checked against the oracle.
+    w = configs.radius_sweep(10.0)
+    eps = 1e-6
+    plan = gpu_lib.Plan(w.pix, w.uvw, eps)
+    info = plan.info()
+    assert info["n_nufft_blocks"] > 0 and info["direct_pairs"] < 0.01 * w.n_pix * w.n_vis
+    V = plan.synthesize(torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+    vis = configs.visibilities_cn(6, w.n_vis)
+    img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
+    plan.close()
+    kv = configs.sample_indices(6, w.n_vis, 300)
+    kp = configs.sample_indices(6, w.n_pix, 300, purpose_offset=1)
+    assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
+    assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
