@@ -31,8 +31,8 @@ STAGE_WORK = {
     "direct": lambda i: 2.0 * i["direct_pairs"],
 }
 
-# FP32 rates of the planner's cost model (seconds per unit of work).
-MODEL = {"spread": 1.0 / 3.0e11, "interp": 1.0 / 1.2e12, "fft": 6.0e-13, "grid": 4.0e-12,
+# FP32 rates of the planner's cost model (seconds per unit of work), as last fitted.
+MODEL = {"spread": 1.0 / 4.75e11, "interp": 1.0 / 1.0e12, "fft": 4.1e-13, "grid": 1.3e-12,
          "direct": 1.0 / 8.5e11}
 
 
