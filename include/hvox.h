@@ -134,6 +134,8 @@ typedef struct {
     double nufft_vis_points;     /* baselines gathered (and, in vis->sky, spread) */
     double spread_cells;         /* n1 grid cells (M1) */
     double fft_work;             /* M2 log2 M2 over the FFT grids */
+    double box_ratio;            /* pixel box dims = ratio x Algorithm 1's, baseline box dims
+                                    = Algorithm 1's / ratio (1: the isotropic optimum) */
 } hvox_info;
 
 /*

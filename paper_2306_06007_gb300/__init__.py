@@ -53,7 +53,7 @@ class Info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_double), ("plan_seconds", ctypes.c_double),
                 ("model_seconds", ctypes.c_double), ("graph_state", ctypes.c_int32),
                 ("nufft_pix_points", ctypes.c_double), ("nufft_vis_points", ctypes.c_double),
-                ("spread_cells", ctypes.c_double), ("fft_work", ctypes.c_double)]
+                ("spread_cells", ctypes.c_double), ("fft_work", ctypes.c_double), ("box_ratio", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):

@@ -467,6 +467,7 @@ void fill_info(const Plan &p, hvox_info *info) {
     info->nufft_vis_points = p.part.nufft_vis_points;
     info->spread_cells = p.part.spread_cells;
     info->fft_work = p.part.fft_work;
+    info->box_ratio = p.part.box_ratio;
 }
 
 void transform(Plan &p, const void *in, void *out, bool s2v) {

@@ -108,6 +108,7 @@ struct PartitionResult {
     std::vector<DirectRect> rects;
     double direct_pairs = 0, nufft_points = 0, nufft_cells = 0, max_grid_bytes = 0;
     double nufft_pix_points = 0, nufft_vis_points = 0, spread_cells = 0, fft_work = 0;
+    double box_ratio = 1.0;   // eta / h split relative to Algorithm 1's isotropic boxes
     double model_seconds = 0;
 };
 

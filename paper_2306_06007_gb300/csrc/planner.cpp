@@ -224,7 +224,7 @@ ChunkStats stats_of(const double *xyz, int64_t n, const std::vector<int64_t> &la
 }
 
 struct Evaluated {
-    double t, h[3], eta[3], budget;
+    double t, h[3], eta[3], budget, ratio = 1.0;
     std::vector<int64_t> pl, vl;
     int64_t npc, nvc;
     ChunkStats ps, vs;
@@ -261,10 +261,20 @@ double nufft_cost(const CostModel &m, const ESKernel &es, double sigma, int64_t 
     return c;
 }
 
-Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, const double P[3], const double B[3]) {
+// ratio: how the Heisenberg volume of Algorithm 1's boxes is split between the two sets
+// (eta scaled by ratio, h by 1 / ratio: the same grid per sub-problem, larger pixel chunks
+// and smaller baseline chunks for ratio > 1).
+Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, const double P[3], const double B[3],
+                   double ratio = 1.0) {
     Evaluated e;
     e.budget = budget;
+    e.ratio = ratio;
     e.t = box_dims(P, B, budget, in.sigma, in.es.w, in.elem_bytes, e.eta, e.h);
+    if (ratio != 1.0)
+        for (int d = 0; d < 3; ++d) {
+            e.eta[d] *= ratio;
+            e.h[d] /= ratio;
+        }
     e.npc = chunk_points(in.pix, in.n_pix, e.eta, e.pl);
     e.nvc = chunk_points(in.uvw, in.n_vis, e.h, e.vl);
     e.ps = stats_of(in.pix, in.n_pix, e.pl, e.npc);
@@ -410,7 +420,30 @@ PartitionResult make_partition(const PlanInputs &in) {
                 evals[c] = Evaluated();
             }
         }
+        // Second pass: at the chosen upsampling and budget, split the Heisenberg volume
+        // differently between pixel and baseline boxes (the number of times each point is
+        // spread or gathered is the number of chunks of the other set it meets).
+        if (best.cost > 0 && !best.nufft_pairs.empty()) {
+            const std::vector<double> ratios{0.25, 0.5, 2.0, 4.0, 8.0};
+            std::vector<Evaluated> rev(ratios.size());
+            PlanInputs cand = in;
+            cand.sigma = best_sigma;
+            cand.es = best_es;
+            const double bud = best.budget;
+            for (size_t c0 = 0; c0 < ratios.size(); c0 += width) {
+                std::vector<std::future<void>> jobs;
+                for (size_t c = c0; c < std::min(ratios.size(), c0 + width); ++c)
+                    jobs.push_back(std::async(std::launch::async,
+                                              [&, c] { rev[c] = evaluate(cand, m, bud, P, B, ratios[c]); }));
+                for (auto &j : jobs) j.get();
+                for (size_t c = c0; c < std::min(ratios.size(), c0 + width); ++c) {
+                    if (rev[c].cost < best.cost) best = std::move(rev[c]);
+                    rev[c] = Evaluated();
+                }
+            }
+        }
     }
+    r.box_ratio = best.ratio;
     r.sigma = best_sigma;
     r.es = best_es;
     r.t = best.t;
