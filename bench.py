@@ -58,6 +58,22 @@ def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The largest x over all ranks (a timed region ends when the slowest replica does)."""
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(units_per_rank_step: float, steps: int, seconds: float, world: int) -> float:
+    """Units processed by all replicas per second of the slowest replica (weak scaling)."""
+    return world * units_per_rank_step * steps / seconds
+
+
 WORKLOADS = {
     1: "HEALPix nside=32 45deg cap (1,740 px) x 200 antennas in a 1 km disk (19,900 baselines)",
     2: WORKLOAD,
@@ -269,13 +285,10 @@ def run_gpu(args):
         clk = clocks.stop()
         if world > 1:
             dist.barrier()
-        total_ms = sum(ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = max_over_ranks(sum(ms), world)
         out = {"plan": plan, "info": info, "ms_per_step": total_ms / args.steps,
-               "value": world * units_per_step * args.steps / (total_ms * 1e-3), "stats": st, "clocks": clk}
+               "value": whole_job_rate(units_per_step, args.steps, total_ms * 1e-3, world), "stats": st,
+               "clocks": clk}
         if with_e2e:
             Ih = torch.as_tensor(w.sky, dtype=plan.real_dtype).pin_memory()
             Vh = torch.as_tensor(vis, dtype=plan.complex_dtype).pin_memory()
@@ -290,13 +303,9 @@ def run_gpu(args):
             for _ in range(args.steps):
                 plan.synthesize(Ih, out=Vo)   # host I in, host V out
                 plan.analyze(Vh, out=Io)      # host V in, host I out
-            el = time.perf_counter() - t0
-            if world > 1:
-                t = torch.tensor([el], device="cuda", dtype=torch.float64)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                el = float(t.item())
+            el = max_over_ranks(time.perf_counter() - t0, world)
             rb = Ih.element_size()
-            out["e2e"] = {"value": world * units_per_step * args.steps / el, "unit": UNIT,
+            out["e2e"] = {"value": whole_job_rate(units_per_step, args.steps, el, world), "unit": UNIT,
                           "h2d_bytes_per_step": w.n_pix * rb + w.n_vis * 2 * rb,
                           "d2h_bytes_per_step": w.n_vis * 2 * rb + w.n_pix * rb,
                           "ms_per_step": el * 1e3 / args.steps}
