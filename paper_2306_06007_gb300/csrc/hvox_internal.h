@@ -67,8 +67,6 @@ struct NufftBlock {
     int64_t n1[3] = {0, 0, 0};
     int64_t n2[3] = {0, 0, 0};
     int64_t psi_off = 0;      // offset of this block's 1/psi tables (n1[0]+n1[1]+n1[2])
-    int64_t prec_off = 0;     // offset of pixel-side records (p1 - p0 entries)
-    int64_t vrec_off = 0;     // offset of baseline-side records (v1 - v0 entries)
     double cost = 0.0;
 };
 

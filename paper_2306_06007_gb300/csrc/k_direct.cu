@@ -10,9 +10,10 @@
 // integer turns dropped exactly, and only the fraction of a turn is carried on:
 //  * FP32 path (eps >= 1e-6): fraction in FP32 (abs error ~1e-7 turn), hardware
 //    sin/cos approximations, FP32 accumulation;
-//  * double-float path (eps < 1e-6): fraction as an unevaluated float pair, sin/cos
-//    from a 256-entry table of exp(j 2 pi m / 256) (float pairs) times a short series,
-//    products and sums in double-float arithmetic (Dekker 1971), ~1e-11 absolute;
+//  * double-float path (eps < 1e-6): fraction as an unevaluated float pair; exp(j 2 pi f)
+//    as the hi parts of a periodic 2048-entry table of exp(j 2 pi m / 2048) plus a lo part
+//    (the table's lo parts and a short series in the remainder, in plain float; error
+//    2.7e-10); products and sums in double-float arithmetic (Dekker 1971);
 //  * plain path: everything in FP64 (the reference form the optimised paths replace).
 #include <cstdint>
 #include <mutex>
