@@ -268,7 +268,7 @@ def run_gpu(args):
     vis = configs.visibilities_cn(args.config, w.n_vis)
 
     def measure(eps, with_e2e):
-        plan = hvox.Plan(w.pix, w.uvw, eps, mode=args.mode, graphs=args.graphs)
+        plan = hvox.Plan(w.pix, w.uvw, eps, mode=args.mode, graphs=args.graphs, plain=args.plain)
         info = plan.info()
         I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
         V = torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")
@@ -355,6 +355,7 @@ def run_gpu(args):
             "config": {"workload": w.name + "; step = sky->vis + vis->sky" if args.radius_km > 0
                        else WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
                        "mode": args.mode, "core_radius": args.core_radius or None, "graphs": args.graphs,
+                       "plain": args.plain,
                        "l2": "flushed before each step (256 MiB write, outside the timed window)",
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
                        "direct_pairs": info["direct_pairs"], "w": info["w"]},
@@ -398,6 +399,8 @@ def main():
     ap.add_argument("--radius-km", type=float, default=0.0,
                     help="study: telescope-radius sweep workload (0.1, 0.3, 1, 3, 10, 30 or 100 km)")
     ap.add_argument("--sparse", type=int, default=0, help="study: keep this many sky pixels (sparse sky)")
+    ap.add_argument("--plain", action="store_true",
+                    help="study: the plain FP64 form (FP64 arithmetic in every kernel, no graph)")
     ap.add_argument("--graphs", type=int, default=0, choices=[-1, 0, 1],
                     help="CUDA graphs: 0 for plans with NUFFT sub-problems, 1 always, -1 never")
     ap.add_argument("--core-radius", type=float, default=0.0,

@@ -101,6 +101,10 @@ typedef struct {
                                     (zeroing, direct launch, every sub-problem on its lane)
                                     into one graph, which later calls replay. Ignored by
                                     the plain form. */
+    int32_t chunk_order;         /* 1: the caller passes and receives I and V in the plan's
+                                    chunk order (hvox_plan_order gives it), so the
+                                    permutations are skipped; the weights a_n are still
+                                    applied. 0: the caller's own point order. */
     void *stream;                /* cudaStream_t; NULL = legacy default stream */
 } hvox_opts;
 
@@ -167,6 +171,16 @@ hvox_status hvox_analyze(hvox_plan_t plan, const void *V, void *I);
 /* Free every resource of the plan (waits for its stream). NULL is accepted. */
 hvox_status hvox_destroy(hvox_plan_t plan);
 
+/* Complex sky (the paper's real=False form of Listing 1): I is ntrans = 1 complex
+ * array of n_pix (float2/double2 interleaved in the plan's precision), V as above; both
+ * device pointers (HVOX_EINVAL for host pointers, HVOX_EUNSUPPORTED for ntrans > 1).
+ *   hvox_synthesize_complex: V_k = sum_n a_n I_n exp(+isign j 2 pi <p_k, r_n>)
+ *   hvox_analyze_complex:    I_n = a_n sum_k V_k exp(-isign j 2 pi <p_k, r_n>) (no real part)
+ * Each runs the real transform twice (linearity: A (x + j y) = A x + j A y, and
+ * A^H v = Re(A^H v) + j Re(A^H (-j v))). */
+hvox_status hvox_synthesize_complex(hvox_plan_t plan, const void *I, void *V);
+hvox_status hvox_analyze_complex(hvox_plan_t plan, const void *V, void *I);
+
 /* Aliases with the direction in the name. */
 hvox_status hvox_dirty2vis(hvox_plan_t plan, const void *I, void *V);
 hvox_status hvox_vis2dirty(hvox_plan_t plan, const void *V, void *I);
@@ -178,6 +192,13 @@ hvox_status hvox_plan_info(hvox_plan_t plan, hvox_info *info);
  * pix_chunk[n] (n_pix entries) and vis_chunk[k] (n_vis entries), host pointers,
  * either may be NULL. Chunks are numbered as Algorithm 2 creates them. */
 hvox_status hvox_plan_chunks(hvox_plan_t plan, int64_t *pix_chunk, int64_t *vis_chunk);
+
+/* The plan's chunk order (Sect. 4: inputs reordered so that every sub-problem reads
+ * contiguous slices): pix_order[m] (n_pix entries) is the caller's index of the pixel at
+ * chunk position m, vis_order[m] (n_vis entries) likewise for baselines. Host pointers,
+ * either may be NULL. A caller that keeps its data in this order plans with
+ * hvox_opts.chunk_order = 1. */
+hvox_status hvox_plan_order(hvox_plan_t plan, int64_t *pix_order, int64_t *vis_order);
 
 /* Stages of a transform, for hvox_get_stats. */
 enum {

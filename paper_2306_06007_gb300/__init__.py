@@ -38,7 +38,7 @@ class Opts(ctypes.Structure):
                 ("chunk_budget_bytes", ctypes.c_double), ("anisotropy", ctypes.c_double),
                 ("direct_threshold", ctypes.c_double), ("search_threshold", ctypes.c_double),
                 ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("graphs", ctypes.c_int32), ("chunk_order", ctypes.c_int32), ("stream", ctypes.c_void_p)]
 
 
 class Info(ctypes.Structure):
@@ -90,6 +90,9 @@ def load():
         "hvox_sync": [P],
         "hvox_plan_info": [P, ctypes.POINTER(Info)],
         "hvox_plan_chunks": [P, PI64, PI64],
+        "hvox_plan_order": [P, PI64, PI64],
+        "hvox_synthesize_complex": [P, P, P],
+        "hvox_analyze_complex": [P, P, P],
         "hvox_profile": [P, ctypes.c_int],
         "hvox_get_stats": [P, ctypes.POINTER(Stats)],
         "hvox_es_params": [ctypes.c_double, ctypes.c_double, ctypes.POINTER(I32), D],
@@ -262,7 +265,7 @@ class Plan:
     def __init__(self, pix, uvw, eps: float, isign: int = -1, weight=None, precision="auto", mode="auto",
                  upsampfac: float = 0.0, chunk_budget_bytes: float = 0.0, anisotropy: float = 0.0,
                  direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, graphs: int = 0,
-                 search_threshold: float = 0.0, stream=None):
+                 search_threshold: float = 0.0, chunk_order: bool = False, stream=None):
         import torch
         lib = load()
         self._handle = ctypes.c_void_p()
@@ -280,6 +283,7 @@ class Plan:
         o.ntrans = ntrans
         o.plain = 1 if plain else 0
         o.graphs = int(graphs)
+        o.chunk_order = 1 if chunk_order else 0
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
@@ -329,6 +333,32 @@ class Plan:
         _check(load().hvox_analyze(self._handle, ctypes.c_void_p(V.data_ptr()), ctypes.c_void_p(I.data_ptr())))
         return I
 
+    def synthesize_complex(self, I):
+        """sky -> vis for a complex sky (device tensor, complex dtype of the plan)."""
+        import torch
+        if self.ntrans != 1:
+            raise ValueError("complex-sky transforms take ntrans = 1")
+        I = torch.as_tensor(I).to(device="cuda", dtype=self.complex_dtype).contiguous()
+        if I.numel() != self.n_pix:
+            raise ValueError(f"expected {self.n_pix} elements, got {I.numel()}")
+        V = torch.empty(self.n_vis, dtype=self.complex_dtype, device="cuda")
+        _check(load().hvox_synthesize_complex(self._handle, ctypes.c_void_p(I.data_ptr()),
+                                              ctypes.c_void_p(V.data_ptr())))
+        return V
+
+    def analyze_complex(self, V):
+        """vis -> sky without taking the real part: a_n sum_k V_k exp(-isign j 2 pi <p_k, r_n>)."""
+        import torch
+        if self.ntrans != 1:
+            raise ValueError("complex-sky transforms take ntrans = 1")
+        V = torch.as_tensor(V).to(device="cuda", dtype=self.complex_dtype).contiguous()
+        if V.numel() != self.n_vis:
+            raise ValueError(f"expected {self.n_vis} elements, got {V.numel()}")
+        I = torch.empty(self.n_pix, dtype=self.complex_dtype, device="cuda")
+        _check(load().hvox_analyze_complex(self._handle, ctypes.c_void_p(V.data_ptr()),
+                                           ctypes.c_void_p(I.data_ptr())))
+        return I
+
     dirty2vis = synthesize
     vis2dirty = analyze
 
@@ -349,6 +379,15 @@ class Plan:
         _check(load().hvox_plan_chunks(self._handle, pc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
                                        vc.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
         return pc, vc
+
+    def order(self):
+        """(pix_order, vis_order): the caller's index of the point at each chunk position."""
+        np = _np()
+        po = np.zeros(self.n_pix, dtype=np.int64)
+        vo = np.zeros(self.n_vis, dtype=np.int64)
+        _check(load().hvox_plan_order(self._handle, po.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)),
+                                      vo.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))))
+        return po, vo
 
     def sync(self):
         _check(load().hvox_sync(self._handle))

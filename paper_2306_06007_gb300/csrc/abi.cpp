@@ -418,6 +418,8 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.plain = o.plain != 0;
     if (o.graphs < -1 || o.graphs > 1) fail(HVOX_EINVAL, "hvox_plan: graphs must be -1, 0 or 1");
     p.graphs_opt = o.graphs;
+    if (o.chunk_order < 0 || o.chunk_order > 1) fail(HVOX_EINVAL, "hvox_plan: chunk_order must be 0 or 1");
+    p.chunk_order = o.chunk_order != 0;
     p.mode = eps == 0.0 ? HVOX_MODE_DIRECT : o.mode;
     p.prec = p.plain ? 2 : (o.precision == HVOX_PREC_AUTO ? (eps >= 1e-6 ? 1 : 2) : o.precision);
     p.ntrans = o.ntrans > 0 ? o.ntrans : 1;
@@ -554,6 +556,28 @@ hvox_status hvox_analyze(hvox_plan_t plan, const void *V, void *I) {
     });
 }
 
+hvox_status hvox_synthesize_complex(hvox_plan_t plan, const void *I, void *V) {
+    return guard([&] {
+        if (!plan || !I || !V) fail(HVOX_EINVAL, "hvox_synthesize_complex: NULL argument");
+        Plan &p = plan->p;
+        check_cuda(cudaSetDevice(p.device), "cudaSetDevice");
+        if (p.ntrans != 1) fail(HVOX_EUNSUPPORTED, "hvox_synthesize_complex: ntrans must be 1");
+        if (!is_device_ptr(I) || !is_device_ptr(V)) fail(HVOX_EINVAL, "hvox_synthesize_complex: device pointers only");
+        run_synthesize_complex(p, I, V);
+    });
+}
+
+hvox_status hvox_analyze_complex(hvox_plan_t plan, const void *V, void *I) {
+    return guard([&] {
+        if (!plan || !I || !V) fail(HVOX_EINVAL, "hvox_analyze_complex: NULL argument");
+        Plan &p = plan->p;
+        check_cuda(cudaSetDevice(p.device), "cudaSetDevice");
+        if (p.ntrans != 1) fail(HVOX_EUNSUPPORTED, "hvox_analyze_complex: ntrans must be 1");
+        if (!is_device_ptr(I) || !is_device_ptr(V)) fail(HVOX_EINVAL, "hvox_analyze_complex: device pointers only");
+        run_analyze_complex(p, V, I);
+    });
+}
+
 hvox_status hvox_dirty2vis(hvox_plan_t plan, const void *I, void *V) { return hvox_synthesize(plan, I, V); }
 hvox_status hvox_vis2dirty(hvox_plan_t plan, const void *V, void *I) { return hvox_analyze(plan, V, I); }
 
@@ -642,6 +666,15 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
                             4.0 * re * (double)std::max(n_pix, 2 * n_vis);
         p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         fill_info(p, info);
+    });
+}
+
+hvox_status hvox_plan_order(hvox_plan_t plan, int64_t *pix_order, int64_t *vis_order) {
+    return guard([&] {
+        if (!plan) fail(HVOX_EINVAL, "hvox_plan_order: NULL plan");
+        const Plan &p = plan->p;
+        if (pix_order) std::memcpy(pix_order, p.part.pix_perm.data(), sizeof(int64_t) * p.n_pix);
+        if (vis_order) std::memcpy(vis_order, p.part.vis_perm.data(), sizeof(int64_t) * p.n_vis);
     });
 }
 

@@ -20,6 +20,10 @@ size_t real_bytes(const Plan &p) { return p.prec == 1 ? sizeof(float) : sizeof(d
 
 const double *weight_ptr(const Plan &p) { return p.has_weight ? p.weight.as<double>() : nullptr; }
 
+// Permutations of the caller's data (null: the caller works in chunk order).
+const int32_t *pix_perm(const Plan &p) { return p.chunk_order ? nullptr : p.pix_perm.as<int32_t>(); }
+const int32_t *vis_perm(const Plan &p) { return p.chunk_order ? nullptr : p.vis_perm.as<int32_t>(); }
+
 cudaEvent_t take_event(Plan &p) {
     if (!p.event_pool.empty()) {
         cudaEvent_t e = p.event_pool.back();
@@ -314,11 +318,11 @@ void run_synthesize(Plan &p, const void *I, void *V) {
         const char *It = (const char *)I + (size_t)t * p.n_pix * re;
         char *Vt = (char *)V + (size_t)t * p.n_vis * 2 * re;
         prof.begin(HVOX_STAGE_PERMUTE, s);
-        launch_s2v_in(p.prec, It, p.pix_perm.as<int32_t>(), weight_ptr(p), p.n_pix, p.src.ptr, s);
+        launch_s2v_in(p.prec, It, pix_perm(p), weight_ptr(p), p.n_pix, p.src.ptr, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
         execute(p, 0);
         prof.begin(HVOX_STAGE_PERMUTE, s);
-        launch_s2v_out(p.prec, p.acc.ptr, p.vis_perm.as<int32_t>(), p.n_vis, Vt, s);
+        launch_s2v_out(p.prec, p.acc.ptr, vis_perm(p), p.n_vis, Vt, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
         p.transforms++;
     }
@@ -332,14 +336,38 @@ void run_analyze(Plan &p, const void *V, void *I) {
         const char *Vt = (const char *)V + (size_t)t * p.n_vis * 2 * re;
         char *It = (char *)I + (size_t)t * p.n_pix * re;
         prof.begin(HVOX_STAGE_PERMUTE, s);
-        launch_v2s_in(p.prec, Vt, p.vis_perm.as<int32_t>(), p.n_vis, p.src.ptr, s);
+        launch_v2s_in(p.prec, Vt, vis_perm(p), p.n_vis, p.src.ptr, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
         execute(p, 1);
         prof.begin(HVOX_STAGE_PERMUTE, s);
-        launch_v2s_out(p.prec, p.acc.ptr, p.pix_perm.as<int32_t>(), weight_ptr(p), p.n_pix, It, s);
+        launch_v2s_out(p.prec, p.acc.ptr, pix_perm(p), weight_ptr(p), p.n_pix, It, s);
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
         p.transforms++;
     }
+}
+
+// A (x + j y) = A x + j A y: both real skies through the ordinary path, then V += j V'.
+void run_synthesize_complex(Plan &p, const void *I, void *V) {
+    const size_t re = real_bytes(p);
+    if (p.cplx_sky.bytes < 2 * (size_t)p.n_pix * re) p.cplx_sky.alloc(2 * (size_t)p.n_pix * re);
+    if (p.cplx_vis.bytes < 2 * (size_t)p.n_vis * re) p.cplx_vis.alloc(2 * (size_t)p.n_vis * re);
+    char *x = (char *)p.cplx_sky.ptr, *y = x + (size_t)p.n_pix * re;
+    launch_split_complex(p.prec, I, p.n_pix, x, y, p.stream);
+    run_synthesize(p, x, V);
+    run_synthesize(p, y, p.cplx_vis.ptr);
+    launch_add_j(p.prec, V, p.cplx_vis.ptr, p.n_vis, p.stream);
+}
+
+// A^H v = Re(A^H v) + j Re(A^H (-j v)): the ordinary (real-part) adjoint twice.
+void run_analyze_complex(Plan &p, const void *V, void *I) {
+    const size_t re = real_bytes(p);
+    if (p.cplx_sky.bytes < 2 * (size_t)p.n_pix * re) p.cplx_sky.alloc(2 * (size_t)p.n_pix * re);
+    if (p.cplx_vis.bytes < 2 * (size_t)p.n_vis * re) p.cplx_vis.alloc(2 * (size_t)p.n_vis * re);
+    char *x = (char *)p.cplx_sky.ptr, *y = x + (size_t)p.n_pix * re;
+    run_analyze(p, V, x);
+    launch_times_mj(p.prec, V, p.n_vis, p.cplx_vis.ptr, p.stream);
+    run_analyze(p, p.cplx_vis.ptr, y);
+    launch_join_complex(p.prec, x, y, p.n_pix, I, p.stream);
 }
 
 }  // namespace hvox

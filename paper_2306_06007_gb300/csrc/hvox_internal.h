@@ -279,8 +279,10 @@ struct Plan {
     // per-call buffers (chunk order)
     DevBuf src, acc;                    // source values, accumulated outputs
     DevBuf io_in, io_out;               // staging for host-pointer calls
+    DevBuf cplx_sky, cplx_vis;          // complex-sky calls: two real skies, one visibility set
 
     // CUDA graphs (per direction, per profiling state)
+    bool chunk_order = false;           // hvox_opts.chunk_order: caller data already in chunk order
     int graphs_opt = 0;                 // hvox_opts.graphs
     int graph_state = 0;                // 0 eager so far, 1 captured, -1 capture failed
     int eager_calls[2] = {0, 0};
@@ -334,6 +336,13 @@ void launch_v2s_out(int prec, const void *acc, const int32_t *perm, const double
 // Transforms.
 void run_synthesize(Plan &p, const void *I_dev, void *V_dev);
 void run_analyze(Plan &p, const void *V_dev, void *I_dev);
+// Complex sky (device pointers, ntrans = 1): two real transforms combined by linearity.
+void run_synthesize_complex(Plan &p, const void *I_dev, void *V_dev);
+void run_analyze_complex(Plan &p, const void *V_dev, void *I_dev);
+void launch_split_complex(int prec, const void *z, int64_t n, void *re, void *im, cudaStream_t s);
+void launch_join_complex(int prec, const void *re, const void *im, int64_t n, void *z, cudaStream_t s);
+void launch_add_j(int prec, void *a, const void *b, int64_t n, cudaStream_t s);
+void launch_times_mj(int prec, const void *a, int64_t n, void *out, cudaStream_t s);
 void collect_stats(Plan &p);
 
 }  // namespace hvox

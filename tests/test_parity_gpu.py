@@ -160,8 +160,9 @@ def test_config1_full(gpu_lib):
     ref_v = oracle.sky2vis(w.pix, w.uvw, w.sky)
     for eps in (1e-9, 1e-6):
         V, y, img, info = _run(gpu_lib, w, eps)
-        assert oracle.rel_l2(V, ref_v) <= 10 * eps
-        assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 10 * eps
+        e_v, e_i = oracle.rel_l2(V, ref_v), oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y))
+        print(f"config 1 eps={eps:g}: rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e}")
+        assert e_v <= 10 * eps and e_i <= 10 * eps
 
 
 @pytest.mark.parametrize("eps", [1e-9, 1e-5])
@@ -177,8 +178,10 @@ def test_config2_full_size_sampled(gpu_lib, eps):
     plan.close()
     kv = configs.sample_indices(2, w.n_vis, 2000)
     kp = configs.sample_indices(2, w.n_pix, 2000, purpose_offset=1)
-    assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
-    assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
+    e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
+    e_i = oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp))
+    print(f"config 2 eps={eps:g}: rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e} (2,000 outputs each)")
+    assert e_v <= 10 * eps and e_i <= 10 * eps
 
 
 def test_config3_dense_core_nufft_sampled(gpu_lib):
@@ -198,8 +201,10 @@ def test_config3_dense_core_nufft_sampled(gpu_lib):
     plan.close()
     kv = configs.sample_indices(3, w.n_vis, 300)
     kp = configs.sample_indices(3, w.n_pix, 300, purpose_offset=1)
-    assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
-    assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
+    e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
+    e_i = oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp))
+    print(f"config 3 dense core eps={eps:g}: rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e} (300 outputs each)")
+    assert e_v <= 10 * eps and e_i <= 10 * eps
 
 
 @pytest.mark.parametrize("eps", [1e-6, 1e-9])
@@ -282,5 +287,71 @@ def test_radius_sweep_10km_sampled(gpu_lib):
     plan.close()
     kv = configs.sample_indices(6, w.n_vis, 300)
     kp = configs.sample_indices(6, w.n_pix, 300, purpose_offset=1)
-    assert oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv)) <= 10 * eps
-    assert oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp)) <= 10 * eps
+    e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
+    e_i = oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp))
+    print(f"radius 10 km eps={eps:g}: rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e} (300 outputs each)")
+    assert e_v <= 10 * eps and e_i <= 10 * eps
+
+
+def test_chunk_order_io_skips_permutations(gpu_lib, small):
+    # A caller that keeps its data in the plan's chunk order (hvox_plan_order) gets the
+    # same transforms, in chunk order, with weights still applied.
+    w = small
+    wt = np.random.default_rng(4).uniform(0.5, 2.0, w.n_pix)
+    for mode in ("nufft", "direct"):
+        ref = gpu_lib.Plan(w.pix, w.uvw, 1e-9, weight=wt, mode=mode)
+        po, vo = ref.order()
+        assert sorted(po.tolist()) == list(range(w.n_pix)) and sorted(vo.tolist()) == list(range(w.n_vis))
+        ch = gpu_lib.Plan(w.pix, w.uvw, 1e-9, weight=wt, mode=mode, chunk_order=True)
+        assert np.array_equal(ch.order()[0], po) and np.array_equal(ch.order()[1], vo)
+        I = torch.as_tensor(w.sky, dtype=torch.float64, device="cuda")
+        V = ref.synthesize(I).cpu().numpy()
+        Vc = ch.synthesize(torch.as_tensor(w.sky[po], dtype=torch.float64, device="cuda")).cpu().numpy()
+        assert oracle.rel_l2(Vc, V[vo]) <= 1e-12
+        y = np.random.default_rng(6).normal(size=w.n_vis) + 1j * np.random.default_rng(7).normal(size=w.n_vis)
+        img = ref.analyze(torch.as_tensor(y, device="cuda")).cpu().numpy()
+        imgc = ch.analyze(torch.as_tensor(y[vo], device="cuda")).cpu().numpy()
+        assert oracle.rel_l2(imgc, img[po]) <= 1e-12
+        ref.close()
+        ch.close()
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_complex_sky_both_directions(gpu_lib, small, eps):
+    # real=False form: a complex sky in, and the adjoint without the real part out; the
+    # oracle's real-sky sums give the reference by linearity.
+    w = small
+    rng = np.random.default_rng(12)
+    x = rng.lognormal(0.0, 1.0, w.n_pix)
+    y = rng.normal(size=w.n_pix)
+    v = rng.normal(size=w.n_vis) + 1j * rng.normal(size=w.n_vis)
+    for mode in ("nufft", "direct"):
+        plan = gpu_lib.Plan(w.pix, w.uvw, eps, mode=mode)
+        V = plan.synthesize_complex(torch.as_tensor(x + 1j * y)).cpu().numpy()
+        img = plan.analyze_complex(torch.as_tensor(v)).cpu().numpy()
+        plan.close()
+        ref_v = oracle.sky2vis(w.pix, w.uvw, x) + 1j * oracle.sky2vis(w.pix, w.uvw, y)
+        ref_i = oracle.vis2sky(w.pix, w.uvw, v) + 1j * oracle.vis2sky(w.pix, w.uvw, -1j * v)
+        assert oracle.rel_l2(V, ref_v) <= 10 * eps
+        assert oracle.rel_l2(img, ref_i) <= 10 * eps
+
+
+def test_config3_full_sampled(gpu_lib):
+    # The SKA-Low-like workload in full (1,470,612 pixels x 4,186,112 baselines): NUFFT
+    # sub-problems for the dense part, direct sums for the rest; 300 seeded outputs per
+    # direction against the oracle.
+    w = configs.config3()
+    eps = 1e-6
+    plan = gpu_lib.Plan(w.pix, w.uvw, eps)
+    info = plan.info()
+    assert info["n_nufft_blocks"] > 0 and info["direct_pairs"] > 0
+    V = plan.synthesize(torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+    vis = configs.visibilities_cn(3, w.n_vis)
+    img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
+    plan.close()
+    kv = configs.sample_indices(3, w.n_vis, 300, purpose_offset=2)
+    kp = configs.sample_indices(3, w.n_pix, 300, purpose_offset=3)
+    e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
+    e_i = oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp))
+    print(f"config 3 eps={eps:g}: rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e} (300 outputs each)")
+    assert e_v <= 10 * eps and e_i <= 10 * eps
