@@ -171,6 +171,17 @@ __device__ __forceinline__ void kahan_add(float &sum, float &comp, float x) {
     sum = t;
 }
 
+// Adds a tile's double-float partial sum (ih + il) into the running sum (oh + ol): the
+// lazy accumulation's lo part rounds at ~2^-24 of itself, which over millions of terms
+// (1.4M baselines per pixel) grows to ~5e-9 of the result; folding every 256 terms keeps
+// that growth to one tile.
+__device__ __forceinline__ void df_fold(float &oh, float &ol, float ih, float il) {
+    float s, e;
+    two_sum(oh, ih, s, e);
+    e = __fadd_rn(e, __fadd_rn(ol, il));
+    fast_two_sum(s, e, oh, ol);
+}
+
 __device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ gT) {
     for (int i = threadIdx.x; i < kTabN; i += blockDim.x) sT[i] = gT[i];
 }
@@ -264,6 +275,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
         const WorkItem w = items[it];
         float3 ph[VPT], pl[VPT];
         float arh[VPT], arl[VPT], aih[VPT], ail[VPT];
+        float orh[VPT], orl[VPT], oih[VPT], oil[VPT];  // running sums, folded per tile
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
@@ -275,6 +287,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
             ph[v] = make_float3(a.x, a.y, a.z);
             pl[v] = make_float3(b.x, b.y, b.z);
             arh[v] = arl[v] = aih[v] = ail[v] = 0.f;
+            orh[v] = orl[v] = oih[v] = oil[v] = 0.f;
         }
         for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
             __syncthreads();
@@ -308,13 +321,19 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
                     df_acc(aih[v], ail[v], th, tl);
                 }
             }
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                df_fold(orh[v], orl[v], arh[v], arl[v]);
+                df_fold(oih[v], oil[v], aih[v], ail[v]);
+                arh[v] = arl[v] = aih[v] = ail[v] = 0.f;
+            }
         }
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             int k = w.o0 + threadIdx.x + v * kThreads;
             if (k < w.o1) {
-                atomicAdd(&acc[k].x, (double)arh[v] + (double)arl[v]);
-                atomicAdd(&acc[k].y, (double)sgn * ((double)aih[v] + (double)ail[v]));
+                atomicAdd(&acc[k].x, (double)orh[v] + (double)orl[v]);
+                atomicAdd(&acc[k].y, (double)sgn * ((double)oih[v] + (double)oil[v]));
             }
         }
     }
@@ -459,7 +478,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
     for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
         const WorkItem w = items[it];
         float4 rh[VPT], rl[VPT];
-        float ah[VPT], al[VPT];
+        float ah[VPT], al[VPT], oh[VPT], ol[VPT];  // tile sums and running sums
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
@@ -470,7 +489,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
             }
             rh[v] = x;
             rl[v] = y;
-            ah[v] = al[v] = 0.f;
+            ah[v] = al[v] = oh[v] = ol[v] = 0.f;
         }
         for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
             __syncthreads();
@@ -505,11 +524,16 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
                     df_acc(ah[v], al[v], th, tl);
                 }
             }
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) {
+                df_fold(oh[v], ol[v], ah[v], al[v]);
+                ah[v] = al[v] = 0.f;
+            }
         }
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
-            if (n < w.o1) atomicAdd(&acc[n], (double)ah[v] + (double)al[v]);
+            if (n < w.o1) atomicAdd(&acc[n], (double)oh[v] + (double)ol[v]);
         }
     }
 }
