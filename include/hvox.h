@@ -236,7 +236,10 @@ hvox_status hvox_sync(hvox_plan_t plan);
 hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis, double eps,
                           const hvox_opts *opts, hvox_info *info);
 
-/* Device memory a plan with these sizes would own (admission control); 0 on error. */
+/* Upper bound of the device memory a plan with these sizes and options could own
+ * (admission control): coordinates, permutations, call buffers and, unless the job is
+ * planned as direct sums without a search, up to four lanes of grids and cuFFT work
+ * areas within the chunk budget (8 GiB when the planner chooses). 0 on error. */
 double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_opts *opts);
 
 /* Thread-local message describing the last failure ("" if none). */

@@ -193,6 +193,20 @@ def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: flo
             for name, _ in Info._fields_}
 
 
+def estimate_bytes(n_pix: int, n_vis: int, eps: float, precision="auto", mode="auto",
+                   chunk_budget_bytes: float = 0.0, ntrans: int = 1, plain: bool = False,
+                   search_threshold: float = 0.0) -> float:
+    """Upper bound of the device memory a plan of these sizes could own (hvox_estimate_bytes)."""
+    o = Opts()
+    o.precision = _PREC[precision]
+    o.mode = _MODE[mode]
+    o.chunk_budget_bytes = chunk_budget_bytes
+    o.ntrans = ntrans
+    o.plain = 1 if plain else 0
+    o.search_threshold = search_threshold
+    return float(load().hvox_estimate_bytes(int(n_pix), int(n_vis), float(eps), ctypes.byref(o)))
+
+
 def direct_synthesize_noalloc(pix, uvw, I, V, isign: int = -1, stream=None):
     """sky -> vis by direct FP32 summation without any allocation (hvox_direct_synthesize_noalloc).
 

@@ -690,7 +690,8 @@ hvox_status hvox_plan_chunks(hvox_plan_t plan, int64_t *pix_chunk, int64_t *vis_
 double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_opts *opts) {
     if (n_pix < 1 || n_vis < 1 || !(eps >= 0.0)) return 0.0;
     int prec = 1;
-    if (opts && opts->plain) prec = 2;
+    const bool plain = opts && opts->plain;
+    if (plain) prec = 2;
     else if (opts && opts->precision) prec = opts->precision;
     else if (eps > 0 && eps < 1e-6) prec = 2;
     const double re = prec == 1 ? 4.0 : 8.0;
@@ -698,8 +699,17 @@ double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_
     double geom = (double)(n_pix + n_vis) * (4.0 + 24.0 + 32.0) + (double)n_pix * 8.0;
     double bufs = 2.0 * std::max((double)n_pix * re, (double)n_vis * 2.0 * re);
     double io = 2.0 * nt * std::max((double)n_pix * re, (double)n_vis * 2.0 * re);
-    double budget = (opts && opts->chunk_budget_bytes > 0) ? opts->chunk_budget_bytes : 256.0 * 1024 * 1024;
-    return geom + bufs + io + 2.0 * budget;
+    // Jobs the planner keeps as direct sums without a search own no NUFFT grids; others
+    // own at most kMaxLanes lanes of grids and cuFFT work areas, each within the budget.
+    const CostModel m = default_cost_model(prec, plain, 0);
+    const double search = (opts && opts->search_threshold > 0) ? opts->search_threshold : 0.01;
+    const bool auto_plan = !(opts && (opts->mode != HVOX_MODE_AUTO || opts->direct_threshold > 0 ||
+                                      opts->chunk_budget_bytes > 0));
+    const bool direct_only = eps == 0.0 || (opts && opts->mode == HVOX_MODE_DIRECT) ||
+                             (auto_plan && 2.0 * m.direct_pair * (double)n_pix * (double)n_vis < search);
+    const double budget = (opts && opts->chunk_budget_bytes > 0) ? opts->chunk_budget_bytes : 8.0 * 1024 * 1024 * 1024;
+    const double grids = direct_only ? 0.0 : 2.0 * kMaxLanes * budget;
+    return geom + bufs + io + grids;
 }
 
 hvox_status hvox_es_params(double eps, double sigma, int32_t *w, double *beta) {

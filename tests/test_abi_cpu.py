@@ -125,3 +125,17 @@ def test_fp32_plans_keep_sigma_above_error_floor():
         wd, beta = hvox.es_params(eps, info["upsampfac"])
         ph = hvox.es_ft(wd, beta, [0.0, math.pi / info["upsampfac"]])
         assert 2.0 ** -24 * (ph[0] / ph[1]) ** 2 <= 5 * eps, info["upsampfac"]
+
+
+def test_estimate_bytes_bounds():
+    import paper_2306_06007_gb300 as hvox
+    # A small job is planned as direct sums without a search: no NUFFT grids.
+    small = hvox.estimate_bytes(1000, 1000, 1e-6)
+    assert 0 < small < 1e6
+    # A large job may get up to four lanes of grids and work areas within 8 GiB each.
+    big = hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6)
+    assert big >= 2 * 4 * 8 * 2**30
+    # A fixed budget bounds the grids instead; direct mode has none.
+    assert hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6, chunk_budget_bytes=1e8) < 1e9
+    assert hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6, mode="direct") < 1e9
+    assert hvox.estimate_bytes(0, 10, 1e-6) == 0.0
