@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-from . import Plan
+from . import HvoxError, Plan, estimate_bytes
 
 
 def geometry_key(pix: np.ndarray, uvw: np.ndarray, eps: float, plain: bool) -> str:
@@ -61,6 +61,7 @@ class ServeReport:
     makespan_s: float = 0.0
     units: float = 0.0                               # sum of (n_pix + n_vis) over requests
     peak_bytes: float = 0.0
+    errors: dict = field(default_factory=dict)       # rid -> message of a request that failed
 
     def summary(self) -> dict:
         lat = sorted(self.latency_s.values())
@@ -69,7 +70,8 @@ class ServeReport:
                 "mean_ms": statistics.mean(lat) * 1e3 if lat else None,
                 "throughput_units_per_s": self.units / self.makespan_s if self.makespan_s > 0 else None,
                 "makespan_s": self.makespan_s, "plans": len(self.plan_s),
-                "plan_s_total": sum(self.plan_s.values()), "peak_bytes": self.peak_bytes}
+                "plan_s_total": sum(self.plan_s.values()), "peak_bytes": self.peak_bytes,
+                "errors": len(self.errors)}
 
 
 class Server:
@@ -102,9 +104,9 @@ class Server:
         return plan, stream, info["workspace_bytes"], time.perf_counter() - t0
 
     def _estimate_plan_bytes(self, req) -> float:
-        # Upper-level estimate used to admit planning (the real figure replaces it).
-        n = len(req.pix) + len(req.uvw)
-        return 120.0 * n + 64e6
+        # Upper bound of what planning may allocate (the plan's own figure replaces it).
+        return estimate_bytes(len(req.pix), len(req.uvw), req.eps, plain=self.plain,
+                              search_threshold=self.search_threshold)
 
     def _evict_idle(self, need: float, protect: set):
         for key, r in sorted(self.resident.items(), key=lambda kv: kv[1].last_used):
@@ -161,7 +163,16 @@ class Server:
                 planning[k] = self.pool.submit(self._make_plan, r)
                 progressed = True
             for k in [k for k, f in planning.items() if f.done()]:
-                plan, stream, nbytes, secs = planning.pop(k).result()
+                try:
+                    plan, stream, nbytes, secs = planning.pop(k).result()
+                except HvoxError as e:
+                    # The requests of this geometry fail; the server carries on.
+                    self.used -= reserved.pop(k)
+                    for r in [x for x in arrived if x._key == k]:
+                        rep.errors[r.rid] = str(e)
+                        arrived.remove(r)
+                    progressed = True
+                    continue
                 self.used += nbytes - reserved.pop(k)
                 self.resident[k] = _Resident(plan, stream, nbytes)
                 rep.plan_s[k] = secs

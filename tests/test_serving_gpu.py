@@ -61,3 +61,23 @@ def test_admission_respects_budget(gpu_lib):
     srv.close()
     assert len(rep.results) == len(reqs)
     assert rep.peak_bytes <= budget
+
+
+def test_failed_request_does_not_stop_the_server(gpu_lib):
+    # A request whose geometry the library rejects (a non-finite coordinate) fails alone;
+    # every other request of the stream completes and matches the oracle.
+    from paper_2306_06007_gb300.serve import Server
+    reqs = _stream(6, seed=2)
+    bad = reqs[2]
+    bad.pix = bad.pix.copy()
+    bad.pix[0, 0] = np.nan
+    srv = Server(max_inflight=4)
+    rep = srv.run(reqs, realtime=False)
+    srv.close()
+    assert set(rep.errors) == {bad.rid}
+    assert set(rep.results) == {r.rid for r in reqs} - {bad.rid}
+    for r in reqs:
+        if r.rid == bad.rid:
+            continue
+        ref = oracle.sky2vis(r.pix, r.uvw, r.data) if r.direction == "s2v" else oracle.vis2sky(r.pix, r.uvw, r.data)
+        assert oracle.rel_l2(rep.results[r.rid], ref) <= 10 * r.eps
