@@ -16,14 +16,16 @@
  *        I_n = a_n Re sum_k V_k exp(-isign * j * 2 pi <p_k, r_n>)
  *
  * isign = -1 reproduces Eq. 2 for sky -> vis. The paper calls the sky -> vis map
- * "analysis" and its adjoint "synthesis"; this library keeps the names its users
- * asked for (synthesize = sky -> vis) and offers the unambiguous aliases
- * dirty2vis / vis2dirty, the names of the paper's user functions (Sect. 4). The
+ * "analysis" and its adjoint "synthesis"; this library names sky -> vis
+ * "synthesize" (synthesising visibilities from a sky model) and offers the unambiguous
+ * aliases dirty2vis / vis2dirty, the names of the paper's user functions (Sect. 4). The
  * vis -> sky output is real (the paper's real=True adjoint, Listing 1): it is the
  * exact adjoint of sky -> vis under the real inner product.
  *
  * Accuracy: each output vector meets relative l2 error <= 10 * eps against the
- * exact sums (eps = 0 selects direct evaluation everywhere, Sect. 4).
+ * exact sums (eps = 0 selects direct evaluation everywhere, Sect. 4), with the
+ * upsampling the planner chooses (a caller-fixed upsampfac below 1.5 on FP32 grids has a
+ * rounding floor of ~2^-24 (Phi(0)/Phi(pi/sigma))^2, 5e-4 at 1.25).
  *
  * Precision. HVOX_PREC_FP32: I is float[n_pix], V is interleaved complex
  * float[2 n_vis]. HVOX_PREC_FP64: double / double[2 n_vis]. AUTO picks FP32 for
