@@ -139,3 +139,16 @@ def test_estimate_bytes_bounds():
     assert hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6, chunk_budget_bytes=1e8) < 1e9
     assert hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6, mode="direct") < 1e9
     assert hvox.estimate_bytes(0, 10, 1e-6) == 0.0
+
+
+def test_plan_dry_rejects_empty_and_bad_inputs():
+    import numpy as np
+    import paper_2306_06007_gb300 as hvox
+    pix = np.array([[0.0, 0.0, 1.0]])
+    uvw = np.array([[10.0, 0.0, 0.0]])
+    for p, u, eps in ((np.zeros((0, 3)), uvw, 1e-6), (pix, np.zeros((0, 3)), 1e-6), (pix, uvw, -1e-6)):
+        with pytest.raises(hvox.HvoxError) as e:
+            hvox.plan_dry(p, u, eps)
+        assert e.value.code == 1  # HVOX_EINVAL
+    # One pixel and one baseline: a valid (direct) plan.
+    assert hvox.plan_dry(pix, uvw, 1e-6)["n_nufft_blocks"] == 0

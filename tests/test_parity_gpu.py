@@ -153,6 +153,10 @@ def test_bad_arguments(gpu_lib, small):
     bad[3, 1] = np.nan
     with pytest.raises(gpu_lib.HvoxError):
         gpu_lib.Plan(bad, w.uvw, 1e-6)
+    for p, u in ((w.pix[:0], w.uvw), (w.pix, w.uvw[:0])):  # empty point sets
+        with pytest.raises(gpu_lib.HvoxError) as e:
+            gpu_lib.Plan(p, u, 1e-6)
+        assert e.value.code == 1
 
 
 def test_config1_full(gpu_lib):
