@@ -140,7 +140,9 @@ void build_items(const std::vector<DirectRect> &rects, bool owner_is_vis, int vp
     const int64_t T = direct_tile(vpt);
     double work = 0;
     for (auto &r : rects) work += (double)(r.p1 - r.p0) * (double)(r.v1 - r.v0);
-    const double target_items = 152.0 * 16.0;
+    // About 32 items per resident CTA (152 SMs x 4), taken dynamically by the kernels
+    // largest first: a launch then ends within a fraction of an item of its ideal time.
+    const double target_items = 152.0 * 4.0 * 32.0;
     int64_t seg = (int64_t)std::ceil(work / ((double)T * target_items) / 256.0) * 256;
     seg = std::max<int64_t>(seg, 2048);
     for (auto &r : rects) {
@@ -151,6 +153,9 @@ void build_items(const std::vector<DirectRect> &rects, bool owner_is_vis, int vp
                 items.push_back(WorkItem{(int32_t)o, (int32_t)std::min(o + T, o1), (int32_t)q,
                                          (int32_t)std::min(q + seg, s1)});
     }
+    std::stable_sort(items.begin(), items.end(), [](const WorkItem &x, const WorkItem &y) {
+        return (int64_t)(x.o1 - x.o0) * (x.s1 - x.s0) > (int64_t)(y.o1 - y.o0) * (y.s1 - y.s0);
+    });
 }
 
 void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const double *w_in) {
@@ -232,6 +237,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         std::vector<WorkItem> a, b;
         build_items(part.rects, true, p.direct_vpt, a);
         build_items(part.rects, false, p.direct_vpt, b);
+        p.item_counter.alloc(2 * sizeof(int));
         upload(p.items_s2v, a.data(), a.size() * sizeof(WorkItem), s);
         upload(p.items_v2s, b.data(), b.size() * sizeof(WorkItem), s);
         p.n_items_s2v = (int64_t)a.size();
@@ -388,7 +394,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
 
     double ws = 0;
     for (DevBuf *b : {&p.pix_perm, &p.vis_perm, &p.weight, &p.pix_xyz, &p.vis_xyz, &p.pix_hi, &p.pix_lo, &p.vis_hi,
-                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.inv_psi, &p.cheb, &p.src, &p.acc, &p.cis_tab})
+                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.item_counter, &p.inv_psi, &p.cheb, &p.src, &p.acc, &p.cis_tab})
         ws += (double)b->bytes;
     for (auto &l : p.lanes) ws += (double)(l->g1.bytes + l->g2.bytes + l->work.bytes);
     p.workspace_bytes = ws;

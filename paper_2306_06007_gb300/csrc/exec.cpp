@@ -127,15 +127,17 @@ void body_s2v(Plan &p, cudaStream_t s, Profiler &prof) {
     if (p.n_items_s2v > 0) {
         prof.begin(HVOX_STAGE_DIRECT, s);
         const WorkItem *it = p.items_s2v.as<WorkItem>();
+        int *counter = p.item_counter.as<int>();
+        check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), s), "memset item counter");
         if (p.plain)
-            launch_direct_s2v_f64(it, p.n_items_s2v, p.vis_xyz.as<double>(), p.n_vis, p.pix_xyz.as<double>(),
+            launch_direct_s2v_f64(it, p.n_items_s2v, counter, p.vis_xyz.as<double>(), p.n_vis, p.pix_xyz.as<double>(),
                                   p.n_pix, p.src.as<double>(), p.acc.as<double2>(), p.isign, p.direct_vpt, s);
         else if (p.prec == 1)
-            launch_direct_s2v_f32(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
+            launch_direct_s2v_f32(it, p.n_items_s2v, counter, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
                                   p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<float>(),
                                   p.acc.as<float2>(), p.isign, p.direct_vpt, s);
         else
-            launch_direct_s2v_df(it, p.n_items_s2v, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
+            launch_direct_s2v_df(it, p.n_items_s2v, counter, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
                                  p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.src.as<double>(),
                                  p.acc.as<double2>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
         prof.end(HVOX_STAGE_DIRECT, 1, s);
@@ -170,15 +172,17 @@ void body_v2s(Plan &p, cudaStream_t s, Profiler &prof) {
     if (p.n_items_v2s > 0) {
         prof.begin(HVOX_STAGE_DIRECT, s);
         const WorkItem *it = p.items_v2s.as<WorkItem>();
+        int *counter = p.item_counter.as<int>() + 1;
+        check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), s), "memset item counter");
         if (p.plain)
-            launch_direct_v2s_f64(it, p.n_items_v2s, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(),
+            launch_direct_v2s_f64(it, p.n_items_v2s, counter, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(),
                                   p.n_vis, p.src.as<double2>(), p.acc.as<double>(), p.isign, p.direct_vpt, s);
         else if (p.prec == 1)
-            launch_direct_v2s_f32(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
+            launch_direct_v2s_f32(it, p.n_items_v2s, counter, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
                                   p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<float2>(),
                                   p.acc.as<float>(), p.isign, p.direct_vpt, s);
         else
-            launch_direct_v2s_df(it, p.n_items_v2s, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
+            launch_direct_v2s_df(it, p.n_items_v2s, counter, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
                                  p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.src.as<double2>(),
                                  p.acc.as<double>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
         prof.end(HVOX_STAGE_DIRECT, 1, s);

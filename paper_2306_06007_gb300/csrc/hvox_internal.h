@@ -262,6 +262,7 @@ struct Plan {
 
     // direct work lists
     DevBuf items_s2v, items_v2s;
+    DevBuf item_counter;                // int[2]: work-item counters of the direct launches
     int64_t n_items_s2v = 0, n_items_v2s = 0;
 
     // NUFFT sub-problems
@@ -304,19 +305,19 @@ void launch_gather_weight(const double *w_orig_dev, const int32_t *perm, int64_t
 
 // Direct kernels (k_direct.cu). Owner tile = direct_tile() points per work item.
 int direct_tile(int vpt);
-void launch_direct_s2v_f32(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+void launch_direct_s2v_f32(const WorkItem *items, int64_t n, int *counter, const float4 *vh, const float4 *vl, const float4 *rh,
                            const float4 *rl, const float *c, float2 *acc, int isign, int vpt, cudaStream_t s);
-void launch_direct_s2v_df(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+void launch_direct_s2v_df(const WorkItem *items, int64_t n, int *counter, const float4 *vh, const float4 *vl, const float4 *rh,
                           const float4 *rl, const double *c, double2 *acc, const float4 *tab, int isign,
                           int vpt, cudaStream_t s);
-void launch_direct_s2v_f64(const WorkItem *items, int64_t n, const double *vxyz, int64_t nv, const double *pxyz,
+void launch_direct_s2v_f64(const WorkItem *items, int64_t n, int *counter, const double *vxyz, int64_t nv, const double *pxyz,
                            int64_t np, const double *c, double2 *acc, int isign, int vpt, cudaStream_t s);
-void launch_direct_v2s_f32(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+void launch_direct_v2s_f32(const WorkItem *items, int64_t n, int *counter, const float4 *rh, const float4 *rl, const float4 *vh,
                            const float4 *vl, const float2 *V, float *acc, int isign, int vpt, cudaStream_t s);
-void launch_direct_v2s_df(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+void launch_direct_v2s_df(const WorkItem *items, int64_t n, int *counter, const float4 *rh, const float4 *rl, const float4 *vh,
                           const float4 *vl, const double2 *V, double *acc, const float4 *tab, int isign,
                           int vpt, cudaStream_t s);
-void launch_direct_v2s_f64(const WorkItem *items, int64_t n, const double *pxyz, int64_t np, const double *vxyz,
+void launch_direct_v2s_f64(const WorkItem *items, int64_t n, int *counter, const double *pxyz, int64_t np, const double *vxyz,
                            int64_t nv, const double2 *V, double *acc, int isign, int vpt, cudaStream_t s);
 
 // NUFFT sub-problems (k_nufft.cu).

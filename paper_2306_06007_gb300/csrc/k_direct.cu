@@ -182,6 +182,17 @@ __device__ __forceinline__ void df_fold(float &oh, float &ol, float ih, float il
     fast_two_sum(s, e, oh, ol);
 }
 
+// The next work item of this CTA, taken from the launch's counter (CTA b starts with
+// item b; the counter is zero at launch): CTAs that finish early take more items, and
+// with the items ordered largest first a launch ends within about one small item of its
+// ideal time.
+__device__ __forceinline__ int next_item(int *counter, int &s_next) {
+    __syncthreads();  // every thread has read the previous s_next
+    if (threadIdx.x == 0) s_next = (int)gridDim.x + atomicAdd(counter, 1);
+    __syncthreads();
+    return s_next;
+}
+
 __device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ gT) {
     for (int i = threadIdx.x; i < kTabN; i += blockDim.x) sT[i] = gT[i];
 }
@@ -190,14 +201,15 @@ __device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ 
 
 // FP32: owner = baselines, streamed = pixels (c real, chunk order).
 template <int VPT>
-__global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
                                                            const float4 *__restrict__ vh, const float4 *__restrict__ vl,
                                                            const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
                                                            const float *__restrict__ c, float2 *__restrict__ acc,
                                                            float sgn) {
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_next;
+    for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         float3 ph[VPT], pl[VPT];
         float are[VPT], aim[VPT], cre[VPT], cim[VPT];
@@ -261,7 +273,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__res
 
 // Double-float: c given in FP64, accumulation returned in FP64.
 template <int VPT>
-__global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
                                                           const double *__restrict__ c, double2 *__restrict__ acc,
@@ -271,7 +283,8 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
     __shared__ float2 sc[kThreads];
     __shared__ float4 sT[kTabN];
     load_tab(sT, gT);
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_next;
+    for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         float3 ph[VPT], pl[VPT];
         float arh[VPT], arl[VPT], aih[VPT], ail[VPT];
@@ -305,7 +318,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
             }
             __syncthreads();
             const int cnt = min(kThreads, w.s1 - s0);
-#pragma unroll 2
+#pragma unroll 4
             for (int q = 0; q < cnt; ++q) {
                 const float4 rh = sh[q], rl = sl[q];
                 const float2 cv = sc[q];
@@ -341,13 +354,14 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
 
 // Plain FP64 reference form.
 template <int VPT>
-__global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
                                                            const double *__restrict__ vxyz, int64_t nv_all,
                                                            const double *__restrict__ pxyz, int64_t np_all,
                                                            const double *__restrict__ c, double2 *__restrict__ acc,
                                                            double sgn) {
     __shared__ double sx[kThreads], sy[kThreads], sz[kThreads], sw[kThreads];
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_next;
+    for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         double px[VPT], py[VPT], pz[VPT], are[VPT], aim[VPT];
 #pragma unroll
@@ -396,14 +410,15 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__res
 
 // FP32: owner = pixels, streamed = baselines (V complex, chunk order). Output real.
 template <int VPT>
-__global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
                                                            const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
                                                            const float4 *__restrict__ vh, const float4 *__restrict__ vl,
                                                            const float2 *__restrict__ V, float *__restrict__ acc,
                                                            float sgn) {
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_next;
+    for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         float3 rh[VPT], rl[VPT];
         float a[VPT], ca[VPT];
@@ -465,7 +480,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__res
 }
 
 template <int VPT>
-__global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
                                                           const double2 *__restrict__ V, double *__restrict__ acc,
@@ -475,7 +490,8 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
     __shared__ float4 sv[kThreads];
     __shared__ float4 sT[kTabN];
     load_tab(sT, gT);
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_next;
+    for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         float4 rh[VPT], rl[VPT];
         float ah[VPT], al[VPT], oh[VPT], ol[VPT];  // tile sums and running sums
@@ -508,7 +524,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
             }
             __syncthreads();
             const int cnt = min(kThreads, w.s1 - s0);
-#pragma unroll 2
+#pragma unroll 4
             for (int q = 0; q < cnt; ++q) {
                 const float4 ph4 = sh[q], pl4 = sl[q], val = sv[q];
                 const float3 ph = make_float3(ph4.x, ph4.y, ph4.z), pl = make_float3(pl4.x, pl4.y, pl4.z);
@@ -539,13 +555,14 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
 }
 
 template <int VPT>
-__global__ void __launch_bounds__(kThreads) direct_v2s_f64(const WorkItem *__restrict__ items, int n_items,
+__global__ void __launch_bounds__(kThreads) direct_v2s_f64(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
                                                            const double *__restrict__ pxyz, int64_t np_all,
                                                            const double *__restrict__ vxyz, int64_t nv_all,
                                                            const double2 *__restrict__ V, double *__restrict__ acc,
                                                            double sgn) {
     __shared__ double sx[kThreads], sy[kThreads], sz[kThreads], sr[kThreads], si[kThreads];
-    for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    __shared__ int s_next;
+    for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         double rx[VPT], ry[VPT], rz[VPT], a[VPT];
 #pragma unroll
@@ -619,65 +636,65 @@ static unsigned grid_for(int64_t n_items) {
     return (unsigned)std::max<int64_t>(g, 1);
 }
 
-void launch_direct_s2v_f32(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+void launch_direct_s2v_f32(const WorkItem *items, int64_t n, int *counter, const float4 *vh, const float4 *vl, const float4 *rh,
                            const float4 *rl, const float *c, float2 *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
     if (vpt == 4)
-        direct_s2v_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, (float)isign);
+        direct_s2v_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, (float)isign);
     else
-        direct_s2v_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, (float)isign);
+        direct_s2v_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, (float)isign);
     check_cuda(cudaGetLastError(), "direct_s2v_f32");
 }
 
-void launch_direct_s2v_df(const WorkItem *items, int64_t n, const float4 *vh, const float4 *vl, const float4 *rh,
+void launch_direct_s2v_df(const WorkItem *items, int64_t n, int *counter, const float4 *vh, const float4 *vl, const float4 *rh,
                           const float4 *rl, const double *c, double2 *acc, const float4 *tab, int isign,
                           int vpt, cudaStream_t s) {
     if (n <= 0) return;
     if (vpt == 4)
-        direct_s2v_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, tab, (float)isign);
+        direct_s2v_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, tab, (float)isign);
     else
-        direct_s2v_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vh, vl, rh, rl, c, acc, tab, (float)isign);
+        direct_s2v_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, tab, (float)isign);
     check_cuda(cudaGetLastError(), "direct_s2v_df");
 }
 
-void launch_direct_s2v_f64(const WorkItem *items, int64_t n, const double *vxyz, int64_t nv, const double *pxyz,
+void launch_direct_s2v_f64(const WorkItem *items, int64_t n, int *counter, const double *vxyz, int64_t nv, const double *pxyz,
                            int64_t np, const double *c, double2 *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
     if (vpt == 4)
-        direct_s2v_f64<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vxyz, nv, pxyz, np, c, acc, (double)isign);
+        direct_s2v_f64<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vxyz, nv, pxyz, np, c, acc, (double)isign);
     else
-        direct_s2v_f64<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, vxyz, nv, pxyz, np, c, acc, (double)isign);
+        direct_s2v_f64<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vxyz, nv, pxyz, np, c, acc, (double)isign);
     check_cuda(cudaGetLastError(), "direct_s2v_f64");
 }
 
-void launch_direct_v2s_f32(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+void launch_direct_v2s_f32(const WorkItem *items, int64_t n, int *counter, const float4 *rh, const float4 *rl, const float4 *vh,
                            const float4 *vl, const float2 *V, float *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
     if (vpt == 4)
-        direct_v2s_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, (float)isign);
+        direct_v2s_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, (float)isign);
     else
-        direct_v2s_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, (float)isign);
+        direct_v2s_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, (float)isign);
     check_cuda(cudaGetLastError(), "direct_v2s_f32");
 }
 
-void launch_direct_v2s_df(const WorkItem *items, int64_t n, const float4 *rh, const float4 *rl, const float4 *vh,
+void launch_direct_v2s_df(const WorkItem *items, int64_t n, int *counter, const float4 *rh, const float4 *rl, const float4 *vh,
                           const float4 *vl, const double2 *V, double *acc, const float4 *tab, int isign,
                           int vpt, cudaStream_t s) {
     if (n <= 0) return;
     if (vpt == 4)
-        direct_v2s_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, tab, (float)isign);
+        direct_v2s_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, tab, (float)isign);
     else
-        direct_v2s_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, rh, rl, vh, vl, V, acc, tab, (float)isign);
+        direct_v2s_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, tab, (float)isign);
     check_cuda(cudaGetLastError(), "direct_v2s_df");
 }
 
-void launch_direct_v2s_f64(const WorkItem *items, int64_t n, const double *pxyz, int64_t np, const double *vxyz,
+void launch_direct_v2s_f64(const WorkItem *items, int64_t n, int *counter, const double *pxyz, int64_t np, const double *vxyz,
                            int64_t nv, const double2 *V, double *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
     if (vpt == 4)
-        direct_v2s_f64<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, pxyz, np, vxyz, nv, V, acc, (double)isign);
+        direct_v2s_f64<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, pxyz, np, vxyz, nv, V, acc, (double)isign);
     else
-        direct_v2s_f64<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, pxyz, np, vxyz, nv, V, acc, (double)isign);
+        direct_v2s_f64<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, pxyz, np, vxyz, nv, V, acc, (double)isign);
     check_cuda(cudaGetLastError(), "direct_v2s_f64");
 }
 
