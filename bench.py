@@ -351,10 +351,13 @@ def run_gpu(args):
                     "taps_per_s": taps_per_launch / avg_s, "avg_launch_ms": avg_s * 1e3,
                     "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
     own = sum(st["launches"][k] for k in ("permute", "direct", "spread", "deconv", "interp"))
+    # Arithmetic of the path: FP64 kernels (plain form), FP32, or double-float pairs of FP32
+    # (eps < 1e-6: FP64 accuracy on the FP32 pipes, FP64 only once per tile and output).
+    dtype = "f64" if args.plain else ("f32" if info["precision"] == 1 else "f32x2")
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded HEALPix + layout)",
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded HEALPix + layout)",
             "config": {"workload": w.name + "; step = sky->vis + vis->sky" if args.radius_km > 0
                        else WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
                        "mode": args.mode, "core_radius": args.core_radius or None, "graphs": args.graphs,
