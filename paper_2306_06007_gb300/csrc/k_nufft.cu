@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <climits>
 #include <cstdint>
+#include <mutex>
 #include <vector>
 
 #include "hvox_internal.h"
@@ -742,15 +743,16 @@ inline unsigned blocks_for(int64_t n, int threads) { return (unsigned)((n + thre
 
 // Dynamic shared memory of the spreading kernels: the tile (real and imaginary planes).
 template <typename T, int W> void set_smem_attrs() {
-    static bool done = false;
-    if (done) return;
-    check_cuda(cudaFuncSetAttribute(spread_pix_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    tile_bytes<T, W>()),
-               "cudaFuncSetAttribute");
-    check_cuda(cudaFuncSetAttribute(spread_vis_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    tile_bytes<T, W>()),
-               "cudaFuncSetAttribute");
-    done = true;
+    // Once per instantiation, also when plans are built and run on several host threads.
+    static std::once_flag once;
+    std::call_once(once, [] {
+        check_cuda(cudaFuncSetAttribute(spread_pix_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        tile_bytes<T, W>()),
+                   "cudaFuncSetAttribute");
+        check_cuda(cudaFuncSetAttribute(spread_vis_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        tile_bytes<T, W>()),
+                   "cudaFuncSetAttribute");
+    });
 }
 
 }  // namespace
