@@ -364,7 +364,8 @@ def run_gpu(args):
                        "plain": args.plain,
                        "l2": "flushed before each step (256 MiB write, outside the timed window)",
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
-                       "direct_pairs": info["direct_pairs"], "w": info["w"]},
+                       "direct_pairs": info["direct_pairs"], "w": info["w"],
+                       "plan_seconds": info["plan_seconds"]},
             "e2e": main.get("e2e"), "roofline": roofline, "gpu_launches": own,
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "clocks": main["clocks"]}
