@@ -30,7 +30,12 @@
  * Precision. HVOX_PREC_FP32: I is float[n_pix], V is interleaved complex
  * float[2 n_vis]. HVOX_PREC_FP64: double / double[2 n_vis]. AUTO picks FP32 for
  * eps >= 1e-6 and FP64 below. Coordinates, phases of large argument and plan-time
- * geometry are always FP64.
+ * geometry are always FP64. FP64 plans evaluate direct sums in double-float
+ * arithmetic on the FP32 units for eps >= 1e-9 (rounding ~3e-10) and with FP64
+ * kernels below 1e-9 (~100x slower, so the planner gives such plans more NUFFT
+ * work); their NUFFT sub-problems run on FP64 grids. Tolerances that would need a
+ * kernel wider than 16 cells at every upsampling (eps below ~1e-14) return
+ * HVOX_EUNSUPPORTED.
  *
  * Memory. Coordinates and weights passed to hvox_plan may be host or device
  * pointers; they are copied (and permuted to chunk order) into plan-owned device

@@ -13,9 +13,11 @@ fitted by least squares through the origin across the workloads:
     direct ms         ~ 2 direct_pairs   * c_direct
 
 The fitted rates are printed beside the model's so that the constants of the planner can
-be replaced by measured ones. Runs on the GPU through the public binding only.
+be replaced by measured ones. Runs on the GPU through the public binding only. At
+eps <= 1e-9 the sub-problems run in FP64; `--mode nufft` forces NUFFT sub-problems where
+the model would choose direct sums, so that their rates can be measured at all.
 
-    python -m paper_2306_06007_gb300.calibrate [--eps 1e-6] [--steps 3]
+    python -m paper_2306_06007_gb300.calibrate [--eps 1e-6] [--steps 3] [--mode nufft]
 """
 from __future__ import annotations
 
@@ -31,9 +33,11 @@ STAGE_WORK = {
     "direct": lambda i: 2.0 * i["direct_pairs"],
 }
 
-# FP32 rates of the planner's cost model (seconds per unit of work), as last fitted.
-MODEL = {"spread": 1.0 / 4.75e11, "interp": 1.0 / 1.0e12, "fft": 4.1e-13, "grid": 1.3e-12,
-         "direct": 1.0 / 8.5e11}
+# Rates of the planner's cost model (seconds per unit of work), FP32 and FP64 sub-problems.
+MODEL = {"f32": {"spread": 1.0 / 4.75e11, "interp": 1.0 / 1.0e12, "fft": 4.1e-13, "grid": 1.3e-12,
+                 "direct": 1.0 / 8.5e11},
+         "f64": {"spread": 1.0 / 1.0e11, "interp": 1.0 / 1.35e11, "fft": 6.8e-12, "grid": 1.8e-12,
+                 "direct": 1.0 / 4.2e11}}
 
 
 def _workloads():
@@ -49,11 +53,11 @@ def _workloads():
     return out
 
 
-def measure(w, eps: float, steps: int):
+def measure(w, eps: float, steps: int, mode: str = "auto"):
     import torch
 
     from . import Plan
-    plan = Plan(w.pix, w.uvw, eps, graphs=-1)
+    plan = Plan(w.pix, w.uvw, eps, graphs=-1, mode=mode)
     info = plan.info()
     I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
     V = torch.zeros(w.n_vis, dtype=plan.complex_dtype, device="cuda")
@@ -86,20 +90,22 @@ def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--mode", default="auto", choices=["auto", "nufft"])
     args = ap.parse_args(argv)
     os.environ["HVOX_NUFFT_LANES"] = "1"  # stages serialised: their times add up
     rows, report = [], []
     for name, w in _workloads():
-        info, ms = measure(w, args.eps, args.steps)
+        info, ms = measure(w, args.eps, args.steps, args.mode)
         rows.append((info, ms))
         report.append({"workload": name, "n_pix": w.n_pix, "n_vis": w.n_vis, "blocks": info["n_nufft_blocks"],
                        "w": info["w"], "upsampfac": info["upsampfac"], "stage_ms": ms,
                        "work": {k: f(info) for k, f in STAGE_WORK.items()}})
     rates = fit(rows)
+    model = MODEL["f64" if rows and rows[0][0]["precision"] == 2 else "f32"]
     for r, (info, ms) in zip(report, rows):
-        r["model_ms"] = {k: 1e3 * MODEL[k] * f(info) for k, f in STAGE_WORK.items()}
+        r["model_ms"] = {k: 1e3 * model[k] * f(info) for k, f in STAGE_WORK.items()}
         r["fitted_ms"] = {k: (1e3 * rates[k] * f(info) if rates[k] else None) for k, f in STAGE_WORK.items()}
-    print(json.dumps({"eps": args.eps, "fitted_seconds_per_unit": rates, "model_seconds_per_unit": MODEL,
+    print(json.dumps({"eps": args.eps, "fitted_seconds_per_unit": rates, "model_seconds_per_unit": model,
                       "workloads": report}, indent=1))
 
 

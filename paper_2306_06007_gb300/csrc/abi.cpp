@@ -128,8 +128,18 @@ void to_host(const double *src, size_t n, std::vector<double> &dst) {
 constexpr int kMaxLanes = 4;
 
 // Tolerance given to the kernel-width rule: the type-3 transform chains two
-// approximations (spread on n1, interpolate on n2), each held to eps.
-constexpr double kEpsMargin = 1.0;
+// approximations (spread on n1, interpolate on n2), each held to eps. FP32 plans use eps
+// itself (their errors sit near the FP32 grids' rounding floor). FP64 plans take a tenth
+// of it, one or two cells more kernel width: the ES error bound holds per output against
+// the sum of |source| (it grows with the number of sources when measured as relative l2),
+// and at eps 1e-9 the bare rule measured 5.8e-9 sky -> vis on 810,000 pixels.
+constexpr double kEpsMarginF32 = 1.0;
+constexpr double kEpsMarginF64 = 0.1;
+
+// The double-float direct sums carry ~3e-10 of rounding (the exp(j 2 pi f) table's lo
+// parts and the phase are FP32-rounded at ~1e-10 turn); below this tolerance the direct
+// sums use the FP64 kernels.
+constexpr double kDoubleFloatMinEps = 1e-9;
 
 void upload(DevBuf &b, const void *host, size_t bytes, cudaStream_t s) {
     b.alloc(bytes);
@@ -179,6 +189,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     in.prec = p.prec;
     in.mode = p.mode;
     in.plain = p.plain;
+    in.direct_f64 = p.direct_f64;
     in.budget = p.budget_opt;
     in.direct_threshold = p.direct_threshold;
     in.search_threshold = p.search_threshold;
@@ -437,7 +448,8 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.search_threshold = o.search_threshold > 0 ? o.search_threshold : 0.01;
     double e = eps > 0 ? eps : 1e-6;
     if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
-    p.eps_es = e * kEpsMargin;
+    p.eps_es = e * (p.prec == 1 ? kEpsMarginF32 : kEpsMarginF64);
+    p.direct_f64 = p.plain || (p.prec == 2 && e < kDoubleFloatMinEps);
     p.es = es_params(p.eps_es, p.sigma);
     // Points per thread of the direct kernels (tuning knob; 2 or 4).
     if (const char *v = std::getenv("HVOX_DIRECT_VPT")) p.direct_vpt = std::atoi(v) == 4 ? 4 : 2;
@@ -654,6 +666,7 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         in.prec = p.prec;
         in.mode = p.mode;
         in.plain = p.plain;
+        in.direct_f64 = p.direct_f64;
         in.budget = p.budget_opt;
         in.direct_threshold = p.direct_threshold;
         in.search_threshold = p.search_threshold;
@@ -707,7 +720,7 @@ double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_
     double io = 2.0 * nt * std::max((double)n_pix * re, (double)n_vis * 2.0 * re);
     // Jobs the planner keeps as direct sums without a search own no NUFFT grids; others
     // own at most kMaxLanes lanes of grids and cuFFT work areas, each within the budget.
-    const CostModel m = default_cost_model(prec, plain, 0);
+    const CostModel m = default_cost_model(prec, plain || (prec == 2 && eps > 0 && eps < kDoubleFloatMinEps), 0);
     const double search = (opts && opts->search_threshold > 0) ? opts->search_threshold : 0.01;
     const bool auto_plan = !(opts && (opts->mode != HVOX_MODE_AUTO || opts->direct_threshold > 0 ||
                                       opts->chunk_budget_bytes > 0));

@@ -11,11 +11,15 @@
 
 namespace hvox {
 
+int es_width(double eps, double sigma) {
+    const double wd = std::ceil(std::log(1.0 / eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)));
+    return (int)std::min(1e6, std::max(2.0, wd));
+}
+
 ESKernel es_params(double eps, double sigma) {
     if (!(eps > 0.0) || !(sigma > 1.0)) fail(HVOX_EINVAL, "es_params: need eps > 0 and sigma > 1");
     ESKernel k;
-    double wd = std::ceil(std::log(1.0 / eps) / (M_PI * std::sqrt(1.0 - 1.0 / sigma)));
-    k.w = (int)std::max(2.0, wd);
+    k.w = es_width(eps, sigma);
     if (k.w > 16) fail(HVOX_EUNSUPPORTED, "es_params: tolerance needs a kernel wider than 16 cells");
     k.beta = 0.97 * M_PI * k.w * (1.0 - 1.0 / (2.0 * sigma));
     return k;

@@ -129,7 +129,7 @@ void body_s2v(Plan &p, cudaStream_t s, Profiler &prof) {
         const WorkItem *it = p.items_s2v.as<WorkItem>();
         int *counter = p.item_counter.as<int>();
         check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), s), "memset item counter");
-        if (p.plain)
+        if (p.direct_f64)
             launch_direct_s2v_f64(it, p.n_items_s2v, counter, p.vis_xyz.as<double>(), p.n_vis, p.pix_xyz.as<double>(),
                                   p.n_pix, p.src.as<double>(), p.acc.as<double2>(), p.isign, p.direct_vpt, s);
         else if (p.prec == 1)
@@ -174,7 +174,7 @@ void body_v2s(Plan &p, cudaStream_t s, Profiler &prof) {
         const WorkItem *it = p.items_v2s.as<WorkItem>();
         int *counter = p.item_counter.as<int>() + 1;
         check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), s), "memset item counter");
-        if (p.plain)
+        if (p.direct_f64)
             launch_direct_v2s_f64(it, p.n_items_v2s, counter, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(),
                                   p.n_vis, p.src.as<double2>(), p.acc.as<double>(), p.isign, p.direct_vpt, s);
         else if (p.prec == 1)

@@ -38,6 +38,7 @@ struct ESKernel {
 };
 
 ESKernel es_params(double eps, double sigma);
+int es_width(double eps, double sigma);  // the width rule of es_params, without its limit of 16
 // Gauss-Legendre nodes/weights on [-1, 1].
 void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &wt);
 // int phi(z) cos(xi z) dz over |z| <= w/2 for each xi (host FP64).
@@ -121,6 +122,7 @@ struct PlanInputs {
     int prec;              // 1 fp32, 2 fp64
     int mode;
     bool plain;
+    bool direct_f64 = false;  // direct sums by the FP64 kernels (plain form, eps < 1e-9)
     double budget;         // 0 -> search
     double max_budget = 0; // > 0: largest budget the search may pick (device memory)
     double direct_threshold;
@@ -238,6 +240,7 @@ struct Plan {
     int prec = 1;          // 1 fp32, 2 fp64
     int mode = 0;
     bool plain = false;
+    bool direct_f64 = false;       // direct sums by the FP64 kernels (plain form, or eps < 1e-9)
     int ntrans = 1;
     int direct_vpt = 2;            // points per thread of the direct kernels (owner tile 256 * vpt)
     double sigma = 2.0;

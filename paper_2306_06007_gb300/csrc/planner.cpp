@@ -188,12 +188,16 @@ CostModel default_cost_model(int prec, bool plain, int w) {
         m.block_fixed = 30e-6;
         m.tile_cells = 12000.0;  // shared tile of a spreading CTA (float planes, w <= 8)
     } else {
-        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 4.0e11;
-        m.scatter_smem = 1.0 / 2.0e9;
-        m.scatter_global = 1.0 / 1.0e9;
-        m.gather_tap = 1.0 / 2.0e9;
-        m.fft_cell = 2.1e-11;
-        m.grid_cell = 1e-11;
+        // FP64 sub-problems, fitted the same way (calibrate.py --eps 1e-9 --mode nufft over
+        // the 1, 3, 10 km cases and the dense core, 4 to 40 sub-problems each). Spreading
+        // taps are one rate: the fit does not separate the shared-tile and global paths.
+        // Z2Z transforms are bound by the FP64 units, ~16x the C2C rate per cell.
+        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 4.2e11;
+        m.scatter_smem = 1.0 / 1.0e11;
+        m.scatter_global = 1.0 / 1.0e11;
+        m.gather_tap = 1.0 / 1.35e11;
+        m.fft_cell = 6.8e-12;
+        m.grid_cell = 1.8e-12;
         m.block_fixed = 50e-6;
         m.tile_cells = 4800.0;   // double planes, w ~ 10
     }
@@ -223,13 +227,15 @@ ChunkStats stats_of(const double *xyz, int64_t n, const std::vector<int64_t> &la
     return s;
 }
 
+constexpr double kMaxCandidatePairs = 16.0 * 1024.0 * 1024.0;
+
 struct Evaluated {
     double t, h[3], eta[3], budget, ratio = 1.0;
     std::vector<int64_t> pl, vl;
     int64_t npc, nvc;
     ChunkStats ps, vs;
     std::vector<std::pair<int64_t, int64_t>> nufft_pairs;  // (pix chunk, vis chunk)
-    double cost;
+    double cost = 0.0;
 };
 
 // Spreading cost per tap for n points on a grid of `cells`: through the shared tile when
@@ -270,6 +276,11 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
     e.budget = budget;
     e.ratio = ratio;
     e.t = box_dims(P, B, budget, in.sigma, in.es.w, in.elem_bytes, e.eta, e.h);
+    if (e.t <= 0.0 && in.mode != HVOX_MODE_DIRECT) {
+        // the budget cannot hold even the smallest grid (2w cells per dimension)
+        e.cost = INFINITY;
+        return e;
+    }
     if (ratio != 1.0)
         for (int d = 0; d < 3; ++d) {
             e.eta[d] *= ratio;
@@ -295,6 +306,13 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
         if ((double)e.ps.count[i] > min_pts) bigp.push_back(i);
     for (int64_t j = 0; j < e.nvc; ++j)
         if ((double)e.vs.count[j] > min_pts) bigv.push_back(j);
+    // A budget so small that the candidate sub-problems number in the tens of millions
+    // (forced NUFFT mode at the smallest budgets) is not a plan: it is marked infeasible
+    // instead of being enumerated.
+    if ((double)bigp.size() * (double)bigv.size() > kMaxCandidatePairs) {
+        e.cost = INFINITY;
+        return e;
+    }
     for (int64_t i : bigp) {
         double pext[3];
         for (int d = 0; d < 3; ++d) pext[d] = e.ps.hi[3 * i + d] - e.ps.lo[3 * i + d];
@@ -339,6 +357,7 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
 PartitionResult make_partition(const PlanInputs &in) {
     PartitionResult r;
     CostModel m = default_cost_model(in.prec, in.plain, in.es.w);
+    if (in.direct_f64) m.direct_pair = default_cost_model(2, true, in.es.w).direct_pair;
     double P[3], B[3];
     for (int d = 0; d < 3; ++d) {
         double lo = INFINITY, hi = -INFINITY;
@@ -380,6 +399,8 @@ PartitionResult make_partition(const PlanInputs &in) {
         std::vector<Cand> cands;
         std::vector<double> sigmas = in.sigma_auto ? std::vector<double>{2.0, 1.5, 1.25} : std::vector<double>{in.sigma};
         for (double sg : sigmas) {
+            // an upsampling whose kernel would be wider than 16 cells is not a candidate
+            if (in.sigma_auto && es_width(in.eps_es, sg) > 16) continue;
             const ESKernel es = in.sigma_auto ? es_params(in.eps_es, sg) : in.es;
             if (in.sigma_auto && in.prec == 1 && sg != sigmas.front()) {
                 // FP32 grids: rounding errors near the band edge are divided twice by the
@@ -398,6 +419,8 @@ PartitionResult make_partition(const PlanInputs &in) {
                 cands.push_back({sg, b, es});
             }
         }
+        if (cands.empty())
+            fail(HVOX_EUNSUPPORTED, "no upsampling keeps the kernel within 16 cells at this tolerance");
         std::vector<Evaluated> evals(cands.size());
         const size_t width = std::max<size_t>(1, std::min<size_t>(4, std::thread::hardware_concurrency()));
         for (size_t c0 = 0; c0 < cands.size(); c0 += width) {
@@ -420,29 +443,49 @@ PartitionResult make_partition(const PlanInputs &in) {
                 evals[c] = Evaluated();
             }
         }
-        // Second pass: at the chosen upsampling and budget, split the Heisenberg volume
-        // differently between pixel and baseline boxes (the number of times each point is
-        // spread or gathered is the number of chunks of the other set it meets).
-        if (best.cost > 0 && !best.nufft_pairs.empty()) {
-            const std::vector<double> ratios{0.25, 0.5, 2.0, 4.0, 8.0};
-            std::vector<Evaluated> rev(ratios.size());
+        // Second pass: split the Heisenberg volume differently between pixel and baseline
+        // boxes (the number of times each point is spread or gathered is the number of
+        // chunks of the other set it meets). When the first pass found a NUFFT sub-problem
+        // the ratios are tried at its upsampling and budget. When it found none (isotropic
+        // boxes cut the sky into chunks too small to pay for a grid, as with a dense core
+        // inside a long-baseline array) every budget is tried with ratios up to 64, so that
+        // a core of short baselines can meet the whole sky in one box.
+        if (best.cost > 0) {
+            const bool none = best.nufft_pairs.empty();
+            std::vector<std::pair<double, double>> rb;  // (budget, ratio)
+            if (!none) {
+                for (double r : {0.25, 0.5, 2.0, 4.0, 8.0}) rb.push_back({best.budget, r});
+            } else {
+                for (double b = 256.0 * 1024.0; b <= 9.0e9; b *= 8.0) {
+                    if (in.max_budget > 0 && b > in.max_budget && b > 256.0 * 1024.0) break;
+                    for (double r : {4.0, 16.0, 64.0}) rb.push_back({b, r});
+                    // the ratio at which one pixel box spans the whole sky (eta = P)
+                    double eta[3], h[3];
+                    const double t = box_dims(P, B, b, best_sigma, best_es.w, in.elem_bytes, eta, h);
+                    if (t > 0.0 && t < 1.0) rb.push_back({b, 1.0 / t});
+                }
+            }
+            std::vector<Evaluated> rev(rb.size());
             PlanInputs cand = in;
             cand.sigma = best_sigma;
             cand.es = best_es;
-            const double bud = best.budget;
-            for (size_t c0 = 0; c0 < ratios.size(); c0 += width) {
+            for (size_t c0 = 0; c0 < rb.size(); c0 += width) {
                 std::vector<std::future<void>> jobs;
-                for (size_t c = c0; c < std::min(ratios.size(), c0 + width); ++c)
+                for (size_t c = c0; c < std::min(rb.size(), c0 + width); ++c)
                     jobs.push_back(std::async(std::launch::async,
-                                              [&, c] { rev[c] = evaluate(cand, m, bud, P, B, ratios[c]); }));
+                                              [&, c] { rev[c] = evaluate(cand, m, rb[c].first, P, B, rb[c].second); }));
                 for (auto &j : jobs) j.get();
-                for (size_t c = c0; c < std::min(ratios.size(), c0 + width); ++c) {
+                for (size_t c = c0; c < std::min(rb.size(), c0 + width); ++c) {
                     if (rev[c].cost < best.cost) best = std::move(rev[c]);
                     rev[c] = Evaluated();
                 }
             }
         }
     }
+    if (!std::isfinite(best.cost))
+        fail(HVOX_EINVAL, "no feasible partition: a chunk budget must hold a grid of 2w cells per dimension "
+                          "and give fewer than " + std::to_string((int64_t)kMaxCandidatePairs) +
+                          " candidate sub-problems; set chunk_budget_bytes larger");
     r.box_ratio = best.ratio;
     r.sigma = best_sigma;
     r.es = best_es;

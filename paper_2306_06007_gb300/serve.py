@@ -78,7 +78,7 @@ class Server:
     """Request loop over libhvox plans (see the module docstring)."""
 
     def __init__(self, hbm_budget_bytes: float = 150e9, max_inflight: int = 8, planner_threads: int = 0,
-                 plain: bool = False, keep_plans: bool = True, search_threshold: float = 0.1):
+                 plain: bool = False, keep_plans: bool = True, search_threshold: float | None = None):
         import os
         if planner_threads <= 0:
             planner_threads = max(2, (os.cpu_count() or 4) // 2)
@@ -88,6 +88,13 @@ class Server:
         self.keep_plans = keep_plans
         # A request's plan is usually used once: skip the partition search for jobs whose
         # direct evaluation is modelled below this many seconds (it costs ~1-3 us a point).
+        # The plain form's direct sums are ~100x slower, but a one-shot plan with NUFFT
+        # sub-problems also pays for the search, its grids and cuFFT plans: on the
+        # benchmark's stream (N up to 3e4) planning plain requests with a 0.1 s threshold
+        # gave p50 / p99 286 / 1,524 ms against 78 / 200 ms with direct sums, so the plain
+        # form searches only above 1 s of direct work.
+        if search_threshold is None:
+            search_threshold = 1.0 if plain else 0.1
         self.search_threshold = float(search_threshold)
         self.pool = cf.ThreadPoolExecutor(max_workers=max(1, planner_threads))
         self.resident: dict[str, _Resident] = {}

@@ -276,15 +276,15 @@ def test_upsampling_factors(gpu_lib, small, sigma, eps):
     assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 10 * eps
 
 
-def test_radius_sweep_10km_sampled(gpu_lib):
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_radius_sweep_10km_sampled(gpu_lib, eps):
     # The paper's 10 km setup at matched resolution (10,240,000 pixels x 237,705
-    # baselines): four large NUFFT sub-problems; 300 seeded outputs per direction are
-    # checked against the oracle.
+    # baselines): four large NUFFT sub-problems (FP32 grids at 1e-6, FP64 at 1e-9); 300
+    # seeded outputs per direction are checked against the oracle.
     w = configs.radius_sweep(10.0)
-    eps = 1e-6
     plan = gpu_lib.Plan(w.pix, w.uvw, eps)
     info = plan.info()
-    assert info["n_nufft_blocks"] > 0 and info["direct_pairs"] < 0.01 * w.n_pix * w.n_vis
+    assert info["n_nufft_blocks"] > 0 and info["direct_pairs"] < 0.05 * w.n_pix * w.n_vis
     V = plan.synthesize(torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
     vis = configs.visibilities_cn(6, w.n_vis)
     img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
@@ -358,4 +358,43 @@ def test_config3_full_sampled(gpu_lib):
     e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
     e_i = oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp))
     print(f"config 3 eps={eps:g}: rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e} (300 outputs each)")
+    assert e_v <= 10 * eps and e_i <= 10 * eps
+
+
+@pytest.mark.parametrize("radius_km", [1.0, 3.0])
+def test_radius_sweep_fp64_nufft_sampled(gpu_lib, radius_km):
+    # At eps = 1e-9 the 1 km (130,000 pixels x 95,266 baselines) and 3 km (810,000 x
+    # 148,240) setups are planned as FP64 NUFFT sub-problems (sigma 1.5, w = 12); 300
+    # seeded outputs per direction are checked against the oracle.
+    w = configs.radius_sweep(radius_km)
+    eps = 1e-9
+    plan = gpu_lib.Plan(w.pix, w.uvw, eps)
+    info = plan.info()
+    assert info["precision"] == 2 and info["n_nufft_blocks"] > 0
+    V = plan.synthesize(torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+    vis = configs.visibilities_cn(6, w.n_vis)
+    img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
+    plan.close()
+    kv = configs.sample_indices(6, w.n_vis, 300, purpose_offset=4)
+    kp = configs.sample_indices(6, w.n_pix, 300, purpose_offset=5)
+    e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
+    e_i = oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp))
+    print(f"radius {radius_km:g} km eps={eps:g} sigma={info['upsampfac']:g} w={info['w']}: "
+          f"rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e} (300 outputs each)")
+    assert e_v <= 10 * eps and e_i <= 10 * eps
+
+
+@pytest.mark.parametrize("mode", ["direct", "nufft"])
+def test_tolerance_below_double_float(gpu_lib, small, mode):
+    # eps = 1e-11 is below what the double-float direct sums reach (~3e-10): direct sums
+    # run on the FP64 kernels and NUFFT sub-problems on FP64 grids with a kernel of up to
+    # 16 cells.
+    w = small
+    eps = 1e-11
+    V, y, img, info = _run(gpu_lib, w, eps, mode=mode)
+    assert info["precision"] == 2 and info["w"] <= 16
+    e_v = oracle.rel_l2(V, oracle.sky2vis(w.pix, w.uvw, w.sky))
+    e_i = oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y))
+    print(f"eps={eps:g} mode={mode} w={info['w']} sigma={info['upsampfac']:g}: rel_l2 sky->vis {e_v:.3e} "
+          f"vis->sky {e_i:.3e}")
     assert e_v <= 10 * eps and e_i <= 10 * eps
