@@ -450,7 +450,7 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
     p.eps_es = e * (p.prec == 1 ? kEpsMarginF32 : kEpsMarginF64);
     p.direct_f64 = p.plain || (p.prec == 2 && e < kDoubleFloatMinEps);
-    p.es = es_params(p.eps_es, p.sigma);
+    p.es = es_params_within(p.eps_es, e, p.sigma);
     // Points per thread of the direct kernels (tuning knob; 2 or 4).
     if (const char *v = std::getenv("HVOX_DIRECT_VPT")) p.direct_vpt = std::atoi(v) == 4 ? 4 : 2;
 }

@@ -25,6 +25,14 @@ ESKernel es_params(double eps, double sigma) {
     return k;
 }
 
+ESKernel es_params_within(double eps_tight, double eps, double sigma) {
+    if (es_width(eps_tight, sigma) <= 16) return es_params(eps_tight, sigma);
+    ESKernel k = es_params(eps, sigma);  // refuses tolerances beyond a 16-cell kernel
+    k.w = 16;
+    k.beta = 0.97 * M_PI * k.w * (1.0 - 1.0 / (2.0 * sigma));
+    return k;
+}
+
 void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &wt) {
     x.assign(q, 0.0);
     wt.assign(q, 0.0);

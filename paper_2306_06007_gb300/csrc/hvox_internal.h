@@ -39,6 +39,9 @@ struct ESKernel {
 
 ESKernel es_params(double eps, double sigma);
 int es_width(double eps, double sigma);  // the width rule of es_params, without its limit of 16
+// The kernel for the tightened tolerance eps_tight, or the 16-cell kernel when that one
+// would be wider and eps itself fits in 16 cells (a caller-fixed upsampling).
+ESKernel es_params_within(double eps_tight, double eps, double sigma);
 // Gauss-Legendre nodes/weights on [-1, 1].
 void gauss_legendre(int q, std::vector<double> &x, std::vector<double> &wt);
 // int phi(z) cos(xi z) dz over |z| <= w/2 for each xi (host FP64).
