@@ -351,9 +351,20 @@ def run_gpu(args):
                     "taps_per_s": taps_per_launch / avg_s, "avg_launch_ms": avg_s * 1e3,
                     "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
     own = sum(st["launches"][k] for k in ("permute", "direct", "spread", "deconv", "interp"))
-    # Arithmetic of the path: FP64 kernels (plain form), FP32, or double-float pairs of FP32
-    # (eps < 1e-6: FP64 accuracy on the FP32 pipes, FP64 only once per tile and output).
-    dtype = "f64" if args.plain else ("f32" if info["precision"] == 1 else "f32x2")
+    # Arithmetic of the path: FP64 kernels (plain form), FP32, or for FP64 plans the direct
+    # sums' double-float pairs of FP32 (FP64 accuracy on the FP32 pipes, FP64 only once per
+    # tile and output; FP64 kernels below eps 1e-9) and the NUFFT sub-problems' FP64 grids.
+    if args.plain:
+        dtype = "f64"
+    elif info["precision"] == 1:
+        dtype = "f32"
+    else:
+        kinds = []
+        if info["direct_pairs"] > 0:
+            kinds.append("f32x2" if args.eps >= 1e-9 else "f64")
+        if info["n_nufft_blocks"] > 0:
+            kinds.append("f64")
+        dtype = "+".join(dict.fromkeys(kinds)) or "f32x2"
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
