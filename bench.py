@@ -215,19 +215,24 @@ class ClockSampler:
 
 # ---------------------------------------------------------------------------- GPU arm
 
-def time_steps(plan, I, V, steps, flush):
+def time_steps(plan, I, V, steps, flush, per_direction=None):
+    """Device time (ms) of each step (sky -> vis then vis -> sky); per_direction, if a
+    list, receives (sky -> vis ms, vis -> sky ms) per step from an event between them."""
     import torch
     times = []
     for _ in range(steps):
         flush.zero_()
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s, m, e = (torch.cuda.Event(enable_timing=True) for _ in range(3))
         s.record()
         plan.synthesize(I)
+        m.record()
         plan.analyze(V)
         e.record()
-        times.append((s, e))
+        times.append((s, m, e))
     torch.cuda.synchronize()
-    return [s.elapsed_time(e) for s, e in times]
+    if per_direction is not None:
+        per_direction.extend((s.elapsed_time(m), m.elapsed_time(e)) for s, m, e in times)
+    return [s.elapsed_time(e) for s, m, e in times]
 
 
 def serving_study():
@@ -283,15 +288,23 @@ def run_gpu(args):
         clocks = ClockSampler(local)
         clocks.start()
         plan.profile(True)
-        ms = time_steps(plan, I, V, args.steps, flush)
+        dirs = []
+        ms = time_steps(plan, I, V, args.steps, flush, dirs)
         st = plan.stats()
         clk = clocks.stop()
         if world > 1:
             dist.barrier()
         total_ms = max_over_ranks(sum(ms), world)
+        s2v_ms = max_over_ranks(sum(d[0] for d in dirs), world) / args.steps
+        v2s_ms = max_over_ranks(sum(d[1] for d in dirs), world) / args.steps
+        units = world * (w.n_pix + w.n_vis)
         out = {"plan": plan, "info": info, "ms_per_step": total_ms / args.steps,
+               "ms_median": max_over_ranks(statistics.median(ms), world),
                "value": whole_job_rate(units_per_step, args.steps, total_ms * 1e-3, world), "stats": st,
-               "clocks": clk}
+               "clocks": clk,
+               "per_direction": {"sky_to_vis_ms": s2v_ms, "vis_to_sky_ms": v2s_ms,
+                                 "sky_to_vis_value": units / (s2v_ms * 1e-3),
+                                 "vis_to_sky_value": units / (v2s_ms * 1e-3), "unit": UNIT}}
         if with_e2e:
             Ih = torch.as_tensor(w.sky, dtype=plan.real_dtype).pin_memory()
             Vh = torch.as_tensor(vis, dtype=plan.complex_dtype).pin_memory()
@@ -367,7 +380,8 @@ def run_gpu(args):
         dtype = "+".join(dict.fromkeys(kinds)) or "f32x2"
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "ms_median": main["ms_median"],
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded HEALPix + layout)",
             "config": {"workload": w.name + "; step = sky->vis + vis->sky" if args.radius_km > 0
                        else WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
@@ -379,10 +393,12 @@ def run_gpu(args):
                        "plan_seconds": info["plan_seconds"]},
             "e2e": main.get("e2e"), "roofline": roofline, "gpu_launches": own,
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
+            "per_direction": main["per_direction"],
             "clocks": main["clocks"]}
     if secondary is not None:
         line["secondary"] = {"eps": 1e-6, "dtype": "f32", "value": secondary["value"],
                              "ms_per_step": secondary["ms_per_step"], "clocks": secondary["clocks"],
+                             "per_direction": secondary["per_direction"],
                              "stage_ms_per_step": {k: v / args.steps for k, v in secondary["stats"]["ms"].items()}}
     main["plan"].close()
     if secondary is not None:
@@ -402,7 +418,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hvox", choices=["hvox", "reference"])
     ap.add_argument("--eps", type=float, default=1e-9)
