@@ -459,10 +459,11 @@ PartitionResult make_partition(const PlanInputs &in) {
                 for (double b = 256.0 * 1024.0; b <= 9.0e9; b *= 8.0) {
                     if (in.max_budget > 0 && b > in.max_budget && b > 256.0 * 1024.0) break;
                     for (double r : {4.0, 16.0, 64.0}) rb.push_back({b, r});
-                    // the ratio at which one pixel box spans the whole sky (eta = P)
+                    // the ratio at which one pixel box spans the whole sky (eta = P, with a
+                    // hair of slack so that the extreme pixels do not start a second cell)
                     double eta[3], h[3];
                     const double t = box_dims(P, B, b, best_sigma, best_es.w, in.elem_bytes, eta, h);
-                    if (t > 0.0 && t < 1.0) rb.push_back({b, 1.0 / t});
+                    if (t > 0.0 && t < 1.0) rb.push_back({b, 1.000001 / t});
                 }
             }
             std::vector<Evaluated> rev(rb.size());
