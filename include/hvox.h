@@ -89,7 +89,10 @@ typedef struct {
     double upsampfac;            /* sigma of both NUFFT stages, in [1.25, 4]; 0 -> chosen by
                                     the planner among 2, 1.5 and 1.25 */
     double chunk_budget_bytes;   /* FFT-grid budget B of one sub-problem (Algorithm 1);
-                                    0 -> chosen by the planner's cost model */
+                                    0 -> chosen by the planner's cost model. A budget that
+                                    cannot hold a grid of 2w cells per dimension, or that
+                                    would cut the job into more than 2^24 candidate
+                                    sub-problems, makes hvox_plan fail with HVOX_EINVAL */
     double anisotropy;           /* Algorithm 1 alpha >= 1; 0 -> 1 (isotropic optimum) */
     double direct_threshold;     /* < 0 or 0 -> cost model; > 0: a block with
                                     n_pix_blk * n_vis_blk <= threshold is direct */
@@ -162,7 +165,8 @@ typedef struct {
  *   opts       may be NULL (defaults).
  *   out        receives the plan handle; set to NULL on failure.
  * Errors: HVOX_EINVAL for n_pix < 1, n_vis < 1, NULL pointers, eps < 0 or not finite,
- * |isign| != 1, non-finite coordinates, bad options; HVOX_ENOMEM; HVOX_ECUDA.
+ * |isign| != 1, non-finite coordinates, bad options (an infeasible chunk budget);
+ * HVOX_EUNSUPPORTED for a tolerance no 16-cell kernel reaches; HVOX_ENOMEM; HVOX_ECUDA.
  */
 hvox_status hvox_plan(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis,
                       const double *pix_weight, double eps, int isign, const hvox_opts *opts,
