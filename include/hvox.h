@@ -224,8 +224,11 @@ enum {
 };
 
 typedef struct {
-    double ms[HVOX_NUM_STAGES];        /* device time per stage: CUDA events recorded on the
-                                          plan's stream around each stage (0 unless profiling) */
+    double ms[HVOX_NUM_STAGES];        /* device time per stage: CUDA events recorded around
+                                          each stage on the stream that runs it (0 unless
+                                          profiling). Stages of sub-problems on concurrent lanes
+                                          overlap one another and the direct sums, so with more
+                                          than one lane the times need not add up to the step */
     int64_t launches[HVOX_NUM_STAGES]; /* kernel launches of this library per stage (FFT: cuFFT
                                           executions; ZERO: memsets) */
     int64_t transforms;                /* transforms run since the last reset */
