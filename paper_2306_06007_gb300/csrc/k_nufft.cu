@@ -343,6 +343,27 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
             const T wz = sh.w[p][2 * W + jz];
             if (tiled) {
                 const int zrow = (pz0 - lo2 + jz) * tyi + (py0 - lo1);
+                if constexpr (sizeof(T) == 8) {
+                    // FP64 grids are bound by the FP64 pipe: fold wz into the value once per
+                    // plane, leaving two multiplies per tap (no per-row wy * wz product).
+                    T zr[kXT], zi[kXT];
+#pragma unroll
+                    for (int t = 0; t < kXT; ++t) {
+                        zr[t] = ar[t] * wz;
+                        zi[t] = ai[t] * wz;
+                    }
+#pragma unroll
+                    for (int jy = 0; jy < W; ++jy) {
+                        const int base = (zrow + jy) * txi;
+#pragma unroll
+                        for (int t = 0; t < kXT; ++t)
+                            if (on[t]) {
+                                atomicAdd(tre + base + cx[t], zr[t] * wy[jy]);
+                                atomicAdd(tim + base + cx[t], zi[t] * wy[jy]);
+                            }
+                    }
+                    continue;
+                }
 #pragma unroll
                 for (int jy = 0; jy < W; ++jy) {
                     const T c = wy[jy] * wz;
@@ -356,6 +377,22 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
                 }
             } else {
                 const int64_t gz = PERIODIC ? wrap(pz0 + jz, ng[2]) : pz0 + jz;
+                if constexpr (sizeof(T) == 8) {
+                    T zr[kXT], zi[kXT];
+#pragma unroll
+                    for (int t = 0; t < kXT; ++t) {
+                        zr[t] = ar[t] * wz;
+                        zi[t] = ai[t] * wz;
+                    }
+                    for (int jy = 0; jy < W; ++jy) {
+                        const int64_t gy = PERIODIC ? wrap(py0 + jy, ng[1]) : py0 + jy;
+                        cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
+#pragma unroll
+                        for (int t = 0; t < kXT; ++t)
+                            if (on[t]) grid_add(row + cx[t], zr[t] * wy[jy], zi[t] * wy[jy]);
+                    }
+                    continue;
+                }
                 for (int jy = 0; jy < W; ++jy) {
                     const T c = wy[jy] * wz;
                     const int64_t gy = PERIODIC ? wrap(py0 + jy, ng[1]) : py0 + jy;
