@@ -103,7 +103,8 @@ typedef struct {
                                     since the search costs ~1-3 us per point. */
     int32_t ntrans;              /* number of stacked inputs on one geometry; 0 -> 1 */
     int32_t plain;               /* 1: the plain reference form: FP64 arithmetic in every
-                                    kernel, blocks launched one by one, no graph */
+                                    kernel, blocks launched one by one (eager launches on
+                                    the same lanes, no graph) */
     int32_t graphs;              /* CUDA graphs: 0 -> for plans with NUFFT sub-problems;
                                     1 -> for every plan; -1 -> never (eager launches).
                                     The first call of each direction runs eagerly; the
