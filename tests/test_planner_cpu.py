@@ -78,6 +78,9 @@ def test_fp64_plans_widen_the_kernel(lib):
     assert hvox.plan_dry(w.pix, w.uvw, 1e-9, mode="nufft", upsampfac=2.0)["w"] == 11
     assert hvox.plan_dry(w.pix, w.uvw, 1e-9, mode="nufft", upsampfac=1.5)["w"] == 13
     assert hvox.es_params(1e-10, 2.0)[0] == 11 and hvox.es_params(1e-9, 2.0)[0] == 10
+    # A caller-fixed sigma 1.25 would need 17 cells with the margin: it keeps the widest
+    # kernel, 16 cells (the bare rule's 15 still fits).
+    assert hvox.plan_dry(w.pix, w.uvw, 1e-9, mode="nufft", upsampfac=1.25)["w"] == 16
     # FP32 plans keep the bare rule.
     assert hvox.plan_dry(w.pix, w.uvw, 1e-6, mode="nufft", upsampfac=2.0)["w"] == 7
 
