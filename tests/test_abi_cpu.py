@@ -74,6 +74,10 @@ def test_box_dims_matches_oracle(lib):
         eta_o, h_o, t_o = partition.box_dims(P, B, budget, sigma, w, eb)
         assert t == t_o
         assert np.array_equal(eta, eta_o) and np.array_equal(h, h_o)
+    # The hand-worked Algorithm 1 case of the oracle's pins: n1 = 110, n2 = 224 per
+    # dimension exactly fill the budget, so t = sqrt(101 / 200).
+    _, _, t = hvox.box_dims([1.0] * 3, [100.0] * 3, 8 * (110 ** 3 + 224 ** 3), 2.0, 7, 8)
+    assert abs(t - math.sqrt(101.0 / 200.0)) < 1e-12
 
 
 def _label_parity(pts, h):

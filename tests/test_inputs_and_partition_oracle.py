@@ -108,6 +108,85 @@ def test_smooth_even():
         assert m >= n and m % 2 == 0
 
 
+# Grid sizes worked by hand from Eq. 5-7 (one grid dimension ~ sigma x pixel extent x
+# baseline extent) with the sizing reading: n1 = even >= sigma P B + w + 2 (spread grid,
+# kernel margin), n2 = smallest even 2,3,5,7-smooth number >= max(sigma n1, 2 w) (FFT
+# grid: the second upsampling of the two-stage type-3), bytes = elem (prod n1 + prod n2).
+# Each value below was derived on paper, not by running the code:
+#   P=0.5, B=100, sigma=2, w=7: need 2*50+9 = 109 -> n1 110; sigma n1 = 220 = 2^2 5 11,
+#       222 = 2 3 37 are not 7-smooth, 224 = 2^5 7 is -> n2 224.
+#   same with sigma=1.5, w=9: need 75+11 = 86 -> n1 86; 1.5*86 = 129 -> even 130 = 2 5 13
+#       no, 132 = 2^2 3 11 no, 134 no, 136 = 2^3 17 no, 138 = 2 3 23 no, 140 = 2^2 5 7 -> 140.
+#   sigma=1.5, w=7: need 75+9 = 84 -> n1 84; 126 = 2 3^2 7 -> n2 126.
+#   degenerate extent (P=0): need w+2 = 9 -> n1 10; sigma=2: max(20, 14) -> 20;
+#       sigma=1.25: max(ceil 12.5 = 13, 2w = 14) -> 14.
+#   degenerate, w=16, sigma=1.25: need 18 -> n1 18; sigma n1 = 22.5 -> 23 -> even 24 = 2^3 3,
+#       but the 2w floor is 32 -> n2 32 (the floor decides).
+GRID_SIZE_CASES = [
+    (0.5, 100.0, 2.0, 7, 110, 224),
+    (0.5, 100.0, 1.5, 9, 86, 140),
+    (0.5, 100.0, 1.5, 7, 84, 126),
+    (0.0, 100.0, 2.0, 7, 10, 20),
+    (0.7, 0.0, 1.25, 7, 10, 14),
+    (0.0, 5.0, 1.25, 16, 18, 32),
+]
+
+
+@pytest.mark.parametrize("P,B,sigma,w,n1,n2", GRID_SIZE_CASES)
+def test_grid_sizes_hand_worked(P, B, sigma, w, n1, n2):
+    assert partition.grid_sizes(P, B, sigma, w) == (n1, n2)
+
+
+def test_grid_bytes_hand_worked():
+    # x, y: as the first case above (110, 224); z: P 0.1, B 10: need 2+9 = 11 -> n1 12,
+    # max(24, 14) = 24 = 2^3 3 -> n2 24. Bytes (complex64) = 8 (110^2 12 + 224^2 24)
+    # = 8 (145,200 + 1,204,224) = 10,795,392.
+    assert partition.grid_bytes([0.5, 0.5, 0.1], [100.0, 100.0, 10.0], 2.0, 7, 8) == 10_795_392
+    # complex128 doubles it.
+    assert partition.grid_bytes([0.5, 0.5, 0.1], [100.0, 100.0, 10.0], 2.0, 7, 16) == 21_590_784
+
+
+# Algorithm 1 at a budget worked by hand: P = (1,1,1), B = (100,100,100), sigma 2, w 7,
+# complex64. At scale t every dimension needs 200 t^2 + 9 cells. The budget is the bytes
+# of n1 = 110, n2 = 224 per dimension: 8 (110^3 + 224^3) = 100,563,392. The grids fit
+# while 200 t^2 + 9 <= 110, i.e. t <= sqrt(101/200); just above, n1 = 112 and n2 =
+# smooth(224) = 224 exceed it. So t* = sqrt(101/200) = 0.71063352...
+# Counting sigma once (n2 = smooth(n1)) or dropping the w + 2 margin would let t grow past it.
+def test_box_dims_hand_worked_budget():
+    budget = 8 * (110 ** 3 + 224 ** 3)
+    assert budget == 100_563_392
+    eta, h, t = partition.box_dims([1.0, 1.0, 1.0], [100.0, 100.0, 100.0], budget, 2.0, 7, 8)
+    assert abs(t - math.sqrt(101.0 / 200.0)) < 1e-12
+    assert np.allclose(h, 100.0 * t) and np.allclose(eta, t)
+
+
+def test_grid_pins_catch_planted_mistakes(monkeypatch):
+    """Mistakes planted in a copy of the oracle's sizing (on the CPU) fail the pins above."""
+    good = partition.grid_sizes
+
+    def sigma_once(P, B, sigma, w):  # FFT grid not upsampled a second time
+        n1, _ = good(P, B, sigma, w)
+        return n1, partition.smooth_even(max(n1, 2 * w))
+
+    def no_margin(P, B, sigma, w):  # kernel margin w + 2 dropped
+        n1 = 2 * int(math.ceil(sigma * P * B / 2.0))
+        return n1, partition.smooth_even(max(int(math.ceil(sigma * n1)), 2 * w))
+
+    def no_floor(P, B, sigma, w):  # 2w floor of the FFT grid dropped
+        n1, _ = good(P, B, sigma, w)
+        return n1, partition.smooth_even(int(math.ceil(sigma * n1)))
+
+    budget = 8 * (110 ** 3 + 224 ** 3)
+    for bad in (sigma_once, no_margin, no_floor):
+        monkeypatch.setattr(partition, "grid_sizes", bad)
+        size_fail = any(bad(P, B, s, w) != (n1, n2) for P, B, s, w, n1, n2 in GRID_SIZE_CASES)
+        _, _, t = partition.box_dims([1.0, 1.0, 1.0], [100.0, 100.0, 100.0], budget, 2.0, 7, 8)
+        assert size_fail, bad.__name__
+        if bad is not no_floor:  # the floor never binds at this budget
+            assert abs(t - math.sqrt(101.0 / 200.0)) > 1e-3, bad.__name__
+    monkeypatch.setattr(partition, "grid_sizes", good)
+
+
 # ------------------------------------------------------------------ Algorithm 2
 
 def _check_partition(pts, h, labels, nc):
