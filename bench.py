@@ -11,6 +11,13 @@ e2e:     the same step through the C ABI with pinned HOST buffers (the library c
          host->device and device->host inside the call), wall clock.
 roofline: the dominant kernel's live CUDA-event time over the timed region.
 secondary: the same step at eps = 1e-6 (FP32 path).
+plain_fp64: the same step at eps = 1e-9 in the plain form (FP64 arithmetic in every
+         kernel, no graph): the comparison the mixed-precision path has to win.
+config3: the SKA-Low-like workload (1,470,612 px x 4,186,112 baselines) at eps = 1e-6,
+         chunked (NUFFT sub-problems + direct sums), with a serial profiled pass that
+         times every kernel alone for the spreading, interpolation and direct rooflines.
+peaks:   throughput probes run live on this GPU (FP32/FP64 FMA, shared-memory atomics,
+         L1 loads) for the denominators the driver's measured peaks do not hold.
 serving: a seeded request stream served with continuous batching against the plain
          FP64 one-at-a-time form (p50/p99 latency, throughput).
 cpu_baseline: the FP64 oracle on this host's cores, on a bounded sample of outputs.
@@ -146,14 +153,23 @@ def run_reference(args):
     import oracle
     per_step = []
     sample = ""
+    sampled_s = 0.0
     for i in range(args.warmup + args.steps):
         rate, dt, sample = oracle_rate(w, 4.0, seed=i)
         if i >= args.warmup:
             per_step.append(2.0 * w.n_pix * w.n_vis / rate)
+            sampled_s += dt
     step_s = statistics.mean(per_step)
     value = 2.0 * (w.n_pix + w.n_vis) / step_s
+    # Each "step" is a bounded sample of the full step's outputs: ms_per_step is the full
+    # step's time extrapolated from the sampled rate by pair count, not a time that ran.
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "higher_is_better": True, "scaling": "weak",
+            "warmup": args.warmup, "ms_per_step": step_s * 1e3, "ms_per_step_extrapolated": True,
+            "timing": (f"each step times the oracle on a bounded sample of outputs ({sampled_s / args.steps:.2f} s "
+                       f"run per step, {sampled_s:.1f} s over the {args.steps} timed steps); value and ms_per_step "
+                       "are extrapolated to the full step by pixel-baseline pair count"),
+            "sampled_seconds_total": round(sampled_s, 2),
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
@@ -259,6 +275,66 @@ def serving_study():
     return out
 
 
+def probe_peaks():
+    """Live throughput probes on this GPU (libhvox_peaks.so): FP32 / FP64 FMA flop/s,
+    shared-memory float atomicAdd/s and L1 load bytes/s; None if the probe is missing."""
+    import ctypes
+    path = os.path.join(ROOT, "paper_2306_06007_gb300", "libhvox_peaks.so")
+    if not os.path.exists(path):
+        return None
+    lib = ctypes.CDLL(path)
+    out = (ctypes.c_double * 4)()
+    if lib.hvox_probe_peaks(out) != 0:
+        return None
+    return {"fp32_flops": out[0], "fp64_flops": out[1], "smem_atomics_per_s": out[2], "l1_load_bytes_per_s": out[3],
+            "how": "own probe kernels, CUDA events, full occupancy: FMA chains, conflict-free shared float "
+                   "atomicAdd, float2 loads from an L1-resident 16 KiB buffer"}
+
+
+def stage_roofline(info, st, steps, peaks):
+    """Per-kernel rooflines of a serial profiled pass (every stage alone on the plan's
+    stream, so each stage time is its own launches' device time): spreading against the
+    shared-memory atomic rate (2 float atomics per tap: real and imaginary planes),
+    interpolation against L1 load bandwidth (one complex grid value per tap), direct sums
+    against the FP32 FMA peak (16 flops per pair)."""
+    out = {}
+    taps_per_step = info["nufft_points"] * info["w"] ** 3  # every NUFFT point spread once and gathered once
+    elem = 8.0 if info["precision"] == 1 else 16.0
+    for stage in ("spread", "interp", "direct"):
+        n = st["launches"][stage]
+        ms = st["ms"][stage]
+        if n <= 0 or ms <= 0:
+            continue
+        avg_s = ms * 1e-3 / n
+        per_launch = n / steps
+        if stage == "direct":
+            work = info["direct_pairs"]  # per direction; one launch per direction
+            achieved = work * FLOPS_PER_PAIR / avg_s
+            peak = peaks["fp32_flops"] if peaks else FP32_PEAK_FLOPS
+            out[stage] = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                          "frac": achieved / peak, "traffic": None, "pairs_per_launch": work,
+                          "avg_launch_ms": avg_s * 1e3, "pairs_per_s": work / avg_s,
+                          "peak_note": "FP32 FMA probe (measured live)" if peaks else "FP32 pipes (derived)"}
+            continue
+        taps = taps_per_step / per_launch
+        if stage == "spread":
+            achieved = 2.0 * taps / avg_s
+            peak = peaks["smem_atomics_per_s"] if peaks else None
+            out[stage] = {"bound": "smem_atomic", "achieved": achieved / 1e12, "peak": peak / 1e12 if peak else None,
+                          "unit": "T atomics/s", "frac": achieved / peak if peak else None, "traffic": None,
+                          "taps_per_s": taps / avg_s, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_launch,
+                          "peak_note": "conflict-free shared-memory float atomicAdd probe (measured live); taps "
+                                       "that miss a CTA's shared tile go to global atomics instead"}
+        else:
+            achieved = elem * taps / avg_s
+            peak = peaks["l1_load_bytes_per_s"] if peaks else None
+            out[stage] = {"bound": "l1", "achieved": achieved / 1e12, "peak": peak / 1e12 if peak else None,
+                          "unit": "TB/s", "frac": achieved / peak if peak else None, "traffic": None,
+                          "taps_per_s": taps / avg_s, "avg_launch_ms": avg_s * 1e3, "launches_per_step": per_launch,
+                          "peak_note": "L1-resident float2 load probe (measured live); one complex grid value per tap"}
+    return out
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -270,18 +346,17 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl", init_method="env://")
-    w = load_workload(args.n_vis, args.config, args.core_radius, args.radius_km, args.sparse)
-    units_per_step = 2.0 * (w.n_pix + w.n_vis)
+    peaks = probe_peaks()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
-    vis = configs.visibilities_cn(args.config, w.n_vis)
 
-    def measure(eps, with_e2e):
-        plan = hvox.Plan(w.pix, w.uvw, eps, mode=args.mode, graphs=args.graphs, plain=args.plain)
+    def measure(w, vis, eps, steps, warmup, with_e2e=False, plain=False, mode=None, serial_steps=0):
+        plan = hvox.Plan(w.pix, w.uvw, eps, mode=mode or args.mode, graphs=args.graphs, plain=plain)
         info = plan.info()
+        units_per_step = 2.0 * (w.n_pix + w.n_vis)
         I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
         V = torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")
         plan.profile(True)  # warm-up runs the profiled form too (its graph is captured there)
-        time_steps(plan, I, V, args.warmup, flush)
+        time_steps(plan, I, V, warmup, flush)
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize()
@@ -289,46 +364,86 @@ def run_gpu(args):
         clocks.start()
         plan.profile(True)
         dirs = []
-        ms = time_steps(plan, I, V, args.steps, flush, dirs)
+        ms = time_steps(plan, I, V, steps, flush, dirs)
         st = plan.stats()
         clk = clocks.stop()
         if world > 1:
             dist.barrier()
         total_ms = max_over_ranks(sum(ms), world)
-        s2v_ms = max_over_ranks(sum(d[0] for d in dirs), world) / args.steps
-        v2s_ms = max_over_ranks(sum(d[1] for d in dirs), world) / args.steps
+        s2v_ms = max_over_ranks(sum(d[0] for d in dirs), world) / steps
+        v2s_ms = max_over_ranks(sum(d[1] for d in dirs), world) / steps
         units = world * (w.n_pix + w.n_vis)
-        out = {"plan": plan, "info": info, "ms_per_step": total_ms / args.steps,
+        out = {"plan": plan, "info": info, "ms_per_step": total_ms / steps, "steps": steps, "warmup": warmup,
                "ms_median": max_over_ranks(statistics.median(ms), world),
-               "value": whole_job_rate(units_per_step, args.steps, total_ms * 1e-3, world), "stats": st,
+               "value": whole_job_rate(units_per_step, steps, total_ms * 1e-3, world), "stats": st,
                "clocks": clk,
                "per_direction": {"sky_to_vis_ms": s2v_ms, "vis_to_sky_ms": v2s_ms,
                                  "sky_to_vis_value": units / (s2v_ms * 1e-3),
                                  "vis_to_sky_value": units / (v2s_ms * 1e-3), "unit": UNIT}}
+        if serial_steps > 0:
+            plan.profile("serial")
+            time_steps(plan, I, V, serial_steps, flush)
+            out["serial"] = plan.stats()
+            out["serial_steps"] = serial_steps
+            plan.profile(False)
         if with_e2e:
             Ih = torch.as_tensor(w.sky, dtype=plan.real_dtype).pin_memory()
             Vh = torch.as_tensor(vis, dtype=plan.complex_dtype).pin_memory()
             Vo = torch.empty(w.n_vis, dtype=plan.complex_dtype).pin_memory()
             Io = torch.empty(w.n_pix, dtype=plan.real_dtype).pin_memory()
-            for _ in range(max(1, args.warmup)):
+            for _ in range(max(1, warmup)):
                 plan.synthesize(Ih, out=Vo)
                 plan.analyze(Vh, out=Io)
             if world > 1:
                 dist.barrier()
             t0 = time.perf_counter()
-            for _ in range(args.steps):
+            for _ in range(steps):
                 plan.synthesize(Ih, out=Vo)   # host I in, host V out
                 plan.analyze(Vh, out=Io)      # host V in, host I out
             el = max_over_ranks(time.perf_counter() - t0, world)
             rb = Ih.element_size()
-            out["e2e"] = {"value": whole_job_rate(units_per_step, args.steps, el, world), "unit": UNIT,
+            out["e2e"] = {"value": whole_job_rate(units_per_step, steps, el, world), "unit": UNIT,
                           "h2d_bytes_per_step": w.n_pix * rb + w.n_vis * 2 * rb,
                           "d2h_bytes_per_step": w.n_vis * 2 * rb + w.n_pix * rb,
-                          "ms_per_step": el * 1e3 / args.steps}
+                          "ms_per_step": el * 1e3 / steps}
         return out
 
-    main = measure(args.eps, not args.no_e2e)
-    secondary = measure(1e-6, False) if not args.no_secondary else None  # FP32 path
+    def path_dtype(info, eps, plain):
+        # Arithmetic of the path: FP64 kernels (plain form), FP32, or for FP64 plans the direct
+        # sums' double-float pairs of FP32 (FP64 accuracy on the FP32 pipes, FP64 only once per
+        # tile and output; FP64 kernels below eps 1e-9) and the NUFFT sub-problems' FP64 grids.
+        if plain:
+            return "f64"
+        if info["precision"] == 1:
+            return "f32"
+        kinds = []
+        if info["direct_pairs"] > 0:
+            kinds.append("f32x2" if eps >= 1e-9 else "f64")
+        if info["n_nufft_blocks"] > 0:
+            kinds.append("f64")
+        return "+".join(dict.fromkeys(kinds)) or "f32x2"
+
+    def summary(m, w, eps, plain=False):
+        info = m["info"]
+        d = {"eps": eps, "dtype": path_dtype(info, eps, plain), "value": m["value"], "unit": UNIT,
+             "ms_per_step": m["ms_per_step"], "ms_median": m["ms_median"], "steps": m["steps"],
+             "warmup": m["warmup"], "n_pix": w.n_pix, "n_vis": w.n_vis, "nufft_blocks": info["n_nufft_blocks"],
+             "direct_pairs": info["direct_pairs"], "w": info["w"], "upsampfac": info["upsampfac"],
+             "plan_seconds": info["plan_seconds"], "per_direction": m["per_direction"], "clocks": m["clocks"],
+             "launches_per_step": {k: v / m["steps"] for k, v in m["stats"]["launches"].items()}}
+        if "serial" in m:
+            ss = m["serial"]
+            d["stage_ms_serial"] = {k: v / m["serial_steps"] for k, v in ss["ms"].items()}
+            d["stage_note"] = ("stage_ms_serial: one serial profiled step (every stage alone on the plan's stream, "
+                               "no lanes or graph) after the timed steps; its stages add up to that step")
+            d["roofline"] = stage_roofline(info, ss, m["serial_steps"], peaks)
+        return d
+
+    w = load_workload(args.n_vis, args.config, args.core_radius, args.radius_km, args.sparse)
+    vis = configs.visibilities_cn(args.config, w.n_vis)
+    full_run = not (args.n_vis or args.core_radius or args.radius_km or args.sparse or args.config != 2)
+    main = measure(w, vis, args.eps, args.steps, args.warmup, with_e2e=not args.no_e2e, plain=args.plain)
+    secondary = measure(w, vis, 1e-6, args.steps, args.warmup) if not args.no_secondary else None  # FP32 path
 
     st = main["stats"]
     stage_ms = st["ms"]
@@ -347,6 +462,8 @@ def run_gpu(args):
                     "pairs_per_launch": pairs_per_launch, "avg_launch_ms": avg_s * 1e3,
                     "pairs_per_s": pairs_per_launch / avg_s,
                     "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
+        if peaks:
+            roofline["frac_of_probe"] = achieved / peaks["fp32_flops"]
         if ipp is not None:
             # FP32-pipe instruction issue against the same pipes' peak (one instruction per
             # lane per cycle): how close the kernel runs to the hardware it is bound by.
@@ -364,25 +481,12 @@ def run_gpu(args):
                     "taps_per_s": taps_per_launch / avg_s, "avg_launch_ms": avg_s * 1e3,
                     "peak_note": "FP32 pipes 152 SMs x 128 lanes x 2 flops x 2.07 GHz (derived)"}
     own = sum(st["launches"][k] for k in ("permute", "direct", "spread", "deconv", "interp"))
-    # Arithmetic of the path: FP64 kernels (plain form), FP32, or for FP64 plans the direct
-    # sums' double-float pairs of FP32 (FP64 accuracy on the FP32 pipes, FP64 only once per
-    # tile and output; FP64 kernels below eps 1e-9) and the NUFFT sub-problems' FP64 grids.
-    if args.plain:
-        dtype = "f64"
-    elif info["precision"] == 1:
-        dtype = "f32"
-    else:
-        kinds = []
-        if info["direct_pairs"] > 0:
-            kinds.append("f32x2" if args.eps >= 1e-9 else "f64")
-        if info["n_nufft_blocks"] > 0:
-            kinds.append("f64")
-        dtype = "+".join(dict.fromkeys(kinds)) or "f32x2"
 
     line = {"metric": METRIC, "value": main["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "ms_median": main["ms_median"],
             "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": dtype, "data": "synthetic (seeded HEALPix + layout)",
+            "scaling": "weak", "vs_baseline": None, "dtype": path_dtype(info, args.eps, args.plain),
+            "data": "synthetic (seeded HEALPix + layout)",
             "config": {"workload": w.name + "; step = sky->vis + vis->sky" if args.radius_km > 0
                        else WORKLOADS[args.config], "eps": args.eps, "n_pix": w.n_pix, "n_vis": w.n_vis,
                        "mode": args.mode, "core_radius": args.core_radius or None, "graphs": args.graphs,
@@ -394,15 +498,30 @@ def run_gpu(args):
             "e2e": main.get("e2e"), "roofline": roofline, "gpu_launches": own,
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "per_direction": main["per_direction"],
-            "clocks": main["clocks"]}
+            "clocks": main["clocks"], "peaks": peaks}
     if secondary is not None:
-        line["secondary"] = {"eps": 1e-6, "dtype": "f32", "value": secondary["value"],
-                             "ms_per_step": secondary["ms_per_step"], "clocks": secondary["clocks"],
-                             "per_direction": secondary["per_direction"],
-                             "stage_ms_per_step": {k: v / args.steps for k, v in secondary["stats"]["ms"].items()}}
-    main["plan"].close()
-    if secondary is not None:
+        line["secondary"] = summary(secondary, w, 1e-6)
         secondary["plan"].close()
+    main["plan"].close()
+    if full_run and not args.no_plain_line and not args.plain:
+        # The plain FP64 form of the same step (the comparison at the same accuracy). Its
+        # steps take seconds, so it runs one warm-up and two timed steps.
+        pl = measure(w, vis, args.eps, 2, 1, plain=True)
+        line["plain_fp64"] = summary(pl, w, args.eps, plain=True)
+        line["plain_fp64"]["speedup_of_headline"] = main["value"] / pl["value"]
+        pl["plan"].close()
+    if full_run and not args.no_config3:
+        # SKA-Low-like, chunked: the metric's eps = 1e-6 configuration. A step takes seconds,
+        # so it times min(steps, 5) steps after 3 warm-ups, then one serial profiled step.
+        w3 = load_workload(config=3)
+        vis3 = configs.visibilities_cn(3, w3.n_vis)
+        c3 = measure(w3, vis3, 1e-6, min(args.steps, 5), 3, mode="auto", serial_steps=1)
+        line["config3"] = summary(c3, w3, 1e-6)
+        line["config3"]["workload"] = WORKLOADS[3]
+        line["config3"]["l2"] = "flushed before each step (256 MiB write, outside the timed window)"
+        line["gpu_launches_config3"] = sum(c3["stats"]["launches"][k]
+                                          for k in ("permute", "direct", "spread", "deconv", "interp"))
+        c3["plan"].close()
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_study()
     if rank == 0 and not args.no_cpu_baseline:
@@ -426,6 +545,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--no-plain-line", action="store_true", help="skip the plain FP64 sub-line")
+    ap.add_argument("--no-config3", action="store_true", help="skip the SKA-Low-like eps = 1e-6 sub-line")
     ap.add_argument("--n-vis", type=int, default=0, help="use the first N baselines (profiler captures)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
                     help="workload (2, the LOFAR-like case, is the benchmark; 1 and 3 for studies)")

@@ -235,8 +235,13 @@ typedef struct {
     int64_t transforms;                /* transforms run since the last reset */
 } hvox_stats;
 
-/* Reset the statistics and turn event timing on (enable = 1) or off (0). Launch counts
- * are always collected. */
+/* Reset the statistics and turn event timing on (enable = 1 or 2) or off (0). Launch
+ * counts are always collected. enable = 1 times the transforms as they normally run
+ * (sub-problems on concurrent lanes, CUDA graphs), so a stage's time also counts the time
+ * its kernels wait for SMs held by concurrent work. enable = 2 is the serial form for
+ * per-kernel measurement: every stage runs alone on the plan's stream, without lanes or
+ * graphs, so each stage time is the device time of its own launches (the transforms run
+ * slower meanwhile). HVOX_EINVAL for other values. */
 hvox_status hvox_profile(hvox_plan_t plan, int enable);
 
 /* Statistics since the last hvox_profile call (waits for the plan's stream). */
@@ -278,13 +283,19 @@ const char *hvox_version(void);
  *   V interleaved complex float[2 n_vis] (overwritten): all DEVICE pointers (host
  *   pointers are rejected with HVOX_EINVAL). stream: cudaStream_t or NULL.
  * Limit: n_pix + n_vis <= 524,288 (HVOX_EINVAL beyond, nothing enqueued). The working
- * memory is one static device array of 16 MiB (coordinate splits) that every GPU which
- * loads the library reserves until the process exits; the call itself calls no
- * cudaMalloc, cudaFree or allocating library routine. The first call on a device looks
- * up that array's device address (cudaGetSymbolAddress) with the device current; make
- * that first call before any stream capture. All calls share the array and it keeps
- * the last call's contents, so calls whose work overlaps on the GPU (different streams,
- * or different host threads) race: serialise them. Asynchronous on `stream`.
+ * memory is one static device array of 16 MiB (coordinate splits), held on every GPU
+ * that loads it until the process exits; the call itself calls no cudaMalloc, cudaFree
+ * or allocating library routine. CUDA loads device code lazily by default, so the array
+ * is reserved on a device by the first call of this function there (or the first
+ * direct-sum launch of any plan there): a caller whose framework will take the whole
+ * device memory pool should make one call before the pool fills, else that first call
+ * can fail with HVOX_ECUDA (out of memory). The first call on a device also looks up the
+ * array's device address (cudaGetSymbolAddress) with the device current; make that first
+ * call before any stream capture. All calls share the array and it keeps the last call's
+ * contents, so calls whose work overlaps on the GPU (different streams, or different
+ * host threads) race: serialise them. The sum over pixels runs in segments of 4096
+ * pixels whose partial sums meet through atomic adds, so the last bits of V may differ
+ * between calls. Asynchronous on `stream`.
  */
 hvox_status hvox_direct_synthesize_noalloc(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis,
                                            const float *I, float *V, int isign, void *stream);

@@ -406,9 +406,11 @@ class Plan:
     def sync(self):
         _check(load().hvox_sync(self._handle))
 
-    def profile(self, enable: bool = True):
-        """Reset statistics; time every stage with CUDA events while enabled."""
-        _check(load().hvox_profile(self._handle, 1 if enable else 0))
+    def profile(self, enable=True):
+        """Reset statistics; time every stage with CUDA events while enabled. enable="serial"
+        runs every stage alone on the plan's stream (per-kernel device times)."""
+        mode = 2 if enable == "serial" else (1 if enable else 0)
+        _check(load().hvox_profile(self._handle, mode))
 
     def stats(self) -> dict:
         """Per-stage device milliseconds and launch counts since the last profile() call."""

@@ -13,6 +13,9 @@ CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhvox.so")
 SOURCES = ["abi.cpp", "exec.cpp", "planner.cpp", "es.cpp", "k_direct.cu", "k_nufft.cu", "k_misc.cu"]
+# Throughput probes for the benchmark's roofline denominators (a library of their own).
+PEAKS_LIB = os.path.join(HERE, "libhvox_peaks.so")
+PEAKS_SOURCES = ["peaks.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -27,9 +30,9 @@ def cuda_home() -> str:
 
 
 def _stale() -> bool:
-    if not os.path.exists(LIB):
+    if not os.path.exists(LIB) or not os.path.exists(PEAKS_LIB):
         return True
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PEAKS_LIB))
     deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "hvox.h"), __file__]
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
@@ -53,17 +56,19 @@ def build(force: bool = False, verbose: bool = False) -> str:
         return obj, r.stderr
 
     with cf.ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4)) as ex:
-        results = list(ex.map(compile_one, SOURCES))
+        results = list(ex.map(compile_one, SOURCES + PEAKS_SOURCES))
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[o for o, _ in results], "-lcufft",
-           "-Xlinker", "-rpath," + os.path.join(home, "lib64"), "-L", os.path.join(home, "lib64")]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0:
-        raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    objs = {src: o for src, (o, _) in zip(SOURCES + PEAKS_SOURCES, results)}
+    for lib, srcs, extra in ((LIB, SOURCES, ["-lcufft"]), (PEAKS_LIB, PEAKS_SOURCES, [])):
+        tmp = lib + f".tmp{os.getpid()}"
+        cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *[objs[s_] for s_ in srcs], *extra,
+               "-Xlinker", "-rpath," + os.path.join(home, "lib64"), "-L", os.path.join(home, "lib64")]
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
+        os.replace(tmp, lib)
     return LIB
 
 

@@ -623,7 +623,9 @@ hvox_status hvox_profile(hvox_plan_t plan, int enable) {
             p.stage_launches[i] = 0;
         }
         p.transforms = 0;
+        if (enable < 0 || enable > 2) fail(HVOX_EINVAL, "hvox_profile: enable must be 0, 1 or 2");
         p.profiling = enable != 0;
+        p.serial = enable == 2;
     });
 }
 

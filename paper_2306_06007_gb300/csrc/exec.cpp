@@ -37,7 +37,10 @@ cudaEvent_t take_event(Plan &p) {
 
 // Counts launches per stage and, when profiling, brackets each stage with events on the
 // stream that runs it (the plan's stream or a NUFFT lane). Stage times are sums of the
-// stages' durations, so stages that overlap on different lanes add up.
+// stages' durations, so stages that overlap on different lanes add up, and a bracket on a
+// lane also counts the time its kernels wait for SMs held by concurrent work. The serial
+// profiling mode runs every stage alone on the plan's stream, so there each bracket is
+// the device time of its own launches.
 // While a graph is captured (g set), launch counts and stage brackets go to the graph, and
 // the brackets become event-record nodes whose events the graph owns.
 struct Profiler final : StageHook {
@@ -95,15 +98,17 @@ template <typename T> NufftArgs<T> nufft_args(const Plan &p) {
     return a;
 }
 
-// Lanes start after everything enqueued so far on stream s.
+// Lanes start after everything enqueued so far on stream s. In the serialised profiling
+// mode there is no fork: every sub-problem runs on s after the direct sums.
 void fork_lanes(Plan &p, cudaStream_t s) {
-    if (p.lanes.empty()) return;
+    if (p.lanes.empty() || p.serial) return;
     check_cuda(cudaEventRecord(p.fork_event, s), "cudaEventRecord");
     for (auto &l : p.lanes) check_cuda(cudaStreamWaitEvent(l->stream, p.fork_event, 0), "cudaStreamWaitEvent");
 }
 
 // Stream s continues after every lane's work.
 void join_lanes(Plan &p, cudaStream_t s) {
+    if (p.serial) return;
     for (auto &l : p.lanes) {
         check_cuda(cudaEventRecord(l->done, l->stream), "cudaEventRecord");
         check_cuda(cudaStreamWaitEvent(s, l->done, 0), "cudaStreamWaitEvent");
@@ -115,6 +120,12 @@ template <typename T> void set_lane(NufftArgs<T> &a, const Plan &p, size_t b) {
     a.G1 = l.g1.as<typename CplxOf<T>::type>();
     a.G2 = l.g2.as<typename CplxOf<T>::type>();
     a.fft = p.block_fft[b];
+}
+
+// Stream of sub-problem b: its lane's, or s itself when profiling serially (the lane's
+// grids and cuFFT plans are still used, one sub-problem after another).
+cudaStream_t block_stream(const Plan &p, size_t b, cudaStream_t s) {
+    return p.serial ? s : p.lanes[p.block_lane[b]]->stream;
 }
 
 // sky -> vis between the permutations: src (chunk-ordered c_n) -> acc (chunk-ordered V).
@@ -148,14 +159,14 @@ void body_s2v(Plan &p, cudaStream_t s, Profiler &prof) {
             for (size_t b = 0; b < p.dblocks.size(); ++b) {
                 set_lane(a, p, b);
                 nufft_block_s2v<float>(p.dblocks[b], a, p.src.as<float>(), p.acc.as<float2>(),
-                                       p.lanes[p.block_lane[b]]->stream, prof);
+                                       block_stream(p, b, s), prof);
             }
         } else {
             NufftArgs<double> a = nufft_args<double>(p);
             for (size_t b = 0; b < p.dblocks.size(); ++b) {
                 set_lane(a, p, b);
                 nufft_block_s2v<double>(p.dblocks[b], a, p.src.as<double>(), p.acc.as<double2>(),
-                                        p.lanes[p.block_lane[b]]->stream, prof);
+                                        block_stream(p, b, s), prof);
             }
         }
     }
@@ -193,14 +204,14 @@ void body_v2s(Plan &p, cudaStream_t s, Profiler &prof) {
             for (size_t b = 0; b < p.dblocks.size(); ++b) {
                 set_lane(a, p, b);
                 nufft_block_v2s<float>(p.dblocks[b], a, p.src.as<float2>(), p.acc.as<float>(),
-                                       p.lanes[p.block_lane[b]]->stream, prof);
+                                       block_stream(p, b, s), prof);
             }
         } else {
             NufftArgs<double> a = nufft_args<double>(p);
             for (size_t b = 0; b < p.dblocks.size(); ++b) {
                 set_lane(a, p, b);
                 nufft_block_v2s<double>(p.dblocks[b], a, p.src.as<double2>(), p.acc.as<double>(),
-                                        p.lanes[p.block_lane[b]]->stream, prof);
+                                        block_stream(p, b, s), prof);
             }
         }
     }
@@ -215,7 +226,7 @@ void body(Plan &p, int dir, cudaStream_t s, Profiler &prof) {
 }
 
 bool graphs_wanted(const Plan &p) {
-    if (p.plain || p.graph_state < 0 || p.graphs_opt < 0) return false;
+    if (p.plain || p.serial || p.graph_state < 0 || p.graphs_opt < 0) return false;
     return p.graphs_opt > 0 || !p.dblocks.empty();
 }
 

@@ -226,6 +226,7 @@ struct GraphRun {
 struct Plan {
     // statistics
     bool profiling = false;
+    bool serial = false;   // profiling mode 2: every stage on the plan's stream, one at a time
     double stage_ms[HVOX_NUM_STAGES] = {0};
     int64_t stage_launches[HVOX_NUM_STAGES] = {0};
     int64_t transforms = 0;

@@ -708,8 +708,10 @@ void launch_direct_v2s_f64(const WorkItem *items, int64_t n, int *counter, const
 // fragments that pool), and iteration loops such as calibration solvers that predict
 // visibilities from a sky model every step, where an allocation (and the device
 // synchronisation cudaFree brings) is not allowed. The caller passes device pointers
-// for everything; the only working memory is the static array below, reserved once
-// per device when the library is loaded and kept until the process exits.
+// for everything; the only working memory is the static array below. CUDA reserves it on
+// a device when it loads this file's device code there (lazily by default: at the first
+// call of the entry point or the first direct-sum launch of any plan on that device) and
+// keeps it until the process exits.
 // ============================================================================
 
 namespace hvox {
@@ -735,8 +737,11 @@ __global__ void noalloc_split_kernel(const double *__restrict__ xyz, int64_t n, 
     lo[i] = make_float4(l[0], l[1], l[2], 0.f);
 }
 
-// Same arithmetic as direct_s2v_f32; the tile (baselines) comes from blockIdx.x and
-// the pixel segment from blockIdx.y instead of a work list.
+// The phase arithmetic and the two-level summation of direct_s2v_f32 (a register sum per
+// 256-pixel shared-memory tile, tile sums added with Kahan compensation); the baseline
+// tile comes from blockIdx.x and a segment of 4096 pixels from blockIdx.y instead of a
+// work list, and the segments' sums meet in V through atomicAdd, so their order (and the
+// last bits of the result) is not deterministic.
 __global__ void __launch_bounds__(kThreads) direct_s2v_f32_noalloc(
     const float4 *__restrict__ vh, const float4 *__restrict__ vl, int n_vis, const float4 *__restrict__ rh_g,
     const float4 *__restrict__ rl_g, const float *__restrict__ c, int n_pix, int seg, float2 *__restrict__ V,
@@ -746,7 +751,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32_noalloc(
     const int o0 = blockIdx.x * kTile, o1 = min(o0 + kTile, n_vis);
     const int s_begin = blockIdx.y * seg, s_end = min(s_begin + seg, n_pix);
     float3 ph[kPerThread], pl[kPerThread];
-    float are[kPerThread], aim[kPerThread];
+    float are[kPerThread], aim[kPerThread], cre[kPerThread], cim[kPerThread];
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) {
         int k = o0 + threadIdx.x + v * kThreads;
@@ -757,8 +762,7 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32_noalloc(
         }
         ph[v] = make_float3(a.x, a.y, a.z);
         pl[v] = make_float3(b.x, b.y, b.z);
-        are[v] = 0.f;
-        aim[v] = 0.f;
+        are[v] = aim[v] = cre[v] = cim[v] = 0.f;
     }
     for (int s0 = s_begin; s0 < s_end; s0 += kThreads) {
         __syncthreads();
@@ -774,6 +778,9 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32_noalloc(
         }
         __syncthreads();
         const int cnt = min(kThreads, s_end - s0);
+        float tre[kPerThread], tim[kPerThread];
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) tre[v] = tim[v] = 0.f;
 #pragma unroll 4
         for (int q = 0; q < cnt; ++q) {
             const float4 rh = sh[q], rl = sl[q];
@@ -782,17 +789,22 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32_noalloc(
                 float f = phase_f32(ph[v], pl[v], rh, rl);
                 float sn, cs;
                 __sincosf(6.28318530717958648f * f, &sn, &cs);
-                are[v] = __fmaf_rn(rh.w, cs, are[v]);
-                aim[v] = __fmaf_rn(rh.w, sn, aim[v]);
+                tre[v] = __fmaf_rn(rh.w, cs, tre[v]);
+                tim[v] = __fmaf_rn(rh.w, sn, tim[v]);
             }
+        }
+#pragma unroll
+        for (int v = 0; v < kPerThread; ++v) {
+            kahan_add(are[v], cre[v], tre[v]);
+            kahan_add(aim[v], cim[v], tim[v]);
         }
     }
 #pragma unroll
     for (int v = 0; v < kPerThread; ++v) {
         int k = o0 + threadIdx.x + v * kThreads;
         if (k < o1) {
-            atomicAdd(&V[k].x, are[v]);
-            atomicAdd(&V[k].y, sgn * aim[v]);
+            atomicAdd(&V[k].x, __fsub_rn(are[v], cre[v]));
+            atomicAdd(&V[k].y, sgn * __fsub_rn(aim[v], cim[v]));
         }
     }
 }

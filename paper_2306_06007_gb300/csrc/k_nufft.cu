@@ -236,18 +236,20 @@ __device__ __forceinline__ void grid_add(double2 *g, double re, double im) {
 // A CTA spreads 128 consecutive points (Morton order in grid-cell units, so they are close
 // on the grid). Phase 1: threads 0..127 each take one point, compute its window start,
 // kernel weights and value, stage them in shared memory and extend the CTA's bounding box.
-// Phase 2: each of the 16 warps handles 4 points at a time, 8 lanes per point, lane j along the
-// window's x taps j (and j + 8 when w > 8), looping over the (z, y) taps: a group's 8 adds
-// fall on 8 consecutive cells, so the 4 groups of a warp meet few bank conflicts. The four
-// points a warp takes together are 32 apart in the CTA's order (mostly disjoint windows),
-// and each group starts its z loop at a different plane. The taps go into a shared tile
-// (separate real and imaginary planes) covering the union of the windows, which is then
-// added to the grid with vector atomics, one warp per tile row; when the tile would not
-// fit, the taps go straight to the grid with the same lane layout.
+// Phase 2: each of the 16 warps takes 8 of the points, one at a time; for a point, lane
+// (g, j) (g = lane / 8, j = lane % 8) adds the taps of x offsets j (and j + 8 when w > 8)
+// in the z planes g, g + 4, ... of the window, looping over its y rows. The taps go into a
+// shared tile (separate real and imaginary planes) covering the union of the windows,
+// whose plane stride is padded to 8 (mod 32) elements: the four groups of a warp then sit
+// 8 banks apart and their 8 lanes on consecutive banks, so every shared atomic of a warp
+// touches 32 distinct banks. The tile is then added to the grid with vector atomics, one
+// warp per tile row; when the tile would not fit, the taps go straight to the grid with
+// the same lane layout.
 constexpr int kGroupLanes = 8;
-static_assert(kSpreadPoints * kGroupLanes % kSpreadThreads == 0 && kSpreadThreads % 32 == 0 &&
-                  (kSpreadThreads / 32) * 4 * (kSpreadPoints * kGroupLanes / kSpreadThreads) == kSpreadPoints,
-              "every point of a spreading CTA is taken by exactly one lane group");
+constexpr int kZGroups = 32 / kGroupLanes;                        // lane groups along z
+constexpr int kPointsPerWarp = kSpreadPoints / (kSpreadThreads / 32);
+static_assert(kSpreadThreads % 32 == 0 && kPointsPerWarp * (kSpreadThreads / 32) == kSpreadPoints,
+              "every point of a spreading CTA is taken by exactly one warp");
 constexpr int kSmemPerCta = 110 * 1024;  // two CTAs per SM
 
 template <typename T, int W> struct SpreadShared {
@@ -261,6 +263,9 @@ template <typename T, int W> struct SpreadShared {
 template <typename T, int W> __host__ __device__ constexpr int tile_bytes() {
     return ((kSmemPerCta - (int)sizeof(SpreadShared<T, W>)) / (2 * (int)sizeof(T) * 32)) * (2 * (int)sizeof(T) * 32);
 }
+
+// Plane stride of a tile with tx * ty cells per plane: the next value = 8 (mod 32).
+__device__ __forceinline__ int64_t tile_plane_stride(int64_t cells) { return cells + ((8 - cells) % 32 + 32) % 32; }
 
 template <typename T, int W, bool PERIODIC>
 __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
@@ -305,10 +310,11 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     const int lo0 = sh.lo[0], lo1 = sh.lo[1], lo2 = sh.lo[2];
     const int64_t tx = (int64_t)sh.hi[0] - lo0 + W, ty = (int64_t)sh.hi[1] - lo1 + W,
                   tz = (int64_t)sh.hi[2] - lo2 + W;
-    const bool tiled = tx * ty * tz <= cap;
-    const int txi = (int)tx, tyi = (int)ty;
+    const int64_t ps64 = tile_plane_stride(tx * ty);
+    const bool tiled = tz * ps64 <= cap;
+    const int txi = (int)tx, tyi = (int)ty, ps = tiled ? (int)ps64 : 0;
     if (tiled) {
-        const int cells = (int)(tx * ty * tz);
+        const int cells = (int)(tz * ps64);
         for (int j = tid; j < cells; j += blockDim.x) {
             tre[j] = T(0);
             tim[j] = T(0);
@@ -317,11 +323,10 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     }
     const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
     constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;  // x taps per lane (1 or 2)
-    constexpr int kRounds = kSpreadPoints * kGroupLanes / kSpreadThreads;  // points per group
-    for (int round = 0; round < kRounds; ++round) {
-        const int p = g * 32 + warp * kRounds + round;  // groups of a warp: points 32 apart
+    for (int round = 0; round < kPointsPerWarp; ++round) {
+        const int p = round * (kSpreadThreads / 32) + warp;  // warps take points 16 apart
         const int px0 = sh.i0[p][0];
-        if (px0 == INT_MIN) continue;
+        if (px0 == INT_MIN) continue;  // uniform across the warp
         const int py0 = sh.i0[p][1], pz0 = sh.i0[p][2];
         T ar[kXT], ai[kXT];
         int cx[kXT];
@@ -338,68 +343,35 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         T wy[W];
 #pragma unroll
         for (int j = 0; j < W; ++j) wy[j] = sh.w[p][W + j];
-        for (int jj = 0; jj < W; ++jj) {
-            const int jz = (jj + 2 * g) % W;
+        for (int jz = g; jz < W; jz += kZGroups) {
             const T wz = sh.w[p][2 * W + jz];
+            // Fold the z weight into the value once per plane: two multiplies per tap.
+            T zr[kXT], zi[kXT];
+#pragma unroll
+            for (int t = 0; t < kXT; ++t) {
+                zr[t] = ar[t] * wz;
+                zi[t] = ai[t] * wz;
+            }
             if (tiled) {
-                const int zrow = (pz0 - lo2 + jz) * tyi + (py0 - lo1);
-                if constexpr (sizeof(T) == 8) {
-                    // FP64 grids are bound by the FP64 pipe: fold wz into the value once per
-                    // plane, leaving two multiplies per tap (no per-row wy * wz product).
-                    T zr[kXT], zi[kXT];
-#pragma unroll
-                    for (int t = 0; t < kXT; ++t) {
-                        zr[t] = ar[t] * wz;
-                        zi[t] = ai[t] * wz;
-                    }
-#pragma unroll
-                    for (int jy = 0; jy < W; ++jy) {
-                        const int base = (zrow + jy) * txi;
-#pragma unroll
-                        for (int t = 0; t < kXT; ++t)
-                            if (on[t]) {
-                                atomicAdd(tre + base + cx[t], zr[t] * wy[jy]);
-                                atomicAdd(tim + base + cx[t], zi[t] * wy[jy]);
-                            }
-                    }
-                    continue;
-                }
+                const int zbase = (pz0 - lo2 + jz) * ps + (py0 - lo1) * txi;
 #pragma unroll
                 for (int jy = 0; jy < W; ++jy) {
-                    const T c = wy[jy] * wz;
-                    const int base = (zrow + jy) * txi;
+                    const int base = zbase + jy * txi;
 #pragma unroll
                     for (int t = 0; t < kXT; ++t)
                         if (on[t]) {
-                            atomicAdd(tre + base + cx[t], ar[t] * c);
-                            atomicAdd(tim + base + cx[t], ai[t] * c);
+                            atomicAdd(tre + base + cx[t], zr[t] * wy[jy]);
+                            atomicAdd(tim + base + cx[t], zi[t] * wy[jy]);
                         }
                 }
             } else {
                 const int64_t gz = PERIODIC ? wrap(pz0 + jz, ng[2]) : pz0 + jz;
-                if constexpr (sizeof(T) == 8) {
-                    T zr[kXT], zi[kXT];
-#pragma unroll
-                    for (int t = 0; t < kXT; ++t) {
-                        zr[t] = ar[t] * wz;
-                        zi[t] = ai[t] * wz;
-                    }
-                    for (int jy = 0; jy < W; ++jy) {
-                        const int64_t gy = PERIODIC ? wrap(py0 + jy, ng[1]) : py0 + jy;
-                        cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
-#pragma unroll
-                        for (int t = 0; t < kXT; ++t)
-                            if (on[t]) grid_add(row + cx[t], zr[t] * wy[jy], zi[t] * wy[jy]);
-                    }
-                    continue;
-                }
                 for (int jy = 0; jy < W; ++jy) {
-                    const T c = wy[jy] * wz;
                     const int64_t gy = PERIODIC ? wrap(py0 + jy, ng[1]) : py0 + jy;
                     cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
 #pragma unroll
                     for (int t = 0; t < kXT; ++t)
-                        if (on[t]) grid_add(row + cx[t], ar[t] * c, ai[t] * c);
+                        if (on[t]) grid_add(row + cx[t], zr[t] * wy[jy], zi[t] * wy[jy]);
                 }
             }
         }
@@ -416,7 +388,7 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
             gz = wrap(gz, ng[2]);
         }
         cplx_t<T> *grow = G + ((int64_t)gz * ng[1] + gy) * ng[0];
-        const int t0 = r * txi;
+        const int t0 = z * ps + y * txi;
         for (int x = lane; x < txi; x += 32) {
             const T re = tre[t0 + x], im = tim[t0 + x];
             if (re == T(0) && im == T(0)) continue;
