@@ -69,9 +69,14 @@ typedef enum {
     HVOX_EINVAL = 1,        /* bad argument; nothing was enqueued */
     HVOX_ENOMEM = 2,        /* device or host allocation failed */
     HVOX_ECUDA = 3,         /* a CUDA runtime or cuFFT call failed */
-    HVOX_ETIMEOUT = 4,      /* a device-side bounded wait gave up */
+    HVOX_ETIMEOUT = 4,      /* reserved: no kernel of this library waits on a flag, a peer
+                               or another kernel, so no call returns it */
     HVOX_EUNSUPPORTED = 5,  /* option combination not supported */
-    HVOX_EINTERNAL = 6      /* internal invariant violated (device error word set) */
+    HVOX_EINTERNAL = 6      /* internal invariant violated; also the plan's device error
+                               word: a kernel found a spreading or interpolation window
+                               outside its grid, clamped it (no out-of-bounds access) and
+                               set the word, which hvox_sync, hvox_get_stats and the calls
+                               that synchronise (host pointers) report and clear */
 } hvox_status;
 
 typedef enum { HVOX_PREC_AUTO = 0, HVOX_PREC_FP32 = 1, HVOX_PREC_FP64 = 2 } hvox_prec;
@@ -247,7 +252,8 @@ hvox_status hvox_profile(hvox_plan_t plan, int enable);
 /* Statistics since the last hvox_profile call (waits for the plan's stream). */
 hvox_status hvox_get_stats(hvox_plan_t plan, hvox_stats *out);
 
-/* Wait for the plan's stream and report any device-side error. */
+/* Wait for the plan's stream and report any device-side error: a CUDA error, or the
+ * plan's device error word (HVOX_EINTERNAL; the word is cleared by the report). */
 hvox_status hvox_sync(hvox_plan_t plan);
 
 /* Host-only dry run of hvox_plan: the partition, the per-sub-problem choices and the

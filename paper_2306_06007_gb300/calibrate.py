@@ -2,9 +2,10 @@
 
 The paper fits its CPU build's runtime by regressing measured stage times on stage work
 (spread, FFT, interpolation). This does the same for the GPU stages: each workload runs
-with one NUFFT lane (so stages do not overlap and their CUDA-event times add up to the
-step), every stage is timed by the library's profiler over a few steps, and each rate is
-fitted by least squares through the origin across the workloads:
+in the library's serial profiling mode (every stage alone on the plan's stream, so the
+CUDA-event stage times are the stages' own device times and add up to the step), over a
+few steps, and each rate is fitted by least squares through the origin across the
+workloads:
 
     spread ms         ~ taps         * c_spread     taps = (pix + vis points) * w^3
     interp ms         ~ taps         * c_interp
@@ -23,7 +24,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import os
 
 STAGE_WORK = {
     "spread": lambda i: (i["nufft_pix_points"] + i["nufft_vis_points"]) * i["w"] ** 3,
@@ -32,6 +32,10 @@ STAGE_WORK = {
     "grid": lambda i: 2.0 * (2.0 * i["spread_cells"] + 2.0 * i["nufft_cells"]),
     "direct": lambda i: 2.0 * i["direct_pairs"],
 }
+
+# Plan-info fields the stage work is computed from (kept with each measured row).
+INFO_KEYS = ("precision", "w", "n_nufft_blocks", "nufft_pix_points", "nufft_vis_points", "spread_cells",
+             "nufft_cells", "fft_work", "direct_pairs", "upsampfac")
 
 # Rates of the planner's cost model (seconds per unit of work), FP32 and FP64 sub-problems.
 MODEL = {"f32": {"spread": 1.0 / 4.75e11, "interp": 1.0 / 1.0e12, "fft": 4.1e-13, "grid": 1.3e-12,
@@ -64,7 +68,7 @@ def measure(w, eps: float, steps: int, mode: str = "auto"):
     plan.synthesize(I)
     plan.analyze(V)
     torch.cuda.synchronize()
-    plan.profile(True)
+    plan.profile("serial")
     for _ in range(steps):
         plan.synthesize(I, out=V)
         plan.analyze(V)
@@ -91,8 +95,8 @@ def main(argv=None):
     ap.add_argument("--eps", type=float, default=1e-6)
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--mode", default="auto", choices=["auto", "nufft"])
+    ap.add_argument("--out", default="", help="also write the JSON report to this file")
     args = ap.parse_args(argv)
-    os.environ["HVOX_NUFFT_LANES"] = "1"  # stages serialised: their times add up
     rows, report = [], []
     for name, w in _workloads():
         info, ms = measure(w, args.eps, args.steps, args.mode)
@@ -105,8 +109,14 @@ def main(argv=None):
     for r, (info, ms) in zip(report, rows):
         r["model_ms"] = {k: 1e3 * model[k] * f(info) for k, f in STAGE_WORK.items()}
         r["fitted_ms"] = {k: (1e3 * rates[k] * f(info) if rates[k] else None) for k, f in STAGE_WORK.items()}
-    print(json.dumps({"eps": args.eps, "fitted_seconds_per_unit": rates, "model_seconds_per_unit": model,
-                      "workloads": report}, indent=1))
+    out = {"eps": args.eps, "mode": args.mode, "steps": args.steps, "fitted_seconds_per_unit": rates,
+           "model_seconds_per_unit": model, "workloads": report,
+           "rows": [{"info": {k: info[k] for k in INFO_KEYS}, "stage_ms": ms} for info, ms in rows]}
+    text = json.dumps(out, indent=1)
+    if args.out:
+        with open(args.out, "w") as f:
+            f.write(text + "\n")
+    print(text)
 
 
 if __name__ == "__main__":

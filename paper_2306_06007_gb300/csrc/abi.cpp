@@ -9,6 +9,8 @@
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -40,9 +42,37 @@ void check_cufft(cufftResult r, const char *what) {
     }
 }
 
+bool fault_hit(const char *site) {
+    static std::mutex mu;
+    static std::string spec;
+    static std::map<std::string, int64_t> seen;
+    const char *v = std::getenv("HVOX_FAULT");
+    std::lock_guard<std::mutex> lock(mu);
+    const std::string now = v ? v : "";
+    if (now != spec) {
+        spec = now;
+        seen.clear();
+    }
+    if (spec.empty()) return false;
+    size_t pos = 0;
+    while (pos <= spec.size()) {
+        size_t end = spec.find(',', pos);
+        if (end == std::string::npos) end = spec.size();
+        const std::string item = spec.substr(pos, end - pos);
+        const size_t colon = item.find(':');
+        if (colon != std::string::npos && item.compare(0, colon, site) == 0) {
+            const int64_t n = std::atoll(item.c_str() + colon + 1);
+            return ++seen[site] == n;
+        }
+        pos = end + 1;
+    }
+    return false;
+}
+
 void DevBuf::alloc(size_t n) {
     free_();
     if (n == 0) return;
+    if (fault_hit("alloc")) fail(HVOX_ENOMEM, "cudaMalloc of " + std::to_string(n) + " bytes failed (injected)");
     cudaError_t e = cudaMalloc(&ptr, n);
     if (e != cudaSuccess) {
         ptr = nullptr;
@@ -85,6 +115,19 @@ Plan::~Plan() {
         cudaEventDestroy(q.b);
     }
     for (cudaEvent_t e : event_pool) cudaEventDestroy(e);
+}
+
+void check_device_error(Plan &p) {
+    if (!p.err.ptr) return;
+    int word = 0;
+    check_cuda(cudaMemcpy(&word, p.err.ptr, sizeof(int), cudaMemcpyDeviceToHost), "read device error word");
+    if (word == 0) return;
+    check_cuda(cudaMemset(p.err.ptr, 0, sizeof(int)), "clear device error word");
+    std::string what;
+    if (word & kDevErrPixWindow) what += " a pixel window fell outside its sub-problem's n1 grid;";
+    if (word & kDevErrVisWindow) what += " a baseline window fell beyond one period of its n2 grid;";
+    fail(HVOX_EINTERNAL, "device error word " + std::to_string(word) + ":" + what +
+                             " the kernels clamped it into the grid, so the transforms since the last check are wrong");
 }
 
 namespace {
@@ -249,6 +292,8 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         build_items(part.rects, true, p.direct_vpt, a);
         build_items(part.rects, false, p.direct_vpt, b);
         p.item_counter.alloc(2 * sizeof(int));
+        p.err.alloc(sizeof(int));
+        check_cuda(cudaMemsetAsync(p.err.ptr, 0, sizeof(int), s), "clear device error word");
         upload(p.items_s2v, a.data(), a.size() * sizeof(WorkItem), s);
         upload(p.items_v2s, b.data(), b.size() * sizeof(WorkItem), s);
         p.n_items_s2v = (int64_t)a.size();
@@ -332,7 +377,8 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         std::vector<size_t> max_ws(n_lanes, 0);
         auto make = [&](cufftHandle &h, int rank, long long *n, long long *emb, long long stride, long long dist,
                         long long batch, size_t &ws) {
-            check_cufft(cufftCreate(&h), "cufftCreate");
+            check_cufft(cufftCreate(&h), "cufftCreate");  // h lives in the lane's map: the lane destroys it
+            if (fault_hit("cufft")) fail(HVOX_ECUDA, "cufftMakePlanMany64: cuFFT error (injected)");
             check_cufft(cufftSetAutoAllocation(h, 0), "cufftSetAutoAllocation");
             check_cufft(cufftMakePlanMany64(h, rank, n, emb, stride, dist, emb, stride, dist, type, batch, &ws),
                         "cufftMakePlanMany64");
@@ -343,7 +389,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             const int64_t half = b.n1[2] / 2;
             auto key = std::make_tuple(b.n2[0], b.n2[1], b.n2[2], prune ? half : (int64_t)-1);
             if (!lane.fft.count(key)) {
-                FftPlans f;
+                FftPlans &f = lane.fft[key];
                 size_t ws = 0;
                 if (prune) {
                     long long nxy[2] = {b.n2[1], b.n2[0]};
@@ -356,7 +402,6 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                     make(f.full, 3, n3, nullptr, 1, 0, 1, ws);
                 }
                 max_ws[p.block_lane[i]] = std::max(max_ws[p.block_lane[i]], ws);
-                lane.fft[key] = f;
             }
             p.block_fft.push_back(lane.fft[key]);
         }
@@ -393,6 +438,12 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                 d.tpa[k] = (float)d.tpa64[k];
             }
             d.psi_off = b.psi_off;
+            d.err = p.err.as<int>();
+            if (fault_hit("window"))
+                for (int k = 0; k < 3; ++k) {
+                    d.a[k] *= 4.0;
+                    split(d.a[k], d.ah[k], d.al[k]);
+                }
             p.dblocks.push_back(d);
         }
     }
@@ -405,7 +456,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
 
     double ws = 0;
     for (DevBuf *b : {&p.pix_perm, &p.vis_perm, &p.weight, &p.pix_xyz, &p.vis_xyz, &p.pix_hi, &p.pix_lo, &p.vis_hi,
-                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.item_counter, &p.inv_psi, &p.cheb, &p.src, &p.acc, &p.cis_tab})
+                      &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.item_counter, &p.inv_psi, &p.cheb, &p.src, &p.acc, &p.cis_tab, &p.err})
         ws += (double)b->bytes;
     for (auto &l : p.lanes) ws += (double)(l->g1.bytes + l->g2.bytes + l->work.bytes);
     p.workspace_bytes = ws;
@@ -516,8 +567,10 @@ void transform(Plan &p, const void *in, void *out, bool s2v) {
     if (!dout) {
         check_cuda(cudaMemcpyAsync(out, dst, out_bytes, cudaMemcpyDeviceToHost, p.stream), "copy output");
         check_cuda(cudaStreamSynchronize(p.stream), "transform");
+        check_device_error(p);
     } else if (!din) {
         check_cuda(cudaStreamSynchronize(p.stream), "transform");
+        check_device_error(p);
     }
 }
 
@@ -609,6 +662,7 @@ hvox_status hvox_sync(hvox_plan_t plan) {
         check_cuda(cudaSetDevice(plan->p.device), "cudaSetDevice");
         check_cuda(cudaStreamSynchronize(plan->p.stream), "hvox_sync");
         check_cuda(cudaGetLastError(), "hvox_sync");
+        check_device_error(plan->p);
     });
 }
 
@@ -635,6 +689,8 @@ hvox_status hvox_get_stats(hvox_plan_t plan, hvox_stats *out) {
         Plan &p = plan->p;
         check_cuda(cudaSetDevice(p.device), "cudaSetDevice");
         collect_stats(p);
+        check_cuda(cudaStreamSynchronize(p.stream), "hvox_get_stats");
+        check_device_error(p);
         for (int i = 0; i < HVOX_NUM_STAGES; ++i) {
             out->ms[i] = p.stage_ms[i];
             out->launches[i] = p.stage_launches[i];

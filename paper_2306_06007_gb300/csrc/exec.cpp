@@ -245,6 +245,10 @@ std::unique_ptr<GraphRun> capture(Plan &p, int dir) {
     if (!p.cap) check_cuda(cudaStreamCreateWithFlags(&p.cap, cudaStreamNonBlocking), "cudaStreamCreate");
     check_cuda(cudaEventCreateWithFlags(&g->done, cudaEventDisableTiming), "cudaEventCreate");
     check_cuda(cudaStreamBeginCapture(p.cap, cudaStreamCaptureModeThreadLocal), "cudaStreamBeginCapture");
+    if (fault_hit("capture")) {
+        abandon_capture(p);
+        return nullptr;
+    }
     try {
         Profiler prof(p, g.get());
         body(p, dir, p.cap, prof);

@@ -30,6 +30,24 @@ struct Error {
 void check_cuda(cudaError_t e, const char *what);
 void check_cufft(cufftResult r, const char *what);
 
+// Host-side fault injection for tests. HVOX_FAULT = "site:n[,site:n...]" makes the n-th
+// event of each named site (counted from the moment the variable last changed) fail the
+// way the real failure would:
+//   alloc    a device allocation (HVOX_ENOMEM, everything allocated so far freed);
+//   cufft    a cuFFT plan creation (HVOX_ECUDA);
+//   capture  a CUDA-graph capture (the plan falls back to eager launches);
+//   window   the pixel scale of one NUFFT sub-problem is multiplied by 4 on the host, so
+//            its kernels clamp the pixels' windows into the grid and set the device
+//            error word (hvox_sync then returns HVOX_EINTERNAL).
+// No GPU fault is involved: every injected failure is raised or prepared on the host.
+bool fault_hit(const char *site);
+
+// Bits of a plan's device error word, set by kernels that had to clamp an index.
+enum : int {
+    kDevErrPixWindow = 1,   // a pixel window outside the n1 grid (clamped into it)
+    kDevErrVisWindow = 2    // a baseline window beyond one period of the n2 grid (clamped)
+};
+
 // ------------------------------------------------------------------ ES kernel
 
 struct ESKernel {
@@ -159,6 +177,7 @@ struct NufftDev {
     double tpa64[3];  // 2 pi / a (0 when a = 0)
     float Ch[3], Cl[3], Dh[3], Dl[3], ah[3], al[3], n2ah[3], n2al[3], tpa[3];
     int64_t psi_off;
+    int *err;         // the plan's device error word (kDevErr* bits)
 };
 
 template <typename T> struct CplxOf;
@@ -283,6 +302,7 @@ struct Plan {
     std::vector<int> block_lane;        // lane of each block
     std::vector<FftPlans> block_fft;    // FFT plans of each block (its lane's plans for its shape)
     DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
+    DevBuf err;                         // int: device error word (kDevErr* bits), read by hvox_sync
 
     // per-call buffers (chunk order)
     DevBuf src, acc;                    // source values, accumulated outputs
@@ -352,5 +372,8 @@ void launch_join_complex(int prec, const void *re, const void *im, int64_t n, vo
 void launch_add_j(int prec, void *a, const void *b, int64_t n, cudaStream_t s);
 void launch_times_mj(int prec, const void *a, int64_t n, void *out, cudaStream_t s);
 void collect_stats(Plan &p);
+// Reads (and clears) the device error word after the plan's stream has been synchronised;
+// a set word fails with HVOX_EINTERNAL.
+void check_device_error(Plan &p);
 
 }  // namespace hvox

@@ -80,21 +80,23 @@ __device__ __forceinline__ float round_fma(float x) { return __fsub_rn(__fadd_rn
 // x - nearest integer, exact (the difference of a float and its rounding is exact).
 __device__ __forceinline__ float frac_fma(float x) { return __fsub_rn(x, round_fma(x)); }
 
+// Fraction of hi(p) hi(r) in turns for one dimension, in three FMA-pipe instructions:
+// t = fl(p r + 1.5 * 2^23) carries n = round(p r) exactly (float spacing 1 there, for
+// |p r| < 2^22), and fma(p, r, -n) forms the exact p r - n (|.| <= 1/2) with one rounding
+// (<= 2^-25 turn).
+__device__ __forceinline__ float prod_frac(float p, float r) {
+    const float n = __fsub_rn(__fmaf_rn(p, r, kRoundMagic), kRoundMagic);
+    return __fmaf_rn(p, r, -n);
+}
+
 // Fraction of <p, r> in turns, FP32 (|error| ~ 1e-7 turn), result in [-0.5, 0.5].
 // Valid for |p_d r_d| < 2^22 turns per dimension.
 __device__ __forceinline__ float phase_f32(const float3 &ph, const float3 &pl, const float4 &rh, const float4 &rl) {
-    float a0, b0, a1, b1, a2, b2;
-    two_prod(ph.x, rh.x, a0, b0);
-    two_prod(ph.y, rh.y, a1, b1);
-    two_prod(ph.z, rh.z, a2, b2);
-    a0 = frac_fma(a0);
-    a1 = frac_fma(a1);
-    a2 = frac_fma(a2);
-    float small = __fadd_rn(__fadd_rn(b0, b1), b2);
-    small = __fmaf_rn(ph.x, rl.x, __fmaf_rn(pl.x, rh.x, small));
+    float small = __fmaf_rn(ph.x, rl.x, __fmul_rn(pl.x, rh.x));
     small = __fmaf_rn(ph.y, rl.y, __fmaf_rn(pl.y, rh.y, small));
     small = __fmaf_rn(ph.z, rl.z, __fmaf_rn(pl.z, rh.z, small));
-    float f = __fadd_rn(__fadd_rn(a0, a1), __fadd_rn(a2, small));
+    const float f = __fadd_rn(__fadd_rn(prod_frac(ph.x, rh.x), prod_frac(ph.y, rh.y)),
+                              __fadd_rn(prod_frac(ph.z, rh.z), small));
     return frac_fma(f);
 }
 

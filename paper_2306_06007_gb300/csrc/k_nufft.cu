@@ -55,12 +55,30 @@ template <typename T, int W> __device__ __forceinline__ void es_weights(T fr, T 
     }
 }
 
-// i mod n for i in [-n, 2n): window cells of points inside a sub-problem's band lie within
-// n2/2 + w of the origin and n2 >= 2w. The clamp keeps any index inside the grid.
+// i mod n for i in [-n, 2n). Every caller indexes a window whose start geo_vis has
+// checked to lie in [-n, 2n - w] (clamping it there and setting the device error word
+// otherwise), and n2 >= 2w, so every argument is in that range.
 __device__ __forceinline__ int wrap(int i, int n) {
     i += i < 0 ? n : 0;
     i -= i >= n ? n : 0;
-    return min(max(i, 0), n - 1);
+    return i;
+}
+
+// Window start of a pixel on the n1 grid: inside [0, n1 - W] for every pixel of the
+// sub-problem's box; anything else is clamped into the grid and reported.
+template <int W> __device__ __forceinline__ int clamp_pix_window(int i0, int n1, int *err) {
+    const int c = min(max(i0, 0), n1 - W);
+    if (c != i0) atomicOr(err, kDevErrPixWindow);
+    return c;
+}
+
+// Window start of a baseline on the periodic n2 grid: baselines of the sub-problem's box
+// lie within n2/2 + W of the origin, so the start is in [-n2, 2 n2 - W]; anything else is
+// clamped there and reported.
+template <int W> __device__ __forceinline__ int check_vis_window(int i0, int n2, int *err) {
+    const int c = min(max(i0, -n2), 2 * n2 - W);
+    if (c != i0) atomicOr(err, kDevErrVisWindow);
+    return c;
 }
 
 // ------------------------------------------------------------------ float helpers
@@ -149,7 +167,7 @@ __device__ __forceinline__ void geo_pix(const NufftDev &b, int64_t n, const floa
         float sh, sl;
         df_mul(b.ah[d], b.al[d], th[d], tl[d], sh, sl);
         window_f32<W>(sh, sl, b.n1[d] / 2, i0[d], fr[d]);
-        i0[d] = min(max(i0[d], 0), b.n1[d] - W);
+        i0[d] = clamp_pix_window<W>(i0[d], b.n1[d], b.err);
     }
     const float f = dot_frac_f32(b.Dh, b.Dl, th, tl);
     float sn, cs;
@@ -167,7 +185,7 @@ __device__ __forceinline__ void geo_pix(const NufftDev &b, int64_t n, const floa
     for (int d = 0; d < 3; ++d) {
         const double r = soa[d * n_all + n] - b.C[d];
         window_f64<W>(b.a[d] * r + 0.5 * b.n1[d], i0[d], fr[d]);
-        i0[d] = min(max(i0[d], 0), b.n1[d] - W);
+        i0[d] = clamp_pix_window<W>(i0[d], b.n1[d], b.err);
         t = fma(b.D[d], r, t);
     }
     t -= rint(t);
@@ -194,6 +212,7 @@ __device__ __forceinline__ void geo_vis(const NufftDev &b, int64_t k, const floa
         float sh, sl;
         df_mul(b.n2ah[d], b.n2al[d], th, tl, sh, sl);
         window_f32<W>(sh, sl, 0, i0[d], fr[d]);
+        i0[d] = check_vis_window<W>(i0[d], b.n2[d], b.err);
         ip *= inv_phi<float>(th * b.tpa[d], cc, deg, inv_tmax2);
     }
     const float f = dot_frac_f32(ph, pl, b.Ch, b.Cl);
@@ -214,6 +233,7 @@ __device__ __forceinline__ void geo_vis(const NufftDev &b, int64_t k, const floa
         const double p = soa[d * n_all + k];
         const double pt = p - b.D[d];
         window_f64<W>(pt * b.n2a[d], i0[d], fr[d]);
+        i0[d] = check_vis_window<W>(i0[d], b.n2[d], b.err);
         ip *= inv_phi<double>(pt * b.tpa64[d], cc, deg, inv_tmax2);
         t = fma(b.C[d], p, t);
     }
