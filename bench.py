@@ -350,7 +350,8 @@ def run_gpu(args):
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MiB > L2
 
     def measure(w, vis, eps, steps, warmup, with_e2e=False, plain=False, mode=None, serial_steps=0):
-        plan = hvox.Plan(w.pix, w.uvw, eps, mode=mode or args.mode, graphs=args.graphs, plain=plain)
+        plan = hvox.Plan(w.pix, w.uvw, eps, mode=mode or args.mode, graphs=args.graphs, plain=plain,
+                         factor=args.factor if args.factor != "auto" else None)
         info = plan.info()
         units_per_step = 2.0 * (w.n_pix + w.n_vis)
         I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
@@ -494,7 +495,8 @@ def run_gpu(args):
                        "l2": "flushed before each step (256 MiB write, outside the timed window)",
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
                        "direct_pairs": info["direct_pairs"], "w": info["w"],
-                       "plan_seconds": info["plan_seconds"]},
+                       "plan_seconds": info["plan_seconds"], "box_ratio": info["box_ratio"],
+                       "factor": args.factor},
             "e2e": main.get("e2e"), "roofline": roofline, "gpu_launches": own,
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "per_direction": main["per_direction"],
@@ -558,6 +560,8 @@ def main():
                     help="study: the plain FP64 form (FP64 arithmetic in every kernel, no graph)")
     ap.add_argument("--graphs", type=int, default=0, choices=[-1, 0, 1],
                     help="CUDA graphs: 0 for plans with NUFFT sub-problems, 1 always, -1 never")
+    ap.add_argument("--factor", default="auto", choices=["auto", "pixels", "baselines"],
+                    help="study: force a factored evaluation (one box spanning the other set)")
     ap.add_argument("--core-radius", type=float, default=0.0,
                     help="keep only baselines with |(u, v)| <= R wavelengths (dense-core study)")
     args = ap.parse_args()

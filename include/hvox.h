@@ -122,6 +122,19 @@ typedef struct {
                                     permutations are skipped; the weights a_n are still
                                     applied. 0: the caller's own point order. */
     void *stream;                /* cudaStream_t; NULL = legacy default stream */
+    int32_t factor;              /* which set's spreading is shared across sub-problems (the
+                                    factored evaluation of Sect. 3, Table 1's "theory" row):
+                                    0 -> chosen by the cost model among the box splits it
+                                    searches, which include both factored forms;
+                                    1 -> pixels: one baseline box spans every baseline, so
+                                    each pixel is spread (and gathered) once and the pixel
+                                    chunks shrink to keep Algorithm 1's grid size;
+                                    2 -> baselines: one pixel box spans the sky, so each
+                                    baseline is spread (and gathered) once.
+                                    A shared spread must resolve every frequency its
+                                    sub-problems read (the kernel transform is evaluated at
+                                    the full p, not p - D_j), so sharing is exact only with
+                                    a box that spans the other set. */
 } hvox_opts;
 
 /* Plan summary (filled by hvox_plan_info). */

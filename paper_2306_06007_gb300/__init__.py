@@ -38,7 +38,10 @@ class Opts(ctypes.Structure):
                 ("chunk_budget_bytes", ctypes.c_double), ("anisotropy", ctypes.c_double),
                 ("direct_threshold", ctypes.c_double), ("search_threshold", ctypes.c_double),
                 ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
-                ("graphs", ctypes.c_int32), ("chunk_order", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("graphs", ctypes.c_int32), ("chunk_order", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("factor", ctypes.c_int32)]
+
+_FACTOR = {None: 0, "auto": 0, "pixels": 1, "baselines": 2}
 
 
 class Info(ctypes.Structure):
@@ -173,7 +176,7 @@ def chunk_points(xyz, h):
 
 def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: float = 0.0,
              chunk_budget_bytes: float = 0.0, direct_threshold: float = 0.0, plain: bool = False,
-             search_threshold: float = 0.0) -> dict:
+             search_threshold: float = 0.0, factor=None) -> dict:
     """Host-only planning (no GPU): partition, block choices and cost-model estimate."""
     np = _np()
     pix = np.ascontiguousarray(pix, dtype=np.float64)
@@ -186,6 +189,7 @@ def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: flo
     o.direct_threshold = direct_threshold
     o.search_threshold = search_threshold
     o.plain = 1 if plain else 0
+    o.factor = _FACTOR[factor]
     inf = Info()
     _check(load().hvox_plan_dry(_dptr(pix), len(pix), _dptr(uvw), len(uvw), float(eps), ctypes.byref(o),
                                 ctypes.byref(inf)))
@@ -279,7 +283,7 @@ class Plan:
     def __init__(self, pix, uvw, eps: float, isign: int = -1, weight=None, precision="auto", mode="auto",
                  upsampfac: float = 0.0, chunk_budget_bytes: float = 0.0, anisotropy: float = 0.0,
                  direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, graphs: int = 0,
-                 search_threshold: float = 0.0, chunk_order: bool = False, stream=None):
+                 search_threshold: float = 0.0, chunk_order: bool = False, stream=None, factor=None):
         import torch
         lib = load()
         self._handle = ctypes.c_void_p()
@@ -298,6 +302,7 @@ class Plan:
         o.plain = 1 if plain else 0
         o.graphs = int(graphs)
         o.chunk_order = 1 if chunk_order else 0
+        o.factor = _FACTOR[factor]
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

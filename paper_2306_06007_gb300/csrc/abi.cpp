@@ -239,6 +239,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     in.elem_bytes = elem;
     in.sigma_auto = p.sigma_auto;
     in.eps_es = p.eps_es;
+    in.factor = p.factor;
     {
         // Up to kMaxLanes lanes each hold the grids of their largest sub-problem and a cuFFT
         // work area of about the same size: keep that within a third of the free memory.
@@ -479,6 +480,8 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     if (!std::isfinite(o.direct_threshold)) fail(HVOX_EINVAL, "hvox_plan: bad direct_threshold");
     if (!(o.search_threshold >= 0.0) || !std::isfinite(o.search_threshold))
         fail(HVOX_EINVAL, "hvox_plan: bad search_threshold");
+    if (o.factor < 0 || o.factor > 2) fail(HVOX_EINVAL, "hvox_plan: factor must be 0, 1 or 2");
+    p.factor = o.factor;
     p.n_pix = n_pix;
     p.n_vis = n_vis;
     p.eps = eps;
@@ -731,6 +734,7 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         in.elem_bytes = elem;
         in.sigma_auto = p.sigma_auto;
         in.eps_es = p.eps_es;
+        in.factor = p.factor;
         p.part = make_partition(in);
         p.sigma = p.part.sigma;
         p.es = p.part.es;

@@ -149,6 +149,7 @@ struct PlanInputs {
     double direct_threshold;
     double search_threshold = 0.01;  // seconds of modelled direct work below which no search
     int elem_bytes;
+    int factor = 0;        // hvox_opts.factor: 0 searched, 1 one baseline box, 2 one pixel box
 };
 
 PartitionResult make_partition(const PlanInputs &in);
@@ -272,6 +273,7 @@ struct Plan {
     double eps_es = 1e-6;          // tolerance given to the kernel-width rule
     double direct_threshold = 0.0; // direct_threshold option
     double search_threshold = 0.01; // search_threshold option (seconds)
+    int factor = 0;                // factor option
     ESKernel es;
     bool has_weight = false;
     cudaStream_t stream = nullptr;

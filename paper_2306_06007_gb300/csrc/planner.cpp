@@ -352,6 +352,18 @@ Evaluated evaluate(const PlanInputs &in, const CostModel &m, double budget, cons
     return e;
 }
 
+// Box split of a factored evaluation at this budget: factor 1 makes the baseline box span
+// every baseline (h = B; pixel boxes shrink by t so that the grid keeps Algorithm 1's size)
+// and factor 2 makes the pixel box span the sky (eta = P). A hair of slack keeps the
+// extreme points in the first lattice cell. 1 when Algorithm 1's boxes already span both.
+double factored_ratio(int factor, const double P[3], const double B[3], double budget, double sigma, int w,
+                      int elem_bytes) {
+    double eta[3], h[3];
+    const double t = box_dims(P, B, budget, sigma, w, elem_bytes, eta, h);
+    if (!(t > 0.0) || t >= 1.0) return 1.0;
+    return factor == 1 ? t / 1.000001 : 1.000001 / t;
+}
+
 }  // namespace
 
 PartitionResult make_partition(const PlanInputs &in) {
@@ -382,7 +394,9 @@ PartitionResult make_partition(const PlanInputs &in) {
     // (~1-3 us per point) would cost more than it could save over the plan's expected use.
     const bool tiny = 2.0 * m.direct_pair * (double)in.n_pix * (double)in.n_vis < in.search_threshold;
     if (in.budget > 0) {
-        best = evaluate(in, m, in.budget, P, B);
+        const double ratio =
+            in.factor ? factored_ratio(in.factor, P, B, in.budget, in.sigma, in.es.w, in.elem_bytes) : 1.0;
+        best = evaluate(in, m, in.budget, P, B, ratio);
     } else if (in.mode == HVOX_MODE_DIRECT || (tiny && in.mode == HVOX_MODE_AUTO && in.direct_threshold <= 0)) {
         PlanInputs direct = in;
         direct.mode = HVOX_MODE_DIRECT;
@@ -430,7 +444,11 @@ PartitionResult make_partition(const PlanInputs &in) {
                     PlanInputs cand = in;
                     cand.sigma = cands[c].sigma;
                     cand.es = cands[c].es;
-                    evals[c] = evaluate(cand, m, cands[c].budget, P, B);
+                    const double ratio =
+                        in.factor ? factored_ratio(in.factor, P, B, cands[c].budget, cand.sigma, cand.es.w,
+                                                   in.elem_bytes)
+                                  : 1.0;
+                    evals[c] = evaluate(cand, m, cands[c].budget, P, B, ratio);
                 }));
             for (auto &j : jobs) j.get();
             // keep only the best so far (bounds host memory on large point sets)
@@ -450,9 +468,16 @@ PartitionResult make_partition(const PlanInputs &in) {
         // boxes cut the sky into chunks too small to pay for a grid, as with a dense core
         // inside a long-baseline array) every budget is tried with ratios up to 64, so that
         // a core of short baselines can meet the whole sky in one box.
-        if (best.cost > 0) {
+        // Both factored forms (one box spanning one of the sets, so that the other set's
+        // points are spread once) are candidates at the chosen budget; a caller-fixed factor
+        // skips this pass.
+        if (best.cost > 0 && !in.factor) {
             const bool none = best.nufft_pairs.empty();
             std::vector<std::pair<double, double>> rb;  // (budget, ratio)
+            for (int f : {1, 2}) {
+                const double r = factored_ratio(f, P, B, best.budget, best_sigma, best_es.w, in.elem_bytes);
+                if (r != 1.0) rb.push_back({best.budget, r});
+            }
             if (!none) {
                 for (double r : {0.25, 0.5, 2.0, 4.0, 8.0}) rb.push_back({best.budget, r});
             } else {

@@ -92,3 +92,17 @@ def test_direct_sums_below_1e9_are_priced_as_fp64(lib):
     a = hvox.plan_dry(w.pix, w.uvw, 1e-9, mode="direct")["model_seconds"]
     b = hvox.plan_dry(w.pix, w.uvw, 1e-11, mode="direct")["model_seconds"]
     assert 50 < b / a < 200
+
+
+@pytest.mark.parametrize("factor,which", [("pixels", "n_vis_chunks"), ("baselines", "n_pix_chunks")])
+def test_factored_plans_span_the_other_set(lib, factor, which):
+    # A factored evaluation shares one set's spreading across sub-problems only when one box
+    # spans the other set: forcing it leaves a single chunk of that set, at a budget where
+    # Algorithm 1's own boxes would cut both sets.
+    w = configs.radius_sweep(1.0)
+    base = hvox.plan_dry(w.pix, w.uvw, 1e-6, mode="nufft", chunk_budget_bytes=4e6)
+    assert base["n_pix_chunks"] > 1 and base["n_vis_chunks"] > 1 and base["t"] < 1.0
+    f = hvox.plan_dry(w.pix, w.uvw, 1e-6, mode="nufft", chunk_budget_bytes=4e6, factor=factor)
+    assert f[which] == 1
+    assert abs(f["t"] - base["t"]) < 1e-12  # the same grid budget per sub-problem
+    assert (f["box_ratio"] < 1.0) == (factor == "pixels")
