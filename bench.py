@@ -16,6 +16,7 @@ plain_fp64: the same step at eps = 1e-9 in the plain form (FP64 arithmetic in ev
 config3: the SKA-Low-like workload (1,470,612 px x 4,186,112 baselines) at eps = 1e-6,
          chunked (NUFFT sub-problems + direct sums), with a serial profiled pass that
          times every kernel alone for the spreading, interpolation and direct rooflines.
+sparse_sky: 500 pixels of interest in the 10 km field x 237,705 baselines at eps = 1e-6.
 peaks:   throughput probes run live on this GPU (FP32/FP64 FMA, shared-memory atomics,
          L1 loads) for the denominators the driver's measured peaks do not hold.
 serving: a seeded request stream served with continuous batching against the plain
@@ -253,25 +254,30 @@ def time_steps(plan, I, V, steps, flush, per_direction=None):
 
 def serving_study():
     """Served (continuous batching, mixed precision) vs plain (FP64, one job at a time) on
-    the same seeded request stream; and a larger served stream. Latency = completion -
-    arrival; throughput = sum of (N_pix + N_vis) over requests / makespan."""
+    the same seeded request stream, as it arrives (latency) and all present at t = 0
+    (throughput, not bound by the arrival rate); and a larger served stream run twice.
+    Latency = completion - arrival; throughput = sum of (N_pix + N_vis) over requests /
+    makespan; tail_ms splits the slowest 1 % into plan wait, slot wait and device time."""
     from hvox_inputs import configs
     from paper_2306_06007_gb300.serve import Server
     out = {}
     small = configs.config5_requests(100, rate_hz=50.0, n_min=1e3, n_max=3e4, seed_offset=11)
     for name, kw in (("served", {"max_inflight": 8}), ("plain", {"plain": True})):
-        srv = Server(**kw)
-        rep = srv.run(small, realtime=True)
-        srv.close()
-        out[name] = rep.summary()
+        for realtime, suffix in ((True, ""), (False, "_saturated")):
+            srv = Server(**kw)
+            rep = srv.run(small, realtime=realtime)
+            srv.close()
+            out[name + suffix] = rep.summary()
     out["stream"] = ("100 requests, Poisson 50/s, N_pix and N_vis log-uniform [1e3, 3e4] (HEALPix caps <= 40 deg; "
-                     "config-2/3 layouts), eps uniform {1e-4, 1e-6, 1e-9}, S or A")
-    big = configs.config5_requests(100, rate_hz=50.0, n_min=1e4, n_max=2e5, seed_offset=12)
-    srv = Server(max_inflight=8)
-    rep = srv.run(big, realtime=True)
-    srv.close()
-    out["served_large"] = rep.summary()
-    out["served_large"]["stream"] = "as above with N log-uniform [1e4, 2e5]"
+                     "config-2/3 layouts), eps uniform {1e-4, 1e-6, 1e-9}, S or A; *_saturated: the same "
+                     "requests all present at t = 0")
+    big = configs.config5_requests(400, rate_hz=50.0, n_min=1e4, n_max=2e5, seed_offset=12)
+    for run in (1, 2):
+        srv = Server(max_inflight=8)
+        rep = srv.run(big, realtime=True)
+        srv.close()
+        out[f"served_large_run{run}"] = rep.summary()
+    out["stream_large"] = "400 requests, Poisson 50/s, N log-uniform [1e4, 2e5], otherwise as above; run twice"
     return out
 
 
@@ -283,10 +289,11 @@ def probe_peaks():
     if not os.path.exists(path):
         return None
     lib = ctypes.CDLL(path)
-    out = (ctypes.c_double * 4)()
+    out = (ctypes.c_double * 6)()
     if lib.hvox_probe_peaks(out) != 0:
         return None
     return {"fp32_flops": out[0], "fp64_flops": out[1], "smem_atomics_per_s": out[2], "l1_load_bytes_per_s": out[3],
+            "smem_int_atomics_per_s": out[4], "smem_float_rmw_per_s": out[5],
             "how": "own probe kernels, CUDA events, full occupancy: FMA chains, conflict-free shared float "
                    "atomicAdd, float2 loads from an L1-resident 16 KiB buffer"}
 
@@ -351,7 +358,7 @@ def run_gpu(args):
 
     def measure(w, vis, eps, steps, warmup, with_e2e=False, plain=False, mode=None, serial_steps=0):
         plan = hvox.Plan(w.pix, w.uvw, eps, mode=mode or args.mode, graphs=args.graphs, plain=plain,
-                         factor=args.factor if args.factor != "auto" else None)
+                         factor=args.factor if args.factor != "auto" else None, autotune=args.autotune)
         info = plan.info()
         units_per_step = 2.0 * (w.n_pix + w.n_vis)
         I = torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")
@@ -496,7 +503,8 @@ def run_gpu(args):
                        "parallelism": f"{world} replica(s)", "nufft_blocks": info["n_nufft_blocks"],
                        "direct_pairs": info["direct_pairs"], "w": info["w"],
                        "plan_seconds": info["plan_seconds"], "box_ratio": info["box_ratio"],
-                       "factor": args.factor},
+                       "factor": args.factor, "autotune": args.autotune,
+                       "spread_bins": [info["spread_bin_pix"], info["spread_bin_vis"]]},
             "e2e": main.get("e2e"), "roofline": roofline, "gpu_launches": own,
             "stage_ms_per_step": {k: v / args.steps for k, v in stage_ms.items()},
             "per_direction": main["per_direction"],
@@ -524,6 +532,15 @@ def run_gpu(args):
         line["gpu_launches_config3"] = sum(c3["stats"]["launches"][k]
                                           for k in ("permute", "direct", "spread", "deconv", "interp"))
         c3["plan"].close()
+    if full_run and not args.no_sparse:
+        # The sparse-sky setup (500 pixels of interest in 5 groups of the 10 km field, all
+        # 237,705 baselines): the planner keeps it direct.
+        ws = load_workload(radius_km=10.0, sparse=500)
+        vs = configs.visibilities_cn(6, ws.n_vis)
+        sp = measure(ws, vs, 1e-6, args.steps, args.warmup, mode="auto")
+        line["sparse_sky"] = summary(sp, ws, 1e-6)
+        line["sparse_sky"]["workload"] = ws.name + "; step = sky->vis + vis->sky"
+        sp["plan"].close()
     if rank == 0 and not args.no_serving:
         line["serving"] = serving_study()
     if rank == 0 and not args.no_cpu_baseline:
@@ -549,6 +566,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--no-plain-line", action="store_true", help="skip the plain FP64 sub-line")
     ap.add_argument("--no-config3", action="store_true", help="skip the SKA-Low-like eps = 1e-6 sub-line")
+    ap.add_argument("--no-sparse", action="store_true", help="skip the sparse-sky sub-line")
     ap.add_argument("--n-vis", type=int, default=0, help="use the first N baselines (profiler captures)")
     ap.add_argument("--config", type=int, default=2, choices=[1, 2, 3],
                     help="workload (2, the LOFAR-like case, is the benchmark; 1 and 3 for studies)")
@@ -562,6 +580,7 @@ def main():
                     help="CUDA graphs: 0 for plans with NUFFT sub-problems, 1 always, -1 never")
     ap.add_argument("--factor", default="auto", choices=["auto", "pixels", "baselines"],
                     help="study: force a factored evaluation (one box spanning the other set)")
+    ap.add_argument("--autotune", action="store_true", help="plan with the measured bin-size autotuner")
     ap.add_argument("--core-radius", type=float, default=0.0,
                     help="keep only baselines with |(u, v)| <= R wavelengths (dense-core study)")
     args = ap.parse_args()

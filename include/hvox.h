@@ -135,6 +135,10 @@ typedef struct {
                                     sub-problems read (the kernel transform is evaluated at
                                     the full p, not p - D_j), so sharing is exact only with
                                     a box that spans the other set. */
+    int32_t autotune;            /* 1: measure at plan time, on the sub-problem with the most
+                                    points of each set, which bin size (points per spreading
+                                    CTA: 32, 64 or 128) spreads fastest, and keep it for that
+                                    direction (a few extra launches during hvox_plan); 0: 128 */
 } hvox_opts;
 
 /* Plan summary (filled by hvox_plan_info). */
@@ -169,6 +173,8 @@ typedef struct {
     double fft_work;             /* M2 log2 M2 over the FFT grids */
     double box_ratio;            /* pixel box dims = ratio x Algorithm 1's, baseline box dims
                                     = Algorithm 1's / ratio (1: the isotropic optimum) */
+    int32_t spread_bin_pix;      /* points per spreading CTA, pixels (sky -> vis) */
+    int32_t spread_bin_vis;      /* points per spreading CTA, baselines (vis -> sky) */
 } hvox_info;
 
 /*

@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("direct_threshold", ctypes.c_double), ("search_threshold", ctypes.c_double),
                 ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("chunk_order", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("factor", ctypes.c_int32)]
+                ("factor", ctypes.c_int32), ("autotune", ctypes.c_int32)]
 
 _FACTOR = {None: 0, "auto": 0, "pixels": 1, "baselines": 2}
 
@@ -56,7 +56,8 @@ class Info(ctypes.Structure):
                 ("workspace_bytes", ctypes.c_double), ("plan_seconds", ctypes.c_double),
                 ("model_seconds", ctypes.c_double), ("graph_state", ctypes.c_int32),
                 ("nufft_pix_points", ctypes.c_double), ("nufft_vis_points", ctypes.c_double),
-                ("spread_cells", ctypes.c_double), ("fft_work", ctypes.c_double), ("box_ratio", ctypes.c_double)]
+                ("spread_cells", ctypes.c_double), ("fft_work", ctypes.c_double), ("box_ratio", ctypes.c_double),
+                ("spread_bin_pix", ctypes.c_int32), ("spread_bin_vis", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):
@@ -283,7 +284,8 @@ class Plan:
     def __init__(self, pix, uvw, eps: float, isign: int = -1, weight=None, precision="auto", mode="auto",
                  upsampfac: float = 0.0, chunk_budget_bytes: float = 0.0, anisotropy: float = 0.0,
                  direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, graphs: int = 0,
-                 search_threshold: float = 0.0, chunk_order: bool = False, stream=None, factor=None):
+                 search_threshold: float = 0.0, chunk_order: bool = False, stream=None, factor=None,
+                 autotune: bool = False):
         import torch
         lib = load()
         self._handle = ctypes.c_void_p()
@@ -303,6 +305,7 @@ class Plan:
         o.graphs = int(graphs)
         o.chunk_order = 1 if chunk_order else 0
         o.factor = _FACTOR[factor]
+        o.autotune = 1 if autotune else 0
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

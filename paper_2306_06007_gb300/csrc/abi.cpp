@@ -211,6 +211,42 @@ void build_items(const std::vector<DirectRect> &rects, bool owner_is_vis, int vp
     });
 }
 
+// Autotuned bin size: the points a spreading CTA takes (32, 64 or 128) trade the size of
+// its shared tile (the bounding box of their windows) against the tile's set-up and flush
+// per point. Each direction's spreading of the sub-problem with the most points of that
+// set is timed with every candidate (after one untimed launch each) and the fastest kept;
+// the values are ones, so the flush writes every touched cell.
+template <typename T> void tune_bins(Plan &p) {
+    NufftArgs<T> a = plan_nufft_args<T>(p);
+    size_t bp = 0, bv = 0;
+    for (size_t b = 0; b < p.dblocks.size(); ++b) {
+        if (p.dblocks[b].np > p.dblocks[bp].np) bp = b;
+        if (p.dblocks[b].nv > p.dblocks[bv].nv) bv = b;
+    }
+    const size_t n = p.src.bytes / sizeof(T);
+    std::vector<T> ones(n, T(1));
+    check_cuda(cudaMemcpy(p.src.ptr, ones.data(), n * sizeof(T), cudaMemcpyHostToDevice), "autotune values");
+    for (int pix = 1; pix >= 0; --pix) {
+        const size_t b = pix ? bp : bv;
+        if ((pix ? p.dblocks[b].np : p.dblocks[b].nv) == 0) continue;
+        const Lane &l = *p.lanes[p.block_lane[b]];
+        a.G1 = l.g1.as<typename CplxOf<T>::type>();
+        a.G2 = l.g2.as<typename CplxOf<T>::type>();
+        a.fft = p.block_fft[b];
+        int best = 128;
+        float best_ms = INFINITY;
+        for (int ppc : {128, 64, 32}) {
+            time_spread<T>(p.dblocks[b], a, pix != 0, p.src.ptr, ppc, p.stream);
+            const float ms = time_spread<T>(p.dblocks[b], a, pix != 0, p.src.ptr, ppc, p.stream);
+            if (ms < best_ms * 0.97f) {  // a smaller bin must win clearly
+                best_ms = ms;
+                best = ppc;
+            }
+        }
+        (pix ? p.ppc_pix : p.ppc_vis) = best;
+    }
+}
+
 void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const double *w_in) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = p.stream;
@@ -454,6 +490,12 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     p.src.alloc(src_bytes);
     p.acc.alloc(src_bytes);
     check_cuda(cudaStreamSynchronize(s), "hvox_plan");
+    if (p.autotune && !p.dblocks.empty()) {
+        if (p.prec == 1)
+            tune_bins<float>(p);
+        else
+            tune_bins<double>(p);
+    }
 
     double ws = 0;
     for (DevBuf *b : {&p.pix_perm, &p.vis_perm, &p.weight, &p.pix_xyz, &p.vis_xyz, &p.pix_hi, &p.pix_lo, &p.vis_hi,
@@ -482,6 +524,8 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
         fail(HVOX_EINVAL, "hvox_plan: bad search_threshold");
     if (o.factor < 0 || o.factor > 2) fail(HVOX_EINVAL, "hvox_plan: factor must be 0, 1 or 2");
     p.factor = o.factor;
+    if (o.autotune < 0 || o.autotune > 1) fail(HVOX_EINVAL, "hvox_plan: autotune must be 0 or 1");
+    p.autotune = o.autotune != 0;
     p.n_pix = n_pix;
     p.n_vis = n_vis;
     p.eps = eps;
@@ -542,6 +586,8 @@ void fill_info(const Plan &p, hvox_info *info) {
     info->spread_cells = p.part.spread_cells;
     info->fft_work = p.part.fft_work;
     info->box_ratio = p.part.box_ratio;
+    info->spread_bin_pix = p.ppc_pix;
+    info->spread_bin_vis = p.ppc_vis;
 }
 
 void transform(Plan &p, const void *in, void *out, bool s2v) {

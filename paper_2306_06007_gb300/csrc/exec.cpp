@@ -95,6 +95,8 @@ template <typename T> NufftArgs<T> nufft_args(const Plan &p) {
     a.cheb = p.cheb.as<T>();
     a.deg = p.cheb_deg;
     a.inv_tmax2 = p.cheb_inv_tmax2;
+    a.ppc_pix = p.ppc_pix;
+    a.ppc_vis = p.ppc_vis;
     return a;
 }
 
@@ -312,6 +314,10 @@ void execute(Plan &p, int dir) {
 }
 
 }  // namespace
+
+template <typename T> NufftArgs<T> plan_nufft_args(const Plan &p) { return nufft_args<T>(p); }
+template NufftArgs<float> plan_nufft_args<float>(const Plan &);
+template NufftArgs<double> plan_nufft_args<double>(const Plan &);
 
 void collect_stats(Plan &p) {
     for (auto &d : p.graph)

@@ -208,6 +208,7 @@ template <typename T> struct NufftArgs {
     const T *cheb = nullptr;   // Chebyshev coefficients of 1/Phi in u = 2 (tau/tau_max)^2 - 1
     int deg = 0;
     double inv_tmax2 = 0.0;    // 1 / tau_max^2
+    int ppc_pix = 128, ppc_vis = 128;  // points per spreading CTA (bin size), <= 128
 };
 
 // Stage boundaries reported by the kernel launchers to the executor's profiler.
@@ -274,6 +275,8 @@ struct Plan {
     double direct_threshold = 0.0; // direct_threshold option
     double search_threshold = 0.01; // search_threshold option (seconds)
     int factor = 0;                // factor option
+    bool autotune = false;         // autotune option
+    int ppc_pix = 128, ppc_vis = 128;  // points per spreading CTA (bin size) of each direction
     ESKernel es;
     bool has_weight = false;
     cudaStream_t stream = nullptr;
@@ -357,11 +360,19 @@ template <typename T>
 void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const typename CplxOf<T>::type *V, T *acc,
                      cudaStream_t s, StageHook &hook);
 
+// Device time (ms) of one spreading launch of block b with ppc points per CTA: pixels onto
+// a.G1 (pix) or baselines onto a.G2, values c / V (the grid is cleared first, untimed).
+template <typename T>
+float time_spread(const NufftDev &b, const NufftArgs<T> &a, bool pix, const void *values, int ppc, cudaStream_t s);
+
 // Permutations between the caller's order and chunk order (k_misc.cu).
 void launch_s2v_in(int prec, const void *I, const int32_t *perm, const double *w, int64_t n, void *src, cudaStream_t s);
 void launch_s2v_out(int prec, const void *acc, const int32_t *perm, int64_t n, void *V, cudaStream_t s);
 void launch_v2s_in(int prec, const void *V, const int32_t *perm, int64_t n, void *src, cudaStream_t s);
 void launch_v2s_out(int prec, const void *acc, const int32_t *perm, const double *w, int64_t n, void *I, cudaStream_t s);
+
+// Plan-wide kernel arguments of the NUFFT launchers (grids and FFT plans set per block).
+template <typename T> NufftArgs<T> plan_nufft_args(const Plan &p);
 
 // Transforms.
 void run_synthesize(Plan &p, const void *I_dev, void *V_dev);

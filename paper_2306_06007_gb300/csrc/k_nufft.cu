@@ -39,7 +39,7 @@ namespace {
 template <typename T> using cplx_t = typename CplxOf<T>::type;
 
 constexpr int kSpreadThreads = 512;  // 16 warps: latency hiding at two CTAs per SM
-constexpr int kSpreadPoints = 128;  // points per spreading CTA: two threads per point
+constexpr int kSpreadPoints = 128;  // largest number of points per spreading CTA (the bin)
 
 __device__ __forceinline__ float es_exp(float x) { return __expf(x); }
 __device__ __forceinline__ double es_exp(double x) { return exp(x); }
@@ -289,7 +289,7 @@ __device__ __forceinline__ int64_t tile_plane_stride(int64_t cells) { return cel
 
 template <typename T, int W, bool PERIODIC>
 __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
-                                           const int ng[3], cplx_t<T> *__restrict__ G) {
+                                           const int ng[3], int ppc, cplx_t<T> *__restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ SpreadShared<T, W> sh;
     constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));
@@ -343,7 +343,8 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     }
     const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
     constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;  // x taps per lane (1 or 2)
-    for (int round = 0; round < kPointsPerWarp; ++round) {
+    const int rounds = (ppc + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32);
+    for (int round = 0; round < rounds; ++round) {
         const int p = round * (kSpreadThreads / 32) + warp;  // warps take points 16 apart
         const int px0 = sh.i0[p][0];
         if (px0 == INT_MIN) continue;  // uniform across the warp
@@ -418,16 +419,17 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     }
 }
 
-// sky -> vis step 1: pixels (values c, prephase P) onto the n1 grid. Thread t < 128 takes
-// point blockIdx.x * 128 + t.
+// sky -> vis step 1: pixels (values c, prephase P) onto the n1 grid. A CTA takes ppc <= 128
+// consecutive points (the bin; the plan may tune it): thread t < ppc takes point
+// blockIdx.x * ppc + t.
 template <typename T, int W>
 __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread_pix_kernel(NufftDev b, const float4 *__restrict__ rh,
                                                                      const float4 *__restrict__ rl,
                                                                      const double *__restrict__ soa, int64_t n_all,
                                                                      const T *__restrict__ c, cplx_t<T> *__restrict__ G1,
-                                                                     T beta, int isign) {
-    const int64_t i = blockIdx.x * (int64_t)kSpreadPoints + threadIdx.x;
-    const bool act = threadIdx.x < kSpreadPoints && i < b.np;
+                                                                     T beta, int isign, int ppc) {
+    const int64_t i = blockIdx.x * (int64_t)ppc + threadIdx.x;
+    const bool act = threadIdx.x < ppc && i < b.np;
     int i0[3] = {0, 0, 0};
     T fr[3] = {0, 0, 0}, vr = 0, vi = 0;
     if (act) {
@@ -438,7 +440,7 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread
         vi = cv * pim;
     }
     const int ng[3] = {b.n1[0], b.n1[1], b.n1[2]};
-    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, ng, G1);
+    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, ng, ppc, G1);
 }
 
 // vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2 grid.
@@ -448,9 +450,9 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread
                                                                      const double *__restrict__ soa, int64_t n_all,
                                                                      const cplx_t<T> *__restrict__ V,
                                                                      const T *__restrict__ cc, int deg, T inv_tmax2,
-                                                                     cplx_t<T> *__restrict__ G2, T beta, int isign) {
-    const int64_t k = blockIdx.x * (int64_t)kSpreadPoints + threadIdx.x;
-    const bool act = threadIdx.x < kSpreadPoints && k < b.nv;
+                                                                     cplx_t<T> *__restrict__ G2, T beta, int isign, int ppc) {
+    const int64_t k = blockIdx.x * (int64_t)ppc + threadIdx.x;
+    const bool act = threadIdx.x < ppc && k < b.nv;
     int i0[3] = {0, 0, 0};
     T fr[3] = {0, 0, 0}, ur = 0, ui = 0;
     if (act) {
@@ -461,7 +463,7 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread
         ui = qr * v.y - qi * v.x;
     }
     const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
-    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, ng, G2);
+    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, ng, ppc, G2);
 }
 
 // ------------------------------------------------------------------ interpolation (gather)
@@ -830,8 +832,8 @@ void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_
         hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_pix_kernel<T, W><<<blocks_for(b.np, kSpreadPoints), kSpreadThreads, tile_bytes<T, W>(), s>>>(         \
-        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, a.G1, bt, a.isign)
+    spread_pix_kernel<T, W><<<blocks_for(b.np, a.ppc_pix), kSpreadThreads, tile_bytes<T, W>(), s>>>(          \
+        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, a.G1, bt, a.isign, a.ppc_pix)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_pix");
@@ -870,8 +872,8 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
         hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_vis_kernel<T, W><<<blocks_for(b.nv, kSpreadPoints), kSpreadThreads, tile_bytes<T, W>(), s>>>(         \
-        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, bt, a.isign)
+    spread_vis_kernel<T, W><<<blocks_for(b.nv, a.ppc_vis), kSpreadThreads, tile_bytes<T, W>(), s>>>(          \
+        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, bt, a.isign, a.ppc_vis)
         HVOX_W_SWITCH(w, CALL)
 #undef CALL
         check_cuda(cudaGetLastError(), "spread_vis");
@@ -896,6 +898,47 @@ void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *
         hook.end(HVOX_STAGE_INTERP, 1, s);
     }
 }
+
+template <typename T>
+float time_spread(const NufftDev &b, const NufftArgs<T> &a, bool pix, const void *values, int ppc, cudaStream_t s) {
+    const int w = a.w;
+    const T bt = (T)a.beta;
+    const int64_t cells = pix ? (int64_t)b.n1[0] * b.n1[1] * b.n1[2] : (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
+    cplx_t<T> *G = pix ? a.G1 : a.G2;
+    check_cuda(cudaMemsetAsync(G, 0, sizeof(cplx_t<T>) * cells, s), "memset grid");
+    cudaEvent_t e0, e1;
+    check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
+    check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
+    check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
+    if (pix) {
+#define CALL(W)                                                                                                   \
+    set_smem_attrs<T, W>();                                                                                       \
+    spread_pix_kernel<T, W><<<blocks_for(b.np, ppc), kSpreadThreads, tile_bytes<T, W>(), s>>>(                  \
+        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, (const T *)values, a.G1, bt, a.isign, ppc)
+        HVOX_W_SWITCH(w, CALL)
+#undef CALL
+    } else {
+#define CALL(W)                                                                                                   \
+    set_smem_attrs<T, W>();                                                                                       \
+    spread_vis_kernel<T, W><<<blocks_for(b.nv, ppc), kSpreadThreads, tile_bytes<T, W>(), s>>>(                  \
+        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, (const cplx_t<T> *)values, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, \
+        bt, a.isign, ppc)
+        HVOX_W_SWITCH(w, CALL)
+#undef CALL
+    }
+    check_cuda(cudaGetLastError(), "spread (timing)");
+    check_cuda(cudaEventRecord(e1, s), "cudaEventRecord");
+    check_cuda(cudaEventSynchronize(e1), "cudaEventSynchronize");
+    float ms = 0.f;
+    check_cuda(cudaEventElapsedTime(&ms, e0, e1), "cudaEventElapsedTime");
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return ms;
+}
+
+template float time_spread<float>(const NufftDev &, const NufftArgs<float> &, bool, const void *, int, cudaStream_t);
+template float time_spread<double>(const NufftDev &, const NufftArgs<double> &, bool, const void *, int,
+                                   cudaStream_t);
 
 template void nufft_block_s2v<float>(const NufftDev &, const NufftArgs<float> &, const float *, float2 *,
                                      cudaStream_t, StageHook &);

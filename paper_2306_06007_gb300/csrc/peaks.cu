@@ -40,6 +40,33 @@ __global__ void __launch_bounds__(kAtomThreads) shared_atomic_kernel(float *out,
     if (threadIdx.x == 0 && buf[0][0] == -1.0f) out[blockIdx.x] = buf[0][1];
 }
 
+// The same pattern with 32-bit integer atomics, and with a plain read-modify-write of
+// lane-private words (load, add, store; no atomic): the alternatives a spreading kernel
+// could use for its shared tile.
+__global__ void __launch_bounds__(kAtomThreads) shared_int_atomic_kernel(float *out, int iters) {
+    __shared__ int buf[kAtomThreads / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (kAtomThreads / 32) * 256; i += blockDim.x) (&buf[0][0])[i] = 0;
+    __syncthreads();
+    for (int i = 0; i < iters; ++i) atomicAdd(&buf[warp][((i & 7) << 5) + lane], 3);
+    __syncthreads();
+    if (threadIdx.x == 0 && buf[0][0] == -1) out[blockIdx.x] = (float)buf[0][1];
+}
+
+__global__ void __launch_bounds__(kAtomThreads) shared_rmw_kernel(float *out, int iters) {
+    __shared__ float buf[kAtomThreads / 32][256];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int i = threadIdx.x; i < (kAtomThreads / 32) * 256; i += blockDim.x) (&buf[0][0])[i] = 0.f;
+    __syncthreads();
+    volatile float *b = &buf[warp][0];
+    for (int i = 0; i < iters; ++i) {
+        const int k = ((i & 7) << 5) + lane;  // lane-private words: no two lanes share one
+        b[k] = b[k] + 1.0f;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && buf[0][0] == -1.0f) out[blockIdx.x] = buf[0][1];
+}
+
 // Every CTA reads the same 16 KiB (float2, lane-consecutive), which stays in each SM's L1.
 constexpr int kL1Elems = 2048;
 __global__ void l1_load_kernel(const float2 *__restrict__ src, float *out, int iters) {
@@ -74,7 +101,9 @@ template <typename F> double time_ms(F &&launch) {
 }  // namespace
 
 // out[0] FP32 FMA flop/s, out[1] FP64 FMA flop/s, out[2] shared-memory float atomicAdd/s,
-// out[3] L1 load bytes/s. Returns 0, or the CUDA error code of the first failing call.
+// out[3] L1 load bytes/s, out[4] shared-memory int atomicAdd/s, out[5] shared-memory
+// float read-modify-writes/s (no atomic). Returns 0, or the CUDA error code of the first
+// failing call.
 extern "C" int hvox_probe_peaks(double *out) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
@@ -107,6 +136,14 @@ extern "C" int hvox_probe_peaks(double *out) {
         const int iters = 1 << 15;
         double ms = time_ms([&] { l1_load_kernel<<<blocks, 256>>>(src, sink, iters); });
         out[3] = 8.0 * (double)iters * blocks * 256 / (ms * 1e-3);
+    }
+    {
+        const int iters = 1 << 15;
+        const unsigned ab = (unsigned)sms * 4;
+        double ms = time_ms([&] { shared_int_atomic_kernel<<<ab, kAtomThreads>>>(sink, iters); });
+        out[4] = (double)iters * ab * kAtomThreads / (ms * 1e-3);
+        ms = time_ms([&] { shared_rmw_kernel<<<ab, kAtomThreads>>>(sink, iters); });
+        out[5] = (double)iters * ab * kAtomThreads / (ms * 1e-3);
     }
     cudaError_t e = cudaDeviceSynchronize();
     cudaFree(sink);

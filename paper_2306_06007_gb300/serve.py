@@ -50,7 +50,7 @@ class _Inflight:
     event: object
     out: object
     io_bytes: float
-    start: float
+    start: float          # admission time (seconds after the start of the run)
 
 
 @dataclass
@@ -62,16 +62,28 @@ class ServeReport:
     units: float = 0.0                               # sum of (n_pix + n_vis) over requests
     peak_bytes: float = 0.0
     errors: dict = field(default_factory=dict)       # rid -> message of a request that failed
+    # rid -> (seconds waiting for its plan, waiting for a slot after that, on the device)
+    phases: dict = field(default_factory=dict)
 
     def summary(self) -> dict:
         lat = sorted(self.latency_s.values())
         q = (lambda f: lat[min(len(lat) - 1, int(round(f * (len(lat) - 1))))] * 1e3) if lat else (lambda f: None)
-        return {"requests": len(lat), "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": q(1.0),
-                "mean_ms": statistics.mean(lat) * 1e3 if lat else None,
-                "throughput_units_per_s": self.units / self.makespan_s if self.makespan_s > 0 else None,
-                "makespan_s": self.makespan_s, "plans": len(self.plan_s),
-                "plan_s_total": sum(self.plan_s.values()), "peak_bytes": self.peak_bytes,
-                "errors": len(self.errors)}
+        out = {"requests": len(lat), "p50_ms": q(0.50), "p99_ms": q(0.99), "max_ms": q(1.0),
+               "mean_ms": statistics.mean(lat) * 1e3 if lat else None,
+               "throughput_units_per_s": self.units / self.makespan_s if self.makespan_s > 0 else None,
+               "makespan_s": self.makespan_s, "plans": len(self.plan_s),
+               "plan_s_total": sum(self.plan_s.values()), "peak_bytes": self.peak_bytes,
+               "errors": len(self.errors)}
+        if lat and self.phases:
+            # Where the time of the slowest 1 % of requests went (mean over them, ms).
+            by_lat = sorted(self.latency_s, key=self.latency_s.get)
+            tail = by_lat[int(0.99 * (len(by_lat) - 1)):]
+            ph = [self.phases[r] for r in tail if r in self.phases]
+            if ph:
+                out["tail_ms"] = {"plan_wait": 1e3 * statistics.mean(p[0] for p in ph),
+                                  "slot_wait": 1e3 * statistics.mean(p[1] for p in ph),
+                                  "device": 1e3 * statistics.mean(p[2] for p in ph), "requests": len(ph)}
+        return out
 
 
 class Server:
@@ -137,6 +149,7 @@ class Server:
         planning: dict[str, cf.Future] = {}
         reserved: dict[str, float] = {}
         inflight: list[_Inflight] = []
+        ready: dict[str, float] = {}   # key -> time its plan became resident
         t0 = time.perf_counter()
         first_arrival = None
         rep.units = float(sum(len(r.pix) + len(r.uvw) for r in requests))
@@ -183,6 +196,7 @@ class Server:
                 self.used += nbytes - reserved.pop(k)
                 self.resident[k] = _Resident(plan, stream, nbytes)
                 rep.plan_s[k] = secs
+                ready[k] = time.perf_counter() - t0
                 progressed = True
             # admission and launch
             i = 0
@@ -221,6 +235,8 @@ class Server:
                 r = f.req
                 arrival = (r.arrival * time_scale) if realtime else 0.0
                 rep.latency_s[r.rid] = done - arrival
+                plan_ready = max(arrival, ready.get(f.key, arrival))
+                rep.phases[r.rid] = (plan_ready - arrival, f.start - plan_ready, done - f.start)
                 rep.results[r.rid] = f.out.numpy().copy()
                 res = self.resident[f.key]
                 res.busy = False

@@ -422,3 +422,26 @@ def test_sparse_sky_full(gpu_lib, eps, mode):
     print(f"sparse sky eps={eps:g} mode={mode}: rel_l2 sky->vis {e_v:.3e} vis->sky {e_i:.3e} "
           f"(blocks {info['n_nufft_blocks']})")
     assert e_v <= 10 * eps and e_i <= 10 * eps
+
+
+@pytest.mark.parametrize("eps", [1e-6, 1e-9])
+def test_autotuned_bins_keep_parity(gpu_lib, small, eps):
+    # The autotuner picks the spreading bin (points per CTA) per direction by timing; any
+    # choice must give the same sums.
+    w = small
+    V, y, img, info = _run(gpu_lib, w, eps, mode="nufft", autotune=True)
+    assert info["n_nufft_blocks"] >= 1
+    assert info["spread_bin_pix"] in (32, 64, 128) and info["spread_bin_vis"] in (32, 64, 128)
+    assert oracle.rel_l2(V, oracle.sky2vis(w.pix, w.uvw, w.sky)) <= 10 * eps
+    assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 10 * eps
+
+
+@pytest.mark.parametrize("factor", ["pixels", "baselines"])
+def test_factored_plans_match_oracle(gpu_lib, small, factor):
+    # One box spanning one set (each point of the other set spread once): Eq. 8 holds for
+    # this partition too.
+    w = small
+    V, y, img, info = _run(gpu_lib, w, 1e-6, mode="nufft", factor=factor)
+    assert info["n_vis_chunks" if factor == "pixels" else "n_pix_chunks"] == 1 and info["n_nufft_blocks"] > 1
+    assert oracle.rel_l2(V, oracle.sky2vis(w.pix, w.uvw, w.sky)) <= 1e-5
+    assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 1e-5
