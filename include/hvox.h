@@ -346,6 +346,14 @@ hvox_status hvox_es_ft(int32_t w, double beta, const double *xi, int64_t n, doub
 hvox_status hvox_box_dims(const double P[3], const double B[3], double budget_bytes, double sigma,
                           int32_t w, int32_t elem_bytes, double eta[3], double h[3], double *t);
 
+/* The planner's cost model (the GPU counterpart of the paper's regression of stage runtimes,
+ * Sect. 4 and its appendix): seconds per unit of work for plans of this precision
+ * (HVOX_PREC_FP32 or HVOX_PREC_FP64) and form (plain = 1: FP64 kernels). rates[0..7] =
+ * direct pair (one direction), spreading tap through a shared tile, spreading tap straight
+ * into the grid, interpolation tap, FFT cell per log2(cells), grid-pass cell, fixed seconds
+ * per sub-problem and direction, and the shared tile's capacity in cells. */
+hvox_status hvox_cost_model(int32_t precision, int32_t plain, double rates[8]);
+
 /* Algorithm 2: chunk labels of n points (row-major (n, 3), host pointer) for maximal
  * box dimensions h; labels[n] host output, *n_chunks the chunk count. */
 hvox_status hvox_chunk_points(const double *xyz, int64_t n, const double h[3], int64_t *labels,

@@ -105,6 +105,7 @@ def load():
         "hvox_chunk_points": [D, I64, D, PI64, PI64],
         "hvox_plan_dry": [D, I64, D, I64, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(Info)],
         "hvox_direct_synthesize_noalloc": [V, I64, V, I64, V, V, ctypes.c_int, V],
+        "hvox_cost_model": [I32, I32, D],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -173,6 +174,17 @@ def chunk_points(xyz, h):
     _check(load().hvox_chunk_points(_dptr(xyz), len(xyz), _dptr(h),
                                     labels.ctypes.data_as(ctypes.POINTER(ctypes.c_int64)), ctypes.byref(nc)))
     return labels, nc.value
+
+
+COST_MODEL_FIELDS = ("direct_pair", "scatter_smem", "scatter_global", "gather_tap", "fft_cell", "grid_cell",
+                     "block_fixed", "tile_cells")
+
+
+def cost_model(precision="fp32", plain: bool = False) -> dict:
+    """The planner's stage rates (seconds per unit of work) for plans of this precision."""
+    out = (ctypes.c_double * 8)()
+    _check(load().hvox_cost_model(_PREC[precision], 1 if plain else 0, out))
+    return dict(zip(COST_MODEL_FIELDS, list(out)))
 
 
 def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: float = 0.0,

@@ -37,11 +37,14 @@ STAGE_WORK = {
 INFO_KEYS = ("precision", "w", "n_nufft_blocks", "nufft_pix_points", "nufft_vis_points", "spread_cells",
              "nufft_cells", "fft_work", "direct_pairs", "upsampfac")
 
-# Rates of the planner's cost model (seconds per unit of work), FP32 and FP64 sub-problems.
-MODEL = {"f32": {"spread": 1.0 / 4.75e11, "interp": 1.0 / 1.0e12, "fft": 4.1e-13, "grid": 1.3e-12,
-                 "direct": 1.0 / 8.5e11},
-         "f64": {"spread": 1.0 / 1.0e11, "interp": 1.0 / 1.35e11, "fft": 6.8e-12, "grid": 1.8e-12,
-                 "direct": 1.0 / 4.2e11}}
+
+
+def model_rates(precision: str) -> dict:
+    """The planner's rates in the stage units above (from the library, FP32 or FP64 plans)."""
+    from . import cost_model
+    m = cost_model("fp32" if precision == "f32" else "fp64")
+    return {"spread": m["scatter_smem"], "interp": m["gather_tap"], "fft": m["fft_cell"], "grid": m["grid_cell"],
+            "direct": m["direct_pair"]}
 
 
 def _workloads():
@@ -105,7 +108,7 @@ def main(argv=None):
                        "w": info["w"], "upsampfac": info["upsampfac"], "stage_ms": ms,
                        "work": {k: f(info) for k, f in STAGE_WORK.items()}})
     rates = fit(rows)
-    model = MODEL["f64" if rows and rows[0][0]["precision"] == 2 else "f32"]
+    model = model_rates("f64" if rows and rows[0][0]["precision"] == 2 else "f32")
     for r, (info, ms) in zip(report, rows):
         r["model_ms"] = {k: 1e3 * model[k] * f(info) for k, f in STAGE_WORK.items()}
         r["fitted_ms"] = {k: (1e3 * rates[k] * f(info) if rates[k] else None) for k, f in STAGE_WORK.items()}

@@ -755,6 +755,18 @@ hvox_status hvox_plan_info(hvox_plan_t plan, hvox_info *info) {
     });
 }
 
+hvox_status hvox_cost_model(int32_t precision, int32_t plain, double rates[8]) {
+    return guard([&] {
+        if (!rates) fail(HVOX_EINVAL, "hvox_cost_model: NULL rates");
+        if (precision != HVOX_PREC_FP32 && precision != HVOX_PREC_FP64)
+            fail(HVOX_EINVAL, "hvox_cost_model: precision must be HVOX_PREC_FP32 or HVOX_PREC_FP64");
+        const CostModel m = default_cost_model(precision, plain != 0, 0);
+        const double v[8] = {m.direct_pair, m.scatter_smem, m.scatter_global, m.gather_tap,
+                             m.fft_cell,    m.grid_cell,    m.block_fixed,    m.tile_cells};
+        for (int i = 0; i < 8; ++i) rates[i] = v[i];
+    });
+}
+
 hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uvw, int64_t n_vis, double eps,
                           const hvox_opts *opts, hvox_info *info) {
     return guard([&] {
