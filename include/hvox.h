@@ -94,7 +94,9 @@ typedef struct {
     double upsampfac;            /* sigma of both NUFFT stages, in [1.25, 4]; 0 -> chosen by
                                     the planner among 2, 1.5 and 1.25 */
     double chunk_budget_bytes;   /* FFT-grid budget B of one sub-problem (Algorithm 1);
-                                    0 -> chosen by the planner's cost model. A budget that
+                                    0 -> chosen by the planner's cost model. A fixed budget
+                                    also caps the grid bytes of a wave (the sub-problems run
+                                    together; otherwise up to 16 GiB). A budget that
                                     cannot hold a grid of 2w cells per dimension, or that
                                     would cut the job into more than 2^24 candidate
                                     sub-problems, makes hvox_plan fail with HVOX_EINVAL */

@@ -6,6 +6,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <numeric>
+#include <tuple>
 #include <cstdlib>
 #include <cmath>
 #include <cstring>
@@ -167,8 +169,11 @@ void to_host(const double *src, size_t n, std::vector<double> &dst) {
         std::memcpy(dst.data(), src, n * sizeof(double));
 }
 
-// Concurrent execution lanes for NUFFT sub-problems.
-constexpr int kMaxLanes = 4;
+// Concurrent execution lanes for waves of NUFFT sub-problems, and the grid bytes of one
+// wave (a lane holds the grids of its largest wave and a cuFFT work area of about the same
+// size, so a plan's NUFFT memory stays below 2 x 2 x 16 GiB).
+constexpr int kMaxLanes = 2;
+constexpr double kWaveBytes = 16.0 * 1024 * 1024 * 1024;
 
 // Tolerance given to the kernel-width rule: the type-3 transform chains two
 // approximations (spread on n1, interpolate on n2), each held to eps. FP32 plans use eps
@@ -213,31 +218,28 @@ void build_items(const std::vector<DirectRect> &rects, bool owner_is_vis, int vp
 
 // Autotuned bin size: the points a spreading CTA takes (32, 64 or 128) trade the size of
 // its shared tile (the bounding box of their windows) against the tile's set-up and flush
-// per point. Each direction's spreading of the sub-problem with the most points of that
-// set is timed with every candidate (after one untimed launch each) and the fastest kept;
-// the values are ones, so the flush writes every touched cell.
+// per point. Each direction's spreading of the wave holding the sub-problem with the most
+// points of that set is timed with every candidate (after one untimed launch each) and the
+// fastest kept; the values are ones, so the flush writes every touched cell.
 template <typename T> void tune_bins(Plan &p) {
     NufftArgs<T> a = plan_nufft_args<T>(p);
-    size_t bp = 0, bv = 0;
-    for (size_t b = 0; b < p.dblocks.size(); ++b) {
-        if (p.dblocks[b].np > p.dblocks[bp].np) bp = b;
-        if (p.dblocks[b].nv > p.dblocks[bv].nv) bv = b;
+    size_t wp = 0, wv = 0;
+    for (size_t w = 0; w < p.waves.size(); ++w) {
+        if (p.waves[w].max_np > p.waves[wp].max_np) wp = w;
+        if (p.waves[w].max_nv > p.waves[wv].max_nv) wv = w;
     }
     const size_t n = p.src.bytes / sizeof(T);
     std::vector<T> ones(n, T(1));
     check_cuda(cudaMemcpy(p.src.ptr, ones.data(), n * sizeof(T), cudaMemcpyHostToDevice), "autotune values");
     for (int pix = 1; pix >= 0; --pix) {
-        const size_t b = pix ? bp : bv;
-        if ((pix ? p.dblocks[b].np : p.dblocks[b].nv) == 0) continue;
-        const Lane &l = *p.lanes[p.block_lane[b]];
-        a.G1 = l.g1.as<typename CplxOf<T>::type>();
-        a.G2 = l.g2.as<typename CplxOf<T>::type>();
-        a.fft = p.block_fft[b];
+        const Wave &w = p.waves[pix ? wp : wv];
+        if ((pix ? w.max_np : w.max_nv) == 0) continue;
+        Lane &l = *p.lanes[w.lane];
         int best = 128;
         float best_ms = INFINITY;
         for (int ppc : {128, 64, 32}) {
-            time_spread<T>(p.dblocks[b], a, pix != 0, p.src.ptr, ppc, p.stream);
-            const float ms = time_spread<T>(p.dblocks[b], a, pix != 0, p.src.ptr, ppc, p.stream);
+            time_spread<T>(w, a, l.g1.ptr, l.g2.ptr, pix != 0, p.src.ptr, ppc, p.stream);
+            const float ms = time_spread<T>(w, a, l.g1.ptr, l.g2.ptr, pix != 0, p.src.ptr, ppc, p.stream);
             if (ms < best_ms * 0.97f) {  // a smaller bin must win clearly
                 best_ms = ms;
                 best = ppc;
@@ -277,8 +279,9 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     in.eps_es = p.eps_es;
     in.factor = p.factor;
     {
-        // Up to kMaxLanes lanes each hold the grids of their largest sub-problem and a cuFFT
-        // work area of about the same size: keep that within a third of the free memory.
+        // Up to kMaxLanes lanes each hold the grids of a wave (at least one sub-problem's)
+        // and a cuFFT work area of about the same size: keep that within a third of the
+        // free memory.
         size_t free_b = 0, total_b = 0;
         check_cuda(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
         in.max_budget = (double)free_b / (3.0 * 2.0 * kMaxLanes);
@@ -385,17 +388,78 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             upload(p.inv_psi, ipsi.data(), ipsi.size() * 8, s);
             upload(p.cheb, cheb.data(), cheb.size() * 8, s);
         }
-        // Execution lanes: sub-problems assigned longest-first to the least-loaded lane.
-        int n_lanes = (int)std::min<size_t>(kMaxLanes, part.blocks.size());
+        // Waves: sub-problems of one grid shape (identical n1 and n2: their FFTs batch)
+        // are kept together, shapes in order of total cost, and packed into waves whose
+        // grids fit the wave budget; the plain form runs one sub-problem per wave.
+        // Waves go longest-first to the least-loaded of (up to) two lanes.
+        const double elem_b = 2.0 * (double)re;
+        auto m1_of = [](const NufftBlock &b) { return b.n1[0] * b.n1[1] * b.n1[2]; };
+        auto m2_of = [](const NufftBlock &b) { return b.n2[0] * b.n2[1] * b.n2[2]; };
+        auto shape_key = [](const NufftBlock &b) {
+            return std::make_tuple(b.n2[0], b.n2[1], b.n2[2], b.n1[0], b.n1[1], b.n1[2]);
+        };
+        std::map<decltype(shape_key(part.blocks[0])), std::vector<size_t>> buckets;
+        for (size_t i = 0; i < part.blocks.size(); ++i) buckets[shape_key(part.blocks[i])].push_back(i);
+        std::vector<std::pair<double, std::vector<size_t>>> shapes;
+        for (auto &kv : buckets) {
+            double c = 0;
+            for (size_t i : kv.second) c += part.blocks[i].cost;
+            shapes.push_back({c, kv.second});
+        }
+        std::stable_sort(shapes.begin(), shapes.end(), [](const auto &x, const auto &y) { return x.first > y.first; });
+        size_t free_b = 0, total_b = 0;
+        check_cuda(cudaMemGetInfo(&free_b, &total_b), "cudaMemGetInfo");
+        // A caller-fixed chunk budget also caps a wave's grids (the plan's memory then stays
+        // within the budget per lane, as with one sub-problem per lane).
+        double wave_cap = p.plain ? 0.0 : std::min((double)free_b / 12.0, kWaveBytes);
+        if (p.budget_opt > 0 && !p.plain) wave_cap = std::min(wave_cap, p.budget_opt);
+        if (const char *v = std::getenv("HVOX_WAVE_BYTES")) wave_cap = std::atof(v);
+        std::vector<size_t> order;              // blocks in wave order
+        std::vector<std::pair<int, int>> wb;    // (first, count) of each wave in `order`
+        double wave_bytes = 0;
+        for (auto &sh : shapes)
+            for (size_t i : sh.second) {
+                const double bytes = elem_b * (double)(m1_of(part.blocks[i]) + m2_of(part.blocks[i]));
+                if (wb.empty() || wave_bytes + bytes > wave_cap) {
+                    wb.push_back({(int)order.size(), 0});
+                    wave_bytes = 0;
+                }
+                order.push_back(i);
+                wb.back().second++;
+                wave_bytes += bytes;
+            }
+        int n_lanes = (int)std::min<size_t>(2, wb.size());
         if (const char *v = std::getenv("HVOX_NUFFT_LANES")) n_lanes = std::max(1, std::min(n_lanes, std::atoi(v)));
         std::vector<double> load(n_lanes, 0.0);
         std::vector<int64_t> lane_m1(n_lanes, 0), lane_m2(n_lanes, 0);
-        for (auto &b : part.blocks) {
-            int l = (int)(std::min_element(load.begin(), load.end()) - load.begin());
-            load[l] += b.cost;
-            p.block_lane.push_back(l);
-            lane_m1[l] = std::max<int64_t>(lane_m1[l], b.n1[0] * b.n1[1] * b.n1[2]);
-            lane_m2[l] = std::max<int64_t>(lane_m2[l], b.n2[0] * b.n2[1] * b.n2[2]);
+        for (auto &f : wb) {
+            Wave w;
+            w.b0 = f.first;
+            w.nb = f.second;
+            for (int k = 0; k < w.nb; ++k) {
+                const NufftBlock &bk = part.blocks[order[w.b0 + k]];
+                w.g1_cells += m1_of(bk);
+                w.g2_cells += m2_of(bk);
+                w.max_np = std::max<int64_t>(w.max_np, bk.p1 - bk.p0);
+                w.max_nv = std::max<int64_t>(w.max_nv, bk.v1 - bk.v0);
+                w.max_rows1 = std::max<int64_t>(w.max_rows1, bk.n1[1] * bk.n1[2]);
+                w.max_rows2 = std::max<int64_t>(w.max_rows2, bk.n2[1] * bk.n2[2]);
+                w.cost += bk.cost;
+            }
+            p.waves.push_back(w);
+        }
+        {
+            std::vector<size_t> by_cost(p.waves.size());
+            std::iota(by_cost.begin(), by_cost.end(), 0);
+            std::stable_sort(by_cost.begin(), by_cost.end(),
+                             [&](size_t x, size_t y) { return p.waves[x].cost > p.waves[y].cost; });
+            for (size_t wi : by_cost) {
+                Wave &w = p.waves[wi];
+                w.lane = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+                load[w.lane] += w.cost;
+                lane_m1[w.lane] = std::max<int64_t>(lane_m1[w.lane], w.g1_cells);
+                lane_m2[w.lane] = std::max<int64_t>(lane_m2[w.lane], w.g2_cells);
+            }
         }
         check_cuda(cudaEventCreateWithFlags(&p.fork_event, cudaEventDisableTiming), "cudaEventCreate");
         const cufftType type = p.prec == 1 ? CUFFT_C2C : CUFFT_Z2Z;
@@ -407,8 +471,10 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             lane->g2.alloc((size_t)lane_m2[l] * 2 * re);
             p.lanes.push_back(std::move(lane));
         }
-        // cuFFT plans per lane and grid shape, one work area per lane. HVOX_FFT_PRUNE=0
-        // selects the full 3-D plans instead of the pruned pair.
+        // Descriptors in wave order: each sub-problem's n1 grid back to back in its lane's g1,
+        // its FFT grid in the interleaved layout of its shape's batch in the lane's g2.
+        // cuFFT plans per lane, shape and batch size, one work area per lane. HVOX_FFT_PRUNE=0
+        // selects full 3-D plans instead of the pruned pair.
         bool prune = true;
         if (const char *v = std::getenv("HVOX_FFT_PRUNE")) prune = std::atoi(v) != 0;
         std::vector<size_t> max_ws(n_lanes, 0);
@@ -420,27 +486,81 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             check_cufft(cufftMakePlanMany64(h, rank, n, emb, stride, dist, emb, stride, dist, type, batch, &ws),
                         "cufftMakePlanMany64");
         };
-        for (size_t i = 0; i < part.blocks.size(); ++i) {
-            const auto &b = part.blocks[i];
-            Lane &lane = *p.lanes[p.block_lane[i]];
-            const int64_t half = b.n1[2] / 2;
-            auto key = std::make_tuple(b.n2[0], b.n2[1], b.n2[2], prune ? half : (int64_t)-1);
-            if (!lane.fft.count(key)) {
-                FftPlans &f = lane.fft[key];
-                size_t ws = 0;
-                if (prune) {
-                    long long nxy[2] = {b.n2[1], b.n2[0]};
-                    make(f.xy, 2, nxy, nullptr, 1, b.n2[0] * b.n2[1], half, ws);
-                    max_ws[p.block_lane[i]] = std::max(max_ws[p.block_lane[i]], ws);
-                    long long nz[1] = {b.n2[2]}, emb[1] = {b.n2[2]};
-                    make(f.z, 1, nz, emb, b.n2[0] * b.n2[1], 1, b.n2[0] * b.n2[1], ws);
-                } else {
-                    long long n3[3] = {b.n2[2], b.n2[1], b.n2[0]};
-                    make(f.full, 3, n3, nullptr, 1, 0, 1, ws);
+        auto split = [](double x, float &h, float &l) {
+            h = (float)x;
+            l = (float)(x - (double)h);
+        };
+        p.dblocks.resize(order.size());
+        for (Wave &w : p.waves) {
+            Lane &lane = *p.lanes[w.lane];
+            char *g1 = static_cast<char *>(lane.g1.ptr), *g2 = static_cast<char *>(lane.g2.ptr);
+            for (int k = 0; k < w.nb;) {
+                // one batch: the run of sub-problems of this shape
+                const NufftBlock &first = part.blocks[order[w.b0 + k]];
+                int K = 1;
+                while (k + K < w.nb && shape_key(part.blocks[order[w.b0 + k + K]]) == shape_key(first)) ++K;
+                FftBatch fb;
+                fb.g2 = g2;
+                for (int d = 0; d < 3; ++d) fb.n2[d] = first.n2[d];
+                fb.half = first.n1[2] / 2;
+                fb.K = K;
+                const int64_t plane = first.n2[0] * first.n2[1];
+                auto key = std::make_tuple(fb.n2[0], fb.n2[1], fb.n2[2], prune ? fb.half : (int64_t)-1, (int64_t)K);
+                if (!lane.fft.count(key)) {
+                    FftPlans &f = lane.fft[key];
+                    size_t ws = 0;
+                    if (prune) {
+                        long long nxy[2] = {fb.n2[1], fb.n2[0]};
+                        make(f.xy, 2, nxy, nullptr, 1, plane, fb.half * K, ws);
+                        max_ws[w.lane] = std::max(max_ws[w.lane], ws);
+                        long long nz[1] = {fb.n2[2]}, emb[1] = {fb.n2[2]};
+                        make(f.z, 1, nz, emb, plane * K, 1, plane * K, ws);
+                    } else {
+                        long long n3[3] = {fb.n2[2], fb.n2[1], fb.n2[0]};
+                        long long e3[3] = {fb.n2[2], fb.n2[1] * K, fb.n2[0]};
+                        make(f.full, 3, n3, e3, 1, plane, K, ws);
+                    }
+                    max_ws[w.lane] = std::max(max_ws[w.lane], ws);
                 }
-                max_ws[p.block_lane[i]] = std::max(max_ws[p.block_lane[i]], ws);
+                fb.plans = lane.fft[key];
+                w.ffts.push_back(fb);
+                for (int g = 0; g < K; ++g, ++k) {
+                    const NufftBlock &bk = part.blocks[order[w.b0 + k]];
+                    NufftDev d;
+                    std::memset(&d, 0, sizeof(d));
+                    d.p0 = bk.p0;
+                    d.np = bk.p1 - bk.p0;
+                    d.v0 = bk.v0;
+                    d.nv = bk.v1 - bk.v0;
+                    for (int q = 0; q < 3; ++q) {
+                        d.n1[q] = (int32_t)bk.n1[q];
+                        d.n2[q] = (int32_t)bk.n2[q];
+                        d.C[q] = bk.C[q];
+                        d.D[q] = bk.D[q];
+                        d.a[q] = bk.a[q];
+                        d.n2a[q] = bk.a[q] > 0 ? (double)bk.n2[q] / bk.a[q] : 0.0;
+                        d.tpa64[q] = bk.a[q] > 0 ? 2.0 * M_PI / bk.a[q] : 0.0;
+                        split(bk.C[q], d.Ch[q], d.Cl[q]);
+                        split(bk.D[q], d.Dh[q], d.Dl[q]);
+                        split(bk.a[q], d.ah[q], d.al[q]);
+                        split(d.n2a[q], d.n2ah[q], d.n2al[q]);
+                        d.tpa[q] = (float)d.tpa64[q];
+                    }
+                    d.psi_off = bk.psi_off;
+                    d.err = p.err.as<int>();
+                    d.g1 = g1;
+                    g1 += (size_t)m1_of(bk) * 2 * re;
+                    d.g2 = g2 + (size_t)g * plane * 2 * re;
+                    d.zs2 = plane * K;
+                    if (fault_hit("window"))
+                        for (int q = 0; q < 3; ++q) {
+                            d.a[q] *= 4.0;
+                            split(d.a[q], d.ah[q], d.al[q]);
+                        }
+                    p.dblocks[w.b0 + k] = d;
+                }
+                g2 += (size_t)K * first.n2[0] * first.n2[1] * first.n2[2] * 2 * re;
             }
-            p.block_fft.push_back(lane.fft[key]);
         }
         for (int l = 0; l < n_lanes; ++l) {
             Lane &lane = *p.lanes[l];
@@ -449,40 +569,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                 for (cufftHandle h : {kv.second.full, kv.second.xy, kv.second.z})
                     if (h) check_cufft(cufftSetWorkArea(h, lane.work.ptr), "cufftSetWorkArea");
         }
-        auto split = [](double x, float &h, float &l) {
-            h = (float)x;
-            l = (float)(x - (double)h);
-        };
-        for (auto &b : part.blocks) {
-            NufftDev d;
-            std::memset(&d, 0, sizeof(d));
-            d.p0 = b.p0;
-            d.np = b.p1 - b.p0;
-            d.v0 = b.v0;
-            d.nv = b.v1 - b.v0;
-            for (int k = 0; k < 3; ++k) {
-                d.n1[k] = (int32_t)b.n1[k];
-                d.n2[k] = (int32_t)b.n2[k];
-                d.C[k] = b.C[k];
-                d.D[k] = b.D[k];
-                d.a[k] = b.a[k];
-                d.n2a[k] = b.a[k] > 0 ? (double)b.n2[k] / b.a[k] : 0.0;
-                d.tpa64[k] = b.a[k] > 0 ? 2.0 * M_PI / b.a[k] : 0.0;
-                split(b.C[k], d.Ch[k], d.Cl[k]);
-                split(b.D[k], d.Dh[k], d.Dl[k]);
-                split(b.a[k], d.ah[k], d.al[k]);
-                split(d.n2a[k], d.n2ah[k], d.n2al[k]);
-                d.tpa[k] = (float)d.tpa64[k];
-            }
-            d.psi_off = b.psi_off;
-            d.err = p.err.as<int>();
-            if (fault_hit("window"))
-                for (int k = 0; k < 3; ++k) {
-                    d.a[k] *= 4.0;
-                    split(d.a[k], d.ah[k], d.al[k]);
-                }
-            p.dblocks.push_back(d);
-        }
+        upload(p.ddescs, p.dblocks.data(), p.dblocks.size() * sizeof(NufftDev), s);
     }
 
     // Per-call buffers.
@@ -797,11 +884,13 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         p.sigma = p.part.sigma;
         p.es = p.part.es;
         // Estimate of what hvox_plan would allocate: coordinates and permutations, the
-        // source and accumulator, and per lane the grids and a cuFFT work area of about
-        // the largest sub-problem's size.
+        // source and accumulator, and per lane the grids of a wave and a cuFFT work area of
+        // about the same size.
         const double re = p.prec == 1 ? 4.0 : 8.0;
         const double lanes = (double)std::min<size_t>(kMaxLanes, p.part.blocks.size());
-        p.workspace_bytes = (double)(n_pix + n_vis) * 60.0 + 2.0 * lanes * p.part.max_grid_bytes +
+        const double all_grids = 2.0 * re * (p.part.spread_cells + p.part.nufft_cells);
+        const double wave = std::max(p.part.max_grid_bytes, std::min(all_grids, kWaveBytes));
+        p.workspace_bytes = (double)(n_pix + n_vis) * 60.0 + 2.0 * lanes * wave +
                             4.0 * re * (double)std::max(n_pix, 2 * n_vis);
         p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
         fill_info(p, info);
@@ -839,7 +928,8 @@ double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_
     double bufs = 2.0 * std::max((double)n_pix * re, (double)n_vis * 2.0 * re);
     double io = 2.0 * nt * std::max((double)n_pix * re, (double)n_vis * 2.0 * re);
     // Jobs the planner keeps as direct sums without a search own no NUFFT grids; others
-    // own at most kMaxLanes lanes of grids and cuFFT work areas, each within the budget.
+    // own at most kMaxLanes lanes of wave grids and cuFFT work areas, each within the
+    // larger of the wave bytes and the chunk budget.
     const CostModel m = default_cost_model(prec, plain || (prec == 2 && eps > 0 && eps < kDoubleFloatMinEps), 0);
     const double search = (opts && opts->search_threshold > 0) ? opts->search_threshold : 0.01;
     const bool auto_plan = !(opts && (opts->mode != HVOX_MODE_AUTO || opts->direct_threshold > 0 ||
@@ -847,7 +937,8 @@ double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_
     const bool direct_only = eps == 0.0 || (opts && opts->mode == HVOX_MODE_DIRECT) ||
                              (auto_plan && 2.0 * m.direct_pair * (double)n_pix * (double)n_vis < search);
     const double budget = (opts && opts->chunk_budget_bytes > 0) ? opts->chunk_budget_bytes : 8.0 * 1024 * 1024 * 1024;
-    const double grids = direct_only ? 0.0 : 2.0 * kMaxLanes * budget;
+    const double wave = (opts && opts->chunk_budget_bytes > 0) ? budget : std::max(budget, kWaveBytes);
+    const double grids = direct_only ? 0.0 : 2.0 * kMaxLanes * wave;
     return geom + bufs + io + grids;
 }
 

@@ -1,6 +1,8 @@
-// Executor: one transform = permute in -> direct rectangles -> NUFFT sub-problems ->
-// permute out, all enqueued on the plan's stream (Fig. 6 flow: inputs to chunk order,
-// sub-transforms, row sums, outputs back to the caller's order).
+// Executor: one transform = permute in -> direct rectangles -> waves of NUFFT sub-problems
+// -> permute out, all enqueued on the plan's stream (Fig. 6 flow: inputs to chunk order,
+// sub-transforms, row sums, outputs back to the caller's order). The sub-problems of a
+// wave share one launch per stage and one batched cuFFT set per grid shape (the parallel
+// sub-transforms of Sect. 3); waves on different lanes run concurrently.
 //
 // The part between the permutations touches plan-owned buffers only, so after one eager
 // call it is captured once per direction into a CUDA graph (the lanes forked from and
@@ -83,6 +85,7 @@ template <typename T> NufftArgs<T> nufft_args(const Plan &p) {
     a.w = p.es.w;
     a.beta = p.es.beta;
     a.isign = p.isign;
+    a.descs = p.ddescs.as<NufftDev>();
     a.ipsi = p.inv_psi.as<T>();
     a.pix_hi = p.pix_hi.as<float4>();
     a.pix_lo = p.pix_lo.as<float4>();
@@ -117,17 +120,25 @@ void join_lanes(Plan &p, cudaStream_t s) {
     }
 }
 
-template <typename T> void set_lane(NufftArgs<T> &a, const Plan &p, size_t b) {
-    const Lane &l = *p.lanes[p.block_lane[b]];
-    a.G1 = l.g1.as<typename CplxOf<T>::type>();
-    a.G2 = l.g2.as<typename CplxOf<T>::type>();
-    a.fft = p.block_fft[b];
+// Stream of a wave: its lane's, or s itself when profiling serially (the lane's grids and
+// cuFFT plans are still used, one wave after another).
+cudaStream_t wave_stream(const Plan &p, const Wave &w, cudaStream_t s) {
+    return p.serial ? s : p.lanes[w.lane]->stream;
 }
 
-// Stream of sub-problem b: its lane's, or s itself when profiling serially (the lane's
-// grids and cuFFT plans are still used, one sub-problem after another).
-cudaStream_t block_stream(const Plan &p, size_t b, cudaStream_t s) {
-    return p.serial ? s : p.lanes[p.block_lane[b]]->stream;
+// Every wave of NUFFT sub-problems of one direction, each on its lane.
+template <typename T, typename In, typename Out>
+void run_waves(Plan &p, int dir, const In *src, Out *acc, cudaStream_t s, Profiler &prof) {
+    const NufftArgs<T> a = nufft_args<T>(p);
+    for (const Wave &w : p.waves) {
+        Lane &l = *p.lanes[w.lane];
+        if (dir == 0)
+            nufft_wave_s2v<T>(w, a, l.g1.ptr, l.g2.ptr, reinterpret_cast<const T *>(src),
+                              reinterpret_cast<typename CplxOf<T>::type *>(acc), wave_stream(p, w, s), prof);
+        else
+            nufft_wave_v2s<T>(w, a, l.g1.ptr, l.g2.ptr, reinterpret_cast<const typename CplxOf<T>::type *>(src),
+                              reinterpret_cast<T *>(acc), wave_stream(p, w, s), prof);
+    }
 }
 
 // sky -> vis between the permutations: src (chunk-ordered c_n) -> acc (chunk-ordered V).
@@ -155,22 +166,11 @@ void body_s2v(Plan &p, cudaStream_t s, Profiler &prof) {
                                  p.acc.as<double2>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
         prof.end(HVOX_STAGE_DIRECT, 1, s);
     }
-    if (!p.dblocks.empty()) {
-        if (p.prec == 1) {
-            NufftArgs<float> a = nufft_args<float>(p);
-            for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                set_lane(a, p, b);
-                nufft_block_s2v<float>(p.dblocks[b], a, p.src.as<float>(), p.acc.as<float2>(),
-                                       block_stream(p, b, s), prof);
-            }
-        } else {
-            NufftArgs<double> a = nufft_args<double>(p);
-            for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                set_lane(a, p, b);
-                nufft_block_s2v<double>(p.dblocks[b], a, p.src.as<double>(), p.acc.as<double2>(),
-                                        block_stream(p, b, s), prof);
-            }
-        }
+    if (!p.waves.empty()) {
+        if (p.prec == 1)
+            run_waves<float>(p, 0, p.src.as<float>(), p.acc.as<float2>(), s, prof);
+        else
+            run_waves<double>(p, 0, p.src.as<double>(), p.acc.as<double2>(), s, prof);
     }
     join_lanes(p, s);
 }
@@ -200,22 +200,11 @@ void body_v2s(Plan &p, cudaStream_t s, Profiler &prof) {
                                  p.acc.as<double>(), p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
         prof.end(HVOX_STAGE_DIRECT, 1, s);
     }
-    if (!p.dblocks.empty()) {
-        if (p.prec == 1) {
-            NufftArgs<float> a = nufft_args<float>(p);
-            for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                set_lane(a, p, b);
-                nufft_block_v2s<float>(p.dblocks[b], a, p.src.as<float2>(), p.acc.as<float>(),
-                                       block_stream(p, b, s), prof);
-            }
-        } else {
-            NufftArgs<double> a = nufft_args<double>(p);
-            for (size_t b = 0; b < p.dblocks.size(); ++b) {
-                set_lane(a, p, b);
-                nufft_block_v2s<double>(p.dblocks[b], a, p.src.as<double2>(), p.acc.as<double>(),
-                                        block_stream(p, b, s), prof);
-            }
-        }
+    if (!p.waves.empty()) {
+        if (p.prec == 1)
+            run_waves<float>(p, 1, p.src.as<float2>(), p.acc.as<float>(), s, prof);
+        else
+            run_waves<double>(p, 1, p.src.as<double2>(), p.acc.as<double>(), s, prof);
     }
     join_lanes(p, s);
 }
@@ -229,7 +218,7 @@ void body(Plan &p, int dir, cudaStream_t s, Profiler &prof) {
 
 bool graphs_wanted(const Plan &p) {
     if (p.plain || p.serial || p.graph_state < 0 || p.graphs_opt < 0) return false;
-    return p.graphs_opt > 0 || !p.dblocks.empty();
+    return p.graphs_opt > 0 || !p.waves.empty();
 }
 
 // Gives up on graphs for this plan after a failed capture: ends the capture, drops the

@@ -179,19 +179,48 @@ struct NufftDev {
     float Ch[3], Cl[3], Dh[3], Dl[3], ah[3], al[3], n2ah[3], n2al[3], tpa[3];
     int64_t psi_off;
     int *err;         // the plan's device error word (kDevErr* bits)
+    void *g1;         // this sub-problem's spread grid (n1 cells, x fastest, contiguous)
+    void *g2;         // its FFT grid: cell (x, y, z) at g2 + z * zs2 + y * n2[0] + x
+    int64_t zs2;      // z-plane stride of g2 in cells (the z planes of a batch are interleaved)
 };
 
 template <typename T> struct CplxOf;
 template <> struct CplxOf<float> { using type = float2; };
 template <> struct CplxOf<double> { using type = double2; };
 
-// cuFFT plans of one FFT-grid shape. Pruned form (xy and z set): the 3-D transform as a 2-D
-// transform of the n1 band's z planes (two slabs of n1z/2 planes, at the start and the end
-// of the grid) and a 1-D transform along z of every column; the other z planes hold only
-// zeros before the transform (sky -> vis) or are not read after it (vis -> sky), so their
-// 2-D transforms are skipped. Full form (full set): one 3-D plan.
+// cuFFT plans of one FFT-grid shape and batch. Pruned form (xy and z set): the 3-D
+// transform as 2-D transforms of the n1 band's z planes (two slabs of n1z/2 planes, at the
+// start and the end of the grid) and 1-D transforms along z of every column; the other z
+// planes hold only zeros before the transform (sky -> vis) or are not read after it (vis ->
+// sky), so their 2-D transforms are skipped. Full form (full set): one 3-D plan per grid.
 struct FftPlans {
     cufftHandle full = 0, xy = 0, z = 0;
+};
+
+// The batched transforms of K sub-problems of one grid shape inside a wave: their FFT
+// grids interleave z planes (plane z of grid g at g2 + (z K + g) * n2x n2y), so that each
+// band slab of all K grids is one contiguous run of planes (one batched 2-D call) and
+// every column of every grid is one strided 1-D transform along z (one batched call).
+struct FftBatch {
+    void *g2 = nullptr;       // plane 0 of grid 0
+    int64_t n2[3] = {0, 0, 0};
+    int64_t half = 0;         // n1z / 2
+    int64_t K = 1;
+    FftPlans plans;
+};
+
+// A wave: sub-problems [b0, b0 + nb) of the plan's descriptor array, run together: one
+// clearing, spreading, deconvolution and interpolation launch each (a 2-D launch grid over
+// (tile, sub-problem)) and one batched FFT set per grid shape. Its grids live in the
+// buffers of its lane (n1 grids back to back, then the n2 grids).
+struct Wave {
+    int b0 = 0, nb = 0;
+    int lane = 0;
+    int64_t g1_cells = 0, g2_cells = 0;      // grid cells of the wave (each set contiguous)
+    int64_t max_np = 0, max_nv = 0;          // most pixels / baselines of one sub-problem
+    int64_t max_rows1 = 0, max_rows2 = 0;    // most n1 rows (n1y n1z) / n2 rows (n2y n2z)
+    std::vector<FftBatch> ffts;
+    double cost = 0.0;
 };
 
 // Plan-wide arguments of the NUFFT launchers.
@@ -199,9 +228,8 @@ template <typename T> struct NufftArgs {
     int w = 0;
     double beta = 0.0;
     int isign = -1;
-    typename CplxOf<T>::type *G1 = nullptr, *G2 = nullptr;
+    const NufftDev *descs = nullptr;  // device array of the plan's sub-problem descriptors
     const T *ipsi = nullptr;
-    FftPlans fft;
     const float4 *pix_hi = nullptr, *pix_lo = nullptr, *vis_hi = nullptr, *vis_lo = nullptr;
     const double *pix_soa = nullptr, *vis_soa = nullptr;
     int64_t n_pix = 0, n_vis = 0;
@@ -218,13 +246,13 @@ struct StageHook {
     virtual ~StageHook() = default;
 };
 
-// An execution lane for NUFFT sub-problems: its own stream, grids, cuFFT plans and
-// cuFFT work area, so that sub-problems on different lanes run concurrently.
+// An execution lane for waves of NUFFT sub-problems: its own stream, grid buffers, cuFFT
+// plans and cuFFT work area, so that waves on different lanes run concurrently.
 struct Lane {
     cudaStream_t stream = nullptr;
     cudaEvent_t done = nullptr;
     DevBuf g1, g2, work;
-    std::map<std::tuple<int64_t, int64_t, int64_t, int64_t>, FftPlans> fft;
+    std::map<std::tuple<int64_t, int64_t, int64_t, int64_t, int64_t>, FftPlans> fft;  // (n2, half, K)
     ~Lane();
 };
 
@@ -303,9 +331,9 @@ struct Plan {
     double cheb_inv_tmax2 = 0.0;
     std::vector<std::unique_ptr<Lane>> lanes;  // NUFFT execution lanes
     cudaEvent_t fork_event = nullptr;   // main stream -> lanes
-    std::vector<NufftDev> dblocks;      // block descriptors (launch order)
-    std::vector<int> block_lane;        // lane of each block
-    std::vector<FftPlans> block_fft;    // FFT plans of each block (its lane's plans for its shape)
+    std::vector<NufftDev> dblocks;      // block descriptors (wave order)
+    DevBuf ddescs;                      // the same descriptors on the device
+    std::vector<Wave> waves;            // waves of blocks (launch order)
     DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
     DevBuf err;                         // int: device error word (kDevErr* bits), read by hvox_sync
 
@@ -352,18 +380,20 @@ void launch_direct_v2s_df(const WorkItem *items, int64_t n, int *counter, const 
 void launch_direct_v2s_f64(const WorkItem *items, int64_t n, int *counter, const double *pxyz, int64_t np, const double *vxyz,
                            int64_t nv, const double2 *V, double *acc, int isign, int vpt, cudaStream_t s);
 
-// NUFFT sub-problems (k_nufft.cu).
+// NUFFT sub-problems, one wave at a time (k_nufft.cu). g1 / g2: the lane's grid buffers.
 template <typename T>
-void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, typename CplxOf<T>::type *acc,
-                     cudaStream_t s, StageHook &hook);
+void nufft_wave_s2v(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, const T *c,
+                    typename CplxOf<T>::type *acc, cudaStream_t s, StageHook &hook);
 template <typename T>
-void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const typename CplxOf<T>::type *V, T *acc,
-                     cudaStream_t s, StageHook &hook);
+void nufft_wave_v2s(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, const typename CplxOf<T>::type *V,
+                    T *acc, cudaStream_t s, StageHook &hook);
 
-// Device time (ms) of one spreading launch of block b with ppc points per CTA: pixels onto
-// a.G1 (pix) or baselines onto a.G2, values c / V (the grid is cleared first, untimed).
+// Device time (ms) of the spreading launch of wave w with ppc points per CTA: pixels onto
+// the n1 grids (pix) or baselines onto the n2 grids, values c / V (the grids are cleared
+// first, untimed).
 template <typename T>
-float time_spread(const NufftDev &b, const NufftArgs<T> &a, bool pix, const void *values, int ppc, cudaStream_t s);
+float time_spread(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, bool pix, const void *values, int ppc,
+                  cudaStream_t s);
 
 // Permutations between the caller's order and chunk order (k_misc.cu).
 void launch_s2v_in(int prec, const void *I, const int32_t *perm, const double *w, int64_t n, void *src, cudaStream_t s);

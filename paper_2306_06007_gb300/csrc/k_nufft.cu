@@ -281,7 +281,18 @@ template <typename T, int W> struct SpreadShared {
 };
 
 template <typename T, int W> __host__ __device__ constexpr int tile_bytes() {
-    return ((kSmemPerCta - (int)sizeof(SpreadShared<T, W>)) / (2 * (int)sizeof(T) * 32)) * (2 * (int)sizeof(T) * 32);
+    return ((kSmemPerCta - (int)sizeof(SpreadShared<T, W>) - (int)sizeof(NufftDev)) / (2 * (int)sizeof(T) * 32)) *
+           (2 * (int)sizeof(T) * 32);
+}
+
+// The CTA's sub-problem descriptor, copied from the plan's device array into shared memory
+// (every thread reads its fields; a shared broadcast instead of a global load each time).
+__device__ __forceinline__ void load_desc(NufftDev &dst, const NufftDev *__restrict__ src) {
+    static_assert(sizeof(NufftDev) % 4 == 0, "descriptor copied as 32-bit words");
+    const int *from = reinterpret_cast<const int *>(src);
+    int *to = reinterpret_cast<int *>(&dst);
+    for (int i = threadIdx.x; i < (int)(sizeof(NufftDev) / 4); i += blockDim.x) to[i] = from[i];
+    __syncthreads();
 }
 
 // Plane stride of a tile with tx * ty cells per plane: the next value = 8 (mod 32).
@@ -289,7 +300,7 @@ __device__ __forceinline__ int64_t tile_plane_stride(int64_t cells) { return cel
 
 template <typename T, int W, bool PERIODIC>
 __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
-                                           const int ng[3], int ppc, cplx_t<T> *__restrict__ G) {
+                                           const int ng[3], int64_t zs, int ppc, cplx_t<T> *__restrict__ G) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ SpreadShared<T, W> sh;
     constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));
@@ -389,7 +400,7 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
                 const int64_t gz = PERIODIC ? wrap(pz0 + jz, ng[2]) : pz0 + jz;
                 for (int jy = 0; jy < W; ++jy) {
                     const int64_t gy = PERIODIC ? wrap(py0 + jy, ng[1]) : py0 + jy;
-                    cplx_t<T> *row = G + (gz * ng[1] + gy) * ng[0];
+                    cplx_t<T> *row = G + gz * zs + gy * ng[0];
 #pragma unroll
                     for (int t = 0; t < kXT; ++t)
                         if (on[t]) grid_add(row + cx[t], zr[t] * wy[jy], zi[t] * wy[jy]);
@@ -408,7 +419,7 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
             gy = wrap(gy, ng[1]);
             gz = wrap(gz, ng[2]);
         }
-        cplx_t<T> *grow = G + ((int64_t)gz * ng[1] + gy) * ng[0];
+        cplx_t<T> *grow = G + (int64_t)gz * zs + (int64_t)gy * ng[0];
         const int t0 = z * ps + y * txi;
         for (int x = lane; x < txi; x += 32) {
             const T re = tre[t0 + x], im = tim[t0 + x];
@@ -419,15 +430,18 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     }
 }
 
-// sky -> vis step 1: pixels (values c, prephase P) onto the n1 grid. A CTA takes ppc <= 128
-// consecutive points (the bin; the plan may tune it): thread t < ppc takes point
-// blockIdx.x * ppc + t.
+// sky -> vis step 1: pixels (values c, prephase P) onto the n1 grids of a wave. blockIdx.y
+// picks the sub-problem (descs[b0 + blockIdx.y]); a CTA takes ppc <= 128 consecutive points
+// of it (the bin; the plan may tune it): thread t < ppc takes point blockIdx.x * ppc + t.
 template <typename T, int W>
-__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread_pix_kernel(NufftDev b, const float4 *__restrict__ rh,
-                                                                     const float4 *__restrict__ rl,
-                                                                     const double *__restrict__ soa, int64_t n_all,
-                                                                     const T *__restrict__ c, cplx_t<T> *__restrict__ G1,
-                                                                     T beta, int isign, int ppc) {
+__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
+    spread_pix_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ rh,
+                      const float4 *__restrict__ rl, const double *__restrict__ soa, int64_t n_all,
+                      const T *__restrict__ c, T beta, int isign, int ppc) {
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
+    if ((int64_t)blockIdx.x * ppc >= b.np) return;  // this sub-problem has fewer bins (uniform)
     const int64_t i = blockIdx.x * (int64_t)ppc + threadIdx.x;
     const bool act = threadIdx.x < ppc && i < b.np;
     int i0[3] = {0, 0, 0};
@@ -440,17 +454,22 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread
         vi = cv * pim;
     }
     const int ng[3] = {b.n1[0], b.n1[1], b.n1[2]};
-    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, ng, ppc, G1);
+    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, ng, (int64_t)ng[0] * ng[1], ppc,
+                            static_cast<cplx_t<T> *>(b.g1));
 }
 
-// vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2 grid.
+// vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2
+// grids of a wave (layout as for pixels).
 template <typename T, int W>
-__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread_vis_kernel(NufftDev b, const float4 *__restrict__ vh,
-                                                                     const float4 *__restrict__ vl,
-                                                                     const double *__restrict__ soa, int64_t n_all,
-                                                                     const cplx_t<T> *__restrict__ V,
-                                                                     const T *__restrict__ cc, int deg, T inv_tmax2,
-                                                                     cplx_t<T> *__restrict__ G2, T beta, int isign, int ppc) {
+__global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
+    spread_vis_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ vh,
+                      const float4 *__restrict__ vl, const double *__restrict__ soa, int64_t n_all,
+                      const cplx_t<T> *__restrict__ V, const T *__restrict__ cc, int deg, T inv_tmax2, T beta,
+                      int isign, int ppc) {
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
+    if ((int64_t)blockIdx.x * ppc >= b.nv) return;
     const int64_t k = blockIdx.x * (int64_t)ppc + threadIdx.x;
     const bool act = threadIdx.x < ppc && k < b.nv;
     int i0[3] = {0, 0, 0};
@@ -463,7 +482,7 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1) spread
         ui = qr * v.y - qi * v.x;
     }
     const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
-    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, ng, ppc, G2);
+    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, ng, b.zs2, ppc, static_cast<cplx_t<T> *>(b.g2));
 }
 
 // ------------------------------------------------------------------ interpolation (gather)
@@ -510,10 +529,11 @@ __device__ __forceinline__ void stage_point(GatherShared<T, W> &sh, int slot, bo
 // lanes: every lane of the group returns the full sum.
 template <typename T, int W, bool PERIODIC>
 __device__ __forceinline__ void gather_window(const GatherShared<T, W> &sh, int slot, int jx0, const int ng[3],
-                                              const cplx_t<T> *__restrict__ G, unsigned mask, T &sr, T &si) {
+                                              int64_t zs, const cplx_t<T> *__restrict__ G, unsigned mask, T &sr,
+                                              T &si) {
     constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;
     const int px0 = sh.i0[slot][0], py0 = sh.i0[slot][1], pz0 = sh.i0[slot][2];
-    const int64_t nx = ng[0], ny = ng[1];
+    const int64_t nx = ng[0];
     T wxv[kXT];
     int cx[kXT];
     bool on[kXT];
@@ -531,11 +551,11 @@ __device__ __forceinline__ void gather_window(const GatherShared<T, W> &sh, int 
     si = T(0);
     for (int jz = 0; jz < W; ++jz) {
         const T wz = sh.w[slot][2 * W + jz];
-        const int64_t zoff = (int64_t)(PERIODIC ? wrap(pz0 + jz, ng[2]) : pz0 + jz) * ny;
+        const int64_t zoff = (int64_t)(PERIODIC ? wrap(pz0 + jz, ng[2]) : pz0 + jz) * zs;
 #pragma unroll
         for (int jy = 0; jy < W; ++jy) {
             const T c = sh.w[slot][W + jy] * wz;
-            const cplx_t<T> *row = G + (zoff + yrow[jy]) * nx;
+            const cplx_t<T> *row = G + zoff + yrow[jy] * nx;
 #pragma unroll
             for (int t = 0; t < kXT; ++t)
                 if (on[t]) {
@@ -553,17 +573,21 @@ __device__ __forceinline__ void gather_window(const GatherShared<T, W> &sh, int 
     }
 }
 
-// sky -> vis steps 3-4: gather the n2 grid at the baselines, times Q; add into acc.
+// sky -> vis steps 3-4: gather the n2 grids of a wave at the baselines, times Q; add into
+// acc. blockIdx.y picks the sub-problem, blockIdx.x a tile of 128 of its baselines.
 template <typename T, int W>
-__global__ void __launch_bounds__(kGatherThreads) interp_vis_kernel(NufftDev b, const float4 *__restrict__ vh,
-                                                                     const float4 *__restrict__ vl,
-                                                                     const double *__restrict__ soa, int64_t n_all,
-                                                                     const cplx_t<T> *__restrict__ G2,
-                                                                     const T *__restrict__ cc, int deg, T inv_tmax2,
-                                                                     cplx_t<T> *__restrict__ acc, T beta, int isign) {
+__global__ void __launch_bounds__(kGatherThreads)
+    interp_vis_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ vh,
+                      const float4 *__restrict__ vl, const double *__restrict__ soa, int64_t n_all,
+                      const T *__restrict__ cc, int deg, T inv_tmax2, cplx_t<T> *__restrict__ acc, T beta,
+                      int isign) {
     __shared__ GatherShared<T, W> sh;
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
     const int tid = threadIdx.x;
     const int64_t base = blockIdx.x * (int64_t)kSpreadPoints;
+    if (base >= b.nv) return;  // uniform
     if (tid < kSpreadPoints) {
         const int64_t k = base + tid;
         int i0[3] = {0, 0, 0};
@@ -576,12 +600,13 @@ __global__ void __launch_bounds__(kGatherThreads) interp_vis_kernel(NufftDev b, 
     const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
     const unsigned mask = 0xFFu << (g * kGroupLanes);
     const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
+    const cplx_t<T> *G2 = static_cast<const cplx_t<T> *>(b.g2);
     constexpr int kRounds = kSpreadPoints * kGroupLanes / kGatherThreads;
     for (int round = 0; round < kRounds; ++round) {
         const int p = g * 32 + warp * kRounds + round;
         if (sh.i0[p][0] == INT_MIN) continue;
         T sr, si;
-        gather_window<T, W, true>(sh, p, jx0, ng, G2, mask, sr, si);
+        gather_window<T, W, true>(sh, p, jx0, ng, b.zs2, G2, mask, sr, si);
         if (jx0 == 0) {
             const T qr = sh.q[p][0], qi = sh.q[p][1];
             grid_add(acc + b.v0 + base + p, qr * sr - qi * si, qr * si + qi * sr);
@@ -589,15 +614,18 @@ __global__ void __launch_bounds__(kGatherThreads) interp_vis_kernel(NufftDev b, 
     }
 }
 
-// vis -> sky steps 3-4 (transpose of the spreading): gather the n1 grid at the pixels,
-// times conj(P), real part into acc. One thread per pixel: neighbouring pixels' windows
-// overlap on the n1 grid, so their row loads hit L1 (95 %), and this layout measured
-// faster here than the 8-lanes-per-point one used for the baselines.
+// vis -> sky steps 3-4 (transpose of the spreading): gather the n1 grids of a wave at the
+// pixels, times conj(P), real part into acc. One thread per pixel: neighbouring pixels'
+// windows overlap on the n1 grid, so their row loads hit L1 (95 %), and this layout
+// measured faster here than the 8-lanes-per-point one used for the baselines.
 template <typename T, int W>
-__global__ void __launch_bounds__(128) interp_pix_kernel(NufftDev b, const float4 *__restrict__ rh,
-                                                          const float4 *__restrict__ rl, const double *__restrict__ soa,
-                                                          int64_t n_all, const cplx_t<T> *__restrict__ G1,
-                                                          T *__restrict__ acc, T beta, int isign) {
+__global__ void __launch_bounds__(128)
+    interp_pix_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ rh,
+                      const float4 *__restrict__ rl, const double *__restrict__ soa, int64_t n_all,
+                      T *__restrict__ acc, T beta, int isign) {
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= b.np) return;
     int i0[3];
@@ -608,6 +636,7 @@ __global__ void __launch_bounds__(128) interp_pix_kernel(NufftDev b, const float
     es_weights<T, W>(fr[1], beta, wy);
     es_weights<T, W>(fr[2], beta, wz);
     const int64_t nx = b.n1[0], ny = b.n1[1];
+    const cplx_t<T> *G1 = static_cast<const cplx_t<T> *>(b.g1);
     T sr = 0, si = 0;
     for (int jz = 0; jz < W; ++jz) {
         for (int jy = 0; jy < W; ++jy) {
@@ -635,10 +664,13 @@ __global__ void __launch_bounds__(128) interp_pix_kernel(NufftDev b, const float
 constexpr int kRowThreads = 256;
 constexpr int kRowUnroll = 4;
 
-inline unsigned row_ctas(int64_t rows) {
-    const int64_t warps = (rows + 1) / 2;  // at least two rows per warp
+// CTAs per sub-problem of a row pass over a wave of nb sub-problems with at most `rows`
+// rows each: at least two rows per warp, about 2,400 CTAs in all.
+inline unsigned row_ctas(int64_t rows, int nb) {
+    const int64_t warps = (rows + 1) / 2;
     const int64_t ctas = (warps + kRowThreads / 32 - 1) / (kRowThreads / 32);
-    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ctas, 152 * 8));
+    const int64_t cap = std::max<int64_t>(8, (152 * 16 + nb - 1) / nb);
+    return (unsigned)std::max<int64_t>(1, std::min<int64_t>(ctas, cap));
 }
 
 // First row and row count of this warp for `rows` rows split over all warps of the grid.
@@ -651,22 +683,28 @@ __device__ __forceinline__ void warp_rows(int64_t rows, int64_t &r0, int64_t &cn
 }
 
 // G2[j] = G1[l + n1/2] / (Psi_x Psi_y Psi_z)(l) for the centred frequency l of FFT index j
-// inside the n1 band, 0 elsewhere (rows of the n2 grid).
+// inside the n1 band, 0 elsewhere (rows of the n2 grid). blockIdx.y picks the sub-problem
+// of the wave, whose rows are split over the gridDim.x CTAs.
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads) deconv_pad_kernel(NufftDev b, const cplx_t<T> *__restrict__ G1,
-                                                                 const T *__restrict__ ipsi,
-                                                                 cplx_t<T> *__restrict__ G2) {
+__global__ void __launch_bounds__(kRowThreads) deconv_pad_kernel(const NufftDev *__restrict__ descs, int b0,
+                                                                 const T *__restrict__ ipsi_all) {
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
     const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
     const int n1x = b.n1[0], n1y = b.n1[1];
     const int h1x = b.n1[0] / 2, h1y = b.n1[1] / 2, h1z = b.n1[2] / 2;
+    const T *ipsi = ipsi_all + b.psi_off;
     const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
+    const cplx_t<T> *G1 = static_cast<const cplx_t<T> *>(b.g1);
+    cplx_t<T> *G2 = static_cast<cplx_t<T> *>(b.g2);
     int64_t r, cnt;
     warp_rows((int64_t)n2y * n2z, r, cnt);
     if (cnt == 0) return;
     int jy = (int)(r % n2y), jz = (int)(r / n2y);
     const int lane = threadIdx.x & 31;
     for (int64_t k = 0; k < cnt; ++k) {
-        cplx_t<T> *out = G2 + ((int64_t)jz * n2y + jy) * n2x;
+        cplx_t<T> *out = G2 + (int64_t)jz * b.zs2 + (int64_t)jy * n2x;
         const int ly = jy < n2y / 2 ? jy : jy - n2y;
         const int lz = jz < n2z / 2 ? jz : jz - n2z;
         cplx_t<T> zero;
@@ -704,14 +742,20 @@ __global__ void __launch_bounds__(kRowThreads) deconv_pad_kernel(NufftDev b, con
     }
 }
 
-// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band (rows of the n1 grid).
+// G1[l + n1/2] = G2[l mod n2] / (Psi_x Psi_y Psi_z)(l), l in the n1 band (rows of the n1
+// grid), for the sub-problem blockIdx.y of the wave.
 template <typename T>
-__global__ void __launch_bounds__(kRowThreads) crop_deconv_kernel(NufftDev b, const cplx_t<T> *__restrict__ G2,
-                                                                  const T *__restrict__ ipsi,
-                                                                  cplx_t<T> *__restrict__ G1) {
+__global__ void __launch_bounds__(kRowThreads) crop_deconv_kernel(const NufftDev *__restrict__ descs, int b0,
+                                                                  const T *__restrict__ ipsi_all) {
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
     const int n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
     const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
+    const T *ipsi = ipsi_all + b.psi_off;
     const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
+    const cplx_t<T> *G2 = static_cast<const cplx_t<T> *>(b.g2);
+    cplx_t<T> *G1 = static_cast<cplx_t<T> *>(b.g1);
     int64_t r, cnt;
     warp_rows((int64_t)n1y * n1z, r, cnt);
     if (cnt == 0) return;
@@ -721,7 +765,7 @@ __global__ void __launch_bounds__(kRowThreads) crop_deconv_kernel(NufftDev b, co
         int jy = iy - n1y / 2, jz = iz - n1z / 2;
         jy += jy < 0 ? n2y : 0;
         jz += jz < 0 ? n2z : 0;
-        const cplx_t<T> *in = G2 + ((int64_t)jz * n2y + jy) * n2x;
+        const cplx_t<T> *in = G2 + (int64_t)jz * b.zs2 + (int64_t)jy * n2x;
         cplx_t<T> *out = G1 + ((int64_t)iz * n1y + iy) * n1x;
         const T fyz = py[iy] * pz[iz];
         for (int x0 = lane; x0 < n1x; x0 += 32 * kRowUnroll) {
@@ -790,140 +834,141 @@ template <typename T, int W> void set_smem_attrs() {
 
 // ------------------------------------------------------------------ host launchers
 
-// In-place transform of the FFT grid with sign dir. band_input: only the n1 band's z planes
-// are nonzero (sky -> vis: 2-D transforms of those planes, then z); otherwise only those
-// planes are read afterwards (vis -> sky: z first, then 2-D transforms of those planes).
-template <typename T>
-void fft_grid(const NufftDev &b, const NufftArgs<T> &a, int dir, bool band_input, cudaStream_t s) {
-    auto exec = [&](cufftHandle h, typename CplxOf<T>::type *g) {
+// In-place transforms of one batch of FFT grids with sign dir. band_input: only the n1
+// band's z planes are nonzero (sky -> vis: 2-D transforms of those planes, then z);
+// otherwise only those planes are read afterwards (vis -> sky: z first, then 2-D).
+// Returns the number of cuFFT executions.
+template <typename T> int fft_batch(const FftBatch &f, int dir, bool band_input, cudaStream_t s) {
+    auto exec = [&](cufftHandle h, void *g) {
         check_cufft(cufftSetStream(h, s), "cufftSetStream");
         if constexpr (sizeof(T) == 4)
             check_cufft(cufftExecC2C(h, (cufftComplex *)g, (cufftComplex *)g, dir), "cufftExecC2C");
         else
             check_cufft(cufftExecZ2Z(h, (cufftDoubleComplex *)g, (cufftDoubleComplex *)g, dir), "cufftExecZ2Z");
     };
-    if (a.fft.full) {
-        exec(a.fft.full, a.G2);
-        return;
+    if (f.plans.full) {
+        exec(f.plans.full, f.g2);
+        return 1;
     }
-    const int64_t plane = (int64_t)b.n2[0] * b.n2[1];
-    typename CplxOf<T>::type *upper = a.G2 + (int64_t)(b.n2[2] - b.n1[2] / 2) * plane;
+    const int64_t planes = f.n2[0] * f.n2[1] * f.K;  // one interleaved z plane of all K grids
+    void *upper = static_cast<typename CplxOf<T>::type *>(f.g2) + (f.n2[2] - f.half) * planes;
     if (band_input) {
-        exec(a.fft.xy, a.G2);
-        exec(a.fft.xy, upper);
-        exec(a.fft.z, a.G2);
+        exec(f.plans.xy, f.g2);
+        exec(f.plans.xy, upper);
+        exec(f.plans.z, f.g2);
     } else {
-        exec(a.fft.z, a.G2);
-        exec(a.fft.xy, a.G2);
-        exec(a.fft.xy, upper);
+        exec(f.plans.z, f.g2);
+        exec(f.plans.xy, f.g2);
+        exec(f.plans.xy, upper);
     }
+    return 3;
 }
 
 template <typename T>
-void nufft_block_s2v(const NufftDev &b, const NufftArgs<T> &a, const T *c, cplx_t<T> *acc, cudaStream_t s,
-                     StageHook &hook) {
-    const int w = a.w;
+void nufft_wave_s2v(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, const T *c, cplx_t<T> *acc,
+                    cudaStream_t s, StageHook &hook) {
+    const int wd = a.w;
     const T bt = (T)a.beta;
-    const int64_t m1 = (int64_t)b.n1[0] * b.n1[1] * b.n1[2];
+    const dim3 sgrid(blocks_for(w.max_np, a.ppc_pix), (unsigned)w.nb);
+    const dim3 dgrid(row_ctas(w.max_rows2, w.nb), (unsigned)w.nb);
+    const dim3 igrid(blocks_for(w.max_nv, kSpreadPoints), (unsigned)w.nb);
     hook.begin(HVOX_STAGE_ZERO, s);
-    check_cuda(cudaMemsetAsync(a.G1, 0, sizeof(cplx_t<T>) * m1, s), "memset G1");
+    check_cuda(cudaMemsetAsync(g1, 0, sizeof(cplx_t<T>) * w.g1_cells, s), "memset G1");
     hook.end(HVOX_STAGE_ZERO, 1, s);
-    if (b.np > 0) {
-        hook.begin(HVOX_STAGE_SPREAD, s);
+    hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_pix_kernel<T, W><<<blocks_for(b.np, a.ppc_pix), kSpreadThreads, tile_bytes<T, W>(), s>>>(          \
-        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, a.G1, bt, a.isign, a.ppc_pix)
-        HVOX_W_SWITCH(w, CALL)
+    spread_pix_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
+        a.descs, w.b0, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, bt, a.isign, a.ppc_pix)
+    HVOX_W_SWITCH(wd, CALL)
 #undef CALL
-        check_cuda(cudaGetLastError(), "spread_pix");
-        hook.end(HVOX_STAGE_SPREAD, 1, s);
-    }
+    check_cuda(cudaGetLastError(), "spread_pix");
+    hook.end(HVOX_STAGE_SPREAD, 1, s);
     hook.begin(HVOX_STAGE_DECONV, s);
-    deconv_pad_kernel<T><<<row_ctas((int64_t)b.n2[1] * b.n2[2]), kRowThreads, 0, s>>>(
-        b, a.G1, a.ipsi + b.psi_off, a.G2);
+    deconv_pad_kernel<T><<<dgrid, kRowThreads, 0, s>>>(a.descs, w.b0, a.ipsi);
     check_cuda(cudaGetLastError(), "deconv_pad");
     hook.end(HVOX_STAGE_DECONV, 1, s);
     hook.begin(HVOX_STAGE_FFT, s);
-    fft_grid<T>(b, a, a.isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE, true, s);
-    hook.end(HVOX_STAGE_FFT, 1, s);
-    if (b.nv > 0) {
-        hook.begin(HVOX_STAGE_INTERP, s);
+    int n_fft = 0;
+    for (const FftBatch &f : w.ffts) n_fft += fft_batch<T>(f, a.isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE, true, s);
+    hook.end(HVOX_STAGE_FFT, n_fft, s);
+    hook.begin(HVOX_STAGE_INTERP, s);
 #define CALL(W)                                                                                                   \
-    interp_vis_kernel<T, W><<<blocks_for(b.nv, kSpreadPoints), kGatherThreads, 0, s>>>(b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, a.G2, \
-                                                                  a.cheb, a.deg, (T)a.inv_tmax2, acc, bt, a.isign)
-        HVOX_W_SWITCH(w, CALL)
+    interp_vis_kernel<T, W><<<igrid, kGatherThreads, 0, s>>>(a.descs, w.b0, a.vis_hi, a.vis_lo, a.vis_soa,     \
+                                                             a.n_vis, a.cheb, a.deg, (T)a.inv_tmax2, acc, bt,    \
+                                                             a.isign)
+    HVOX_W_SWITCH(wd, CALL)
 #undef CALL
-        check_cuda(cudaGetLastError(), "interp_vis");
-        hook.end(HVOX_STAGE_INTERP, 1, s);
-    }
+    check_cuda(cudaGetLastError(), "interp_vis");
+    hook.end(HVOX_STAGE_INTERP, 1, s);
 }
 
 template <typename T>
-void nufft_block_v2s(const NufftDev &b, const NufftArgs<T> &a, const cplx_t<T> *V, T *acc, cudaStream_t s,
-                     StageHook &hook) {
-    const int w = a.w;
+void nufft_wave_v2s(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, const cplx_t<T> *V, T *acc,
+                    cudaStream_t s, StageHook &hook) {
+    const int wd = a.w;
     const T bt = (T)a.beta;
-    const int64_t m2 = (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
+    const dim3 sgrid(blocks_for(w.max_nv, a.ppc_vis), (unsigned)w.nb);
+    const dim3 cgrid(row_ctas(w.max_rows1, w.nb), (unsigned)w.nb);
+    const dim3 igrid(blocks_for(w.max_np, 128), (unsigned)w.nb);
     hook.begin(HVOX_STAGE_ZERO, s);
-    check_cuda(cudaMemsetAsync(a.G2, 0, sizeof(cplx_t<T>) * m2, s), "memset G2");
+    check_cuda(cudaMemsetAsync(g2, 0, sizeof(cplx_t<T>) * w.g2_cells, s), "memset G2");
     hook.end(HVOX_STAGE_ZERO, 1, s);
-    if (b.nv > 0) {
-        hook.begin(HVOX_STAGE_SPREAD, s);
+    hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_vis_kernel<T, W><<<blocks_for(b.nv, a.ppc_vis), kSpreadThreads, tile_bytes<T, W>(), s>>>(          \
-        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, bt, a.isign, a.ppc_vis)
-        HVOX_W_SWITCH(w, CALL)
+    spread_vis_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
+        a.descs, w.b0, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, bt, a.isign,   \
+        a.ppc_vis)
+    HVOX_W_SWITCH(wd, CALL)
 #undef CALL
-        check_cuda(cudaGetLastError(), "spread_vis");
-        hook.end(HVOX_STAGE_SPREAD, 1, s);
-    }
+    check_cuda(cudaGetLastError(), "spread_vis");
+    hook.end(HVOX_STAGE_SPREAD, 1, s);
     hook.begin(HVOX_STAGE_FFT, s);
-    fft_grid<T>(b, a, a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD, false, s);  // transpose: opposite sign
-    hook.end(HVOX_STAGE_FFT, 1, s);
+    int n_fft = 0;
+    for (const FftBatch &f : w.ffts)  // transpose: opposite sign
+        n_fft += fft_batch<T>(f, a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD, false, s);
+    hook.end(HVOX_STAGE_FFT, n_fft, s);
     hook.begin(HVOX_STAGE_DECONV, s);
-    crop_deconv_kernel<T><<<row_ctas((int64_t)b.n1[1] * b.n1[2]), kRowThreads, 0, s>>>(
-        b, a.G2, a.ipsi + b.psi_off, a.G1);
+    crop_deconv_kernel<T><<<cgrid, kRowThreads, 0, s>>>(a.descs, w.b0, a.ipsi);
     check_cuda(cudaGetLastError(), "crop_deconv");
     hook.end(HVOX_STAGE_DECONV, 1, s);
-    if (b.np > 0) {
-        hook.begin(HVOX_STAGE_INTERP, s);
+    hook.begin(HVOX_STAGE_INTERP, s);
 #define CALL(W)                                                                                                   \
-    interp_pix_kernel<T, W><<<blocks_for(b.np, 128), 128, 0, s>>>(b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, a.G1, \
-                                                                  acc, bt, a.isign)
-        HVOX_W_SWITCH(w, CALL)
+    interp_pix_kernel<T, W><<<igrid, 128, 0, s>>>(a.descs, w.b0, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, acc,   \
+                                                  bt, a.isign)
+    HVOX_W_SWITCH(wd, CALL)
 #undef CALL
-        check_cuda(cudaGetLastError(), "interp_pix");
-        hook.end(HVOX_STAGE_INTERP, 1, s);
-    }
+    check_cuda(cudaGetLastError(), "interp_pix");
+    hook.end(HVOX_STAGE_INTERP, 1, s);
 }
 
 template <typename T>
-float time_spread(const NufftDev &b, const NufftArgs<T> &a, bool pix, const void *values, int ppc, cudaStream_t s) {
-    const int w = a.w;
+float time_spread(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, bool pix, const void *values, int ppc,
+                  cudaStream_t s) {
+    const int wd = a.w;
     const T bt = (T)a.beta;
-    const int64_t cells = pix ? (int64_t)b.n1[0] * b.n1[1] * b.n1[2] : (int64_t)b.n2[0] * b.n2[1] * b.n2[2];
-    cplx_t<T> *G = pix ? a.G1 : a.G2;
-    check_cuda(cudaMemsetAsync(G, 0, sizeof(cplx_t<T>) * cells, s), "memset grid");
+    check_cuda(cudaMemsetAsync(pix ? g1 : g2, 0, sizeof(cplx_t<T>) * (pix ? w.g1_cells : w.g2_cells), s),
+               "memset grid");
     cudaEvent_t e0, e1;
     check_cuda(cudaEventCreate(&e0), "cudaEventCreate");
     check_cuda(cudaEventCreate(&e1), "cudaEventCreate");
     check_cuda(cudaEventRecord(e0, s), "cudaEventRecord");
+    const dim3 grid(blocks_for(pix ? w.max_np : w.max_nv, ppc), (unsigned)w.nb);
     if (pix) {
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_pix_kernel<T, W><<<blocks_for(b.np, ppc), kSpreadThreads, tile_bytes<T, W>(), s>>>(                  \
-        b, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, (const T *)values, a.G1, bt, a.isign, ppc)
-        HVOX_W_SWITCH(w, CALL)
+    spread_pix_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
+        a.descs, w.b0, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, (const T *)values, bt, a.isign, ppc)
+        HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     } else {
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_vis_kernel<T, W><<<blocks_for(b.nv, ppc), kSpreadThreads, tile_bytes<T, W>(), s>>>(                  \
-        b, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, (const cplx_t<T> *)values, a.cheb, a.deg, (T)a.inv_tmax2, a.G2, \
-        bt, a.isign, ppc)
-        HVOX_W_SWITCH(w, CALL)
+    spread_vis_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
+        a.descs, w.b0, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, (const cplx_t<T> *)values, a.cheb, a.deg,         \
+        (T)a.inv_tmax2, bt, a.isign, ppc)
+        HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     }
     check_cuda(cudaGetLastError(), "spread (timing)");
@@ -936,17 +981,17 @@ float time_spread(const NufftDev &b, const NufftArgs<T> &a, bool pix, const void
     return ms;
 }
 
-template float time_spread<float>(const NufftDev &, const NufftArgs<float> &, bool, const void *, int, cudaStream_t);
-template float time_spread<double>(const NufftDev &, const NufftArgs<double> &, bool, const void *, int,
+template float time_spread<float>(const Wave &, const NufftArgs<float> &, void *, void *, bool, const void *, int,
+                                  cudaStream_t);
+template float time_spread<double>(const Wave &, const NufftArgs<double> &, void *, void *, bool, const void *, int,
                                    cudaStream_t);
-
-template void nufft_block_s2v<float>(const NufftDev &, const NufftArgs<float> &, const float *, float2 *,
-                                     cudaStream_t, StageHook &);
-template void nufft_block_s2v<double>(const NufftDev &, const NufftArgs<double> &, const double *, double2 *,
-                                      cudaStream_t, StageHook &);
-template void nufft_block_v2s<float>(const NufftDev &, const NufftArgs<float> &, const float2 *, float *,
-                                     cudaStream_t, StageHook &);
-template void nufft_block_v2s<double>(const NufftDev &, const NufftArgs<double> &, const double2 *, double *,
-                                      cudaStream_t, StageHook &);
+template void nufft_wave_s2v<float>(const Wave &, const NufftArgs<float> &, void *, void *, const float *, float2 *,
+                                    cudaStream_t, StageHook &);
+template void nufft_wave_s2v<double>(const Wave &, const NufftArgs<double> &, void *, void *, const double *,
+                                     double2 *, cudaStream_t, StageHook &);
+template void nufft_wave_v2s<float>(const Wave &, const NufftArgs<float> &, void *, void *, const float2 *, float *,
+                                    cudaStream_t, StageHook &);
+template void nufft_wave_v2s<double>(const Wave &, const NufftArgs<double> &, void *, void *, const double2 *,
+                                     double *, cudaStream_t, StageHook &);
 
 }  // namespace hvox

@@ -136,9 +136,9 @@ def test_estimate_bytes_bounds():
     # A small job is planned as direct sums without a search: no NUFFT grids.
     small = hvox.estimate_bytes(1000, 1000, 1e-6)
     assert 0 < small < 1e6
-    # A large job may get up to four lanes of grids and work areas within 8 GiB each.
+    # A large job may get two lanes of wave grids and work areas within 16 GiB each.
     big = hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6)
-    assert big >= 2 * 4 * 8 * 2**30
+    assert big >= 2 * 2 * 16 * 2**30
     # A fixed budget bounds the grids instead; direct mode has none.
     assert hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6, chunk_budget_bytes=1e8) < 1e9
     assert hvox.estimate_bytes(1_000_000, 1_000_000, 1e-6, mode="direct") < 1e9
