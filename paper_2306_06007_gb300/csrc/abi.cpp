@@ -552,11 +552,6 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                     g1 += (size_t)m1_of(bk) * 2 * re;
                     d.g2 = g2 + (size_t)g * plane * 2 * re;
                     d.zs2 = plane * K;
-                    if (fault_hit("window"))
-                        for (int q = 0; q < 3; ++q) {
-                            d.a[q] *= 4.0;
-                            split(d.a[q], d.ah[q], d.al[q]);
-                        }
                     p.dblocks[w.b0 + k] = d;
                 }
                 g2 += (size_t)K * first.n2[0] * first.n2[1] * first.n2[2] * 2 * re;
@@ -568,6 +563,14 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             for (auto &kv : lane.fft)
                 for (cufftHandle h : {kv.second.full, kv.second.xy, kv.second.z})
                     if (h) check_cufft(cufftSetWorkArea(h, lane.work.ptr), "cufftSetWorkArea");
+        }
+        if (fault_hit("window")) {  // the sub-problem with the most pixels (a pixel extent to scale)
+            NufftDev &d = *std::max_element(p.dblocks.begin(), p.dblocks.end(),
+                                            [](const NufftDev &x, const NufftDev &y) { return x.np < y.np; });
+            for (int q = 0; q < 3; ++q) {
+                d.a[q] *= 4.0;
+                split(d.a[q], d.ah[q], d.al[q]);
+            }
         }
         upload(p.ddescs, p.dblocks.data(), p.dblocks.size() * sizeof(NufftDev), s);
     }

@@ -36,9 +36,9 @@ void check_cufft(cufftResult r, const char *what);
 //   alloc    a device allocation (HVOX_ENOMEM, everything allocated so far freed);
 //   cufft    a cuFFT plan creation (HVOX_ECUDA);
 //   capture  a CUDA-graph capture (the plan falls back to eager launches);
-//   window   the pixel scale of one NUFFT sub-problem is multiplied by 4 on the host, so
-//            its kernels clamp the pixels' windows into the grid and set the device
-//            error word (hvox_sync then returns HVOX_EINTERNAL).
+//   window   the pixel scale of the NUFFT sub-problem with the most pixels is multiplied
+//            by 4 on the host, so its kernels clamp the pixels' windows into the grid and
+//            set the device error word (hvox_sync then returns HVOX_EINTERNAL).
 // No GPU fault is involved: every injected failure is raised or prepared on the host.
 bool fault_hit(const char *site);
 
