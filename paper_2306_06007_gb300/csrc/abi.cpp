@@ -493,14 +493,15 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         p.dblocks.resize(order.size());
         for (Wave &w : p.waves) {
             Lane &lane = *p.lanes[w.lane];
-            char *g1 = static_cast<char *>(lane.g1.ptr), *g2 = static_cast<char *>(lane.g2.ptr);
+            char *g2 = static_cast<char *>(lane.g2.ptr);
+            int64_t off1 = 0, off2 = 0;  // cells into the lane's g1 / g2
             for (int k = 0; k < w.nb;) {
                 // one batch: the run of sub-problems of this shape
                 const NufftBlock &first = part.blocks[order[w.b0 + k]];
                 int K = 1;
                 while (k + K < w.nb && shape_key(part.blocks[order[w.b0 + k + K]]) == shape_key(first)) ++K;
                 FftBatch fb;
-                fb.g2 = g2;
+                fb.g2 = g2 + (size_t)off2 * 2 * re;
                 for (int d = 0; d < 3; ++d) fb.n2[d] = first.n2[d];
                 fb.half = first.n1[2] / 2;
                 fb.K = K;
@@ -548,13 +549,13 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                     }
                     d.psi_off = bk.psi_off;
                     d.err = p.err.as<int>();
-                    d.g1 = g1;
-                    g1 += (size_t)m1_of(bk) * 2 * re;
-                    d.g2 = g2 + (size_t)g * plane * 2 * re;
+                    d.g1_off = off1;
+                    off1 += m1_of(bk);
+                    d.g2_off = off2 + (int64_t)g * plane;
                     d.zs2 = plane * K;
                     p.dblocks[w.b0 + k] = d;
                 }
-                g2 += (size_t)K * first.n2[0] * first.n2[1] * first.n2[2] * 2 * re;
+                off2 += (int64_t)K * first.n2[0] * first.n2[1] * first.n2[2];
             }
         }
         for (int l = 0; l < n_lanes; ++l) {

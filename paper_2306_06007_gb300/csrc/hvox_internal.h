@@ -179,9 +179,9 @@ struct NufftDev {
     float Ch[3], Cl[3], Dh[3], Dl[3], ah[3], al[3], n2ah[3], n2al[3], tpa[3];
     int64_t psi_off;
     int *err;         // the plan's device error word (kDevErr* bits)
-    void *g1;         // this sub-problem's spread grid (n1 cells, x fastest, contiguous)
-    void *g2;         // its FFT grid: cell (x, y, z) at g2 + z * zs2 + y * n2[0] + x
-    int64_t zs2;      // z-plane stride of g2 in cells (the z planes of a batch are interleaved)
+    int64_t g1_off;   // its spread grid: n1 cells (x fastest) from cell g1_off of its lane's g1
+    int64_t g2_off;   // its FFT grid: cell (x, y, z) at g2_off + z * zs2 + y * n2[0] + x of g2
+    int64_t zs2;      // z-plane stride of the FFT grid in cells (a batch interleaves its planes)
 };
 
 template <typename T> struct CplxOf;

@@ -298,9 +298,24 @@ __device__ __forceinline__ void load_desc(NufftDev &dst, const NufftDev *__restr
 // Plane stride of a tile with tx * ty cells per plane: the next value = 8 (mod 32).
 __device__ __forceinline__ int64_t tile_plane_stride(int64_t cells) { return cells + ((8 - cells) % 32 + 32) % 32; }
 
+// The grid of a spreading CTA, read from its shared descriptor where it is used (the
+// untiled path and the flush) rather than held in registers across the tap loop: the n1
+// grid (pixels, contiguous) or the n2 grid (baselines, z planes zs2 apart).
+// The lane's buffer arrives as a kernel parameter, so the compiler treats every grid
+// address as global memory (fire-and-forget vector reductions in the flush).
+template <typename T, bool PERIODIC> struct SpreadGrid {
+    const NufftDev &b;
+    cplx_t<T> *__restrict__ base;  // the lane's g1 (pixels) or g2 (baselines)
+    __device__ __forceinline__ int n(int d) const { return PERIODIC ? b.n2[d] : b.n1[d]; }
+    __device__ __forceinline__ cplx_t<T> *row(int64_t z, int64_t y) const {
+        if (PERIODIC) return base + b.g2_off + z * b.zs2 + y * b.n2[0];
+        return base + b.g1_off + (z * b.n1[1] + y) * b.n1[0];
+    }
+};
+
 template <typename T, int W, bool PERIODIC>
 __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
-                                           const int ng[3], int64_t zs, int ppc, cplx_t<T> *__restrict__ G) {
+                                           const SpreadGrid<T, PERIODIC> grid, int ppc) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ SpreadShared<T, W> sh;
     constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));
@@ -370,7 +385,7 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
             const T wxv = on[t] ? sh.w[p][jx] : T(0);
             ar[t] = sh.v[p][0] * wxv;
             ai[t] = sh.v[p][1] * wxv;
-            cx[t] = tiled ? px0 - lo0 + jx : (PERIODIC ? wrap(px0 + jx, ng[0]) : px0 + jx);
+            cx[t] = tiled ? px0 - lo0 + jx : (PERIODIC ? wrap(px0 + jx, grid.n(0)) : px0 + jx);
         }
         T wy[W];
 #pragma unroll
@@ -397,10 +412,10 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
                         }
                 }
             } else {
-                const int64_t gz = PERIODIC ? wrap(pz0 + jz, ng[2]) : pz0 + jz;
+                const int64_t gz = PERIODIC ? wrap(pz0 + jz, grid.n(2)) : pz0 + jz;
                 for (int jy = 0; jy < W; ++jy) {
-                    const int64_t gy = PERIODIC ? wrap(py0 + jy, ng[1]) : py0 + jy;
-                    cplx_t<T> *row = G + gz * zs + gy * ng[0];
+                    const int64_t gy = PERIODIC ? wrap(py0 + jy, grid.n(1)) : py0 + jy;
+                    cplx_t<T> *row = grid.row(gz, gy);
 #pragma unroll
                     for (int t = 0; t < kXT; ++t)
                         if (on[t]) grid_add(row + cx[t], zr[t] * wy[jy], zi[t] * wy[jy]);
@@ -416,15 +431,15 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         const int y = r % tyi, z = r / tyi;
         int gy = lo1 + y, gz = lo2 + z;
         if (PERIODIC) {
-            gy = wrap(gy, ng[1]);
-            gz = wrap(gz, ng[2]);
+            gy = wrap(gy, grid.n(1));
+            gz = wrap(gz, grid.n(2));
         }
-        cplx_t<T> *grow = G + (int64_t)gz * zs + (int64_t)gy * ng[0];
+        cplx_t<T> *grow = grid.row(gz, gy);
         const int t0 = z * ps + y * txi;
         for (int x = lane; x < txi; x += 32) {
             const T re = tre[t0 + x], im = tim[t0 + x];
             if (re == T(0) && im == T(0)) continue;
-            const int gx = PERIODIC ? wrap(lo0 + x, ng[0]) : lo0 + x;
+            const int gx = PERIODIC ? wrap(lo0 + x, grid.n(0)) : lo0 + x;
             grid_add(grow + gx, re, im);
         }
     }
@@ -435,9 +450,9 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
 // of it (the bin; the plan may tune it): thread t < ppc takes point blockIdx.x * ppc + t.
 template <typename T, int W>
 __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
-    spread_pix_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ rh,
-                      const float4 *__restrict__ rl, const double *__restrict__ soa, int64_t n_all,
-                      const T *__restrict__ c, T beta, int isign, int ppc) {
+    spread_pix_kernel(const NufftDev *__restrict__ descs, int b0, cplx_t<T> *__restrict__ G1,
+                      const float4 *__restrict__ rh, const float4 *__restrict__ rl, const double *__restrict__ soa,
+                      int64_t n_all, const T *__restrict__ c, T beta, int isign, int ppc) {
     __shared__ NufftDev sb;
     load_desc(sb, descs + b0 + blockIdx.y);
     const NufftDev &b = sb;
@@ -453,19 +468,17 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         vr = cv * pr;
         vi = cv * pim;
     }
-    const int ng[3] = {b.n1[0], b.n1[1], b.n1[2]};
-    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, ng, (int64_t)ng[0] * ng[1], ppc,
-                            static_cast<cplx_t<T> *>(b.g1));
+    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
 }
 
 // vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2
 // grids of a wave (layout as for pixels).
 template <typename T, int W>
 __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
-    spread_vis_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ vh,
-                      const float4 *__restrict__ vl, const double *__restrict__ soa, int64_t n_all,
-                      const cplx_t<T> *__restrict__ V, const T *__restrict__ cc, int deg, T inv_tmax2, T beta,
-                      int isign, int ppc) {
+    spread_vis_kernel(const NufftDev *__restrict__ descs, int b0, cplx_t<T> *__restrict__ G2,
+                      const float4 *__restrict__ vh, const float4 *__restrict__ vl, const double *__restrict__ soa,
+                      int64_t n_all, const cplx_t<T> *__restrict__ V, const T *__restrict__ cc, int deg,
+                      T inv_tmax2, T beta, int isign, int ppc) {
     __shared__ NufftDev sb;
     load_desc(sb, descs + b0 + blockIdx.y);
     const NufftDev &b = sb;
@@ -481,8 +494,7 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         ur = qr * v.x + qi * v.y;  // conj(Q) v
         ui = qr * v.y - qi * v.x;
     }
-    const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
-    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, ng, b.zs2, ppc, static_cast<cplx_t<T> *>(b.g2));
+    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
 }
 
 // ------------------------------------------------------------------ interpolation (gather)
@@ -577,10 +589,10 @@ __device__ __forceinline__ void gather_window(const GatherShared<T, W> &sh, int 
 // acc. blockIdx.y picks the sub-problem, blockIdx.x a tile of 128 of its baselines.
 template <typename T, int W>
 __global__ void __launch_bounds__(kGatherThreads)
-    interp_vis_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ vh,
-                      const float4 *__restrict__ vl, const double *__restrict__ soa, int64_t n_all,
-                      const T *__restrict__ cc, int deg, T inv_tmax2, cplx_t<T> *__restrict__ acc, T beta,
-                      int isign) {
+    interp_vis_kernel(const NufftDev *__restrict__ descs, int b0, const cplx_t<T> *__restrict__ G2base,
+                      const float4 *__restrict__ vh, const float4 *__restrict__ vl, const double *__restrict__ soa,
+                      int64_t n_all, const T *__restrict__ cc, int deg, T inv_tmax2, cplx_t<T> *__restrict__ acc,
+                      T beta, int isign) {
     __shared__ GatherShared<T, W> sh;
     __shared__ NufftDev sb;
     load_desc(sb, descs + b0 + blockIdx.y);
@@ -600,7 +612,7 @@ __global__ void __launch_bounds__(kGatherThreads)
     const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
     const unsigned mask = 0xFFu << (g * kGroupLanes);
     const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
-    const cplx_t<T> *G2 = static_cast<const cplx_t<T> *>(b.g2);
+    const cplx_t<T> *G2 = G2base + b.g2_off;
     constexpr int kRounds = kSpreadPoints * kGroupLanes / kGatherThreads;
     for (int round = 0; round < kRounds; ++round) {
         const int p = g * 32 + warp * kRounds + round;
@@ -620,9 +632,9 @@ __global__ void __launch_bounds__(kGatherThreads)
 // measured faster here than the 8-lanes-per-point one used for the baselines.
 template <typename T, int W>
 __global__ void __launch_bounds__(128)
-    interp_pix_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ rh,
-                      const float4 *__restrict__ rl, const double *__restrict__ soa, int64_t n_all,
-                      T *__restrict__ acc, T beta, int isign) {
+    interp_pix_kernel(const NufftDev *__restrict__ descs, int b0, const cplx_t<T> *__restrict__ G1base,
+                      const float4 *__restrict__ rh, const float4 *__restrict__ rl, const double *__restrict__ soa,
+                      int64_t n_all, T *__restrict__ acc, T beta, int isign) {
     __shared__ NufftDev sb;
     load_desc(sb, descs + b0 + blockIdx.y);
     const NufftDev &b = sb;
@@ -636,7 +648,7 @@ __global__ void __launch_bounds__(128)
     es_weights<T, W>(fr[1], beta, wy);
     es_weights<T, W>(fr[2], beta, wz);
     const int64_t nx = b.n1[0], ny = b.n1[1];
-    const cplx_t<T> *G1 = static_cast<const cplx_t<T> *>(b.g1);
+    const cplx_t<T> *G1 = G1base + b.g1_off;
     T sr = 0, si = 0;
     for (int jz = 0; jz < W; ++jz) {
         for (int jy = 0; jy < W; ++jy) {
@@ -687,6 +699,8 @@ __device__ __forceinline__ void warp_rows(int64_t rows, int64_t &r0, int64_t &cn
 // of the wave, whose rows are split over the gridDim.x CTAs.
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads) deconv_pad_kernel(const NufftDev *__restrict__ descs, int b0,
+                                                                 const cplx_t<T> *__restrict__ G1base,
+                                                                 cplx_t<T> *__restrict__ G2base,
                                                                  const T *__restrict__ ipsi_all) {
     __shared__ NufftDev sb;
     load_desc(sb, descs + b0 + blockIdx.y);
@@ -696,8 +710,8 @@ __global__ void __launch_bounds__(kRowThreads) deconv_pad_kernel(const NufftDev 
     const int h1x = b.n1[0] / 2, h1y = b.n1[1] / 2, h1z = b.n1[2] / 2;
     const T *ipsi = ipsi_all + b.psi_off;
     const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
-    const cplx_t<T> *G1 = static_cast<const cplx_t<T> *>(b.g1);
-    cplx_t<T> *G2 = static_cast<cplx_t<T> *>(b.g2);
+    const cplx_t<T> *G1 = G1base + b.g1_off;
+    cplx_t<T> *G2 = G2base + b.g2_off;
     int64_t r, cnt;
     warp_rows((int64_t)n2y * n2z, r, cnt);
     if (cnt == 0) return;
@@ -746,6 +760,8 @@ __global__ void __launch_bounds__(kRowThreads) deconv_pad_kernel(const NufftDev 
 // grid), for the sub-problem blockIdx.y of the wave.
 template <typename T>
 __global__ void __launch_bounds__(kRowThreads) crop_deconv_kernel(const NufftDev *__restrict__ descs, int b0,
+                                                                  const cplx_t<T> *__restrict__ G2base,
+                                                                  cplx_t<T> *__restrict__ G1base,
                                                                   const T *__restrict__ ipsi_all) {
     __shared__ NufftDev sb;
     load_desc(sb, descs + b0 + blockIdx.y);
@@ -754,8 +770,8 @@ __global__ void __launch_bounds__(kRowThreads) crop_deconv_kernel(const NufftDev
     const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
     const T *ipsi = ipsi_all + b.psi_off;
     const T *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
-    const cplx_t<T> *G2 = static_cast<const cplx_t<T> *>(b.g2);
-    cplx_t<T> *G1 = static_cast<cplx_t<T> *>(b.g1);
+    const cplx_t<T> *G2 = G2base + b.g2_off;
+    cplx_t<T> *G1 = G1base + b.g1_off;
     int64_t r, cnt;
     warp_rows((int64_t)n1y * n1z, r, cnt);
     if (cnt == 0) return;
@@ -879,13 +895,15 @@ void nufft_wave_s2v(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
     spread_pix_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
-        a.descs, w.b0, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, bt, a.isign, a.ppc_pix)
+        a.descs, w.b0, static_cast<cplx_t<T> *>(g1), a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, bt, a.isign,    \
+        a.ppc_pix)
     HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     check_cuda(cudaGetLastError(), "spread_pix");
     hook.end(HVOX_STAGE_SPREAD, 1, s);
     hook.begin(HVOX_STAGE_DECONV, s);
-    deconv_pad_kernel<T><<<dgrid, kRowThreads, 0, s>>>(a.descs, w.b0, a.ipsi);
+    deconv_pad_kernel<T><<<dgrid, kRowThreads, 0, s>>>(a.descs, w.b0, static_cast<const cplx_t<T> *>(g1),
+                                                       static_cast<cplx_t<T> *>(g2), a.ipsi);
     check_cuda(cudaGetLastError(), "deconv_pad");
     hook.end(HVOX_STAGE_DECONV, 1, s);
     hook.begin(HVOX_STAGE_FFT, s);
@@ -894,9 +912,9 @@ void nufft_wave_s2v(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
     hook.end(HVOX_STAGE_FFT, n_fft, s);
     hook.begin(HVOX_STAGE_INTERP, s);
 #define CALL(W)                                                                                                   \
-    interp_vis_kernel<T, W><<<igrid, kGatherThreads, 0, s>>>(a.descs, w.b0, a.vis_hi, a.vis_lo, a.vis_soa,     \
-                                                             a.n_vis, a.cheb, a.deg, (T)a.inv_tmax2, acc, bt,    \
-                                                             a.isign)
+    interp_vis_kernel<T, W><<<igrid, kGatherThreads, 0, s>>>(                                                \
+        a.descs, w.b0, static_cast<const cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, a.cheb, a.deg, \
+        (T)a.inv_tmax2, acc, bt, a.isign)
     HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     check_cuda(cudaGetLastError(), "interp_vis");
@@ -918,8 +936,8 @@ void nufft_wave_v2s(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
     spread_vis_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
-        a.descs, w.b0, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg, (T)a.inv_tmax2, bt, a.isign,   \
-        a.ppc_vis)
+        a.descs, w.b0, static_cast<cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg,   \
+        (T)a.inv_tmax2, bt, a.isign, a.ppc_vis)
     HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     check_cuda(cudaGetLastError(), "spread_vis");
@@ -930,13 +948,14 @@ void nufft_wave_v2s(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
         n_fft += fft_batch<T>(f, a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD, false, s);
     hook.end(HVOX_STAGE_FFT, n_fft, s);
     hook.begin(HVOX_STAGE_DECONV, s);
-    crop_deconv_kernel<T><<<cgrid, kRowThreads, 0, s>>>(a.descs, w.b0, a.ipsi);
+    crop_deconv_kernel<T><<<cgrid, kRowThreads, 0, s>>>(a.descs, w.b0, static_cast<const cplx_t<T> *>(g2),
+                                                        static_cast<cplx_t<T> *>(g1), a.ipsi);
     check_cuda(cudaGetLastError(), "crop_deconv");
     hook.end(HVOX_STAGE_DECONV, 1, s);
     hook.begin(HVOX_STAGE_INTERP, s);
 #define CALL(W)                                                                                                   \
-    interp_pix_kernel<T, W><<<igrid, 128, 0, s>>>(a.descs, w.b0, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, acc,   \
-                                                  bt, a.isign)
+    interp_pix_kernel<T, W><<<igrid, 128, 0, s>>>(a.descs, w.b0, static_cast<const cplx_t<T> *>(g1), a.pix_hi,  \
+                                                  a.pix_lo, a.pix_soa, a.n_pix, acc, bt, a.isign)
     HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     check_cuda(cudaGetLastError(), "interp_pix");
@@ -959,15 +978,16 @@ float time_spread(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, bool
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
     spread_pix_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
-        a.descs, w.b0, a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, (const T *)values, bt, a.isign, ppc)
+        a.descs, w.b0, static_cast<cplx_t<T> *>(g1), a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, (const T *)values, \
+        bt, a.isign, ppc)
         HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     } else {
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
     spread_vis_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
-        a.descs, w.b0, a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, (const cplx_t<T> *)values, a.cheb, a.deg,         \
-        (T)a.inv_tmax2, bt, a.isign, ppc)
+        a.descs, w.b0, static_cast<cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis,                   \
+        (const cplx_t<T> *)values, a.cheb, a.deg, (T)a.inv_tmax2, bt, a.isign, ppc)
         HVOX_W_SWITCH(wd, CALL)
 #undef CALL
     }
