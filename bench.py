@@ -46,11 +46,12 @@ WORKLOAD = ("LOFAR-like: HEALPix nside=256 30deg cap (52,812 px) x 300 antennas 
 FP32_PEAK_FLOPS = 152 * 128 * 2 * 2.07e9  # FP32 FMA pipes x 2 flops x max SM clock
 FLOPS_PER_PAIR = 16.0                      # algorithmic flops per (pixel, baseline) pair
 
-# From one ncu capture of the direct kernels on the LOFAR-like workload at eps = 1e-9, valid
-# only for the kernel source it was taken on: DRAM bytes per launch (dram__bytes_read.sum +
-# dram__bytes_write.sum of the full-size launches, mean of the s2v and v2s launches) and
-# thread instructions per pair (smsp__inst_executed.sum x 32 / pairs, 100k-baseline case).
-DIRECT_COUNTERS = {1e-9: ("e6a65023222cef8e2ddcf97f1a340885e46f4dd9278497f99aac4e9b5fb42b42", 209284224.0, 80.0)}
+# From ncu captures of the direct kernels on the LOFAR-like workload at eps = 1e-9, valid
+# only for the kernel source they were taken on: DRAM bytes per launch (dram__bytes_read.sum +
+# dram__bytes_write.sum of the full-size launches, mean of two steps' s2v and v2s launches)
+# and thread instructions per pair of the double-float kernels (smsp__inst_executed.sum x 32
+# / pairs, 100k-baseline case; those kernels are unchanged since that capture).
+DIRECT_COUNTERS = {1e-9: ("5091eb9e8be659d494b7577f44d17bbdbb0ead139d7b9923b6f6c23085fc6b25", 210022528.0, 80.0)}
 
 
 def direct_counters(eps, config, other_workload, n_vis):

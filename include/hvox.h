@@ -137,10 +137,19 @@ typedef struct {
                                     sub-problems read (the kernel transform is evaluated at
                                     the full p, not p - D_j), so sharing is exact only with
                                     a box that spans the other set. */
-    int32_t autotune;            /* 1: measure at plan time, on the sub-problem with the most
-                                    points of each set, which bin size (points per spreading
-                                    CTA: 32, 64 or 128) spreads fastest, and keep it for that
-                                    direction (a few extra launches during hvox_plan); 0: 128 */
+    int32_t autotune;            /* 1: measure at plan time (a few extra launches and a
+                                    probe during hvox_plan): (a) the kernel width: the
+                                    NUFFT sub-problem with the most points (its pixels and
+                                    up to 2,048 of its baselines) is evaluated by direct
+                                    sums and by the NUFFT with 1 and 2 cells less than the
+                                    width rule gives; the narrowest width whose measured
+                                    relative l2 error is within 2.5 eps is kept and the job
+                                    re-planned with it (hvox_info.probe_error); (b) which
+                                    bin size (points per spreading CTA: 32, 64 or 128)
+                                    spreads fastest, per direction. 0: the width rule and
+                                    bins of 128 */
+    int32_t kernel_width;        /* 0: the width rule; 2..16: this width for every upsampling
+                                    (shape parameter from the same rule); HVOX_EINVAL else */
 } hvox_opts;
 
 /* Plan summary (filled by hvox_plan_info). */
@@ -177,6 +186,9 @@ typedef struct {
                                     = Algorithm 1's / ratio (1: the isotropic optimum) */
     int32_t spread_bin_pix;      /* points per spreading CTA, pixels (sky -> vis) */
     int32_t spread_bin_vis;      /* points per spreading CTA, baselines (vis -> sky) */
+    int32_t kernel_width_rule;   /* the width rule's kernel width at the plan's upsampling */
+    double probe_error;          /* autotune: measured error of the chosen width on the probe
+                                    sub-problem; -1 when not measured */
 } hvox_info;
 
 /*

@@ -39,7 +39,7 @@ class Opts(ctypes.Structure):
                 ("direct_threshold", ctypes.c_double), ("search_threshold", ctypes.c_double),
                 ("ntrans", ctypes.c_int32), ("plain", ctypes.c_int32),
                 ("graphs", ctypes.c_int32), ("chunk_order", ctypes.c_int32), ("stream", ctypes.c_void_p),
-                ("factor", ctypes.c_int32), ("autotune", ctypes.c_int32)]
+                ("factor", ctypes.c_int32), ("autotune", ctypes.c_int32), ("kernel_width", ctypes.c_int32)]
 
 _FACTOR = {None: 0, "auto": 0, "pixels": 1, "baselines": 2}
 
@@ -57,7 +57,8 @@ class Info(ctypes.Structure):
                 ("model_seconds", ctypes.c_double), ("graph_state", ctypes.c_int32),
                 ("nufft_pix_points", ctypes.c_double), ("nufft_vis_points", ctypes.c_double),
                 ("spread_cells", ctypes.c_double), ("fft_work", ctypes.c_double), ("box_ratio", ctypes.c_double),
-                ("spread_bin_pix", ctypes.c_int32), ("spread_bin_vis", ctypes.c_int32)]
+                ("spread_bin_pix", ctypes.c_int32), ("spread_bin_vis", ctypes.c_int32),
+                ("kernel_width_rule", ctypes.c_int32), ("probe_error", ctypes.c_double)]
 
 
 class Stats(ctypes.Structure):
@@ -189,7 +190,7 @@ def cost_model(precision="fp32", plain: bool = False) -> dict:
 
 def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: float = 0.0,
              chunk_budget_bytes: float = 0.0, direct_threshold: float = 0.0, plain: bool = False,
-             search_threshold: float = 0.0, factor=None) -> dict:
+             search_threshold: float = 0.0, factor=None, kernel_width: int = 0) -> dict:
     """Host-only planning (no GPU): partition, block choices and cost-model estimate."""
     np = _np()
     pix = np.ascontiguousarray(pix, dtype=np.float64)
@@ -203,6 +204,7 @@ def plan_dry(pix, uvw, eps: float, precision="auto", mode="auto", upsampfac: flo
     o.search_threshold = search_threshold
     o.plain = 1 if plain else 0
     o.factor = _FACTOR[factor]
+    o.kernel_width = int(kernel_width)
     inf = Info()
     _check(load().hvox_plan_dry(_dptr(pix), len(pix), _dptr(uvw), len(uvw), float(eps), ctypes.byref(o),
                                 ctypes.byref(inf)))
@@ -297,7 +299,7 @@ class Plan:
                  upsampfac: float = 0.0, chunk_budget_bytes: float = 0.0, anisotropy: float = 0.0,
                  direct_threshold: float = 0.0, ntrans: int = 1, plain: bool = False, graphs: int = 0,
                  search_threshold: float = 0.0, chunk_order: bool = False, stream=None, factor=None,
-                 autotune: bool = False):
+                 autotune: bool = False, kernel_width: int = 0):
         import torch
         lib = load()
         self._handle = ctypes.c_void_p()
@@ -318,6 +320,7 @@ class Plan:
         o.chunk_order = 1 if chunk_order else 0
         o.factor = _FACTOR[factor]
         o.autotune = 1 if autotune else 0
+        o.kernel_width = int(kernel_width)
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream

@@ -249,6 +249,93 @@ template <typename T> void tune_bins(Plan &p) {
     }
 }
 
+// The sums of a probe sub-problem (host coordinates) through the library itself, with
+// seeded values in [0, 1): V (complex, host) of sky -> vis.
+std::vector<double> probe_sums(const hvox_opts &o, const std::vector<double> &pix, const std::vector<double> &uvw,
+                               int prec, int isign) {
+    const int64_t np = (int64_t)pix.size() / 3, nv = (int64_t)uvw.size() / 3;
+    hvox_plan_t h = nullptr;
+    if (hvox_plan(pix.data(), np, uvw.data(), nv, nullptr, prec == 1 ? 1e-6 : 1e-9, isign, &o, &h) != HVOX_OK)
+        fail(HVOX_EINTERNAL, std::string("autotune probe plan: ") + get_error());
+    std::vector<double> out(2 * nv);
+    uint64_t state = 0x9E3779B97F4A7C15ull;
+    auto next = [&] {  // splitmix64 -> [0, 1)
+        uint64_t z = (state += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return (double)((z ^ (z >> 31)) >> 11) * 0x1.0p-53;
+    };
+    hvox_status st;
+    if (prec == 1) {
+        std::vector<float> I(np), V(2 * nv);
+        for (auto &x : I) x = (float)next();
+        st = hvox_synthesize(h, I.data(), V.data());
+        for (int64_t k = 0; k < 2 * nv; ++k) out[k] = V[k];
+    } else {
+        std::vector<double> I(np);
+        for (auto &x : I) x = next();
+        st = hvox_synthesize(h, I.data(), out.data());
+    }
+    const std::string msg = get_error();
+    hvox_destroy(h);
+    if (st != HVOX_OK) fail(HVOX_EINTERNAL, "autotune probe transform: " + msg);
+    return out;
+}
+
+// Autotuned kernel width: the width rule of Barnett, Magland and af Klinteberg is an upper
+// bound. The NUFFT sub-problem with the most points is taken as a probe (its pixels, and
+// up to 2,048 of its baselines evenly spaced), evaluated by direct sums of the plan's
+// precision (FP32 ~1e-7, double-float ~3e-10) and by a single type-3 NUFFT at the planned
+// upsampling with widths w_rule - 2 and w_rule - 1; the narrowest whose relative l2 error
+// is within 2.5 eps (a quarter of the bound the plan answers for, which sums many
+// sub-problems) is kept, else the rule's width. The measured error is kept for the plan
+// info.
+int tune_width(Plan &p, const std::vector<double> &pix, const std::vector<double> &uvw) {
+    const PartitionResult &part = p.part;
+    size_t bi = 0;
+    for (size_t i = 1; i < part.blocks.size(); ++i) {
+        const NufftBlock &a = part.blocks[i], &b = part.blocks[bi];
+        if ((a.p1 - a.p0) + (a.v1 - a.v0) > (b.p1 - b.p0) + (b.v1 - b.v0)) bi = i;
+    }
+    const NufftBlock &b = part.blocks[bi];
+    std::vector<double> ppix, puvw;
+    for (int64_t m = b.p0; m < b.p1; ++m)
+        for (int d = 0; d < 3; ++d) ppix.push_back(pix[3 * part.pix_perm[m] + d]);
+    const int64_t nv = b.v1 - b.v0, take = std::min<int64_t>(nv, 2048);
+    for (int64_t t = 0; t < take; ++t) {
+        const int64_t m = b.v0 + t * nv / take;
+        for (int d = 0; d < 3; ++d) puvw.push_back(uvw[3 * part.vis_perm[m] + d]);
+    }
+    hvox_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.precision = p.prec;
+    o.graphs = -1;
+    o.stream = p.stream;
+    o.mode = HVOX_MODE_DIRECT;
+    const std::vector<double> ref = probe_sums(o, ppix, puvw, p.prec, p.isign);
+    double nref = 0.0;
+    for (double x : ref) nref += x * x;
+    auto rel_err = [&](const std::vector<double> &v) {
+        double e = 0.0;
+        for (size_t k = 0; k < v.size(); ++k) e += (v[k] - ref[k]) * (v[k] - ref[k]);
+        return nref > 0.0 ? std::sqrt(e / nref) : std::sqrt(e);
+    };
+    o.mode = HVOX_MODE_NUFFT;
+    o.upsampfac = part.sigma;
+    o.chunk_budget_bytes = 1e15;  // one sub-problem
+    const double tol = 2.5 * std::max(p.eps, 1e-12);
+    const int rule = part.es.w;
+    for (int w = std::max(2, rule - 2); w <= rule; ++w) {
+        o.kernel_width = w;
+        const double err = rel_err(probe_sums(o, ppix, puvw, p.prec, p.isign));
+        if (err <= tol || w == rule) {
+            p.probe_error = err;
+            return w;
+        }
+    }
+    return rule;
+}
+
 void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const double *w_in) {
     auto t0 = std::chrono::steady_clock::now();
     cudaStream_t s = p.stream;
@@ -278,6 +365,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     in.sigma_auto = p.sigma_auto;
     in.eps_es = p.eps_es;
     in.factor = p.factor;
+    in.fixed_w = p.fixed_w;
     {
         // Up to kMaxLanes lanes each hold the grids of a wave (at least one sub-problem's)
         // and a cuFFT work area of about the same size: keep that within a third of the
@@ -287,6 +375,18 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         in.max_budget = (double)free_b / (3.0 * 2.0 * kMaxLanes);
     }
     p.part = make_partition(in);
+    if (p.autotune && !p.fixed_w && !p.plain && !p.part.blocks.empty()) {
+        // Measured kernel width: re-plan at the chosen upsampling with a narrower kernel
+        // when the probe sub-problem meets the tolerance with it.
+        const int w = tune_width(p, pix, uvw);
+        if (w != p.part.es.w) {
+            in.fixed_w = w;
+            in.sigma = p.part.sigma;
+            in.es = es_with_width(w, in.sigma);
+            in.sigma_auto = false;
+            p.part = make_partition(in);
+        }
+    }
     PartitionResult &part = p.part;
     p.sigma = part.sigma;
     p.es = part.es;
@@ -617,6 +717,9 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.factor = o.factor;
     if (o.autotune < 0 || o.autotune > 1) fail(HVOX_EINVAL, "hvox_plan: autotune must be 0 or 1");
     p.autotune = o.autotune != 0;
+    if (o.kernel_width != 0 && (o.kernel_width < 2 || o.kernel_width > 16))
+        fail(HVOX_EINVAL, "hvox_plan: kernel_width must be 0 or in [2, 16]");
+    p.fixed_w = o.kernel_width;
     p.n_pix = n_pix;
     p.n_vis = n_vis;
     p.eps = eps;
@@ -639,7 +742,7 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     if (p.prec == 1 && e < 1e-7) fail(HVOX_EUNSUPPORTED, "hvox_plan: FP32 cannot reach eps < 1e-7");
     p.eps_es = e * (p.prec == 1 ? kEpsMarginF32 : kEpsMarginF64);
     p.direct_f64 = p.plain || (p.prec == 2 && e < kDoubleFloatMinEps);
-    p.es = es_params_within(p.eps_es, e, p.sigma);
+    p.es = p.fixed_w ? es_with_width(p.fixed_w, p.sigma) : es_params_within(p.eps_es, e, p.sigma);
     // Points per thread of the direct kernels (tuning knob; 2 or 4).
     if (const char *v = std::getenv("HVOX_DIRECT_VPT")) p.direct_vpt = std::atoi(v) == 4 ? 4 : 2;
 }
@@ -679,6 +782,8 @@ void fill_info(const Plan &p, hvox_info *info) {
     info->box_ratio = p.part.box_ratio;
     info->spread_bin_pix = p.ppc_pix;
     info->spread_bin_vis = p.ppc_vis;
+    info->kernel_width_rule = es_params_within(p.eps_es, p.eps > 0 ? p.eps : 1e-6, p.sigma).w;
+    info->probe_error = p.probe_error;
 }
 
 void transform(Plan &p, const void *in, void *out, bool s2v) {
@@ -884,6 +989,8 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         in.sigma_auto = p.sigma_auto;
         in.eps_es = p.eps_es;
         in.factor = p.factor;
+        in.fixed_w = p.fixed_w;
+    in.fixed_w = p.fixed_w;
         p.part = make_partition(in);
         p.sigma = p.part.sigma;
         p.es = p.part.es;

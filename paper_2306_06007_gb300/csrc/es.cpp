@@ -25,6 +25,14 @@ ESKernel es_params(double eps, double sigma) {
     return k;
 }
 
+ESKernel es_with_width(int w, double sigma) {
+    if (w < 2 || w > 16 || !(sigma > 1.0)) fail(HVOX_EINVAL, "es_with_width: need 2 <= w <= 16 and sigma > 1");
+    ESKernel k;
+    k.w = w;
+    k.beta = 0.97 * M_PI * k.w * (1.0 - 1.0 / (2.0 * sigma));
+    return k;
+}
+
 ESKernel es_params_within(double eps_tight, double eps, double sigma) {
     if (es_width(eps_tight, sigma) <= 16) return es_params(eps_tight, sigma);
     ESKernel k = es_params(eps, sigma);  // refuses tolerances beyond a 16-cell kernel

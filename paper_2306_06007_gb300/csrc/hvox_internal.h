@@ -57,6 +57,7 @@ struct ESKernel {
 
 ESKernel es_params(double eps, double sigma);
 int es_width(double eps, double sigma);  // the width rule of es_params, without its limit of 16
+ESKernel es_with_width(int w, double sigma);  // a caller-fixed width, the same shape rule
 // The kernel for the tightened tolerance eps_tight, or the 16-cell kernel when that one
 // would be wider and eps itself fits in 16 cells (a caller-fixed upsampling).
 ESKernel es_params_within(double eps_tight, double eps, double sigma);
@@ -150,6 +151,7 @@ struct PlanInputs {
     double search_threshold = 0.01;  // seconds of modelled direct work below which no search
     int elem_bytes;
     int factor = 0;        // hvox_opts.factor: 0 searched, 1 one baseline box, 2 one pixel box
+    int fixed_w = 0;       // > 0: kernel width for every upsampling (shape from the width rule)
 };
 
 PartitionResult make_partition(const PlanInputs &in);
@@ -304,6 +306,8 @@ struct Plan {
     double search_threshold = 0.01; // search_threshold option (seconds)
     int factor = 0;                // factor option
     bool autotune = false;         // autotune option
+    int fixed_w = 0;               // kernel_width option (0: the width rule)
+    double probe_error = -1.0;     // measured error of the chosen width on the autotuner's probe
     int ppc_pix = 128, ppc_vis = 128;  // points per spreading CTA (bin size) of each direction
     ESKernel es;
     bool has_weight = false;

@@ -418,8 +418,10 @@ PartitionResult make_partition(const PlanInputs &in) {
         std::vector<double> sigmas = in.sigma_auto ? std::vector<double>{2.0, 1.5, 1.25} : std::vector<double>{in.sigma};
         for (double sg : sigmas) {
             // an upsampling whose kernel would be wider than 16 cells is not a candidate
-            if (in.sigma_auto && es_width(in.eps_es, sg) > 16) continue;
-            const ESKernel es = in.sigma_auto ? es_params(in.eps_es, sg) : in.es;
+            if (in.sigma_auto && !in.fixed_w && es_width(in.eps_es, sg) > 16) continue;
+            const ESKernel es = !in.sigma_auto ? in.es
+                                : in.fixed_w   ? es_with_width(in.fixed_w, sg)
+                                               : es_params(in.eps_es, sg);
             if (in.sigma_auto && in.prec == 1 && sg != sigmas.front()) {
                 // FP32 grids: rounding errors near the band edge are divided twice by the
                 // kernel transform (1/Psi before the FFT, 1/Phi after the interpolation),

@@ -445,3 +445,24 @@ def test_factored_plans_match_oracle(gpu_lib, small, factor):
     assert info["n_vis_chunks" if factor == "pixels" else "n_pix_chunks"] == 1 and info["n_nufft_blocks"] > 1
     assert oracle.rel_l2(V, oracle.sky2vis(w.pix, w.uvw, w.sky)) <= 1e-5
     assert oracle.rel_l2(img, oracle.vis2sky(w.pix, w.uvw, y)) <= 1e-5
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6, 1e-9])
+def test_autotuned_width_meets_the_bound(gpu_lib, eps):
+    # The autotuner may narrow the kernel below the width rule when its probe sub-problem
+    # measures within 2.5 eps; the whole job must still meet the 10 eps bound.
+    w = configs.radius_sweep(1.0)
+    plan = gpu_lib.Plan(w.pix, w.uvw, eps, mode="nufft", autotune=True)
+    info = plan.info()
+    V = plan.synthesize(torch.as_tensor(w.sky, dtype=plan.real_dtype, device="cuda")).cpu().numpy()
+    vis = configs.visibilities_cn(6, w.n_vis)
+    img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
+    plan.close()
+    assert info["w"] <= info["kernel_width_rule"] and 0.0 <= info["probe_error"] <= 2.5 * eps
+    kv = configs.sample_indices(6, w.n_vis, 300)
+    kp = configs.sample_indices(6, w.n_pix, 300, purpose_offset=1)
+    e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
+    e_i = oracle.rel_l2(img[kp], oracle.vis2sky(w.pix, w.uvw, vis, sample=kp))
+    print(f"autotuned width eps={eps:g}: w {info['w']} (rule {info['kernel_width_rule']}), probe "
+          f"{info['probe_error']:.2e}, rel_l2 sky->vis {e_v:.2e} vis->sky {e_i:.2e}")
+    assert e_v <= 10 * eps and e_i <= 10 * eps

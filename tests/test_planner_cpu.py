@@ -106,3 +106,15 @@ def test_factored_plans_span_the_other_set(lib, factor, which):
     assert f[which] == 1
     assert abs(f["t"] - base["t"]) < 1e-12  # the same grid budget per sub-problem
     assert (f["box_ratio"] < 1.0) == (factor == "pixels")
+
+
+def test_caller_fixed_kernel_width(lib):
+    # hvox_opts.kernel_width fixes the width for every upsampling the search tries (the
+    # shape parameter from the same rule); the rule's own width is reported beside it.
+    w = configs.radius_sweep(1.0)
+    rule = hvox.plan_dry(w.pix, w.uvw, 1e-6, mode="nufft")
+    fixed = hvox.plan_dry(w.pix, w.uvw, 1e-6, mode="nufft", kernel_width=rule["w"] - 1)
+    assert fixed["w"] == rule["w"] - 1
+    assert fixed["kernel_width_rule"] == rule["w"] or fixed["upsampfac"] != rule["upsampfac"]
+    with pytest.raises(hvox.HvoxError):
+        hvox.plan_dry(w.pix, w.uvw, 1e-6, kernel_width=17)
