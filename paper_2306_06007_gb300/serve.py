@@ -99,7 +99,8 @@ class Server:
         self.plain = plain
         self.keep_plans = keep_plans
         # A request's plan is usually used once: skip the partition search for jobs whose
-        # direct evaluation is modelled below this many seconds (it costs ~1-3 us a point).
+        # direct evaluation is modelled below this many seconds, or below the search's own
+        # cost (~2 us a point, see _threshold).
         # The plain form's direct sums are ~100x slower, but a one-shot plan with NUFFT
         # sub-problems also pays for the search, its grids and cuFFT plans: on the
         # benchmark's stream (N up to 3e4) planning plain requests with a 0.1 s threshold
@@ -113,19 +114,26 @@ class Server:
         self.used = 0.0
 
     # ------------------------------------------------------------------ plans
+    # Seconds of partition search per point (both point sets; measured on a 16-core host):
+    # a one-shot plan searches only when its direct work could repay that.
+    SEARCH_SECONDS_PER_POINT = 2e-6
+
+    def _threshold(self, req) -> float:
+        return max(self.search_threshold, self.SEARCH_SECONDS_PER_POINT * (len(req.pix) + len(req.uvw)))
+
     def _make_plan(self, req):
         import torch
         t0 = time.perf_counter()
         stream = torch.cuda.Stream()
         plan = Plan(req.pix, req.uvw, req.eps, plain=self.plain, stream=stream,
-                    search_threshold=self.search_threshold)
+                    search_threshold=self._threshold(req))
         info = plan.info()
         return plan, stream, info["workspace_bytes"], time.perf_counter() - t0
 
     def _estimate_plan_bytes(self, req) -> float:
         # Upper bound of what planning may allocate (the plan's own figure replaces it).
         return estimate_bytes(len(req.pix), len(req.uvw), req.eps, plain=self.plain,
-                              search_threshold=self.search_threshold)
+                              search_threshold=self._threshold(req))
 
     def _evict_idle(self, need: float, protect: set):
         for key, r in sorted(self.resident.items(), key=lambda kv: kv[1].last_used):
