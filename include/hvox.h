@@ -189,6 +189,9 @@ typedef struct {
     int32_t kernel_width_rule;   /* the width rule's kernel width at the plan's upsampling */
     double probe_error;          /* autotune: measured error of the chosen width on the probe
                                     sub-problem; -1 when not measured */
+    int32_t fft_batches;         /* batched FFTs of a transform (one per grid shape and wave) */
+    int32_t fft_batches_df;      /* of those, FP64 grids transformed in double-float arithmetic
+                                    on the FP32 pipes (the rest: cuFFT) */
 } hvox_info;
 
 /*

@@ -12,7 +12,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OBJ = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhvox.so")
-SOURCES = ["abi.cpp", "exec.cpp", "planner.cpp", "es.cpp", "k_direct.cu", "k_nufft.cu", "k_misc.cu"]
+SOURCES = ["abi.cpp", "exec.cpp", "planner.cpp", "es.cpp", "k_direct.cu", "k_nufft.cu", "k_misc.cu", "k_dffft.cu"]
 # Throughput probes for the benchmark's roofline denominators (a library of their own).
 PEAKS_LIB = os.path.join(HERE, "libhvox_peaks.so")
 PEAKS_SOURCES = ["peaks.cu"]

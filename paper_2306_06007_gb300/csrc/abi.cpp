@@ -577,6 +577,9 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         // selects full 3-D plans instead of the pruned pair.
         bool prune = true;
         if (const char *v = std::getenv("HVOX_FFT_PRUNE")) prune = std::atoi(v) != 0;
+        // HVOX_DF_FFT=0 keeps cuFFT Z2Z for FP64 grids (for comparisons).
+        bool use_dfft = true;
+        if (const char *v = std::getenv("HVOX_DF_FFT")) use_dfft = std::atoi(v) != 0;
         std::vector<size_t> max_ws(n_lanes, 0);
         auto make = [&](cufftHandle &h, int rank, long long *n, long long *emb, long long stride, long long dist,
                         long long batch, size_t &ws) {
@@ -605,9 +608,29 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                 for (int d = 0; d < 3; ++d) fb.n2[d] = first.n2[d];
                 fb.half = first.n1[2] / 2;
                 fb.K = K;
+                fb.h1y = first.n1[1] / 2;
                 const int64_t plane = first.n2[0] * first.n2[1];
+                // FP64 grids: the double-float FFT on the FP32 pipes where it covers the shape.
+                // Its ~48-bit significands hold to eps >= 1e-11; tighter plans, and the plain
+                // FP64 form, keep cuFFT Z2Z.
+                fb.df = p.prec == 2 && !p.plain && use_dfft && prune && p.eps >= 1e-11 && dfft_supported(fb.n2);
+                if (fb.df) {
+                    DfftDev *dd[3] = {&fb.dx, &fb.dy, &fb.dz};
+                    for (int q = 0; q < 3; ++q) {
+                        const int n = (int)fb.n2[q];
+                        dfft_factor(n, *dd[q]);
+                        auto &tab = p.dfft_tw[n];
+                        if (!tab) {
+                            std::vector<float> t;
+                            dfft_twiddles(n, t);
+                            tab = std::make_unique<DevBuf>();
+                            upload(*tab, t.data(), t.size() * sizeof(float), s);
+                        }
+                        dd[q]->tw = tab->as<float4>();
+                    }
+                }
                 auto key = std::make_tuple(fb.n2[0], fb.n2[1], fb.n2[2], prune ? fb.half : (int64_t)-1, (int64_t)K);
-                if (!lane.fft.count(key)) {
+                if (!fb.df && !lane.fft.count(key)) {
                     FftPlans &f = lane.fft[key];
                     size_t ws = 0;
                     if (prune) {
@@ -623,7 +646,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                     }
                     max_ws[w.lane] = std::max(max_ws[w.lane], ws);
                 }
-                fb.plans = lane.fft[key];
+                if (!fb.df) fb.plans = lane.fft[key];
                 w.ffts.push_back(fb);
                 for (int g = 0; g < K; ++g, ++k) {
                     const NufftBlock &bk = part.blocks[order[w.b0 + k]];
@@ -693,6 +716,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                       &p.vis_lo, &p.items_s2v, &p.items_v2s, &p.item_counter, &p.inv_psi, &p.cheb, &p.src, &p.acc, &p.cis_tab, &p.err})
         ws += (double)b->bytes;
     for (auto &l : p.lanes) ws += (double)(l->g1.bytes + l->g2.bytes + l->work.bytes);
+    for (auto &kv : p.dfft_tw) ws += (double)kv.second->bytes;
     p.workspace_bytes = ws;
     p.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
 }
@@ -784,6 +808,12 @@ void fill_info(const Plan &p, hvox_info *info) {
     info->spread_bin_vis = p.ppc_vis;
     info->kernel_width_rule = es_params_within(p.eps_es, p.eps > 0 ? p.eps : 1e-6, p.sigma).w;
     info->probe_error = p.probe_error;
+    info->fft_batches = info->fft_batches_df = 0;
+    for (const Wave &w : p.waves)
+        for (const FftBatch &f : w.ffts) {
+            ++info->fft_batches;
+            info->fft_batches_df += f.df ? 1 : 0;
+        }
 }
 
 void transform(Plan &p, const void *in, void *out, bool s2v) {

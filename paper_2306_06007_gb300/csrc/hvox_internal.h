@@ -199,6 +199,15 @@ struct FftPlans {
     cufftHandle full = 0, xy = 0, z = 0;
 };
 
+// One length of the double-float FFT (k_dffft.cu): radices of its Stockham stages and its
+// twiddle table exp(2 pi i q / n), q < n, as float pairs (cos h, cos l, sin h, sin l).
+constexpr int kDfftMaxStages = 16;
+struct DfftDev {
+    int n = 0, stages = 0;
+    int radix[kDfftMaxStages] = {0};
+    const float4 *tw = nullptr;
+};
+
 // The batched transforms of K sub-problems of one grid shape inside a wave: their FFT
 // grids interleave z planes (plane z of grid g at g2 + (z K + g) * n2x n2y), so that each
 // band slab of all K grids is one contiguous run of planes (one batched 2-D call) and
@@ -209,7 +218,18 @@ struct FftBatch {
     int64_t half = 0;         // n1z / 2
     int64_t K = 1;
     FftPlans plans;
+    bool df = false;          // FP64 grids through the double-float FFT instead of cuFFT Z2Z
+    DfftDev dx, dy, dz;       // its three lengths
+    int64_t h1y = 0;          // n1y / 2: the band rows are [0, h1y) and [n2y - h1y, n2y)
 };
+
+// Double-float FFT (k_dffft.cu): radices of length n (false when a factor other than 2, 3,
+// 5, 7 remains), whether a grid shape is covered, the twiddle table of a length, and the
+// batched pruned 3-D transform of one batch (sign -1 or +1; band_input as fft_batch).
+bool dfft_factor(int n, DfftDev &d);
+bool dfft_supported(const int64_t n2[3]);
+void dfft_twiddles(int n, std::vector<float> &tab);
+int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s);
 
 // A wave: sub-problems [b0, b0 + nb) of the plan's descriptor array, run together: one
 // clearing, spreading, deconvolution and interpolation launch each (a 2-D launch grid over
@@ -338,6 +358,7 @@ struct Plan {
     std::vector<NufftDev> dblocks;      // block descriptors (wave order)
     DevBuf ddescs;                      // the same descriptors on the device
     std::vector<Wave> waves;            // waves of blocks (launch order)
+    std::map<int, std::unique_ptr<DevBuf>> dfft_tw;  // twiddle tables of the double-float FFT
     DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
     DevBuf err;                         // int: device error word (kDevErr* bits), read by hvox_sync
 

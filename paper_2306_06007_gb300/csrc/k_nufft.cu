@@ -855,6 +855,7 @@ template <typename T, int W> void set_smem_attrs() {
 // otherwise only those planes are read afterwards (vis -> sky: z first, then 2-D).
 // Returns the number of cuFFT executions.
 template <typename T> int fft_batch(const FftBatch &f, int dir, bool band_input, cudaStream_t s) {
+    if (f.df) return dfft_batch(f, dir, band_input, s);
     auto exec = [&](cufftHandle h, void *g) {
         check_cufft(cufftSetStream(h, s), "cufftSetStream");
         if constexpr (sizeof(T) == 4)
