@@ -44,27 +44,44 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
     e = __fsub_rn(b, __fsub_rn(s, a));
 }
 
-// Accurate double-float sum (both parts summed with error-free transformations).
+// Double-float sum: an exact TwoSum of the high parts, the low parts added in FP32, then
+// renormalised (the "sloppy" sum of Dekker 1971 / QD). Its error is bounded by ~2^-47 of
+// |a| + |b|, which is the norm-wise bound an FFT needs (an exactly-rounded sum would cost
+// twice the instructions).
 __device__ __forceinline__ DF dadd(DF a, DF b) {
-    float s, e, t, f;
+    float s, e;
     two_sum(a.h, b.h, s, e);
-    two_sum(a.l, b.l, t, f);
-    e = __fadd_rn(e, t);
-    fast_two_sum(s, e, s, e);
-    e = __fadd_rn(e, f);
+    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
     fast_two_sum(s, e, s, e);
     return {s, e};
 }
 
 __device__ __forceinline__ DF dneg(DF a) { return {-a.h, -a.l}; }
 
+// a b as an unnormalised pair (p, e): p = fl(a.h b.h), e = the rounding error of p (FMA,
+// exact) + the cross terms (a.l b.l, below 2^-46 of the product, is dropped).
+__device__ __forceinline__ void dmul_raw(DF a, DF b, float &p, float &e) {
+    p = __fmul_rn(a.h, b.h);
+    e = __fmaf_rn(a.l, b.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.h, b.h, -p)));
+}
+
 __device__ __forceinline__ DF dmul(DF a, DF b) {
-    const float p = __fmul_rn(a.h, b.h);
-    float e = __fmaf_rn(a.h, b.h, -p);
-    e = __fmaf_rn(a.h, b.l, __fmaf_rn(a.l, b.h, e));
-    float s;
+    float p, e, s;
+    dmul_raw(a, b, p, e);
     fast_two_sum(p, e, s, e);
     return {s, e};
+}
+
+// a b + sg c d for sg = +-1, with one renormalisation (the real or imaginary part of a
+// complex product).
+__device__ __forceinline__ DF dmul2(DF a, DF b, DF c, DF d, float sg) {
+    float p, e, q, f, s, t;
+    dmul_raw(a, b, p, e);
+    dmul_raw(c, d, q, f);
+    two_sum(p, sg * q, s, t);
+    t = __fadd_rn(t, __fmaf_rn(sg, f, e));
+    fast_two_sum(s, t, s, t);
+    return {s, t};
 }
 
 __device__ __forceinline__ DC cadd(const DC &a, const DC &b) { return {dadd(a.re, b.re), dadd(a.im, b.im)}; }
@@ -72,7 +89,7 @@ __device__ __forceinline__ DC csub(const DC &a, const DC &b) { return {dadd(a.re
 
 // a * (c + j s) for real double-float c, s.
 __device__ __forceinline__ DC cmul(const DC &a, DF c, DF s) {
-    return {dadd(dmul(a.re, c), dneg(dmul(a.im, s))), dadd(dmul(a.re, s), dmul(a.im, c))};
+    return {dmul2(a.re, c, a.im, s, -1.f), dmul2(a.re, s, a.im, c, 1.f)};
 }
 
 // a * (j sg) for sg = +-1.
@@ -83,17 +100,54 @@ __device__ __forceinline__ DC times_j(const DC &a, float sg) {
 __device__ __forceinline__ DC from4(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 __device__ __forceinline__ float4 to4(const DC &c) { return make_float4(c.re.h, c.re.l, c.im.h, c.im.l); }
 
-__device__ __forceinline__ DF split(double x) {
-    const float h = __double2float_rn(x);
-    return {h, __double2float_rn(x - (double)h)};
+// FP64 <-> double-float by bit manipulation: GB300 issues FP64 instructions (conversions
+// included) at 1/64 of its FP32 rate, more than the transform's own arithmetic.
+// split: hi = x truncated to 24 significant bits (exact), lo = the remaining 29 bits of the
+// significand rounded to 24 (one integer-to-float conversion and an exact power-of-two
+// scale). |x| below 2^-126 flushes to 0, lo below 2^-126 too (|x| < 2^-102 keeps fewer
+// bits); |x| >= 2^128 becomes infinite.
+__device__ __forceinline__ DF split_bits(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
+    const unsigned sign = hi32 & 0x80000000u;
+    const int e = (int)((hi32 >> 20) & 0x7FFu) - 896;  // biased float exponent (1023 - 127)
+    if (e <= 0) return {0.f, 0.f};
+    if (e >= 255) return {__uint_as_float(sign | 0x7F800000u), 0.f};
+    const float h = __uint_as_float(sign | ((unsigned)e << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
+    // lo = r 2^(E - 1075) with E the double's biased exponent = (r 2^-29) 2^(e - 150); the
+    // second factor is a normal float (biased exponent e - 23) for e >= 24.
+    const float scale = e >= 24 ? __uint_as_float(sign | ((unsigned)(e - 23) << 23)) : 0.f;
+    return {h, __fmul_rn(__fmul_rn(__uint2float_rn(lo32 & 0x1FFFFFFFu), 0x1p-29f), scale)};
 }
-__device__ __forceinline__ float4 load_cell(const double2 *p) {
+
+// A float as the double of the same value (exact; subnormal floats, below 2^-126, as 0).
+__device__ __forceinline__ double f2d_bits(float f) {
+    const unsigned u = __float_as_uint(f);
+    const unsigned ef = (u >> 23) & 0xFFu;
+    if (ef == 0) return 0.0;
+    const unsigned long long E = ef == 255 ? 2047ull : (unsigned long long)(ef + 896);
+    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) | (E << 52) |
+                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
+}
+
+__device__ __forceinline__ float4 load_f64(const double2 *p) {
     const double2 v = *p;
-    const DF re = split(v.x), im = split(v.y);
+    const DF re = split_bits(v.x), im = split_bits(v.y);
     return make_float4(re.h, re.l, im.h, im.l);
 }
-__device__ __forceinline__ void store_cell(double2 *p, float4 v) {
-    *p = make_double2((double)v.x + (double)v.y, (double)v.z + (double)v.w);
+__device__ __forceinline__ void store_f64(double2 *p, float4 v) {
+    *p = make_double2(f2d_bits(v.x) + f2d_bits(v.y), f2d_bits(v.z) + f2d_bits(v.w));
+}
+
+// A grid cell in either format: FP64 (double2) or, between the passes of one transform, the
+// double-float form itself (float4 of the same 16 bytes; zero is all-zero bits in both).
+template <bool F64> __device__ __forceinline__ float4 load_cell(double2 *p) {
+    if constexpr (F64) return load_f64(p);
+    else return *reinterpret_cast<const float4 *>(p);
+}
+template <bool F64> __device__ __forceinline__ void store_cell(double2 *p, float4 v) {
+    if constexpr (F64) store_f64(p, v);
+    else *reinterpret_cast<float4 *>(p) = v;
 }
 
 // Twiddle exp(s 2 pi i e / n) from the table of exp(2 pi i q / n) (cos h, cos l, sin h, sin l).
@@ -201,6 +255,8 @@ __device__ __forceinline__ int64_t band_plane(int64_t P, int64_t halfK, int64_t 
 }
 
 // Rows (x): sequence s = (band plane P, row R) with R over all n2y rows or only the band rows.
+// IN64 / OUT64: the grid holds FP64 values before / after the pass (else double-float).
+template <bool IN64, bool OUT64>
 __global__ void __launch_bounds__(kFftThreads) dfft_rows_kernel(double2 *__restrict__ g, DfftDev d, int64_t n2y,
                                                                  int64_t halfK, int64_t n2z, int64_t K, int64_t half,
                                                                  int64_t rows, int64_t h1y, float sg) {
@@ -211,15 +267,15 @@ __global__ void __launch_bounds__(kFftThreads) dfft_rows_kernel(double2 *__restr
     const int64_t y = h1y > 0 ? (R < h1y ? R : n2y - h1y + (R - h1y)) : R;
     double2 *row = g + (band_plane(P, halfK, n2z, K, half) * n2y + y) * n;
     float4 *a = smem, *b = smem + n;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = load_cell(row + i);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = load_cell<IN64>(row + i);
     __syncthreads();
     const float4 *out = fft_smem<1>(a, b, d, sg);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) store_cell(row + i, out[i]);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) store_cell<OUT64>(row + i, out[i]);
 }
 
 // Columns: TX adjacent columns starting at column c0 of a plane (y: columns of one band plane,
 // stride n2x; z: every column of the batch, stride K n2x n2y), element q at c + q * stride.
-template <int TX>
+template <int TX, bool IN64, bool OUT64>
 __global__ void __launch_bounds__(kFftThreads) dfft_cols_kernel(double2 *__restrict__ g, DfftDev d, int64_t stride,
                                                                  int64_t ncols, int64_t plane_cells, int64_t halfK,
                                                                  int64_t n2z, int64_t K, int64_t half, int band,
@@ -233,13 +289,13 @@ __global__ void __launch_bounds__(kFftThreads) dfft_cols_kernel(double2 *__restr
     float4 *a = smem, *b = smem + (size_t)n * TX;
     for (int e = threadIdx.x; e < n * TX; e += blockDim.x) {
         const int q = e / TX, t = e - q * TX;
-        a[e] = t < valid ? load_cell(base + q * stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        a[e] = t < valid ? load_cell<IN64>(base + q * stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
     const float4 *out = fft_smem<TX>(a, b, d, sg);
     for (int e = threadIdx.x; e < n * TX; e += blockDim.x) {
         const int q = e / TX, t = e - q * TX;
-        if (t < valid) store_cell(base + q * stride + t, out[e]);
+        if (t < valid) store_cell<OUT64>(base + q * stride + t, out[e]);
     }
 }
 
@@ -250,14 +306,24 @@ template <typename K> void allow_smem(K kernel) {
                "cudaFuncSetAttribute");
 }
 
+// Cell formats of a pass: kDD double-float in and out, kFD FP64 in, kDF FP64 out.
+enum Io { kDD = 0, kFD = 1, kDF = 2 };
+
+template <int TX> void allow_cols() {
+    allow_smem(dfft_cols_kernel<TX, false, false>);
+    allow_smem(dfft_cols_kernel<TX, true, false>);
+    allow_smem(dfft_cols_kernel<TX, false, true>);
+}
+
 void set_fft_attrs() {
     static std::once_flag once;
     std::call_once(once, [] {
-        allow_smem(dfft_rows_kernel);
-        allow_smem(dfft_cols_kernel<1>);
-        allow_smem(dfft_cols_kernel<2>);
-        allow_smem(dfft_cols_kernel<8>);
-        allow_smem(dfft_cols_kernel<64>);
+        allow_smem(dfft_rows_kernel<true, false>);
+        allow_smem(dfft_rows_kernel<false, true>);
+        allow_cols<1>();
+        allow_cols<2>();
+        allow_cols<8>();
+        allow_cols<64>();
     });
 }
 
@@ -269,23 +335,32 @@ int cols_per_cta(int n, int want) {
     return 0;
 }
 
-template <int TX>
+template <int TX, bool IN64, bool OUT64>
 void launch_cols(double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells, int64_t planes,
                  int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, float sg, cudaStream_t s) {
     const int64_t tiles = (ncols + TX - 1) / TX;
     const size_t smem = (size_t)2 * d.n * TX * sizeof(float4);
-    dfft_cols_kernel<TX><<<(unsigned)(planes * tiles), kFftThreads, smem, s>>>(g, d, stride, ncols, plane_cells, halfK,
-                                                                               n2z, K, half, band, sg);
+    dfft_cols_kernel<TX, IN64, OUT64><<<(unsigned)(planes * tiles), kFftThreads, smem, s>>>(
+        g, d, stride, ncols, plane_cells, halfK, n2z, K, half, band, sg);
     check_cuda(cudaGetLastError(), "dfft_cols");
 }
 
-void cols(int tx, double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells, int64_t planes,
-          int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, float sg, cudaStream_t s) {
+template <int TX>
+void launch_cols_io(Io io, double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells,
+                    int64_t planes, int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, float sg,
+                    cudaStream_t s) {
+    if (io == kFD) launch_cols<TX, true, false>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s);
+    else if (io == kDF) launch_cols<TX, false, true>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s);
+    else launch_cols<TX, false, false>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s);
+}
+
+void cols(int tx, Io io, double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells,
+          int64_t planes, int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, float sg, cudaStream_t s) {
     switch (tx) {
-        case 64: launch_cols<64>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
-        case 8: launch_cols<8>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
-        case 2: launch_cols<2>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
-        default: launch_cols<1>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
+        case 64: launch_cols_io<64>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
+        case 8: launch_cols_io<8>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
+        case 2: launch_cols_io<2>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
+        default: launch_cols_io<1>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
     }
 }
 
@@ -330,27 +405,32 @@ int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s) {
     const int64_t n2x = f.n2[0], n2y = f.n2[1], n2z = f.n2[2], K = f.K, half = f.half;
     const int64_t halfK = half * K, band_planes = 2 * halfK, plane = n2x * n2y;
     const float sg = (float)sign;
-    auto rows = [&](bool band_rows) {
-        const int64_t r = band_rows ? 2 * f.h1y : n2y;
+    // The grid is FP64 before the first pass and after the last; in between it holds the
+    // double-float values.
+    auto rows = [&](Io io) {
+        const int64_t r = 2 * f.h1y;  // band rows only
         const size_t smem = (size_t)2 * n2x * sizeof(float4);
-        dfft_rows_kernel<<<(unsigned)(band_planes * r), kFftThreads, smem, s>>>(
-            g, f.dx, n2y, halfK, n2z, K, half, r, band_rows ? f.h1y : 0, sg);
+        const unsigned grid = (unsigned)(band_planes * r);
+        if (io == kFD)
+            dfft_rows_kernel<true, false><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
+        else
+            dfft_rows_kernel<false, true><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
         check_cuda(cudaGetLastError(), "dfft_rows");
     };
     auto ycols = [&] {
-        cols(cols_per_cta((int)n2y, 2), g, f.dy, n2x, n2x, plane, band_planes, halfK, n2z, K, half, 1, sg, s);
+        cols(cols_per_cta((int)n2y, 2), kDD, g, f.dy, n2x, n2x, plane, band_planes, halfK, n2z, K, half, 1, sg, s);
     };
-    auto zcols = [&] {
-        cols(cols_per_cta((int)n2z, 64), g, f.dz, K * plane, K * plane, 0, 1, halfK, n2z, K, half, 0, sg, s);
+    auto zcols = [&](Io io) {
+        cols(cols_per_cta((int)n2z, 64), io, g, f.dz, K * plane, K * plane, 0, 1, halfK, n2z, K, half, 0, sg, s);
     };
     if (band_input) {  // only the band rows of the band planes are nonzero
-        rows(true);
+        rows(kFD);
         ycols();
-        zcols();
+        zcols(kDF);
     } else {  // only the band rows of the band planes are read afterwards
-        zcols();
+        zcols(kFD);
         ycols();
-        rows(true);
+        rows(kDF);
     }
     return 3;
 }
