@@ -189,6 +189,16 @@ constexpr double kEpsMarginF64 = 0.1;
 // sums use the FP64 kernels.
 constexpr double kDoubleFloatMinEps = 1e-9;
 
+// FP64 plans transform their grids with the double-float FFT (k_dffft.cu) unless eps is
+// below 1e-11 (beyond its ~48-bit significands), the plan is the plain FP64 form, or
+// HVOX_DF_FFT=0 (comparisons); each grid shape must also be one it covers.
+constexpr double kDfftMinEps = 1e-11;
+bool dfft_wanted(int prec, bool plain, double eps) {
+    if (const char *v = std::getenv("HVOX_DF_FFT"))
+        if (std::atoi(v) == 0) return false;
+    return prec == 2 && !plain && eps >= kDfftMinEps;
+}
+
 void upload(DevBuf &b, const void *host, size_t bytes, cudaStream_t s) {
     b.alloc(bytes);
     if (bytes) check_cuda(cudaMemcpyAsync(b.ptr, host, bytes, cudaMemcpyHostToDevice, s), "upload");
@@ -358,6 +368,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
     in.mode = p.mode;
     in.plain = p.plain;
     in.direct_f64 = p.direct_f64;
+    in.z2z_fft = !dfft_wanted(p.prec, p.plain, p.eps);
     in.budget = p.budget_opt;
     in.direct_threshold = p.direct_threshold;
     in.search_threshold = p.search_threshold;
@@ -577,9 +588,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         // selects full 3-D plans instead of the pruned pair.
         bool prune = true;
         if (const char *v = std::getenv("HVOX_FFT_PRUNE")) prune = std::atoi(v) != 0;
-        // HVOX_DF_FFT=0 keeps cuFFT Z2Z for FP64 grids (for comparisons).
-        bool use_dfft = true;
-        if (const char *v = std::getenv("HVOX_DF_FFT")) use_dfft = std::atoi(v) != 0;
+        const bool use_dfft = dfft_wanted(p.prec, p.plain, p.eps);
         std::vector<size_t> max_ws(n_lanes, 0);
         auto make = [&](cufftHandle &h, int rank, long long *n, long long *emb, long long stride, long long dist,
                         long long batch, size_t &ws) {
@@ -611,9 +620,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                 fb.h1y = first.n1[1] / 2;
                 const int64_t plane = first.n2[0] * first.n2[1];
                 // FP64 grids: the double-float FFT on the FP32 pipes where it covers the shape.
-                // Its ~48-bit significands hold to eps >= 1e-11; tighter plans, and the plain
-                // FP64 form, keep cuFFT Z2Z.
-                fb.df = p.prec == 2 && !p.plain && use_dfft && prune && p.eps >= 1e-11 && dfft_supported(fb.n2);
+                fb.df = use_dfft && prune && dfft_supported(fb.n2);
                 if (fb.df) {
                     DfftDev *dd[3] = {&fb.dx, &fb.dy, &fb.dz};
                     for (int q = 0; q < 3; ++q) {
@@ -1012,6 +1019,7 @@ hvox_status hvox_plan_dry(const double *pix_xyz, int64_t n_pix, const double *uv
         in.mode = p.mode;
         in.plain = p.plain;
         in.direct_f64 = p.direct_f64;
+        in.z2z_fft = !dfft_wanted(p.prec, p.plain, p.eps);
         in.budget = p.budget_opt;
         in.direct_threshold = p.direct_threshold;
         in.search_threshold = p.search_threshold;
@@ -1071,7 +1079,8 @@ double hvox_estimate_bytes(int64_t n_pix, int64_t n_vis, double eps, const hvox_
     // Jobs the planner keeps as direct sums without a search own no NUFFT grids; others
     // own at most kMaxLanes lanes of wave grids and cuFFT work areas, each within the
     // larger of the wave bytes and the chunk budget.
-    const CostModel m = default_cost_model(prec, plain || (prec == 2 && eps > 0 && eps < kDoubleFloatMinEps), 0);
+    const CostModel m = default_cost_model(prec, plain || (prec == 2 && eps > 0 && eps < kDoubleFloatMinEps), 0,
+                                           !dfft_wanted(prec, plain, eps));
     const double search = (opts && opts->search_threshold > 0) ? opts->search_threshold : 0.01;
     const bool auto_plan = !(opts && (opts->mode != HVOX_MODE_AUTO || opts->direct_threshold > 0 ||
                                       opts->chunk_budget_bytes > 0));

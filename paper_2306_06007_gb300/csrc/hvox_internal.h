@@ -114,7 +114,8 @@ struct CostModel {
     double tile_cells = 0;       // shared-memory tile capacity of the spreading kernels
 };
 
-CostModel default_cost_model(int prec, bool plain, int w);
+// z2z_fft: FP64 grids go through cuFFT Z2Z instead of the double-float FFT.
+CostModel default_cost_model(int prec, bool plain, int w, bool z2z_fft = false);
 
 struct PartitionResult {
     double t = 1.0, h[3] = {0, 0, 0}, eta[3] = {0, 0, 0}, budget = 0;
@@ -152,6 +153,7 @@ struct PlanInputs {
     int elem_bytes;
     int factor = 0;        // hvox_opts.factor: 0 searched, 1 one baseline box, 2 one pixel box
     int fixed_w = 0;       // > 0: kernel width for every upsampling (shape from the width rule)
+    bool z2z_fft = false;  // FP64 grids by cuFFT Z2Z (cost model), see dfft_wanted
 };
 
 PartitionResult make_partition(const PlanInputs &in);
@@ -199,12 +201,18 @@ struct FftPlans {
     cufftHandle full = 0, xy = 0, z = 0;
 };
 
-// One length of the double-float FFT (k_dffft.cu): radices of its Stockham stages and its
-// twiddle table exp(2 pi i q / n), q < n, as float pairs (cos h, cos l, sin h, sin l).
+// One length of the double-float FFT (k_dffft.cu): radices of its Stockham stages, the
+// divisor of each stage's butterfly index as a multiplier (floor(2^32 / Ns) + 1, exact for
+// indices below 2^14 and Ns >= 2), the odd radices' DFT coefficients cos and sin of
+// 2 pi m / r (m = q k mod r; r = 3 at [0], 5 at [1, 5), 7 at [5, 14), entry (q - 1) h + k - 1
+// with h = r / 2) and the twiddle table exp(2 pi i q / n), q < n; every value a float pair
+// (cos h, cos l, sin h, sin l).
 constexpr int kDfftMaxStages = 16;
 struct DfftDev {
     int n = 0, stages = 0;
     int radix[kDfftMaxStages] = {0};
+    unsigned ns_magic[kDfftMaxStages] = {0};
+    float4 odd[14];
     const float4 *tw = nullptr;
 };
 

@@ -84,6 +84,36 @@ __device__ __forceinline__ DF dmul2(DF a, DF b, DF c, DF d, float sg) {
     return {s, t};
 }
 
+// Lazy sum of several double-float terms with one renormalisation at the end: s is the
+// exact running sum of the high parts (TwoSum), e collects the low parts and the TwoSum
+// errors in FP32 (error ~2^-47 of the sum of magnitudes).
+struct DAcc {
+    float s, e;
+};
+__device__ __forceinline__ DAcc acc_of(DF a) { return {a.h, a.l}; }
+__device__ __forceinline__ void acc_add(DAcc &a, float p, float e) {
+    float s, t;
+    two_sum(a.s, p, s, t);
+    a.s = s;
+    a.e = __fadd_rn(a.e, __fadd_rn(t, e));
+}
+// a += x y for double-float x, y
+__device__ __forceinline__ void acc_fma(DAcc &a, DF x, DF y) {
+    float p, e;
+    dmul_raw(x, y, p, e);
+    acc_add(a, p, e);
+}
+__device__ __forceinline__ DAcc acc_mul(DF x, DF y) {
+    float p, e;
+    dmul_raw(x, y, p, e);
+    return {p, e};
+}
+__device__ __forceinline__ DF acc_done(DAcc a) {
+    float s, e;
+    fast_two_sum(a.s, a.e, s, e);
+    return {s, e};
+}
+
 __device__ __forceinline__ DC cadd(const DC &a, const DC &b) { return {dadd(a.re, b.re), dadd(a.im, b.im)}; }
 __device__ __forceinline__ DC csub(const DC &a, const DC &b) { return {dadd(a.re, dneg(b.re)), dadd(a.im, dneg(b.im))}; }
 
@@ -162,14 +192,14 @@ __device__ __forceinline__ void twiddle(const float4 *__restrict__ tw, int e, fl
 // the R outputs to (j / Ns) Ns R + k + q Ns. q k span < n, so the table index needs no wrap.
 template <int R, int TX>
 __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__restrict__ b, const DfftDev &d, int Ns,
-                                      float sg) {
+                                      unsigned magic, float sg) {
     const int n = d.n, m = n / R, span = n / (Ns * R);
     for (int wk = threadIdx.x; wk < m * TX; wk += blockDim.x) {
         const int j = wk / TX, t = wk - j * TX;
         DC v[R];
 #pragma unroll
         for (int q = 0; q < R; ++q) v[q] = from4(a[(j + q * m) * TX + t]);
-        const int jn = j / Ns, k = j - jn * Ns;
+        const int jn = Ns == 1 ? j : (int)__umulhi((unsigned)j, magic), k = j - jn * Ns;
         if (k != 0) {
 #pragma unroll
             for (int q = 1; q < R; ++q) {
@@ -192,28 +222,44 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__re
         } else {
             // odd R: s_q = v_q + v_{R-q}, d_q = v_q - v_{R-q} (q = 1 .. H); X_0 = v_0 + sum s_q;
             // A_k = v_0 + sum s_q cos(2 pi q k / R), B_k = sum d_q sin(2 pi q k / R);
-            // X_k = A_k + s j B_k, X_{R-k} = A_k - s j B_k.
+            // X_k = A_k + s j B_k, X_{R-k} = A_k - s j B_k. The coefficients come from the
+            // kernel parameters at compile-time offsets (constant-bank operands).
             constexpr int H = R / 2;
-            const int rstep = n / R;
+            constexpr int off = R == 3 ? 0 : (R == 5 ? 1 : 5);
             DC sq[H], dq[H];
-            y[0] = v[0];
 #pragma unroll
             for (int q = 1; q <= H; ++q) {
                 sq[q - 1] = cadd(v[q], v[R - q]);
                 dq[q - 1] = csub(v[q], v[R - q]);
-                y[0] = cadd(y[0], sq[q - 1]);
+            }
+            {
+                DAcc re = acc_of(v[0].re), im = acc_of(v[0].im);
+#pragma unroll
+                for (int q = 0; q < H; ++q) {
+                    acc_add(re, sq[q].re.h, sq[q].re.l);
+                    acc_add(im, sq[q].im.h, sq[q].im.l);
+                }
+                y[0] = {acc_done(re), acc_done(im)};
             }
 #pragma unroll
             for (int kk = 1; kk <= H; ++kk) {
-                DC A = v[0], B = {{0.f, 0.f}, {0.f, 0.f}};
+                DAcc ar = acc_of(v[0].re), ai = acc_of(v[0].im), br, bi;
 #pragma unroll
                 for (int q = 1; q <= H; ++q) {
-                    DF c, s;
-                    twiddle(d.tw, ((q * kk) % R) * rstep, 1.f, c, s);
-                    A = cadd(A, {dmul(sq[q - 1].re, c), dmul(sq[q - 1].im, c)});
-                    B = cadd(B, {dmul(dq[q - 1].re, s), dmul(dq[q - 1].im, s)});
+                    const float4 cs = d.odd[off + (q - 1) * H + (kk - 1)];
+                    const DF c = {cs.x, cs.y}, sn = {cs.z, cs.w};
+                    acc_fma(ar, sq[q - 1].re, c);
+                    acc_fma(ai, sq[q - 1].im, c);
+                    if (q == 1) {
+                        br = acc_mul(dq[0].re, sn);
+                        bi = acc_mul(dq[0].im, sn);
+                    } else {
+                        acc_fma(br, dq[q - 1].re, sn);
+                        acc_fma(bi, dq[q - 1].im, sn);
+                    }
                 }
-                const DC jb = times_j(B, sg);
+                const DC A = {acc_done(ar), acc_done(ai)};
+                const DC jb = times_j({acc_done(br), acc_done(bi)}, sg);
                 y[kk] = cadd(A, jb);
                 y[R - kk] = csub(A, jb);
             }
@@ -232,12 +278,13 @@ __device__ float4 *fft_smem(float4 *a, float4 *b, const DfftDev &d, float sg) {
     int Ns = 1;
     for (int st = 0; st < d.stages; ++st) {
         const int r = d.radix[st];
+        const unsigned mg = d.ns_magic[st];
         switch (r) {
-            case 4: stage<4, TX>(a, b, d, Ns, sg); break;
-            case 2: stage<2, TX>(a, b, d, Ns, sg); break;
-            case 3: stage<3, TX>(a, b, d, Ns, sg); break;
-            case 5: stage<5, TX>(a, b, d, Ns, sg); break;
-            default: stage<7, TX>(a, b, d, Ns, sg); break;
+            case 4: stage<4, TX>(a, b, d, Ns, mg, sg); break;
+            case 2: stage<2, TX>(a, b, d, Ns, mg, sg); break;
+            case 3: stage<3, TX>(a, b, d, Ns, mg, sg); break;
+            case 5: stage<5, TX>(a, b, d, Ns, mg, sg); break;
+            default: stage<7, TX>(a, b, d, Ns, mg, sg); break;
         }
         __syncthreads();
         float4 *tmp = a;
@@ -366,6 +413,15 @@ void cols(int tx, Io io, double2 *g, const DfftDev &d, int64_t stride, int64_t n
 
 }  // namespace
 
+namespace {
+float4 cis_pair(int m, int r) {
+    const double ang = 2.0 * M_PI * (double)m / (double)r;
+    const double c = std::cos(ang), s = std::sin(ang);
+    const float ch = (float)c, sh = (float)s;
+    return make_float4(ch, (float)(c - (double)ch), sh, (float)(s - (double)sh));
+}
+}  // namespace
+
 bool dfft_factor(int n, DfftDev &d) {
     d.n = n;
     d.stages = 0;
@@ -376,6 +432,15 @@ bool dfft_factor(int n, DfftDev &d) {
             d.radix[d.stages++] = r;
             m /= r;
         }
+    long long Ns = 1;
+    for (int st = 0; st < d.stages; ++st) {
+        d.ns_magic[st] = Ns >= 2 ? (unsigned)((1ull << 32) / (unsigned long long)Ns + 1) : 0u;
+        Ns *= d.radix[st];
+    }
+    int at = 0;
+    for (int r : {3, 5, 7})
+        for (int q = 1; q <= r / 2; ++q)
+            for (int k = 1; k <= r / 2; ++k) d.odd[at++] = cis_pair((q * k) % r, r);
     return m == 1 && n >= 2;
 }
 

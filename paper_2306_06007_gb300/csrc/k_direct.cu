@@ -163,6 +163,38 @@ __device__ __forceinline__ void df_acc(float &acc_h, float &acc_l, float th, flo
     acc_l = __fadd_rn(acc_l, __fadd_rn(e, tl));
 }
 
+// Offset double-float accumulation of one streamed tile: the running high sum starts at a
+// power of two M above twice the tile's sum of term magnitudes S, so it stays in
+// [M - S, M + S], never below any term, and the rounding error of each add is recovered
+// exactly by Fast2Sum (three instructions instead of TwoSum's six). The low part collects
+// those errors and the terms' own low parts. At the tile's end hi - M is exact (Sterbenz).
+__device__ __forceinline__ void df_acc_off(float &acc_h, float &acc_l, float th, float tl) {
+    const float s = __fadd_rn(acc_h, th);
+    const float e = __fsub_rn(th, __fsub_rn(s, acc_h));
+    acc_h = s;
+    acc_l = __fadd_rn(acc_l, __fadd_rn(e, tl));
+}
+
+// The offset for a tile whose term magnitudes sum to at most S: 2^(floor(log2 S) + 2) > 2 S
+// (S from the block's own values; tiny or zero S gives 2^-100).
+__device__ __forceinline__ float tile_offset(float S) {
+    const unsigned e = __float_as_uint(fmaxf(S, 0x1p-102f)) & 0x7F800000u;
+    return __uint_as_float(e + (2u << 23));
+}
+
+// Sum of x over the CTA (every thread gets it). red holds one float per warp; the caller
+// has a __syncthreads() between this call and the previous use of red.
+__device__ __forceinline__ float block_sum(float x, float *red) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    float t = 0.f;
+#pragma unroll
+    for (int w = 0; w < kThreads / 32; ++w) t += red[w];
+    return t;
+}
+
 // Kahan-compensated accumulation of per-tile partial sums: the FP32 paths sum each
 // 256-term shared-memory tile in registers and add the tile sums here, which keeps the
 // rounding error of sums over millions of terms near that of a 256-term sum.
@@ -284,12 +316,13 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
     __shared__ float4 sl[kThreads];
     __shared__ float2 sc[kThreads];
     __shared__ float4 sT[kTabN];
+    __shared__ float red[kThreads / 32];
     load_tab(sT, gT);
     __shared__ int s_next;
     for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         float3 ph[VPT], pl[VPT];
-        float arh[VPT], arl[VPT], aih[VPT], ail[VPT];
+        float arh[VPT], arl[VPT], aih[VPT], ail[VPT];  // tile sums, offset by M
         float orh[VPT], orl[VPT], oih[VPT], oil[VPT];  // running sums, folded per tile
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
@@ -307,19 +340,24 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
         for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
             __syncthreads();
             int n = s0 + threadIdx.x;
+            float mag = 0.f;
             if (n < w.s1) {
                 sh[threadIdx.x] = rh_g[n];
                 sl[threadIdx.x] = rl_g[n];
                 double cv = c[n];
                 float chi = (float)cv;
                 sc[threadIdx.x] = make_float2(chi, (float)(cv - (double)chi));
+                mag = fabsf(chi);
             } else {
                 sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
                 sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
                 sc[threadIdx.x] = make_float2(0.f, 0.f);
             }
-            __syncthreads();
+            // |c (cos, sin)| <= |c| (1 + 2^-23): S = 1.01 sum |c| bounds each partial sum
+            const float M = tile_offset(1.01f * block_sum(mag, red));
             const int cnt = min(kThreads, w.s1 - s0);
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) arh[v] = aih[v] = M;
 #pragma unroll 4
             for (int q = 0; q < cnt; ++q) {
                 const float4 rh = sh[q], rl = sl[q];
@@ -331,16 +369,16 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
                     cis_tab(fh, fl, sT, reh, rel, imh, iml);
                     float th, tl;
                     df_mul(cv.x, cv.y, reh, rel, th, tl);
-                    df_acc(arh[v], arl[v], th, tl);
+                    df_acc_off(arh[v], arl[v], th, tl);
                     df_mul(cv.x, cv.y, imh, iml, th, tl);
-                    df_acc(aih[v], ail[v], th, tl);
+                    df_acc_off(aih[v], ail[v], th, tl);
                 }
             }
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
-                df_fold(orh[v], orl[v], arh[v], arl[v]);
-                df_fold(oih[v], oil[v], aih[v], ail[v]);
-                arh[v] = arl[v] = aih[v] = ail[v] = 0.f;
+                df_fold(orh[v], orl[v], __fsub_rn(arh[v], M), arl[v]);
+                df_fold(oih[v], oil[v], __fsub_rn(aih[v], M), ail[v]);
+                arl[v] = ail[v] = 0.f;
             }
         }
 #pragma unroll
@@ -491,12 +529,13 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
     __shared__ float4 sl[kThreads];
     __shared__ float4 sv[kThreads];
     __shared__ float4 sT[kTabN];
+    __shared__ float red[kThreads / 32];
     load_tab(sT, gT);
     __shared__ int s_next;
     for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
         float4 rh[VPT], rl[VPT];
-        float ah[VPT], al[VPT], oh[VPT], ol[VPT];  // tile sums and running sums
+        float ah[VPT], al[VPT], oh[VPT], ol[VPT];  // tile sums (offset by M) and running sums
 #pragma unroll
         for (int v = 0; v < VPT; ++v) {
             int n = w.o0 + threadIdx.x + v * kThreads;
@@ -512,6 +551,7 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
         for (int s0 = w.s0; s0 < w.s1; s0 += kThreads) {
             __syncthreads();
             int k = s0 + threadIdx.x;
+            float mag = 0.f;
             if (k < w.s1) {
                 sh[threadIdx.x] = vh[k];
                 sl[threadIdx.x] = vl[k];
@@ -519,13 +559,17 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
                 double vi = (double)sgn * val.y;
                 float rh_ = (float)val.x, ih_ = (float)vi;
                 sv[threadIdx.x] = make_float4(rh_, (float)(val.x - (double)rh_), ih_, (float)(vi - (double)ih_));
+                mag = fabsf(rh_) + fabsf(ih_);
             } else {
                 sh[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
                 sl[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
                 sv[threadIdx.x] = make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            __syncthreads();
+            // each pair adds Vre cos + Vim sin: S = 1.01 sum (|Vre| + |Vim|) bounds the partial sums
+            const float M = tile_offset(1.01f * block_sum(mag, red));
             const int cnt = min(kThreads, w.s1 - s0);
+#pragma unroll
+            for (int v = 0; v < VPT; ++v) ah[v] = M;
 #pragma unroll 4
             for (int q = 0; q < cnt; ++q) {
                 const float4 ph4 = sh[q], pl4 = sl[q], val = sv[q];
@@ -537,15 +581,15 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
                     cis_tab(fh, fl, sT, reh, rel, imh, iml);
                     float th, tl;
                     df_mul(val.x, val.y, reh, rel, th, tl);
-                    df_acc(ah[v], al[v], th, tl);
+                    df_acc_off(ah[v], al[v], th, tl);
                     df_mul(val.z, val.w, imh, iml, th, tl);
-                    df_acc(ah[v], al[v], th, tl);
+                    df_acc_off(ah[v], al[v], th, tl);
                 }
             }
 #pragma unroll
             for (int v = 0; v < VPT; ++v) {
-                df_fold(oh[v], ol[v], ah[v], al[v]);
-                ah[v] = al[v] = 0.f;
+                df_fold(oh[v], ol[v], __fsub_rn(ah[v], M), al[v]);
+                al[v] = 0.f;
             }
         }
 #pragma unroll

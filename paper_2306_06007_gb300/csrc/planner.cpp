@@ -168,12 +168,12 @@ int64_t chunk_points(const double *xyz, int64_t n, const double h[3], std::vecto
     return n_chunks;
 }
 
-CostModel default_cost_model(int prec, bool plain, int w) {
+CostModel default_cost_model(int prec, bool plain, int w, bool z2z_fft) {
     // Seconds per unit of work on one GB300, measured with this library's kernels: direct
     // pairs/s of the FP32, double-float and FP64 kernels; spreading taps/s through
     // shared-memory tiles and straight into the grid (vector atomics); interpolation
-    // taps/s; cuFFT C2C (HBM-bound) and Z2Z (bound by GB300's FP64 units) per cell and
-    // log2(cells); grid passes at HBM speed.
+    // taps/s; cuFFT C2C (HBM-bound), the double-float FFT of FP64 grids and cuFFT Z2Z
+    // (bound by GB300's FP64 units) per cell and log2(cells); grid passes at HBM speed.
     (void)w;
     CostModel m;
     if (prec == 1 && !plain) {
@@ -192,16 +192,17 @@ CostModel default_cost_model(int prec, bool plain, int w) {
         m.tile_cells = 12000.0;  // shared tile of a spreading CTA (float planes, w <= 8)
     } else {
         // FP64 sub-problems, fitted the same way (calibrate.py --eps 1e-9 --mode nufft, 1 to
-        // 29 sub-problems per workload). Spreading taps are one rate: the fit does not
-        // separate the shared-tile and global paths. Z2Z transforms are bound by the FP64
-        // units, ~17x the C2C rate per cell. The double-float direct rate is the LOFAR-like
-        // benchmark's launch.
-        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 4.2e11;
-        m.scatter_smem = 1.0 / 1.15e11;
-        m.scatter_global = 1.0 / 1.15e11;
-        m.gather_tap = 1.0 / 1.22e11;
-        m.fft_cell = 7.2e-12;
-        m.grid_cell = 1.9e-12;
+        // 22 sub-problems per workload). Spreading taps are one rate: the fit does not
+        // separate the shared-tile and global paths. The FFT rate is the double-float FFT's
+        // (4.2x cheaper per cell than cuFFT Z2Z, which is bound by the FP64 units at ~17x
+        // the C2C rate and still serves the plain form and eps < 1e-11, measured earlier).
+        // The double-float direct rate is the LOFAR-like benchmark's launch.
+        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 4.5e11;
+        m.scatter_smem = 1.0 / 1.21e11;
+        m.scatter_global = 1.0 / 1.21e11;
+        m.gather_tap = 1.0 / 1.31e11;
+        m.fft_cell = (plain || z2z_fft) ? 7.2e-12 : 1.7e-12;
+        m.grid_cell = 1.7e-12;
         m.block_fixed = 50e-6;
         m.tile_cells = 4800.0;   // double planes, w ~ 10
     }
@@ -372,7 +373,7 @@ double factored_ratio(int factor, const double P[3], const double B[3], double b
 
 PartitionResult make_partition(const PlanInputs &in) {
     PartitionResult r;
-    CostModel m = default_cost_model(in.prec, in.plain, in.es.w);
+    CostModel m = default_cost_model(in.prec, in.plain, in.es.w, in.z2z_fft);
     if (in.direct_f64) m.direct_pair = default_cost_model(2, true, in.es.w).direct_pair;
     double P[3], B[3];
     for (int d = 0; d < 3; ++d) {
