@@ -51,7 +51,7 @@ FLOPS_PER_PAIR = 16.0                      # algorithmic flops per (pixel, basel
 # dram__bytes_write.sum of the full-size launches, mean of two steps' s2v and v2s launches)
 # and thread instructions per pair of the double-float kernels (smsp__inst_executed.sum x 32
 # / pairs, 100k-baseline case; those kernels are unchanged since that capture).
-DIRECT_COUNTERS = {1e-9: ("5091eb9e8be659d494b7577f44d17bbdbb0ead139d7b9923b6f6c23085fc6b25", 210022528.0, 80.0)}
+DIRECT_COUNTERS = {1e-9: ("4bd864c34d1267f8e16c78fc6e727b931df1b0290a13386a3647fb00d039eb9d", 183560000.0, 74.0)}
 
 
 def direct_counters(eps, config, other_workload, n_vis):

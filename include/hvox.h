@@ -234,6 +234,31 @@ hvox_status hvox_destroy(hvox_plan_t plan);
 hvox_status hvox_synthesize_complex(hvox_plan_t plan, const void *I, void *V);
 hvox_status hvox_analyze_complex(hvox_plan_t plan, const void *V, void *I);
 
+/*
+ * hvox_synthesize_batch / hvox_analyze_batch — the transforms of n distinct plans in one
+ * call, the parallel sub-transforms of Sect. 3 carried across jobs: on `stream`, each
+ * plan's input permutation and NUFFT sub-problems as in hvox_synthesize / hvox_analyze,
+ * but the direct sub-problems of every plan whose direct sums run on the FP32 or the
+ * double-float kernels merged into one launch per kernel form (their work items in one
+ * list, largest first, each tagged with its plan), so that small jobs share kernels and
+ * their dynamic schedule. Plans with FP64 direct sums (the plain form, eps < 1e-9) launch
+ * theirs separately.
+ *   plans      n distinct plans on one device, each with ntrans = 1.
+ *   I / V      n device pointers each (plan i's input and output, layouts as above).
+ *   stream     cudaStream_t or NULL (legacy default stream). The call is ordered after
+ *              the work already queued on every plan's own stream, and each plan's stream
+ *              is ordered after the call; the call returns once everything is enqueued.
+ *   direct_launches  may be NULL; receives the number of direct-sum launches made.
+ * Profiling (hvox_profile) covers the plans' NUFFT stages; merged direct launches are
+ * not bracketed. Errors: HVOX_EINVAL for NULL or host pointers, a repeated plan or
+ * plans on different devices, n < 0; HVOX_EUNSUPPORTED for ntrans > 1; HVOX_ECUDA.
+ * n = 0 does nothing.
+ */
+hvox_status hvox_synthesize_batch(const hvox_plan_t *plans, const void *const *I, void *const *V, int32_t n,
+                                  void *stream, int32_t *direct_launches);
+hvox_status hvox_analyze_batch(const hvox_plan_t *plans, const void *const *V, void *const *I, int32_t n,
+                               void *stream, int32_t *direct_launches);
+
 /* Aliases with the direction in the name. */
 hvox_status hvox_dirty2vis(hvox_plan_t plan, const void *I, void *V);
 hvox_status hvox_vis2dirty(hvox_plan_t plan, const void *V, void *I);

@@ -108,6 +108,8 @@ def load():
         "hvox_plan_dry": [D, I64, D, I64, ctypes.c_double, ctypes.POINTER(Opts), ctypes.POINTER(Info)],
         "hvox_direct_synthesize_noalloc": [V, I64, V, I64, V, V, ctypes.c_int, V],
         "hvox_cost_model": [I32, I32, D],
+        "hvox_synthesize_batch": [ctypes.POINTER(P), ctypes.POINTER(V), ctypes.POINTER(V), I32, V, ctypes.POINTER(I32)],
+        "hvox_analyze_batch": [ctypes.POINTER(P), ctypes.POINTER(V), ctypes.POINTER(V), I32, V, ctypes.POINTER(I32)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -460,3 +462,51 @@ class Plan:
 
     def __exit__(self, *exc):
         self.close()
+
+
+def _batch(entry, plans, xs, s2v: bool, stream, return_launches: bool):
+    import torch
+    plans = list(plans)
+    xs = list(xs)
+    if len(plans) != len(xs):
+        raise ValueError("one input per plan")
+    cur = torch.cuda.current_stream()
+    if stream is None:
+        stream = cur
+    elif stream != cur:
+        stream.wait_stream(cur)  # inputs and fresh outputs are ordered on the current stream
+    ins, outs = [], []
+    for p, x in zip(plans, xs):
+        if p.ntrans != 1:
+            raise ValueError("batched transforms take plans with ntrans = 1")
+        if s2v:
+            x = p._input(x, p.real_dtype, p.n_pix)
+            y = torch.empty(p.n_vis, dtype=p.complex_dtype, device=x.device)
+        else:
+            x = p._input(x, p.complex_dtype, p.n_vis)
+            y = torch.empty(p.n_pix, dtype=p.real_dtype, device=x.device)
+        if not x.is_cuda:
+            raise ValueError("batched transforms take device tensors")
+        ins.append(x)
+        outs.append(y)
+    n = len(plans)
+    P = (ctypes.c_void_p * max(n, 1))(*[p._handle.value for p in plans])
+    Vin = (ctypes.c_void_p * max(n, 1))(*[x.data_ptr() for x in ins])
+    Vout = (ctypes.c_void_p * max(n, 1))(*[y.data_ptr() for y in outs])
+    launches = ctypes.c_int32(0)
+    _check(entry(P, Vin, Vout, n, ctypes.c_void_p(stream.cuda_stream), ctypes.byref(launches)))
+    for t in ins + outs:
+        t.record_stream(stream)
+    return (outs, launches.value) if return_launches else outs
+
+
+def synthesize_batch(plans, skies, stream=None, return_launches: bool = False):
+    """sky -> vis for several plans in one call (hvox_synthesize_batch): the direct sums of
+    plans on the FP32 or double-float kernels share one launch per kernel form. skies: one
+    device tensor per plan. Returns the visibilities (and the number of direct launches)."""
+    return _batch(load().hvox_synthesize_batch, plans, skies, True, stream, return_launches)
+
+
+def analyze_batch(plans, vis, stream=None, return_launches: bool = False):
+    """vis -> sky for several plans in one call (hvox_analyze_batch); see synthesize_batch."""
+    return _batch(load().hvox_analyze_batch, plans, vis, False, stream, return_launches)

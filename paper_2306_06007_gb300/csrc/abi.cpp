@@ -112,6 +112,7 @@ Plan::~Plan() {
     if (cap) cudaStreamDestroy(cap);
     lanes.clear();
     if (fork_event) cudaEventDestroy(fork_event);
+    if (batch_event) cudaEventDestroy(batch_event);
     for (auto &q : pending) {
         cudaEventDestroy(q.a);
         cudaEventDestroy(q.b);
@@ -449,6 +450,8 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         upload(p.items_v2s, b.data(), b.size() * sizeof(WorkItem), s);
         p.n_items_s2v = (int64_t)a.size();
         p.n_items_v2s = (int64_t)b.size();
+        p.host_items[0] = std::move(a);
+        p.host_items[1] = std::move(b);
     }
 
     // exp(j 2 pi m / 2048), m = 0 .. 2047, split into float pairs (double-float direct path).
@@ -907,6 +910,47 @@ hvox_status hvox_analyze(hvox_plan_t plan, const void *V, void *I) {
         if (!plan || !I || !V) fail(HVOX_EINVAL, "hvox_analyze: NULL argument");
         transform(plan->p, V, I, false);
     });
+}
+
+namespace {
+hvox_status batch_call(const hvox_plan_t *plans, const void *const *in, void *const *out, int32_t n, void *stream,
+                       int32_t *direct_launches, int dir) {
+    const char *name = dir == 0 ? "hvox_synthesize_batch" : "hvox_analyze_batch";
+    return guard([&] {
+        if (direct_launches) *direct_launches = 0;
+        if (n < 0 || (n > 0 && (!plans || !in || !out))) fail(HVOX_EINVAL, std::string(name) + ": NULL argument");
+        if (n == 0) return;
+        std::vector<Plan *> ps((size_t)n);
+        std::vector<const void *> ins((size_t)n);
+        std::vector<void *> outs((size_t)n);
+        for (int32_t i = 0; i < n; ++i) {
+            if (!plans[i] || !in[i] || !out[i]) fail(HVOX_EINVAL, std::string(name) + ": NULL plan or buffer");
+            ps[i] = &plans[i]->p;
+            for (int32_t j = 0; j < i; ++j)
+                if (ps[j] == ps[i]) fail(HVOX_EINVAL, std::string(name) + ": a plan appears twice");
+            if (ps[i]->device != ps[0]->device) fail(HVOX_EINVAL, std::string(name) + ": plans on different devices");
+            if (ps[i]->ntrans != 1) fail(HVOX_EUNSUPPORTED, std::string(name) + ": ntrans must be 1");
+            ins[i] = in[i];
+            outs[i] = out[i];
+        }
+        check_cuda(cudaSetDevice(ps[0]->device), "cudaSetDevice");
+        for (int32_t i = 0; i < n; ++i)
+            if (!is_device_ptr(ins[i]) || !is_device_ptr(outs[i]))
+                fail(HVOX_EINVAL, std::string(name) + ": device pointers only");
+        const int l = run_batch(ps, ins, outs, dir, static_cast<cudaStream_t>(stream));
+        if (direct_launches) *direct_launches = l;
+    });
+}
+}  // namespace
+
+hvox_status hvox_synthesize_batch(const hvox_plan_t *plans, const void *const *I, void *const *V, int32_t n,
+                                  void *stream, int32_t *direct_launches) {
+    return batch_call(plans, I, V, n, stream, direct_launches, 0);
+}
+
+hvox_status hvox_analyze_batch(const hvox_plan_t *plans, const void *const *V, void *const *I, int32_t n,
+                               void *stream, int32_t *direct_launches) {
+    return batch_call(plans, V, I, n, stream, direct_launches, 1);
 }
 
 hvox_status hvox_synthesize_complex(hvox_plan_t plan, const void *I, void *V) {

@@ -10,6 +10,8 @@
 // whose pointers are the caller's, stay ordinary launches around the replay.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <cstring>
 #include <map>
 
 #include "hvox_internal.h"
@@ -358,6 +360,176 @@ void run_analyze(Plan &p, const void *V, void *I) {
         prof.end(HVOX_STAGE_PERMUTE, 1, s);
         p.transforms++;
     }
+}
+
+namespace {
+
+// The direct sums of one plan alone (FP64 kernels, or any plan outside a merged launch).
+void direct_alone(Plan &p, int dir, cudaStream_t s) {
+    const int64_t n = dir == 0 ? p.n_items_s2v : p.n_items_v2s;
+    if (n <= 0) return;
+    const WorkItem *it = (dir == 0 ? p.items_s2v : p.items_v2s).as<WorkItem>();
+    int *counter = p.item_counter.as<int>() + dir;
+    check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), s), "memset item counter");
+    if (dir == 0) {
+        if (p.direct_f64)
+            launch_direct_s2v_f64(it, n, counter, p.vis_xyz.as<double>(), p.n_vis, p.pix_xyz.as<double>(), p.n_pix,
+                                  p.src.as<double>(), p.acc.as<double2>(), p.isign, p.direct_vpt, s);
+        else if (p.prec == 1)
+            launch_direct_s2v_f32(it, n, counter, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.pix_hi.as<float4>(),
+                                  p.pix_lo.as<float4>(), p.src.as<float>(), p.acc.as<float2>(), p.isign,
+                                  p.direct_vpt, s);
+        else
+            launch_direct_s2v_df(it, n, counter, p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.pix_hi.as<float4>(),
+                                 p.pix_lo.as<float4>(), p.src.as<double>(), p.acc.as<double2>(),
+                                 p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
+    } else {
+        if (p.direct_f64)
+            launch_direct_v2s_f64(it, n, counter, p.pix_xyz.as<double>(), p.n_pix, p.vis_xyz.as<double>(), p.n_vis,
+                                  p.src.as<double2>(), p.acc.as<double>(), p.isign, p.direct_vpt, s);
+        else if (p.prec == 1)
+            launch_direct_v2s_f32(it, n, counter, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.vis_hi.as<float4>(),
+                                  p.vis_lo.as<float4>(), p.src.as<float2>(), p.acc.as<float>(), p.isign,
+                                  p.direct_vpt, s);
+        else
+            launch_direct_v2s_df(it, n, counter, p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.vis_hi.as<float4>(),
+                                 p.vis_lo.as<float4>(), p.src.as<double2>(), p.acc.as<double>(),
+                                 p.cis_tab.as<float4>(), p.isign, p.direct_vpt, s);
+    }
+    p.stage_launches[HVOX_STAGE_DIRECT] += 1;
+}
+
+// The job of a plan in a merged direct launch.
+DirectJob job_of_plan(const Plan &p, int dir) {
+    if (dir == 0)
+        return {p.vis_hi.as<float4>(), p.vis_lo.as<float4>(), p.pix_hi.as<float4>(), p.pix_lo.as<float4>(),
+                p.src.ptr,             p.acc.ptr,             (float)p.isign};
+    return {p.pix_hi.as<float4>(), p.pix_lo.as<float4>(), p.vis_hi.as<float4>(), p.vis_lo.as<float4>(),
+            p.src.ptr,             p.acc.ptr,             (float)p.isign};
+}
+
+// One merged launch over the work items of the plans in `group` (same kernel form and
+// owners per thread). Its lists live in one stream-ordered allocation freed after it.
+void direct_merged(const std::vector<Plan *> &group, int dir, int kind, int vpt, cudaStream_t s) {
+    std::vector<DirectJob> jobs;
+    std::vector<std::pair<int64_t, int>> order;  // (pairs, index into flat) for the sort
+    std::vector<WorkItem> flat;
+    std::vector<int> flat_job;
+    for (size_t j = 0; j < group.size(); ++j) {
+        jobs.push_back(job_of_plan(*group[j], dir));
+        for (const WorkItem &w : group[j]->host_items[dir]) {
+            order.push_back({(int64_t)(w.o1 - w.o0) * (int64_t)(w.s1 - w.s0), (int)flat.size()});
+            flat.push_back(w);
+            flat_job.push_back((int)j);
+        }
+    }
+    // largest first (the schedule's assumption); ties keep plan order
+    std::stable_sort(order.begin(), order.end(), [](const auto &a, const auto &b) { return a.first > b.first; });
+    const int64_t n = (int64_t)flat.size();
+    const size_t b_items = sizeof(WorkItem) * (size_t)n, b_job = sizeof(int) * (size_t)n;
+    const size_t b_jobs = sizeof(DirectJob) * jobs.size();
+    auto up = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    std::vector<char> host(up(b_items) + up(b_job) + up(b_jobs), 0);
+    WorkItem *hi = reinterpret_cast<WorkItem *>(host.data());
+    int *hj = reinterpret_cast<int *>(host.data() + up(b_items));
+    for (int64_t i = 0; i < n; ++i) {
+        hi[i] = flat[order[i].second];
+        hj[i] = flat_job[order[i].second];
+    }
+    std::memcpy(host.data() + up(b_items) + up(b_job), jobs.data(), b_jobs);
+    void *dev = nullptr;
+    const size_t total = host.size() + 256;
+    if (fault_hit("alloc")) fail(HVOX_ENOMEM, "batch work list: injected allocation failure");
+    check_cuda(cudaMallocAsync(&dev, total, s), "cudaMallocAsync (batch work list)");
+    char *d = static_cast<char *>(dev);
+    check_cuda(cudaMemcpyAsync(d, host.data(), host.size(), cudaMemcpyHostToDevice, s), "copy batch work list");
+    int *counter = reinterpret_cast<int *>(d + host.size());
+    check_cuda(cudaMemsetAsync(counter, 0, sizeof(int), s), "memset batch counter");
+    launch_direct_batch(kind, dir, reinterpret_cast<const WorkItem *>(d), n, counter,
+                        reinterpret_cast<const DirectJob *>(d + up(b_items) + up(b_job)),
+                        reinterpret_cast<const int *>(d + up(b_items)), group[0]->cis_tab.as<float4>(), vpt, s);
+    check_cuda(cudaFreeAsync(dev, s), "cudaFreeAsync (batch work list)");
+    for (Plan *p : group) p->stage_launches[HVOX_STAGE_DIRECT] += 1;
+}
+
+}  // namespace
+
+int run_batch(const std::vector<Plan *> &plans, const std::vector<const void *> &in, const std::vector<void *> &out,
+              int dir, cudaStream_t s) {
+    // order after each plan's own stream
+    for (Plan *p : plans) {
+        if (!p->batch_event)
+            check_cuda(cudaEventCreateWithFlags(&p->batch_event, cudaEventDisableTiming), "cudaEventCreate");
+        if (p->stream != s) {
+            check_cuda(cudaEventRecord(p->batch_event, p->stream), "cudaEventRecord");
+            check_cuda(cudaStreamWaitEvent(s, p->batch_event, 0), "cudaStreamWaitEvent");
+        }
+    }
+    // inputs to chunk order, accumulators cleared, lanes forked
+    for (size_t i = 0; i < plans.size(); ++i) {
+        Plan &p = *plans[i];
+        const size_t re = real_bytes(p);
+        if (dir == 0) {
+            launch_s2v_in(p.prec, in[i], pix_perm(p), weight_ptr(p), p.n_pix, p.src.ptr, s);
+            check_cuda(cudaMemsetAsync(p.acc.ptr, 0, (size_t)p.n_vis * 2 * re, s), "memset acc");
+        } else {
+            launch_v2s_in(p.prec, in[i], vis_perm(p), p.n_vis, p.src.ptr, s);
+            check_cuda(cudaMemsetAsync(p.acc.ptr, 0, (size_t)p.n_pix * re, s), "memset acc");
+        }
+        p.stage_launches[HVOX_STAGE_PERMUTE] += 1;
+        p.stage_launches[HVOX_STAGE_ZERO] += 1;
+        fork_lanes(p, s);
+    }
+    // direct sums: merged per (kernel form, owners per thread); FP64 kernels alone
+    int launches = 0;
+    std::map<std::pair<int, int>, std::vector<Plan *>> groups;
+    for (Plan *p : plans) {
+        if ((dir == 0 ? p->n_items_s2v : p->n_items_v2s) <= 0) continue;
+        if (p->direct_f64) {
+            direct_alone(*p, dir, s);
+            ++launches;
+        } else {
+            groups[{p->prec == 1 ? 0 : 1, p->direct_vpt}].push_back(p);
+        }
+    }
+    for (auto &g : groups) {
+        if (g.second.size() == 1)
+            direct_alone(*g.second[0], dir, s);
+        else
+            direct_merged(g.second, dir, g.first.first, g.first.second, s);
+        ++launches;
+    }
+    // NUFFT sub-problems on each plan's lanes, outputs back to the callers' order
+    for (size_t i = 0; i < plans.size(); ++i) {
+        Plan &p = *plans[i];
+        Profiler prof(p);
+        if (!p.waves.empty()) {
+            if (p.prec == 1) {
+                if (dir == 0)
+                    run_waves<float>(p, 0, p.src.as<float>(), p.acc.as<float2>(), s, prof);
+                else
+                    run_waves<float>(p, 1, p.src.as<float2>(), p.acc.as<float>(), s, prof);
+            } else {
+                if (dir == 0)
+                    run_waves<double>(p, 0, p.src.as<double>(), p.acc.as<double2>(), s, prof);
+                else
+                    run_waves<double>(p, 1, p.src.as<double2>(), p.acc.as<double>(), s, prof);
+            }
+        }
+        join_lanes(p, s);
+        if (dir == 0)
+            launch_s2v_out(p.prec, p.acc.ptr, vis_perm(p), p.n_vis, out[i], s);
+        else
+            launch_v2s_out(p.prec, p.acc.ptr, pix_perm(p), weight_ptr(p), p.n_pix, out[i], s);
+        p.stage_launches[HVOX_STAGE_PERMUTE] += 1;
+        p.transforms++;
+    }
+    // each plan's own stream continues after the call
+    cudaEvent_t done = plans[0]->batch_event;
+    check_cuda(cudaEventRecord(done, s), "cudaEventRecord");
+    for (Plan *p : plans)
+        if (p->stream != s) check_cuda(cudaStreamWaitEvent(p->stream, done, 0), "cudaStreamWaitEvent");
+    return launches;
 }
 
 // A (x + j y) = A x + j A y: both real skies through the ordinary path, then V += j V'.

@@ -103,6 +103,17 @@ struct WorkItem {
     int32_t o0, o1, s0, s1;
 };
 
+// Device pointers of one job of a direct launch (one plan's chunk-ordered buffers): owner
+// coordinates (sky -> vis: baselines, vis -> sky: pixels) and streamed coordinates as
+// hi / lo float4 splits, the streamed values (c or V), the owners' accumulators, and the
+// exponent's sign.
+struct DirectJob {
+    const float4 *own_hi, *own_lo, *str_hi, *str_lo;
+    const void *val;
+    void *acc;
+    float sgn;
+};
+
 struct CostModel {
     double direct_pair = 0;      // seconds per (pixel, baseline) pair, one direction
     double scatter_smem = 0;     // seconds per tap of spreading through a shared-memory tile
@@ -355,6 +366,8 @@ struct Plan {
     DevBuf items_s2v, items_v2s;
     DevBuf item_counter;                // int[2]: work-item counters of the direct launches
     int64_t n_items_s2v = 0, n_items_v2s = 0;
+    std::vector<WorkItem> host_items[2];  // the same lists on the host (merged batch launches)
+    cudaEvent_t batch_event = nullptr;  // orders a batch call against the plan's own stream
 
     // NUFFT sub-problems
     DevBuf inv_psi;                     // T per (block, dim, l): 1 / Psi on the n1 band
@@ -412,6 +425,9 @@ void launch_direct_v2s_df(const WorkItem *items, int64_t n, int *counter, const 
                           int vpt, cudaStream_t s);
 void launch_direct_v2s_f64(const WorkItem *items, int64_t n, int *counter, const double *pxyz, int64_t np, const double *vxyz,
                            int64_t nv, const double2 *V, double *acc, int isign, int vpt, cudaStream_t s);
+// Several jobs' items in one launch: kind 0 FP32, 1 double-float; dir 0 sky -> vis, 1 vis -> sky.
+void launch_direct_batch(int kind, int dir, const WorkItem *items, int64_t n, int *counter, const DirectJob *jobs,
+                         const int *item_job, const float4 *tab, int vpt, cudaStream_t s);
 
 // NUFFT sub-problems, one wave at a time (k_nufft.cu). g1 / g2: the lane's grid buffers.
 template <typename T>
@@ -448,6 +464,12 @@ void launch_join_complex(int prec, const void *re, const void *im, int64_t n, vo
 void launch_add_j(int prec, void *a, const void *b, int64_t n, cudaStream_t s);
 void launch_times_mj(int prec, const void *a, int64_t n, void *out, cudaStream_t s);
 void collect_stats(Plan &p);
+// Transforms of several distinct plans (ntrans = 1, device pointers) on stream s, direction
+// dir (0 sky -> vis, 1 vis -> sky), with the direct sums of the plans that use the FP32 or
+// the double-float kernels merged into one launch per kernel form. Returns the number of
+// direct-sum launches made.
+int run_batch(const std::vector<Plan *> &plans, const std::vector<const void *> &in, const std::vector<void *> &out,
+              int dir, cudaStream_t s);
 // Reads (and clears) the device error word after the plan's stream has been synchronised;
 // a set word fails with HVOX_EINTERNAL.
 void check_device_error(Plan &p);

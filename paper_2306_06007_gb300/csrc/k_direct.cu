@@ -231,20 +231,36 @@ __device__ __forceinline__ void load_tab(float4 *sT, const float4 *__restrict__ 
     for (int i = threadIdx.x; i < kTabN; i += blockDim.x) sT[i] = gT[i];
 }
 
+// The pointers of one job of a direct launch: a plan's chunk-ordered buffers. A launch
+// serves one job (BATCH false: the kernel parameter J0) or several (BATCH true: work item
+// it belongs to job item_job[it] of the device table jobs, so the sums of several plans
+// share one launch and its dynamic schedule).
+template <bool BATCH>
+__device__ __forceinline__ DirectJob job_of(const DirectJob &J0, const DirectJob *__restrict__ jobs,
+                                            const int *__restrict__ item_job, int it) {
+    if constexpr (BATCH)
+        return jobs[item_job[it]];
+    else
+        return J0;
+}
+
 // ------------------------------------------------------------- sky -> vis
 
 // FP32: owner = baselines, streamed = pixels (c real, chunk order).
-template <int VPT>
+template <int VPT, bool BATCH>
 __global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
-                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
-                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
-                                                           const float *__restrict__ c, float2 *__restrict__ acc,
-                                                           float sgn) {
+    const DirectJob J0, const DirectJob *__restrict__ jobs, const int *__restrict__ item_job) {
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
     __shared__ int s_next;
     for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
+        const DirectJob J = job_of<BATCH>(J0, jobs, item_job, it);
+        const float4 *__restrict__ vh = J.own_hi, *__restrict__ vl = J.own_lo;
+        const float4 *__restrict__ rh_g = J.str_hi, *__restrict__ rl_g = J.str_lo;
+        const float *__restrict__ c = static_cast<const float *>(J.val);
+        float2 *__restrict__ acc = static_cast<float2 *>(J.acc);
+        const float sgn = J.sgn;
         float3 ph[VPT], pl[VPT];
         float are[VPT], aim[VPT], cre[VPT], cim[VPT];
 #pragma unroll
@@ -306,12 +322,9 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f32(const WorkItem *__res
 }
 
 // Double-float: c given in FP64, accumulation returned in FP64.
-template <int VPT>
-__global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
-                                                          const float4 *__restrict__ vh, const float4 *__restrict__ vl,
-                                                          const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
-                                                          const double *__restrict__ c, double2 *__restrict__ acc,
-                                                          const float4 *__restrict__ gT, float sgn) {
+template <int VPT, bool BATCH>
+__global__ void __launch_bounds__(kThreads, BATCH && VPT == 2 ? 4 : 0) direct_s2v_df(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
+    const DirectJob J0, const DirectJob *__restrict__ jobs, const int *__restrict__ item_job, const float4 *__restrict__ gT) {
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
     __shared__ float2 sc[kThreads];
@@ -321,6 +334,12 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_df(const WorkItem *__rest
     __shared__ int s_next;
     for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
+        const DirectJob J = job_of<BATCH>(J0, jobs, item_job, it);
+        const float4 *__restrict__ vh = J.own_hi, *__restrict__ vl = J.own_lo;
+        const float4 *__restrict__ rh_g = J.str_hi, *__restrict__ rl_g = J.str_lo;
+        const double *__restrict__ c = static_cast<const double *>(J.val);
+        double2 *__restrict__ acc = static_cast<double2 *>(J.acc);
+        const float sgn = J.sgn;
         float3 ph[VPT], pl[VPT];
         float arh[VPT], arl[VPT], aih[VPT], ail[VPT];  // tile sums, offset by M
         float orh[VPT], orl[VPT], oih[VPT], oil[VPT];  // running sums, folded per tile
@@ -449,17 +468,20 @@ __global__ void __launch_bounds__(kThreads) direct_s2v_f64(const WorkItem *__res
 // ------------------------------------------------------------- vis -> sky
 
 // FP32: owner = pixels, streamed = baselines (V complex, chunk order). Output real.
-template <int VPT>
+template <int VPT, bool BATCH>
 __global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
-                                                           const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
-                                                           const float4 *__restrict__ vh, const float4 *__restrict__ vl,
-                                                           const float2 *__restrict__ V, float *__restrict__ acc,
-                                                           float sgn) {
+    const DirectJob J0, const DirectJob *__restrict__ jobs, const int *__restrict__ item_job) {
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
     __shared__ int s_next;
     for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
+        const DirectJob J = job_of<BATCH>(J0, jobs, item_job, it);
+        const float4 *__restrict__ rh_g = J.own_hi, *__restrict__ rl_g = J.own_lo;
+        const float4 *__restrict__ vh = J.str_hi, *__restrict__ vl = J.str_lo;
+        const float2 *__restrict__ V = static_cast<const float2 *>(J.val);
+        float *__restrict__ acc = static_cast<float *>(J.acc);
+        const float sgn = J.sgn;
         float3 rh[VPT], rl[VPT];
         float a[VPT], ca[VPT];
 #pragma unroll
@@ -519,12 +541,9 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_f32(const WorkItem *__res
     }
 }
 
-template <int VPT>
+template <int VPT, bool BATCH>
 __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__restrict__ items, int n_items, int *__restrict__ counter,
-                                                          const float4 *__restrict__ rh_g, const float4 *__restrict__ rl_g,
-                                                          const float4 *__restrict__ vh, const float4 *__restrict__ vl,
-                                                          const double2 *__restrict__ V, double *__restrict__ acc,
-                                                          const float4 *__restrict__ gT, float sgn) {
+    const DirectJob J0, const DirectJob *__restrict__ jobs, const int *__restrict__ item_job, const float4 *__restrict__ gT) {
     __shared__ float4 sh[kThreads];
     __shared__ float4 sl[kThreads];
     __shared__ float4 sv[kThreads];
@@ -534,6 +553,12 @@ __global__ void __launch_bounds__(kThreads) direct_v2s_df(const WorkItem *__rest
     __shared__ int s_next;
     for (int it = blockIdx.x; it < n_items; it = next_item(counter, s_next)) {
         const WorkItem w = items[it];
+        const DirectJob J = job_of<BATCH>(J0, jobs, item_job, it);
+        const float4 *__restrict__ rh_g = J.own_hi, *__restrict__ rl_g = J.own_lo;
+        const float4 *__restrict__ vh = J.str_hi, *__restrict__ vl = J.str_lo;
+        const double2 *__restrict__ V = static_cast<const double2 *>(J.val);
+        double *__restrict__ acc = static_cast<double *>(J.acc);
+        const float sgn = J.sgn;
         float4 rh[VPT], rl[VPT];
         float ah[VPT], al[VPT], oh[VPT], ol[VPT];  // tile sums (offset by M) and running sums
 #pragma unroll
@@ -685,10 +710,11 @@ static unsigned grid_for(int64_t n_items) {
 void launch_direct_s2v_f32(const WorkItem *items, int64_t n, int *counter, const float4 *vh, const float4 *vl, const float4 *rh,
                            const float4 *rl, const float *c, float2 *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
+    const DirectJob J{vh, vl, rh, rl, c, acc, (float)isign};
     if (vpt == 4)
-        direct_s2v_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, (float)isign);
+        direct_s2v_f32<4, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr);
     else
-        direct_s2v_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, (float)isign);
+        direct_s2v_f32<2, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr);
     check_cuda(cudaGetLastError(), "direct_s2v_f32");
 }
 
@@ -696,10 +722,11 @@ void launch_direct_s2v_df(const WorkItem *items, int64_t n, int *counter, const 
                           const float4 *rl, const double *c, double2 *acc, const float4 *tab, int isign,
                           int vpt, cudaStream_t s) {
     if (n <= 0) return;
+    const DirectJob J{vh, vl, rh, rl, c, acc, (float)isign};
     if (vpt == 4)
-        direct_s2v_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, tab, (float)isign);
+        direct_s2v_df<4, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr, tab);
     else
-        direct_s2v_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, vh, vl, rh, rl, c, acc, tab, (float)isign);
+        direct_s2v_df<2, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr, tab);
     check_cuda(cudaGetLastError(), "direct_s2v_df");
 }
 
@@ -716,10 +743,11 @@ void launch_direct_s2v_f64(const WorkItem *items, int64_t n, int *counter, const
 void launch_direct_v2s_f32(const WorkItem *items, int64_t n, int *counter, const float4 *rh, const float4 *rl, const float4 *vh,
                            const float4 *vl, const float2 *V, float *acc, int isign, int vpt, cudaStream_t s) {
     if (n <= 0) return;
+    const DirectJob J{rh, rl, vh, vl, V, acc, (float)isign};
     if (vpt == 4)
-        direct_v2s_f32<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, (float)isign);
+        direct_v2s_f32<4, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr);
     else
-        direct_v2s_f32<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, (float)isign);
+        direct_v2s_f32<2, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr);
     check_cuda(cudaGetLastError(), "direct_v2s_f32");
 }
 
@@ -727,11 +755,37 @@ void launch_direct_v2s_df(const WorkItem *items, int64_t n, int *counter, const 
                           const float4 *vl, const double2 *V, double *acc, const float4 *tab, int isign,
                           int vpt, cudaStream_t s) {
     if (n <= 0) return;
+    const DirectJob J{rh, rl, vh, vl, V, acc, (float)isign};
     if (vpt == 4)
-        direct_v2s_df<4><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, tab, (float)isign);
+        direct_v2s_df<4, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr, tab);
     else
-        direct_v2s_df<2><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, rh, rl, vh, vl, V, acc, tab, (float)isign);
+        direct_v2s_df<2, false><<<grid_for(n), kThreads, 0, s>>>(items, (int)n, counter, J, nullptr, nullptr, tab);
     check_cuda(cudaGetLastError(), "direct_v2s_df");
+}
+
+// Several jobs' work items in one launch (kind 0 FP32, 1 double-float; dir 0 sky -> vis,
+// 1 vis -> sky); jobs and item_job in device memory, items sorted largest first.
+void launch_direct_batch(int kind, int dir, const WorkItem *items, int64_t n, int *counter, const DirectJob *jobs,
+                         const int *item_job, const float4 *tab, int vpt, cudaStream_t s) {
+    if (n <= 0) return;
+    const DirectJob J0{};
+    const unsigned g = grid_for(n);
+#define HVOX_BATCH(KERNEL, ...)                                                                              \
+    if (vpt == 4)                                                                                            \
+        KERNEL<4, true><<<g, kThreads, 0, s>>>(items, (int)n, counter, J0, jobs, item_job __VA_ARGS__);      \
+    else                                                                                                     \
+        KERNEL<2, true><<<g, kThreads, 0, s>>>(items, (int)n, counter, J0, jobs, item_job __VA_ARGS__);
+    if (kind == 0 && dir == 0) {
+        HVOX_BATCH(direct_s2v_f32)
+    } else if (kind == 0) {
+        HVOX_BATCH(direct_v2s_f32)
+    } else if (dir == 0) {
+        HVOX_BATCH(direct_s2v_df, , tab)
+    } else {
+        HVOX_BATCH(direct_v2s_df, , tab)
+    }
+#undef HVOX_BATCH
+    check_cuda(cudaGetLastError(), "direct_batch");
 }
 
 void launch_direct_v2s_f64(const WorkItem *items, int64_t n, int *counter, const double *pxyz, int64_t np, const double *vxyz,

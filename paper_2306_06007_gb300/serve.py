@@ -5,7 +5,9 @@ server keeps plans resident on the device (one per geometry and tolerance, each 
 to its own CUDA stream), plans new geometries on worker threads while the GPU works,
 admits a request as soon as a slot is free, its plan is idle and the HBM budget has
 room for the plan and the request's buffers, and overlaps the admitted requests on the
-device through their streams. Completion is detected by polling a CUDA event recorded
+device through their streams. Requests of one direction admitted in the same pass go
+through one batched call (hvox_synthesize_batch / hvox_analyze_batch), so that their
+direct sums share kernel launches and one dynamic schedule, not only the device. Completion is detected by polling a CUDA event recorded
 after each request's device-to-host copy; latency = completion - arrival.
 
 `plain=True` gives the comparison form: one request at a time in arrival order, plans
@@ -64,6 +66,8 @@ class ServeReport:
     errors: dict = field(default_factory=dict)       # rid -> message of a request that failed
     # rid -> (seconds waiting for its plan, waiting for a slot after that, on the device)
     phases: dict = field(default_factory=dict)
+    # sizes of the batched calls (requests admitted together whose direct sums shared launches)
+    batches: list = field(default_factory=list)
 
     def summary(self) -> dict:
         lat = sorted(self.latency_s.values())
@@ -73,7 +77,8 @@ class ServeReport:
                "throughput_units_per_s": self.units / self.makespan_s if self.makespan_s > 0 else None,
                "makespan_s": self.makespan_s, "plans": len(self.plan_s),
                "plan_s_total": sum(self.plan_s.values()), "peak_bytes": self.peak_bytes,
-               "errors": len(self.errors)}
+               "errors": len(self.errors), "batch_calls": len(self.batches),
+               "batched_requests": sum(self.batches)}
         if lat and self.phases:
             # Where the time of the slowest 1 % of requests went (mean over them, ms).
             by_lat = sorted(self.latency_s, key=self.latency_s.get)
@@ -206,9 +211,10 @@ class Server:
                 rep.plan_s[k] = secs
                 ready[k] = time.perf_counter() - t0
                 progressed = True
-            # admission and launch
+            # admission
+            admitted = []
             i = 0
-            while i < len(arrived) and len(inflight) < self.max_inflight:
+            while i < len(arrived) and len(inflight) + len(admitted) < self.max_inflight:
                 r = arrived[i]
                 res = self.resident.get(r._key)
                 if res is None or res.busy:
@@ -217,24 +223,28 @@ class Server:
                         break
                     continue
                 io = 16.0 * (len(r.pix) + len(r.uvw)) * 2
-                if self.used + io > self.budget and inflight:
+                if self.used + io > self.budget and (inflight or admitted):
                     break
                 arrived.pop(i)
                 res.busy = True
                 self.used += io
                 rep.peak_bytes = max(rep.peak_bytes, self.used)
-                with torch.cuda.stream(res.stream):
-                    if r.direction == "s2v":
-                        x = torch.as_tensor(r.data, dtype=res.plan.real_dtype).pin_memory().to("cuda", non_blocking=True)
-                        y = res.plan.synthesize(x)
-                    else:
-                        x = torch.as_tensor(r.data, dtype=res.plan.complex_dtype).pin_memory().to("cuda", non_blocking=True)
-                        y = res.plan.analyze(x)
-                    out = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
-                    out.copy_(y, non_blocking=True)
-                    ev = torch.cuda.Event()
-                    ev.record(res.stream)
-                inflight.append(_Inflight(r, r._key, ev, out, io, time.perf_counter() - t0))
+                admitted.append((r, res, io))
+            # launch: requests of one direction admitted together go through one batched
+            # call (their direct sums share launches); a lone request uses its plan alone
+            groups = {}
+            for a in admitted:
+                groups.setdefault(a[0].direction, []).append(a)
+            for direction, grp in groups.items():
+                t_start = time.perf_counter() - t0
+                if len(grp) >= 2 and not self.plain:
+                    for ent in self._launch_batch(direction, grp):
+                        inflight.append(_Inflight(ent[0], ent[0]._key, ent[3], ent[4], ent[2], t_start))
+                    rep.batches.append(len(grp))
+                else:
+                    for r, res, io in grp:
+                        ev, out = self._launch_one(r, res)
+                        inflight.append(_Inflight(r, r._key, ev, out, io, t_start))
                 progressed = True
             # completions
             for f in [f for f in inflight if f.event.query()]:
@@ -259,6 +269,42 @@ class Server:
                 time.sleep(0.0002)
         rep.makespan_s = (time.perf_counter() - t0) - (first_arrival or 0.0)
         return rep
+
+    @staticmethod
+    def _input(r, res):
+        import torch
+        dt = res.plan.real_dtype if r.direction == "s2v" else res.plan.complex_dtype
+        return torch.as_tensor(r.data, dtype=dt).pin_memory().to("cuda", non_blocking=True)
+
+    def _launch_one(self, r, res):
+        import torch
+        with torch.cuda.stream(res.stream):
+            x = self._input(r, res)
+            y = res.plan.synthesize(x) if r.direction == "s2v" else res.plan.analyze(x)
+            out = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+            out.copy_(y, non_blocking=True)
+            ev = torch.cuda.Event()
+            ev.record(res.stream)
+        return ev, out
+
+    def _launch_batch(self, direction, grp):
+        """One batched call over the plans of grp (on the first plan's stream): one event
+        marks the whole group's completion."""
+        import torch
+        from . import analyze_batch, synthesize_batch
+        s = grp[0][1].stream
+        with torch.cuda.stream(s):
+            xs = [self._input(r, res) for r, res, _ in grp]
+            plans = [res.plan for _, res, _ in grp]
+            ys = synthesize_batch(plans, xs) if direction == "s2v" else analyze_batch(plans, xs)
+            outs = []
+            for y in ys:
+                o = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+                o.copy_(y, non_blocking=True)
+                outs.append(o)
+            ev = torch.cuda.Event()
+            ev.record(s)
+        return [(r, res, io, ev, o) for (r, res, io), o in zip(grp, outs)]
 
     def close(self):
         for r in self.resident.values():

@@ -81,3 +81,27 @@ def test_failed_request_does_not_stop_the_server(gpu_lib):
             continue
         ref = oracle.sky2vis(r.pix, r.uvw, r.data) if r.direction == "s2v" else oracle.vis2sky(r.pix, r.uvw, r.data)
         assert oracle.rel_l2(rep.results[r.rid], ref) <= 10 * r.eps
+
+
+def test_batched_admission_matches_alone(gpu_lib):
+    # With every plan resident (a second pass over the same stream), the requests admitted
+    # together go through batched calls whose direct sums share launches; each result
+    # still equals the request run alone and the oracle.
+    from paper_2306_06007_gb300.serve import Server
+    reqs = _stream(10, seed=3)
+    alone = Server(max_inflight=1)
+    rep_a = alone.run(reqs, realtime=False)
+    alone.close()
+    srv = Server(max_inflight=8)
+    srv.run(reqs, realtime=False)
+    rep = srv.run(reqs, realtime=False)
+    srv.close()
+    assert rep.batches and max(rep.batches) >= 2, rep.batches
+    assert set(rep.results) == {r.rid for r in reqs}
+    for r in reqs:
+        a, m = rep_a.results[r.rid], rep.results[r.rid]
+        assert oracle.rel_l2(m, a) <= _tol(r.eps, a), (r.rid, r.eps)
+        ref = oracle.sky2vis(r.pix, r.uvw, r.data) if r.direction == "s2v" else oracle.vis2sky(r.pix, r.uvw, r.data)
+        assert oracle.rel_l2(m, ref) <= 10 * r.eps, (r.rid, r.eps, r.direction)
+    s = rep.summary()
+    assert s["batch_calls"] == len(rep.batches) and s["batched_requests"] == sum(rep.batches)
