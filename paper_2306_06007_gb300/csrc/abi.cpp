@@ -191,13 +191,15 @@ constexpr double kEpsMarginF64 = 0.1;
 constexpr double kDoubleFloatMinEps = 1e-9;
 
 // FP64 plans transform their grids with the double-float FFT (k_dffft.cu) unless eps is
-// below 1e-11 (beyond its ~48-bit significands), the plan is the plain FP64 form, or
-// HVOX_DF_FFT=0 (comparisons); each grid shape must also be one it covers.
+// below 1e-11 (beyond its ~48-bit significands) or the plan is the plain FP64 form; each
+// grid shape must also be one it covers. The cost model prices plans by this rule alone.
 constexpr double kDfftMinEps = 1e-11;
-bool dfft_wanted(int prec, bool plain, double eps) {
-    if (const char *v = std::getenv("HVOX_DF_FFT"))
-        if (std::atoi(v) == 0) return false;
-    return prec == 2 && !plain && eps >= kDfftMinEps;
+bool dfft_wanted(int prec, bool plain, double eps) { return prec == 2 && !plain && eps >= kDfftMinEps; }
+
+// HVOX_DF_FFT=0 runs the same plan's FP64 grids through cuFFT Z2Z instead (comparisons).
+bool dfft_switched_off() {
+    const char *v = std::getenv("HVOX_DF_FFT");
+    return v && std::atoi(v) == 0;
 }
 
 void upload(DevBuf &b, const void *host, size_t bytes, cudaStream_t s) {
@@ -591,7 +593,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
         // selects full 3-D plans instead of the pruned pair.
         bool prune = true;
         if (const char *v = std::getenv("HVOX_FFT_PRUNE")) prune = std::atoi(v) != 0;
-        const bool use_dfft = dfft_wanted(p.prec, p.plain, p.eps);
+        const bool use_dfft = dfft_wanted(p.prec, p.plain, p.eps) && !dfft_switched_off();
         std::vector<size_t> max_ws(n_lanes, 0);
         auto make = [&](cufftHandle &h, int rank, long long *n, long long *emb, long long stride, long long dist,
                         long long batch, size_t &ws) {

@@ -482,8 +482,11 @@ int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s) {
             dfft_rows_kernel<false, true><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
         check_cuda(cudaGetLastError(), "dfft_rows");
     };
+    // y columns: two adjacent columns per CTA (32-byte segments) unless that leaves fewer than
+    // two CTAs per SM (long columns), then one (twice the DRAM sectors, at ~15 % of HBM).
+    const int ty = (size_t)2 * n2y * 2 * sizeof(float4) <= kFftSmemMax / 2 ? 2 : 1;
     auto ycols = [&] {
-        cols(cols_per_cta((int)n2y, 2), kDD, g, f.dy, n2x, n2x, plane, band_planes, halfK, n2z, K, half, 1, sg, s);
+        cols(cols_per_cta((int)n2y, ty), kDD, g, f.dy, n2x, n2x, plane, band_planes, halfK, n2z, K, half, 1, sg, s);
     };
     auto zcols = [&](Io io) {
         cols(cols_per_cta((int)n2z, 64), io, g, f.dz, K * plane, K * plane, 0, 1, halfK, n2z, K, half, 0, sg, s);
