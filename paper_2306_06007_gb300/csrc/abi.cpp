@@ -607,6 +607,10 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
             h = (float)x;
             l = (float)(x - (double)h);
         };
+        // Double-float FFT only when it covers every grid shape of the plan, so that the
+        // grids of every wave share one format after the FFT.
+        p.df_grids = use_dfft && prune;
+        for (const NufftBlock &bk : part.blocks) p.df_grids = p.df_grids && dfft_supported(bk.n2);
         p.dblocks.resize(order.size());
         for (Wave &w : p.waves) {
             Lane &lane = *p.lanes[w.lane];
@@ -625,7 +629,7 @@ void build_plan(Plan &p, const double *pix_in, const double *uvw_in, const doubl
                 fb.h1y = first.n1[1] / 2;
                 const int64_t plane = first.n2[0] * first.n2[1];
                 // FP64 grids: the double-float FFT on the FP32 pipes where it covers the shape.
-                fb.df = use_dfft && prune && dfft_supported(fb.n2);
+                fb.df = p.df_grids;
                 if (fb.df) {
                     DfftDev *dd[3] = {&fb.dx, &fb.dy, &fb.dz};
                     for (int q = 0; q < 3; ++q) {

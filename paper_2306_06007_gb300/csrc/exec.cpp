@@ -102,6 +102,7 @@ template <typename T> NufftArgs<T> nufft_args(const Plan &p) {
     a.inv_tmax2 = p.cheb_inv_tmax2;
     a.ppc_pix = p.ppc_pix;
     a.ppc_vis = p.ppc_vis;
+    a.df_grids = p.df_grids;
     return a;
 }
 

@@ -238,6 +238,7 @@ struct FftBatch {
     int64_t K = 1;
     FftPlans plans;
     bool df = false;          // FP64 grids through the double-float FFT instead of cuFFT Z2Z
+                              // (FP64 cells in, double-float cells out: Plan::df_grids)
     DfftDev dx, dy, dz;       // its three lengths
     int64_t h1y = 0;          // n1y / 2: the band rows are [0, h1y) and [n2y - h1y, n2y)
 };
@@ -278,6 +279,9 @@ template <typename T> struct NufftArgs {
     int deg = 0;
     double inv_tmax2 = 0.0;    // 1 / tau_max^2
     int ppc_pix = 128, ppc_vis = 128;  // points per spreading CTA (bin size), <= 128
+    // FP64 plans whose FFT grids go through the double-float FFT: after the FFT the grid
+    // holds float pairs (float4 per cell), which the double-float gathers and crop read.
+    bool df_grids = false;
 };
 
 // Stage boundaries reported by the kernel launchers to the executor's profiler.
@@ -380,6 +384,7 @@ struct Plan {
     DevBuf ddescs;                      // the same descriptors on the device
     std::vector<Wave> waves;            // waves of blocks (launch order)
     std::map<int, std::unique_ptr<DevBuf>> dfft_tw;  // twiddle tables of the double-float FFT
+    bool df_grids = false;              // every FFT batch double-float (NufftArgs::df_grids)
     DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
     DevBuf err;                         // int: device error word (kDevErr* bits), read by hvox_sync
 

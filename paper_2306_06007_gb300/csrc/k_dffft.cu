@@ -7,8 +7,8 @@
 // runs in shared memory on the FP32 pipes: Stockham auto-sorting stages of radix 4, 2, 3, 5
 // and 7 (the odd radices through the symmetric form X_k, X_{r-k} = A_k +- s i B_k, half the
 // multiplications of a plain DFT), with twiddles exp(2 pi i q / n) computed in FP64 on the
-// host and stored as float pairs. One pass per dimension reads the FP64 grid, transforms
-// and writes it back in place:
+// host and stored as float pairs. One pass per dimension transforms the grid in place; the
+// first reads FP64 cells, every pass writes float pairs (the same 16 bytes per cell):
 //   rows (x): one row per CTA, only the rows that the pruned transform needs;
 //   columns (y): two adjacent columns per CTA (32-byte sectors), every column of a plane;
 //   columns (z): 64 adjacent columns per CTA, the planes of a batch interleaved.
@@ -18,101 +18,20 @@
 #include <cstdint>
 #include <mutex>
 
+#include "dfloat.cuh"
 #include "hvox_internal.h"
 
 namespace hvox {
 
 namespace {
 
+using namespace df;
+
 constexpr int kFftThreads = 256;
 
-struct DF {
-    float h, l;
-};
 struct DC {
     DF re, im;
 };
-
-__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
-    s = __fadd_rn(a, b);
-    e = __fsub_rn(b, __fsub_rn(s, a));
-}
-
-// Double-float sum: an exact TwoSum of the high parts, the low parts added in FP32, then
-// renormalised (the "sloppy" sum of Dekker 1971 / QD). Its error is bounded by ~2^-47 of
-// |a| + |b|, which is the norm-wise bound an FFT needs (an exactly-rounded sum would cost
-// twice the instructions).
-__device__ __forceinline__ DF dadd(DF a, DF b) {
-    float s, e;
-    two_sum(a.h, b.h, s, e);
-    e = __fadd_rn(e, __fadd_rn(a.l, b.l));
-    fast_two_sum(s, e, s, e);
-    return {s, e};
-}
-
-__device__ __forceinline__ DF dneg(DF a) { return {-a.h, -a.l}; }
-
-// a b as an unnormalised pair (p, e): p = fl(a.h b.h), e = the rounding error of p (FMA,
-// exact) + the cross terms (a.l b.l, below 2^-46 of the product, is dropped).
-__device__ __forceinline__ void dmul_raw(DF a, DF b, float &p, float &e) {
-    p = __fmul_rn(a.h, b.h);
-    e = __fmaf_rn(a.l, b.h, __fmaf_rn(a.h, b.l, __fmaf_rn(a.h, b.h, -p)));
-}
-
-__device__ __forceinline__ DF dmul(DF a, DF b) {
-    float p, e, s;
-    dmul_raw(a, b, p, e);
-    fast_two_sum(p, e, s, e);
-    return {s, e};
-}
-
-// a b + sg c d for sg = +-1, with one renormalisation (the real or imaginary part of a
-// complex product).
-__device__ __forceinline__ DF dmul2(DF a, DF b, DF c, DF d, float sg) {
-    float p, e, q, f, s, t;
-    dmul_raw(a, b, p, e);
-    dmul_raw(c, d, q, f);
-    two_sum(p, sg * q, s, t);
-    t = __fadd_rn(t, __fmaf_rn(sg, f, e));
-    fast_two_sum(s, t, s, t);
-    return {s, t};
-}
-
-// Lazy sum of several double-float terms with one renormalisation at the end: s is the
-// exact running sum of the high parts (TwoSum), e collects the low parts and the TwoSum
-// errors in FP32 (error ~2^-47 of the sum of magnitudes).
-struct DAcc {
-    float s, e;
-};
-__device__ __forceinline__ DAcc acc_of(DF a) { return {a.h, a.l}; }
-__device__ __forceinline__ void acc_add(DAcc &a, float p, float e) {
-    float s, t;
-    two_sum(a.s, p, s, t);
-    a.s = s;
-    a.e = __fadd_rn(a.e, __fadd_rn(t, e));
-}
-// a += x y for double-float x, y
-__device__ __forceinline__ void acc_fma(DAcc &a, DF x, DF y) {
-    float p, e;
-    dmul_raw(x, y, p, e);
-    acc_add(a, p, e);
-}
-__device__ __forceinline__ DAcc acc_mul(DF x, DF y) {
-    float p, e;
-    dmul_raw(x, y, p, e);
-    return {p, e};
-}
-__device__ __forceinline__ DF acc_done(DAcc a) {
-    float s, e;
-    fast_two_sum(a.s, a.e, s, e);
-    return {s, e};
-}
 
 __device__ __forceinline__ DC cadd(const DC &a, const DC &b) { return {dadd(a.re, b.re), dadd(a.im, b.im)}; }
 __device__ __forceinline__ DC csub(const DC &a, const DC &b) { return {dadd(a.re, dneg(b.re)), dadd(a.im, dneg(b.im))}; }
@@ -129,36 +48,6 @@ __device__ __forceinline__ DC times_j(const DC &a, float sg) {
 
 __device__ __forceinline__ DC from4(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
 __device__ __forceinline__ float4 to4(const DC &c) { return make_float4(c.re.h, c.re.l, c.im.h, c.im.l); }
-
-// FP64 <-> double-float by bit manipulation: GB300 issues FP64 instructions (conversions
-// included) at 1/64 of its FP32 rate, more than the transform's own arithmetic.
-// split: hi = x truncated to 24 significant bits (exact), lo = the remaining 29 bits of the
-// significand rounded to 24 (one integer-to-float conversion and an exact power-of-two
-// scale). |x| below 2^-126 flushes to 0, lo below 2^-126 too (|x| < 2^-102 keeps fewer
-// bits); |x| >= 2^128 becomes infinite.
-__device__ __forceinline__ DF split_bits(double x) {
-    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
-    const unsigned hi32 = (unsigned)(b >> 32), lo32 = (unsigned)b;
-    const unsigned sign = hi32 & 0x80000000u;
-    const int e = (int)((hi32 >> 20) & 0x7FFu) - 896;  // biased float exponent (1023 - 127)
-    if (e <= 0) return {0.f, 0.f};
-    if (e >= 255) return {__uint_as_float(sign | 0x7F800000u), 0.f};
-    const float h = __uint_as_float(sign | ((unsigned)e << 23) | ((hi32 & 0xFFFFFu) << 3) | (lo32 >> 29));
-    // lo = r 2^(E - 1075) with E the double's biased exponent = (r 2^-29) 2^(e - 150); the
-    // second factor is a normal float (biased exponent e - 23) for e >= 24.
-    const float scale = e >= 24 ? __uint_as_float(sign | ((unsigned)(e - 23) << 23)) : 0.f;
-    return {h, __fmul_rn(__fmul_rn(__uint2float_rn(lo32 & 0x1FFFFFFFu), 0x1p-29f), scale)};
-}
-
-// A float as the double of the same value (exact; subnormal floats, below 2^-126, as 0).
-__device__ __forceinline__ double f2d_bits(float f) {
-    const unsigned u = __float_as_uint(f);
-    const unsigned ef = (u >> 23) & 0xFFu;
-    if (ef == 0) return 0.0;
-    const unsigned long long E = ef == 255 ? 2047ull : (unsigned long long)(ef + 896);
-    return __longlong_as_double((long long)(((unsigned long long)(u & 0x80000000u) << 32) | (E << 52) |
-                                            ((unsigned long long)(u & 0x7FFFFFu) << 29)));
-}
 
 __device__ __forceinline__ float4 load_f64(const double2 *p) {
     const double2 v = *p;
@@ -366,7 +255,7 @@ void set_fft_attrs() {
     static std::once_flag once;
     std::call_once(once, [] {
         allow_smem(dfft_rows_kernel<true, false>);
-        allow_smem(dfft_rows_kernel<false, true>);
+        allow_smem(dfft_rows_kernel<false, false>);
         allow_cols<1>();
         allow_cols<2>();
         allow_cols<8>();
@@ -470,8 +359,9 @@ int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s) {
     const int64_t n2x = f.n2[0], n2y = f.n2[1], n2z = f.n2[2], K = f.K, half = f.half;
     const int64_t halfK = half * K, band_planes = 2 * halfK, plane = n2x * n2y;
     const float sg = (float)sign;
-    // The grid is FP64 before the first pass and after the last; in between it holds the
-    // double-float values.
+    // The grid is FP64 before the first pass (written by the deconvolution or the spreading)
+    // and holds double-float values after it: the last pass leaves them for the
+    // double-float gathers (sky -> vis) or crop (vis -> sky).
     auto rows = [&](Io io) {
         const int64_t r = 2 * f.h1y;  // band rows only
         const size_t smem = (size_t)2 * n2x * sizeof(float4);
@@ -479,7 +369,7 @@ int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s) {
         if (io == kFD)
             dfft_rows_kernel<true, false><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
         else
-            dfft_rows_kernel<false, true><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
+            dfft_rows_kernel<false, false><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
         check_cuda(cudaGetLastError(), "dfft_rows");
     };
     // y columns: two adjacent columns per CTA (32-byte segments) unless that leaves fewer than
@@ -494,11 +384,11 @@ int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s) {
     if (band_input) {  // only the band rows of the band planes are nonzero
         rows(kFD);
         ycols();
-        zcols(kDF);
+        zcols(kDD);
     } else {  // only the band rows of the band planes are read afterwards
         zcols(kFD);
         ycols();
-        rows(kDF);
+        rows(kDD);
     }
     return 3;
 }

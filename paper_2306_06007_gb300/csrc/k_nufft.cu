@@ -30,6 +30,7 @@
 #include <mutex>
 #include <vector>
 
+#include "dfloat.cuh"
 #include "hvox_internal.h"
 
 namespace hvox {
@@ -668,6 +669,182 @@ __global__ void __launch_bounds__(128)
     atomicAdd(acc + b.p0 + i, pr * sr + pim * si);  // Re(conj(P) y)
 }
 
+// FP64 plans whose grids hold float pairs after the double-float FFT: the gathers in
+// double-float arithmetic on the FP32 pipes. The kernel weights are evaluated in FP64 once
+// per point and split into float pairs; every tap is a double-float product added to a
+// lazy double-float sum (~24 FP32 instructions, where the FP64 form spends two FP64 FMAs
+// issued at 1/64 of the FP32 rate). Layout as the FP64 kernels above.
+template <int W> struct GatherSharedDF {
+    static constexpr int kWStride = 3 * W + 1;
+    float2 w[kSpreadPoints][kWStride];  // x, y, z weights of each point (hi, lo)
+    double q[kSpreadPoints][2];         // complex factor applied to the window sum
+    int i0[kSpreadPoints][3];           // window start (i0[.][0] = INT_MIN: no point)
+};
+
+template <int W>
+__device__ __forceinline__ void stage_point_df(GatherSharedDF<W> &sh, int slot, bool act, const int i0[3],
+                                               const double fr[3], double qr, double qi, double beta) {
+    if (!act) {
+        sh.i0[slot][0] = INT_MIN;
+        return;
+    }
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        double t[W];
+        es_weights<double, W>(fr[d], beta, t);
+#pragma unroll
+        for (int j = 0; j < W; ++j) {
+            const df::DF v = df::split_bits(t[j]);
+            sh.w[slot][d * W + j] = make_float2(v.h, v.l);
+        }
+    }
+    sh.q[slot][0] = qr;
+    sh.q[slot][1] = qi;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) sh.i0[slot][d] = i0[d];
+}
+
+__device__ __forceinline__ df::DF df_of(float2 v) { return {v.x, v.y}; }
+
+// Window sum of point `slot` over the double-float grid G (this lane's x taps), reduced
+// over the group's 8 lanes: every lane of the group returns the full sum.
+template <int W>
+__device__ __forceinline__ void gather_window_df(const GatherSharedDF<W> &sh, int slot, int jx0, const int ng[3],
+                                                 int64_t zs, const float4 *__restrict__ G, unsigned mask, double &sr,
+                                                 double &si) {
+    constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;
+    const int px0 = sh.i0[slot][0], py0 = sh.i0[slot][1], pz0 = sh.i0[slot][2];
+    const int64_t nx = ng[0];
+    df::DF wxv[kXT];
+    int cx[kXT];
+    bool on[kXT];
+#pragma unroll
+    for (int t = 0; t < kXT; ++t) {
+        const int jx = jx0 + t * kGroupLanes;
+        on[t] = jx < W;
+        wxv[t] = on[t] ? df_of(sh.w[slot][jx]) : df::DF{0.f, 0.f};
+        cx[t] = on[t] ? wrap(px0 + jx, ng[0]) : 0;
+    }
+    int yrow[W];
+#pragma unroll
+    for (int j = 0; j < W; ++j) yrow[j] = wrap(py0 + j, ng[1]);
+    df::DAcc ar{0.f, 0.f}, ai{0.f, 0.f};
+    for (int jz = 0; jz < W; ++jz) {
+        const df::DF wz = df_of(sh.w[slot][2 * W + jz]);
+        const int64_t zoff = (int64_t)wrap(pz0 + jz, ng[2]) * zs;
+#pragma unroll
+        for (int jy = 0; jy < W; ++jy) {
+            const df::DF c = df::dmul(df_of(sh.w[slot][W + jy]), wz);
+            const float4 *row = G + zoff + yrow[jy] * nx;
+#pragma unroll
+            for (int t = 0; t < kXT; ++t)
+                if (on[t]) {
+                    const float4 g = row[cx[t]];
+                    const df::DF f = df::dmul(wxv[t], c);
+                    df::acc_fma(ar, {g.x, g.y}, f);
+                    df::acc_fma(ai, {g.z, g.w}, f);
+                }
+        }
+    }
+    df::DF a = df::acc_done(ar), b = df::acc_done(ai);
+#pragma unroll
+    for (int off = kGroupLanes / 2; off > 0; off >>= 1) {
+        const df::DF oa = {__shfl_xor_sync(mask, a.h, off, kGroupLanes), __shfl_xor_sync(mask, a.l, off, kGroupLanes)};
+        const df::DF ob = {__shfl_xor_sync(mask, b.h, off, kGroupLanes), __shfl_xor_sync(mask, b.l, off, kGroupLanes)};
+        a = df::dadd(a, oa);
+        b = df::dadd(b, ob);
+    }
+    sr = df::to_double(a);
+    si = df::to_double(b);
+}
+
+template <int W>
+__global__ void __launch_bounds__(kGatherThreads)
+    interp_vis_df_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ G2base,
+                         const float4 *__restrict__ vh, const float4 *__restrict__ vl, const double *__restrict__ soa,
+                         int64_t n_all, const double *__restrict__ cc, int deg, double inv_tmax2,
+                         double2 *__restrict__ acc, double beta, int isign) {
+    __shared__ GatherSharedDF<W> sh;
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
+    const int tid = threadIdx.x;
+    const int64_t base = blockIdx.x * (int64_t)kSpreadPoints;
+    if (base >= b.nv) return;  // uniform
+    if (tid < kSpreadPoints) {
+        const int64_t k = base + tid;
+        int i0[3] = {0, 0, 0};
+        double fr[3] = {0, 0, 0}, qr = 0, qi = 0;
+        const bool act = k < b.nv;
+        if (act) geo_vis<W>(b, b.v0 + k, vh, vl, soa, n_all, isign, cc, deg, inv_tmax2, i0, fr, qr, qi);
+        stage_point_df<W>(sh, tid, act, i0, fr, qr, qi, beta);
+    }
+    __syncthreads();
+    const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
+    const unsigned mask = 0xFFu << (g * kGroupLanes);
+    const int ng[3] = {b.n2[0], b.n2[1], b.n2[2]};
+    const float4 *G2 = G2base + b.g2_off;
+    constexpr int kRounds = kSpreadPoints * kGroupLanes / kGatherThreads;
+    for (int round = 0; round < kRounds; ++round) {
+        const int p = g * 32 + warp * kRounds + round;
+        if (sh.i0[p][0] == INT_MIN) continue;
+        double sr, si;
+        gather_window_df<W>(sh, p, jx0, ng, b.zs2, G2, mask, sr, si);
+        if (jx0 == 0) {
+            const double qr = sh.q[p][0], qi = sh.q[p][1];
+            grid_add(acc + b.v0 + base + p, qr * sr - qi * si, qr * si + qi * sr);
+        }
+    }
+}
+
+template <int W>
+__global__ void __launch_bounds__(128)
+    interp_pix_df_kernel(const NufftDev *__restrict__ descs, int b0, const float4 *__restrict__ G1base,
+                         const float4 *__restrict__ rh, const float4 *__restrict__ rl, const double *__restrict__ soa,
+                         int64_t n_all, double *__restrict__ acc, double beta, int isign) {
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= b.np) return;
+    int i0[3];
+    double fr[3], pr, pim;
+    geo_pix<W>(b, b.p0 + i, rh, rl, soa, n_all, isign, i0, fr, pr, pim);
+    df::DF wx[W], wy[W], wz[W];
+    {
+        double t[W];
+        es_weights<double, W>(fr[0], beta, t);
+#pragma unroll
+        for (int j = 0; j < W; ++j) wx[j] = df::split_bits(t[j]);
+        es_weights<double, W>(fr[1], beta, t);
+#pragma unroll
+        for (int j = 0; j < W; ++j) wy[j] = df::split_bits(t[j]);
+        es_weights<double, W>(fr[2], beta, t);
+#pragma unroll
+        for (int j = 0; j < W; ++j) wz[j] = df::split_bits(t[j]);
+    }
+    const int64_t nx = b.n1[0], ny = b.n1[1];
+    const float4 *G1 = G1base + b.g1_off;
+    df::DAcc sr{0.f, 0.f}, si{0.f, 0.f};
+    for (int jz = 0; jz < W; ++jz) {
+        for (int jy = 0; jy < W; ++jy) {
+            const float4 *row = G1 + ((int64_t)(i0[2] + jz) * ny + (i0[1] + jy)) * nx + i0[0];
+            df::DAcc rr{0.f, 0.f}, ri{0.f, 0.f};
+#pragma unroll
+            for (int jx = 0; jx < W; ++jx) {
+                const float4 g = row[jx];
+                df::acc_fma(rr, {g.x, g.y}, wx[jx]);
+                df::acc_fma(ri, {g.z, g.w}, wx[jx]);
+            }
+            const df::DF wyz = df::dmul(wy[jy], wz[jz]);
+            df::acc_fma(sr, df::acc_done(rr), wyz);
+            df::acc_fma(si, df::acc_done(ri), wyz);
+        }
+    }
+    // Re(conj(P) y)
+    atomicAdd(acc + b.p0 + i, pr * df::to_double(df::acc_done(sr)) + pim * df::to_double(df::acc_done(si)));
+}
+
 // ------------------------------------------------------------------ deconvolution passes
 
 // Row-wise passes over (y, z) rows of a grid: each warp takes a contiguous range of rows,
@@ -809,6 +986,59 @@ __global__ void __launch_bounds__(kRowThreads) crop_deconv_kernel(const NufftDev
     }
 }
 
+// crop_deconv for double-float grids (after the double-float FFT): reads float-pair cells
+// of the n2 band, writes the n1 grid as float pairs for interp_pix_df_kernel; the
+// deconvolution factor is formed in FP64 once per cell and multiplied in double-float.
+__global__ void __launch_bounds__(kRowThreads) crop_deconv_df_kernel(const NufftDev *__restrict__ descs, int b0,
+                                                                     const float4 *__restrict__ G2base,
+                                                                     float4 *__restrict__ G1base,
+                                                                     const double *__restrict__ ipsi_all) {
+    __shared__ NufftDev sb;
+    load_desc(sb, descs + b0 + blockIdx.y);
+    const NufftDev &b = sb;
+    const int n1x = b.n1[0], n1y = b.n1[1], n1z = b.n1[2];
+    const int n2x = b.n2[0], n2y = b.n2[1], n2z = b.n2[2];
+    const double *ipsi = ipsi_all + b.psi_off;
+    const double *px = ipsi, *py = ipsi + n1x, *pz = py + n1y;
+    const float4 *G2 = G2base + b.g2_off;
+    float4 *G1 = G1base + b.g1_off;
+    int64_t r, cnt;
+    warp_rows((int64_t)n1y * n1z, r, cnt);
+    if (cnt == 0) return;
+    int iy = (int)(r % n1y), iz = (int)(r / n1y);
+    const int lane = threadIdx.x & 31;
+    for (int64_t k = 0; k < cnt; ++k) {
+        int jy = iy - n1y / 2, jz = iz - n1z / 2;
+        jy += jy < 0 ? n2y : 0;
+        jz += jz < 0 ? n2z : 0;
+        const float4 *in = G2 + (int64_t)jz * b.zs2 + (int64_t)jy * n2x;
+        float4 *out = G1 + ((int64_t)iz * n1y + iy) * n1x;
+        const double fyz = py[iy] * pz[iz];
+        for (int x0 = lane; x0 < n1x; x0 += 32 * kRowUnroll) {
+            float4 v[kRowUnroll];
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u) {
+                const int ix = x0 + 32 * u;
+                if (ix < n1x) {
+                    int jx = ix - n1x / 2;
+                    jx += jx < 0 ? n2x : 0;
+                    const float4 g = in[jx];
+                    const df::DF f = df::split_bits(px[ix] * fyz);
+                    const df::DF re = df::dmul({g.x, g.y}, f), im = df::dmul({g.z, g.w}, f);
+                    v[u] = make_float4(re.h, re.l, im.h, im.l);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kRowUnroll; ++u)
+                if (x0 + 32 * u < n1x) out[x0 + 32 * u] = v[u];
+        }
+        if (++iy == n1y) {
+            iy = 0;
+            ++iz;
+        }
+    }
+}
+
 #define HVOX_W_SWITCH(w, CALL)                                         \
     switch (w) {                                                       \
         case 2: CALL(2); break;                                        \
@@ -912,6 +1142,19 @@ void nufft_wave_s2v(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
     for (const FftBatch &f : w.ffts) n_fft += fft_batch<T>(f, a.isign < 0 ? CUFFT_FORWARD : CUFFT_INVERSE, true, s);
     hook.end(HVOX_STAGE_FFT, n_fft, s);
     hook.begin(HVOX_STAGE_INTERP, s);
+    if constexpr (sizeof(T) == 8) {
+        if (a.df_grids) {
+#define CALL(W)                                                                                                   \
+    interp_vis_df_kernel<W><<<igrid, kGatherThreads, 0, s>>>(a.descs, w.b0, static_cast<const float4 *>(g2),      \
+                                                             a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, a.cheb, a.deg, \
+                                                             a.inv_tmax2, acc, a.beta, a.isign)
+            HVOX_W_SWITCH(wd, CALL)
+#undef CALL
+            check_cuda(cudaGetLastError(), "interp_vis_df");
+            hook.end(HVOX_STAGE_INTERP, 1, s);
+            return;
+        }
+    }
 #define CALL(W)                                                                                                   \
     interp_vis_kernel<T, W><<<igrid, kGatherThreads, 0, s>>>(                                                \
         a.descs, w.b0, static_cast<const cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, a.cheb, a.deg, \
@@ -948,6 +1191,24 @@ void nufft_wave_v2s(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
     for (const FftBatch &f : w.ffts)  // transpose: opposite sign
         n_fft += fft_batch<T>(f, a.isign < 0 ? CUFFT_INVERSE : CUFFT_FORWARD, false, s);
     hook.end(HVOX_STAGE_FFT, n_fft, s);
+    if constexpr (sizeof(T) == 8) {
+        if (a.df_grids) {
+            hook.begin(HVOX_STAGE_DECONV, s);
+            crop_deconv_df_kernel<<<cgrid, kRowThreads, 0, s>>>(a.descs, w.b0, static_cast<const float4 *>(g2),
+                                                                static_cast<float4 *>(g1), a.ipsi);
+            check_cuda(cudaGetLastError(), "crop_deconv_df");
+            hook.end(HVOX_STAGE_DECONV, 1, s);
+            hook.begin(HVOX_STAGE_INTERP, s);
+#define CALL(W)                                                                                                   \
+    interp_pix_df_kernel<W><<<igrid, 128, 0, s>>>(a.descs, w.b0, static_cast<const float4 *>(g1), a.pix_hi,      \
+                                                  a.pix_lo, a.pix_soa, a.n_pix, acc, a.beta, a.isign)
+            HVOX_W_SWITCH(wd, CALL)
+#undef CALL
+            check_cuda(cudaGetLastError(), "interp_pix_df");
+            hook.end(HVOX_STAGE_INTERP, 1, s);
+            return;
+        }
+    }
     hook.begin(HVOX_STAGE_DECONV, s);
     crop_deconv_kernel<T><<<cgrid, kRowThreads, 0, s>>>(a.descs, w.b0, static_cast<const cplx_t<T> *>(g2),
                                                         static_cast<cplx_t<T> *>(g1), a.ipsi);
