@@ -765,6 +765,12 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.eps = eps;
     p.isign = isign;
     p.plain = o.plain != 0;
+    // Fixed-point spreading tiles for FP32 plans (measured 3-7 % faster than float shared
+    // atomics and exact in the sums). FP64 plans keep FP64 shared atomics: with double-float
+    // products the fixed-point tile measured slower there (24.2 against 16.8 ms on the 3 km
+    // case at eps 1e-9). HVOX_SPREAD_TILE=float selects float atomics for FP32 plans too.
+    p.int_tile = p.prec == 1 && !p.plain;
+    if (const char *v = std::getenv("HVOX_SPREAD_TILE")) p.int_tile = p.int_tile && std::string(v) != "float";
     if (o.graphs < -1 || o.graphs > 1) fail(HVOX_EINVAL, "hvox_plan: graphs must be -1, 0 or 1");
     p.graphs_opt = o.graphs;
     if (o.chunk_order < 0 || o.chunk_order > 1) fail(HVOX_EINVAL, "hvox_plan: chunk_order must be 0 or 1");
