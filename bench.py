@@ -51,19 +51,22 @@ FLOPS_PER_PAIR = 16.0                      # algorithmic flops per (pixel, basel
 # dram__bytes_write.sum of the full-size launches, mean of two steps' s2v and v2s launches)
 # and thread instructions per pair of the double-float kernels (smsp__inst_executed.sum x 32
 # / pairs, 100k-baseline case; those kernels are unchanged since that capture).
-DIRECT_COUNTERS = {1e-9: ("4bd864c34d1267f8e16c78fc6e727b931df1b0290a13386a3647fb00d039eb9d", 183560000.0, 74.0)}
+# ncu counters of the direct kernels on the full LOFAR-like workload, valid while the kernel
+# source and the owners per thread are those they were taken with:
+# eps -> (sha256 of k_direct.cu, owners per thread, DRAM bytes per launch, instructions per pair)
+DIRECT_COUNTERS = {1e-9: ("4bd864c34d1267f8e16c78fc6e727b931df1b0290a13386a3647fb00d039eb9d", 4, 126990144.0, 73.0)}
 
 
-def direct_counters(eps, config, other_workload, n_vis):
+def direct_counters(eps, config, other_workload, n_vis, vpt):
     """(traffic bytes per launch, instructions per pair) or (None, None)."""
     import hashlib
     entry = DIRECT_COUNTERS.get(eps)
-    if entry is None or config != 2 or other_workload or n_vis:
+    if entry is None or config != 2 or other_workload or n_vis or vpt != entry[1]:
         return None, None
     path = os.path.join(ROOT, "paper_2306_06007_gb300", "csrc", "k_direct.cu")
     with open(path, "rb") as f:
         digest = hashlib.sha256(f.read()).hexdigest()
-    return (entry[1], entry[2]) if digest == entry[0] else (None, None)
+    return (entry[2], entry[3]) if digest == entry[0] else (None, None)
 
 
 def dist_env():
@@ -464,7 +467,8 @@ def run_gpu(args):
     if dom == "direct":
         pairs_per_launch = info["direct_pairs"]
         achieved = pairs_per_launch * FLOPS_PER_PAIR / avg_s
-        traffic, ipp = direct_counters(args.eps, args.config, args.core_radius or args.radius_km, args.n_vis)
+        traffic, ipp = direct_counters(args.eps, args.config, args.core_radius or args.radius_km, args.n_vis,
+                                       info.get("direct_vpt"))
         roofline = {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK_FLOPS / 1e12,
                     "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_FLOPS, "traffic": traffic,
                     "kernel": "direct_s2v + direct_v2s (one launch each per step)",

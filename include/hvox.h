@@ -192,6 +192,7 @@ typedef struct {
     int32_t fft_batches;         /* batched FFTs of a transform (one per grid shape and wave) */
     int32_t fft_batches_df;      /* of those, FP64 grids transformed in double-float arithmetic
                                     on the FP32 pipes (the rest: cuFFT) */
+    int32_t direct_vpt;          /* owners (points) per thread of the direct kernels, 2 or 4 */
 } hvox_info;
 
 /*

@@ -59,7 +59,8 @@ class Info(ctypes.Structure):
                 ("spread_cells", ctypes.c_double), ("fft_work", ctypes.c_double), ("box_ratio", ctypes.c_double),
                 ("spread_bin_pix", ctypes.c_int32), ("spread_bin_vis", ctypes.c_int32),
                 ("kernel_width_rule", ctypes.c_int32), ("probe_error", ctypes.c_double),
-                ("fft_batches", ctypes.c_int32), ("fft_batches_df", ctypes.c_int32)]
+                ("fft_batches", ctypes.c_int32), ("fft_batches_df", ctypes.c_int32),
+                ("direct_vpt", ctypes.c_int32)]
 
 
 class Stats(ctypes.Structure):

@@ -765,12 +765,6 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.eps = eps;
     p.isign = isign;
     p.plain = o.plain != 0;
-    // Fixed-point spreading tiles for FP32 plans (measured 3-7 % faster than float shared
-    // atomics and exact in the sums). FP64 plans keep FP64 shared atomics: with double-float
-    // products the fixed-point tile measured slower there (24.2 against 16.8 ms on the 3 km
-    // case at eps 1e-9). HVOX_SPREAD_TILE=float selects float atomics for FP32 plans too.
-    p.int_tile = p.prec == 1 && !p.plain;
-    if (const char *v = std::getenv("HVOX_SPREAD_TILE")) p.int_tile = p.int_tile && std::string(v) != "float";
     if (o.graphs < -1 || o.graphs > 1) fail(HVOX_EINVAL, "hvox_plan: graphs must be -1, 0 or 1");
     p.graphs_opt = o.graphs;
     if (o.chunk_order < 0 || o.chunk_order > 1) fail(HVOX_EINVAL, "hvox_plan: chunk_order must be 0 or 1");
@@ -789,7 +783,17 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.eps_es = e * (p.prec == 1 ? kEpsMarginF32 : kEpsMarginF64);
     p.direct_f64 = p.plain || (p.prec == 2 && e < kDoubleFloatMinEps);
     p.es = p.fixed_w ? es_with_width(p.fixed_w, p.sigma) : es_params_within(p.eps_es, e, p.sigma);
-    // Points per thread of the direct kernels (tuning knob; 2 or 4).
+    // Fixed-point spreading tiles for FP32 plans (measured 3-7 % faster than float shared
+    // atomics and exact in the sums). FP64 plans keep FP64 shared atomics: with double-float
+    // products the fixed-point tile measured slower there (24.1 against 16.7 ms on the 3 km
+    // case at eps 1e-9). HVOX_SPREAD_TILE=float selects float atomics for FP32 plans too.
+    p.int_tile = p.prec == 1 && !p.plain;
+    if (const char *v = std::getenv("HVOX_SPREAD_TILE")) p.int_tile = p.int_tile && std::string(v) != "float";
+    // Owners per thread of the direct kernels: four for the double-float kernels (LOFAR-like
+    // sky x 1.4M baselines at eps 1e-9: 320.2 against 327.8 ms per step), two for the FP32
+    // ones (config 2 at eps 1e-6: 125.3 against 126.8 ms) and the FP64 ones. HVOX_DIRECT_VPT
+    // (2 or 4) overrides.
+    p.direct_vpt = (p.prec == 2 && !p.direct_f64) ? 4 : 2;
     if (const char *v = std::getenv("HVOX_DIRECT_VPT")) p.direct_vpt = std::atoi(v) == 4 ? 4 : 2;
 }
 
@@ -830,6 +834,7 @@ void fill_info(const Plan &p, hvox_info *info) {
     info->spread_bin_vis = p.ppc_vis;
     info->kernel_width_rule = es_params_within(p.eps_es, p.eps > 0 ? p.eps : 1e-6, p.sigma).w;
     info->probe_error = p.probe_error;
+    info->direct_vpt = p.direct_vpt;
     info->fft_batches = info->fft_batches_df = 0;
     for (const Wave &w : p.waves)
         for (const FftBatch &f : w.ffts) {

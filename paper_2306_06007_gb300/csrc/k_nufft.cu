@@ -277,9 +277,26 @@ template <typename T, int W> struct SpreadShared {
     static constexpr int kWStride = 3 * W + 1;  // odd row stride: fewer bank conflicts
     T w[kSpreadPoints][kWStride];                // x, y, z weights of each point
     T v[kSpreadPoints][2];                       // complex value
+    T fr[kSpreadPoints][3];                      // fractional window offsets
     int i0[kSpreadPoints][3];                    // window start (i0[.][0] = INT_MIN: no point)
     int lo[3], hi[3];
 };
+
+// Kernel weights of the staged points: 3 x 128 rows (point, dimension), one per thread of
+// the first 384, so the exponentials of a bin are spread over 12 warps instead of 4.
+template <typename T, int W> __device__ __forceinline__ void stage_weights(SpreadShared<T, W> &sh, T beta) {
+    const int tid = threadIdx.x;
+    static_assert(kSpreadThreads >= 3 * kSpreadPoints, "one thread per weight row");
+    if (tid < 3 * kSpreadPoints) {
+        const int p = tid % kSpreadPoints, d = tid / kSpreadPoints;
+        if (sh.i0[p][0] != INT_MIN) {
+            T wv[W];
+            es_weights<T, W>(sh.fr[p][d], beta, wv);
+#pragma unroll
+            for (int j = 0; j < W; ++j) sh.w[p][d * W + j] = wv[j];
+        }
+    }
+}
 
 template <typename T, int W> __host__ __device__ constexpr int tile_bytes() {
     return ((kSmemPerCta - (int)sizeof(SpreadShared<T, W>) - (int)sizeof(NufftDev)) / (2 * (int)sizeof(T) * 32)) *
@@ -330,20 +347,11 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     __syncthreads();
     if (tid < kSpreadPoints) {
         if (act) {
-            T wx[W], wy[W], wz[W];
-            es_weights<T, W>(fr[0], beta, wx);
-            es_weights<T, W>(fr[1], beta, wy);
-            es_weights<T, W>(fr[2], beta, wz);
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                sh.w[tid][j] = wx[j];
-                sh.w[tid][W + j] = wy[j];
-                sh.w[tid][2 * W + j] = wz[j];
-            }
             sh.v[tid][0] = vr;
             sh.v[tid][1] = vi;
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
+                sh.fr[tid][d] = fr[d];
                 sh.i0[tid][d] = i0[d];
                 atomicMin(&sh.lo[d], i0[d]);
                 atomicMax(&sh.hi[d], i0[d]);
@@ -354,6 +362,8 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     }
     __syncthreads();
     if (sh.hi[0] < sh.lo[0]) return;  // no point in this CTA (uniform across the CTA)
+    stage_weights<T, W>(sh, beta);
+    __syncthreads();
     const int lo0 = sh.lo[0], lo1 = sh.lo[1], lo2 = sh.lo[2];
     const int64_t tx = (int64_t)sh.hi[0] - lo0 + W, ty = (int64_t)sh.hi[1] - lo1 + W,
                   tz = (int64_t)sh.hi[2] - lo2 + W;
@@ -507,18 +517,9 @@ __device__ __forceinline__ void spread_cta_int(bool act, const int i0[3], const 
     __syncthreads();
     if (tid < kSpreadPoints) {
         if (act) {
-            T wx[W], wy[W], wz[W];
-            es_weights<T, W>(fr[0], beta, wx);
-            es_weights<T, W>(fr[1], beta, wy);
-            es_weights<T, W>(fr[2], beta, wz);
-#pragma unroll
-            for (int j = 0; j < W; ++j) {
-                sh.w[tid][j] = wx[j];
-                sh.w[tid][W + j] = wy[j];
-                sh.w[tid][2 * W + j] = wz[j];
-            }
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
+                sh.fr[tid][d] = fr[d];
                 sh.i0[tid][d] = i0[d];
                 atomicMin(&sh.lo[d], i0[d]);
                 atomicMax(&sh.hi[d], i0[d]);
@@ -532,6 +533,7 @@ __device__ __forceinline__ void spread_cta_int(bool act, const int i0[3], const 
     }
     __syncthreads();
     if (sh.hi[0] < sh.lo[0] || s_maxbits == 0u) return;  // nothing to add (uniform)
+    stage_weights<T, W>(sh, beta);
     // every |value| < 2^e; taps in units 2^(e - 43)
     const int e = (int)((s_maxbits >> 23) & 0xFFu) - 126;
     if (tid < kSpreadPoints && act) {
