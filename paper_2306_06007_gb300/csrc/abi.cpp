@@ -783,12 +783,6 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     p.eps_es = e * (p.prec == 1 ? kEpsMarginF32 : kEpsMarginF64);
     p.direct_f64 = p.plain || (p.prec == 2 && e < kDoubleFloatMinEps);
     p.es = p.fixed_w ? es_with_width(p.fixed_w, p.sigma) : es_params_within(p.eps_es, e, p.sigma);
-    // Fixed-point spreading tiles for FP32 plans (measured 3-7 % faster than float shared
-    // atomics and exact in the sums). FP64 plans keep FP64 shared atomics: with double-float
-    // products the fixed-point tile measured slower there (24.1 against 16.7 ms on the 3 km
-    // case at eps 1e-9). HVOX_SPREAD_TILE=float selects float atomics for FP32 plans too.
-    p.int_tile = p.prec == 1 && !p.plain;
-    if (const char *v = std::getenv("HVOX_SPREAD_TILE")) p.int_tile = p.int_tile && std::string(v) != "float";
     // Owners per thread of the direct kernels: four for the double-float kernels (LOFAR-like
     // sky x 1.4M baselines at eps 1e-9: 320.2 against 327.8 ms per step), two for the FP32
     // ones (config 2 at eps 1e-6: 125.3 against 126.8 ms) and the FP64 ones. HVOX_DIRECT_VPT

@@ -282,9 +282,6 @@ template <typename T> struct NufftArgs {
     // FP64 plans whose FFT grids go through the double-float FFT: after the FFT the grid
     // holds float pairs (float4 per cell), which the double-float gathers and crop read.
     bool df_grids = false;
-    // Spreading tiles of fixed-point 32-bit limbs (native shared integer atomics) instead of
-    // float / FP64 shared atomics (compare-and-swap loops); FP32 plans.
-    bool int_tile = false;
 };
 
 // Stage boundaries reported by the kernel launchers to the executor's profiler.
@@ -388,7 +385,6 @@ struct Plan {
     std::vector<Wave> waves;            // waves of blocks (launch order)
     std::map<int, std::unique_ptr<DevBuf>> dfft_tw;  // twiddle tables of the double-float FFT
     bool df_grids = false;              // every FFT batch double-float (NufftArgs::df_grids)
-    bool int_tile = false;              // NufftArgs::int_tile
     DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
     DevBuf err;                         // int: device error word (kDevErr* bits), read by hvox_sync
 

@@ -363,7 +363,6 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     __syncthreads();
     if (sh.hi[0] < sh.lo[0]) return;  // no point in this CTA (uniform across the CTA)
     stage_weights<T, W>(sh, beta);
-    __syncthreads();
     const int lo0 = sh.lo[0], lo1 = sh.lo[1], lo2 = sh.lo[2];
     const int64_t tx = (int64_t)sh.hi[0] - lo0 + W, ty = (int64_t)sh.hi[1] - lo1 + W,
                   tz = (int64_t)sh.hi[2] - lo2 + W;
@@ -376,8 +375,8 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
             tre[j] = T(0);
             tim[j] = T(0);
         }
-        __syncthreads();
     }
+    __syncthreads();
     const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
     constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;  // x taps per lane (1 or 2)
     const int rounds = (ppc + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32);
@@ -456,219 +455,10 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     }
 }
 
-// Integer tile (the default for FP32 plans): the shared tile holds each
-// cell's real and imaginary parts as fixed-point numbers in two 32-bit limbs, value =
-// (H 2^22 + L) u with u = 2^(e - 43) per CTA and every |value| of the CTA's points below
-// 2^e, so a tap is two native 32-bit shared atomicAdds per part (a float atomicAdd into
-// shared memory is a compare-and-swap loop on this GPU and an FP64 one a slower loop;
-// see the probes). A tap x (in units u, |x| <= 2^43) gives H = rint(x 2^-22) and
-// L = rint(x - H 2^22) by FMA rounding against 1.5 2^23 (|H|, |L| <= 2^21), so the at most
-// 128 taps a cell receives from one CTA sum below 2^28 in each limb. Products are FP32
-// (float plans) or double-float (FP64 plans, where it measured slower than FP64 shared
-// atomics and is not selected); the tile adds them exactly up to u / 2 per tap, where
-// float atomics round every add. Each cell takes 16 bytes (half the FP32 tile's capacity).
-// The flush converts each cell back to T.
-constexpr float kLimbMagic = 12582912.0f;  // 1.5 * 2^23
-
-__device__ __forceinline__ void limbs(float xh, float xl, int &H, int &L) {
-    const float t = __fmaf_rn(xh, 0x1p-22f, kLimbMagic);
-    H = __float_as_int(t) - __float_as_int(kLimbMagic);
-    const float hf = __fsub_rn(t, kLimbMagic);
-    const float r = __fadd_rn(__fmaf_rn(-hf, 0x1p22f, xh), xl);
-    L = __float_as_int(__fadd_rn(r, kLimbMagic)) - __float_as_int(kLimbMagic);
-}
-
-// A point's value and its x-weighted parts in the tap arithmetic of each precision: T for
-// float plans, float pairs for FP64 plans.
-template <typename T> struct TapNum;
-template <> struct TapNum<float> {
-    using N = float;
-    __device__ static N of(float v) { return v; }
-    __device__ static N mul(N a, N b) { return __fmul_rn(a, b); }
-    __device__ static void split(N x, int &H, int &L) { limbs(x, 0.f, H, L); }
-};
-template <> struct TapNum<double> {
-    using N = df::DF;
-    __device__ static N of(double v) { return df::split_bits(v); }
-    __device__ static N mul(N a, N b) { return df::dmul(a, b); }
-    __device__ static void split(N x, int &H, int &L) { limbs(x.h, x.l, H, L); }
-};
-
-template <typename T> __device__ __forceinline__ T scale2(T v, int k) { return ldexp(v, k); }
-template <> __device__ __forceinline__ float scale2<float>(float v, int k) { return ldexpf(v, k); }
-
-template <typename T, int W, bool PERIODIC>
-__device__ __forceinline__ void spread_cta_int(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
-                                               const SpreadGrid<T, PERIODIC> grid, int ppc) {
-    using TN = TapNum<T>;
-    using N = typename TN::N;
-    extern __shared__ unsigned char smem_raw[];
-    __shared__ SpreadShared<T, W> sh;
-    __shared__ unsigned s_maxbits;
-    constexpr int cap = tile_bytes<T, W>() / 16;
-    int *tHr = reinterpret_cast<int *>(smem_raw);
-    int *tLr = tHr + cap, *tHi = tLr + cap, *tLi = tHi + cap;
-    const int tid = threadIdx.x;
-    if (tid < 3) {
-        sh.lo[tid] = INT_MAX;
-        sh.hi[tid] = INT_MIN;
-    }
-    if (tid == 0) s_maxbits = 0u;
-    __syncthreads();
-    if (tid < kSpreadPoints) {
-        if (act) {
-#pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                sh.fr[tid][d] = fr[d];
-                sh.i0[tid][d] = i0[d];
-                atomicMin(&sh.lo[d], i0[d]);
-                atomicMax(&sh.hi[d], i0[d]);
-            }
-            // an upper bound of |vr|, |vi| as a float (non-negative floats order as integers)
-            const double m = fmax(fabs((double)vr), fabs((double)vi));
-            atomicMax(&s_maxbits, __float_as_uint(__double2float_ru(m)));
-        } else {
-            sh.i0[tid][0] = INT_MIN;
-        }
-    }
-    __syncthreads();
-    if (sh.hi[0] < sh.lo[0] || s_maxbits == 0u) return;  // nothing to add (uniform)
-    stage_weights<T, W>(sh, beta);
-    // every |value| < 2^e; taps in units 2^(e - 43)
-    const int e = (int)((s_maxbits >> 23) & 0xFFu) - 126;
-    if (tid < kSpreadPoints && act) {
-        sh.v[tid][0] = scale2<T>(vr, 43 - e);
-        sh.v[tid][1] = scale2<T>(vi, 43 - e);
-    }
-    const int lo0 = sh.lo[0], lo1 = sh.lo[1], lo2 = sh.lo[2];
-    const int64_t tx = (int64_t)sh.hi[0] - lo0 + W, ty = (int64_t)sh.hi[1] - lo1 + W,
-                  tz = (int64_t)sh.hi[2] - lo2 + W;
-    const int64_t ps64 = tile_plane_stride(tx * ty);
-    if (tz * ps64 > cap) {
-        // Too large for the tile: the taps go to the grid in T (untiled, as spread_cta).
-        if (tid < kSpreadPoints && act) {
-            sh.v[tid][0] = vr;
-            sh.v[tid][1] = vi;
-        }
-        __syncthreads();
-        const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
-        constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;
-        const int rounds = (ppc + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32);
-        for (int round = 0; round < rounds; ++round) {
-            const int p = round * (kSpreadThreads / 32) + warp;
-            const int px0 = sh.i0[p][0];
-            if (px0 == INT_MIN) continue;
-            const int py0 = sh.i0[p][1], pz0 = sh.i0[p][2];
-            for (int jz = g; jz < W; jz += kZGroups) {
-                const int64_t gz = PERIODIC ? wrap(pz0 + jz, grid.n(2)) : pz0 + jz;
-                const T wz = sh.w[p][2 * W + jz];
-                for (int jy = 0; jy < W; ++jy) {
-                    const int64_t gy = PERIODIC ? wrap(py0 + jy, grid.n(1)) : py0 + jy;
-                    cplx_t<T> *row = grid.row(gz, gy);
-                    const T wyz = sh.w[p][W + jy] * wz;
-#pragma unroll
-                    for (int t = 0; t < kXT; ++t) {
-                        const int jx = jx0 + t * kGroupLanes;
-                        if (jx < W) {
-                            const int gx = PERIODIC ? wrap(px0 + jx, grid.n(0)) : px0 + jx;
-                            const T f = sh.w[p][jx] * wyz;
-                            grid_add(row + gx, sh.v[p][0] * f, sh.v[p][1] * f);
-                        }
-                    }
-                }
-            }
-        }
-        return;
-    }
-    const int txi = (int)tx, tyi = (int)ty, ps = (int)ps64;
-    {
-        const int cells = (int)(tz * ps64);
-        for (int j = tid; j < cells; j += blockDim.x) {
-            tHr[j] = 0;
-            tLr[j] = 0;
-            tHi[j] = 0;
-            tLi[j] = 0;
-        }
-    }
-    __syncthreads();
-    const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
-    constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;  // x taps per lane (1 or 2)
-    const int rounds = (ppc + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32);
-    for (int round = 0; round < rounds; ++round) {
-        const int p = round * (kSpreadThreads / 32) + warp;  // warps take points 16 apart
-        const int px0 = sh.i0[p][0];
-        if (px0 == INT_MIN) continue;  // uniform across the warp
-        const int py0 = sh.i0[p][1], pz0 = sh.i0[p][2];
-        N ar[kXT], ai[kXT];
-        int cx[kXT];
-        bool on[kXT];
-        const N vr_ = TN::of(sh.v[p][0]), vi_ = TN::of(sh.v[p][1]);
-#pragma unroll
-        for (int t = 0; t < kXT; ++t) {
-            const int jx = jx0 + t * kGroupLanes;
-            on[t] = jx < W;
-            const N wxv = TN::of(on[t] ? sh.w[p][jx] : T(0));
-            ar[t] = TN::mul(vr_, wxv);
-            ai[t] = TN::mul(vi_, wxv);
-            cx[t] = px0 - lo0 + jx;
-        }
-        N wy[W];
-#pragma unroll
-        for (int j = 0; j < W; ++j) wy[j] = TN::of(sh.w[p][W + j]);
-        for (int jz = g; jz < W; jz += kZGroups) {
-            const N wz = TN::of(sh.w[p][2 * W + jz]);
-            N zr[kXT], zi[kXT];
-#pragma unroll
-            for (int t = 0; t < kXT; ++t) {
-                zr[t] = TN::mul(ar[t], wz);
-                zi[t] = TN::mul(ai[t], wz);
-            }
-            const int zbase = (pz0 - lo2 + jz) * ps + (py0 - lo1) * txi;
-#pragma unroll
-            for (int jy = 0; jy < W; ++jy) {
-                const int base = zbase + jy * txi;
-#pragma unroll
-                for (int t = 0; t < kXT; ++t)
-                    if (on[t]) {
-                        int H, L;
-                        TN::split(TN::mul(zr[t], wy[jy]), H, L);
-                        atomicAdd(tHr + base + cx[t], H);
-                        atomicAdd(tLr + base + cx[t], L);
-                        TN::split(TN::mul(zi[t], wy[jy]), H, L);
-                        atomicAdd(tHi + base + cx[t], H);
-                        atomicAdd(tLi + base + cx[t], L);
-                    }
-            }
-        }
-    }
-    __syncthreads();
-    // Flush: one warp per (y, z) row of the tile, lanes along x; each cell back to T.
-    const int rows = (int)(ty * tz);
-    const int ue = e - 43;
-    for (int r = warp; r < rows; r += blockDim.x >> 5) {
-        const int y = r % tyi, z = r / tyi;
-        int gy = lo1 + y, gz = lo2 + z;
-        if (PERIODIC) {
-            gy = wrap(gy, grid.n(1));
-            gz = wrap(gz, grid.n(2));
-        }
-        cplx_t<T> *grow = grid.row(gz, gy);
-        const int t0 = z * ps + y * txi;
-        for (int x = lane; x < txi; x += 32) {
-            const int hr = tHr[t0 + x], lr = tLr[t0 + x], hi = tHi[t0 + x], li = tLi[t0 + x];
-            if ((hr | lr | hi | li) == 0) continue;
-            const int gx = PERIODIC ? wrap(lo0 + x, grid.n(0)) : lo0 + x;
-            // (H 2^22 + L) exactly as a 64-bit integer, then to T and scaled by the unit
-            const long long qr = ((long long)hr << 22) + lr, qi = ((long long)hi << 22) + li;
-            grid_add(grow + gx, scale2<T>((T)qr, ue), scale2<T>((T)qi, ue));
-        }
-    }
-}
-
 // sky -> vis step 1: pixels (values c, prephase P) onto the n1 grids of a wave. blockIdx.y
 // picks the sub-problem (descs[b0 + blockIdx.y]); a CTA takes ppc <= 128 consecutive points
 // of it (the bin; the plan may tune it): thread t < ppc takes point blockIdx.x * ppc + t.
-template <typename T, int W, bool IT>
+template <typename T, int W>
 __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
     spread_pix_kernel(const NufftDev *__restrict__ descs, int b0, cplx_t<T> *__restrict__ G1,
                       const float4 *__restrict__ rh, const float4 *__restrict__ rl, const double *__restrict__ soa,
@@ -688,15 +478,12 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         vr = cv * pr;
         vi = cv * pim;
     }
-    if constexpr (IT)
-        spread_cta_int<T, W, false>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
-    else
-        spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
+    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
 }
 
 // vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2
 // grids of a wave (layout as for pixels).
-template <typename T, int W, bool IT>
+template <typename T, int W>
 __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
     spread_vis_kernel(const NufftDev *__restrict__ descs, int b0, cplx_t<T> *__restrict__ G2,
                       const float4 *__restrict__ vh, const float4 *__restrict__ vl, const double *__restrict__ soa,
@@ -717,10 +504,7 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         ur = qr * v.x + qi * v.y;  // conj(Q) v
         ui = qr * v.y - qi * v.x;
     }
-    if constexpr (IT)
-        spread_cta_int<T, W, true>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
-    else
-        spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
+    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
 }
 
 // ------------------------------------------------------------------ interpolation (gather)
@@ -1292,12 +1076,12 @@ template <typename T, int W> void set_smem_attrs() {
     // Once per instantiation, also when plans are built and run on several host threads.
     static std::once_flag once;
     std::call_once(once, [] {
-        for (auto k : {spread_pix_kernel<T, W, false>, spread_pix_kernel<T, W, true>})
-            check_cuda(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes<T, W>()),
-                       "cudaFuncSetAttribute");
-        for (auto k : {spread_vis_kernel<T, W, false>, spread_vis_kernel<T, W, true>})
-            check_cuda(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes<T, W>()),
-                       "cudaFuncSetAttribute");
+        check_cuda(cudaFuncSetAttribute(spread_pix_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        tile_bytes<T, W>()),
+                   "cudaFuncSetAttribute");
+        check_cuda(cudaFuncSetAttribute(spread_vis_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        tile_bytes<T, W>()),
+                   "cudaFuncSetAttribute");
     });
 }
 
@@ -1350,8 +1134,7 @@ void nufft_wave_s2v(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
     hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    (a.int_tile ? spread_pix_kernel<T, W, true> : spread_pix_kernel<T, W, false>)<<<sgrid, kSpreadThreads,      \
-                                                                                 tile_bytes<T, W>(), s>>>(       \
+    spread_pix_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g1), a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, bt, a.isign,    \
         a.ppc_pix)
     HVOX_W_SWITCH(wd, CALL)
@@ -1405,8 +1188,7 @@ void nufft_wave_v2s(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
     hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    (a.int_tile ? spread_vis_kernel<T, W, true> : spread_vis_kernel<T, W, false>)<<<sgrid, kSpreadThreads,      \
-                                                                                 tile_bytes<T, W>(), s>>>(       \
+    spread_vis_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg,   \
         (T)a.inv_tmax2, bt, a.isign, a.ppc_vis)
     HVOX_W_SWITCH(wd, CALL)
@@ -1466,8 +1248,7 @@ float time_spread(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, bool
     if (pix) {
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    (a.int_tile ? spread_pix_kernel<T, W, true> : spread_pix_kernel<T, W, false>)<<<grid, kSpreadThreads,       \
-                                                                                 tile_bytes<T, W>(), s>>>(       \
+    spread_pix_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g1), a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, (const T *)values, \
         bt, a.isign, ppc)
         HVOX_W_SWITCH(wd, CALL)
@@ -1475,8 +1256,7 @@ float time_spread(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, bool
     } else {
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    (a.int_tile ? spread_vis_kernel<T, W, true> : spread_vis_kernel<T, W, false>)<<<grid, kSpreadThreads,       \
-                                                                                 tile_bytes<T, W>(), s>>>(       \
+    spread_vis_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis,                   \
         (const cplx_t<T> *)values, a.cheb, a.deg, (T)a.inv_tmax2, bt, a.isign, ppc)
         HVOX_W_SWITCH(wd, CALL)

@@ -189,7 +189,7 @@ CostModel default_cost_model(int prec, bool plain, int w, bool z2z_fft) {
         m.fft_cell = 4.1e-13;
         m.grid_cell = 8.8e-13;
         m.block_fixed = 30e-6;
-        m.tile_cells = 6000.0;   // shared tile of a spreading CTA (two 32-bit limbs per part)
+        m.tile_cells = 12000.0;  // shared tile of a spreading CTA (float planes, w <= 8)
     } else {
         // FP64 sub-problems, fitted the same way (calibrate.py --eps 1e-9 --mode nufft, 1 to
         // 22 sub-problems per workload). Spreading taps are one rate: the fit does not
