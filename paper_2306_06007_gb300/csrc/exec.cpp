@@ -103,6 +103,7 @@ template <typename T> NufftArgs<T> nufft_args(const Plan &p) {
     a.ppc_pix = p.ppc_pix;
     a.ppc_vis = p.ppc_vis;
     a.df_grids = p.df_grids;
+    a.int_tile = p.int_tile;
     return a;
 }
 

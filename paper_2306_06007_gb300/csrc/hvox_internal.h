@@ -282,6 +282,9 @@ template <typename T> struct NufftArgs {
     // FP64 plans whose FFT grids go through the double-float FFT: after the FFT the grid
     // holds float pairs (float4 per cell), which the double-float gathers and crop read.
     bool df_grids = false;
+    // FP64 spreading into fixed-point tiles of 32-bit limbs (k_nufft.cu) instead of FP64
+    // shared atomics.
+    bool int_tile = false;
 };
 
 // Stage boundaries reported by the kernel launchers to the executor's profiler.
@@ -385,6 +388,7 @@ struct Plan {
     std::vector<Wave> waves;            // waves of blocks (launch order)
     std::map<int, std::unique_ptr<DevBuf>> dfft_tw;  // twiddle tables of the double-float FFT
     bool df_grids = false;              // every FFT batch double-float (NufftArgs::df_grids)
+    bool int_tile = false;              // NufftArgs::int_tile
     DevBuf cis_tab;                     // exp(j 2 pi m / 2048) as float pairs (double-float path)
     DevBuf err;                         // int: device error word (kDevErr* bits), read by hvox_sync
 

@@ -271,7 +271,9 @@ constexpr int kZGroups = 32 / kGroupLanes;                        // lane groups
 constexpr int kPointsPerWarp = kSpreadPoints / (kSpreadThreads / 32);
 static_assert(kSpreadThreads % 32 == 0 && kPointsPerWarp * (kSpreadThreads / 32) == kSpreadPoints,
               "every point of a spreading CTA is taken by exactly one warp");
-constexpr int kSmemPerCta = 110 * 1024;  // two CTAs per SM
+// Shared memory of a spreading CTA: two CTAs per SM for FP32 grids; one CTA per SM for
+// FP64 grids (the w = 13 windows of eps <= 1e-9 need the larger tile to fit a bin at all).
+template <typename T> constexpr int smem_per_cta() { return sizeof(T) == 4 ? 110 * 1024 : 224 * 1024; }
 
 template <typename T, int W> struct SpreadShared {
     static constexpr int kWStride = 3 * W + 1;  // odd row stride: fewer bank conflicts
@@ -299,7 +301,8 @@ template <typename T, int W> __device__ __forceinline__ void stage_weights(Sprea
 }
 
 template <typename T, int W> __host__ __device__ constexpr int tile_bytes() {
-    return ((kSmemPerCta - (int)sizeof(SpreadShared<T, W>) - (int)sizeof(NufftDev)) / (2 * (int)sizeof(T) * 32)) *
+    return ((smem_per_cta<T>() - (int)sizeof(SpreadShared<T, W>) - (int)sizeof(NufftDev) - 64) /
+            (2 * (int)sizeof(T) * 32)) *
            (2 * (int)sizeof(T) * 32);
 }
 
@@ -331,19 +334,55 @@ template <typename T, bool PERIODIC> struct SpreadGrid {
     }
 };
 
-template <typename T, int W, bool PERIODIC>
+// Fixed-point tile (FP64 plans): the shared tile holds each cell's real and imaginary parts
+// as fixed-point numbers in two 32-bit limbs, value = (H 2^22 + L) u with u = 2^(e - 43)
+// per CTA and every |value| of the CTA's points below 2^e, so a tap costs no FP64
+// instruction: its product in double-float arithmetic (FP32 pipes) splits into
+// H = rint(x 2^-22) and L = rint(x - H 2^22) by FMA rounding against 1.5 2^23 (|H|, |L| <=
+// 2^21; the at most 128 taps a cell receives from one CTA keep each limb below 2^28), added
+// by native 32-bit shared integer atomics (FP64 shared atomics are compare-and-swap loops
+// around an FP64 add). Sums are exact up to u / 2 = 2^-44 of the CTA's largest value per
+// tap. The flush converts each cell back to FP64.
+constexpr float kLimbMagic = 12582912.0f;  // 1.5 * 2^23
+
+// q 2^k as a double for |q| < 2^52, exactly, by integer operations (no FP64 instruction:
+// the flush of a large tile would otherwise spend two FP64 operations per part and cell).
+__device__ __forceinline__ double i64_pow2(long long q, int k) {
+    if (q == 0) return 0.0;
+    const unsigned long long sign = q < 0 ? (1ull << 63) : 0ull;
+    unsigned long long m = (unsigned long long)(q < 0 ? -q : q);
+    const int msb = 63 - __clzll((long long)m);
+    m <<= (52 - msb);  // leading one at bit 52 (msb <= 51)
+    return __longlong_as_double((long long)(sign | ((unsigned long long)(msb + k + 1023) << 52) |
+                                            (m & ((1ull << 52) - 1ull))));
+}
+
+__device__ __forceinline__ void limbs(df::DF x, int &H, int &L) {
+    const float t = __fmaf_rn(x.h, 0x1p-22f, kLimbMagic);
+    H = __float_as_int(t) - __float_as_int(kLimbMagic);
+    const float hf = __fsub_rn(t, kLimbMagic);
+    const float r = __fadd_rn(__fmaf_rn(-hf, 0x1p22f, x.h), x.l);
+    L = __float_as_int(__fadd_rn(r, kLimbMagic)) - __float_as_int(kLimbMagic);
+}
+
+template <typename T, int W, bool PERIODIC, bool IT>
 __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
                                            const SpreadGrid<T, PERIODIC> grid, int ppc) {
+    static_assert(!IT || sizeof(T) == 8, "the fixed-point tile serves FP64 grids");
     extern __shared__ unsigned char smem_raw[];
     __shared__ SpreadShared<T, W> sh;
-    constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));
+    __shared__ unsigned s_maxbits;
+    constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));  // cells (16 bytes each for FP64)
     T *tre = reinterpret_cast<T *>(smem_raw);
     T *tim = tre + cap;
+    int *tHr = reinterpret_cast<int *>(smem_raw);  // fixed-point form: four int planes
+    int *tLr = tHr + cap, *tHi = tLr + cap, *tLi = tHi + cap;
     const int tid = threadIdx.x;
     if (tid < 3) {
         sh.lo[tid] = INT_MAX;
         sh.hi[tid] = INT_MIN;
     }
+    if (tid == 0) s_maxbits = 0u;
     __syncthreads();
     if (tid < kSpreadPoints) {
         if (act) {
@@ -355,6 +394,11 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
                 sh.i0[tid][d] = i0[d];
                 atomicMin(&sh.lo[d], i0[d]);
                 atomicMax(&sh.hi[d], i0[d]);
+            }
+            if (IT) {
+                // an upper bound of |vr|, |vi| as a float (non-negative floats order as integers)
+                const double m = fmax(fabs((double)vr), fabs((double)vi));
+                atomicMax(&s_maxbits, __float_as_uint(__double2float_ru(m)));
             }
         } else {
             sh.i0[tid][0] = INT_MIN;
@@ -368,8 +412,18 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
                   tz = (int64_t)sh.hi[2] - lo2 + W;
     const int64_t ps64 = tile_plane_stride(tx * ty);
     const bool tiled = tz * ps64 <= cap;
+    const bool fixed = IT && tiled && s_maxbits != 0u;  // fixed-point form of the tile
+    const int e = (int)((s_maxbits >> 23) & 0xFFu) - 126;  // every |value| < 2^e
     const int txi = (int)tx, tyi = (int)ty, ps = tiled ? (int)ps64 : 0;
-    if (tiled) {
+    if (fixed) {
+        const int cells = (int)(tz * ps64);
+        for (int j = tid; j < cells; j += blockDim.x) {
+            tHr[j] = 0;
+            tLr[j] = 0;
+            tHi[j] = 0;
+            tLi[j] = 0;
+        }
+    } else if (tiled) {
         const int cells = (int)(tz * ps64);
         for (int j = tid; j < cells; j += blockDim.x) {
             tre[j] = T(0);
@@ -385,6 +439,54 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         const int px0 = sh.i0[p][0];
         if (px0 == INT_MIN) continue;  // uniform across the warp
         const int py0 = sh.i0[p][1], pz0 = sh.i0[p][2];
+        if constexpr (IT) {
+            if (fixed) {
+                // taps in units 2^(e - 43), double-float products, two limbs, four int atomics
+                df::DF ar[kXT], ai[kXT];
+                int cx[kXT];
+                bool on[kXT];
+                const df::DF vr_ = df::split_bits(ldexp((double)sh.v[p][0], 43 - e));
+                const df::DF vi_ = df::split_bits(ldexp((double)sh.v[p][1], 43 - e));
+#pragma unroll
+                for (int t = 0; t < kXT; ++t) {
+                    const int jx = jx0 + t * kGroupLanes;
+                    on[t] = jx < W;
+                    const df::DF wxv = df::split_bits(on[t] ? (double)sh.w[p][jx] : 0.0);
+                    ar[t] = df::dmul(vr_, wxv);
+                    ai[t] = df::dmul(vi_, wxv);
+                    cx[t] = px0 - lo0 + jx;
+                }
+                df::DF wy[W];
+#pragma unroll
+                for (int j = 0; j < W; ++j) wy[j] = df::split_bits((double)sh.w[p][W + j]);
+                for (int jz = g; jz < W; jz += kZGroups) {
+                    const df::DF wz = df::split_bits((double)sh.w[p][2 * W + jz]);
+                    df::DF zr[kXT], zi[kXT];
+#pragma unroll
+                    for (int t = 0; t < kXT; ++t) {
+                        zr[t] = df::dmul(ar[t], wz);
+                        zi[t] = df::dmul(ai[t], wz);
+                    }
+                    const int zbase = (pz0 - lo2 + jz) * ps + (py0 - lo1) * txi;
+#pragma unroll
+                    for (int jy = 0; jy < W; ++jy) {
+                        const int base = zbase + jy * txi;
+#pragma unroll
+                        for (int t = 0; t < kXT; ++t)
+                            if (on[t]) {
+                                int H, L;
+                                limbs(df::dmul(zr[t], wy[jy]), H, L);
+                                atomicAdd(tHr + base + cx[t], H);
+                                atomicAdd(tLr + base + cx[t], L);
+                                limbs(df::dmul(zi[t], wy[jy]), H, L);
+                                atomicAdd(tHi + base + cx[t], H);
+                                atomicAdd(tLi + base + cx[t], L);
+                            }
+                    }
+                }
+                continue;
+            }
+        }
         T ar[kXT], ai[kXT];
         int cx[kXT];
         bool on[kXT];
@@ -447,8 +549,18 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         cplx_t<T> *grow = grid.row(gz, gy);
         const int t0 = z * ps + y * txi;
         for (int x = lane; x < txi; x += 32) {
-            const T re = tre[t0 + x], im = tim[t0 + x];
-            if (re == T(0) && im == T(0)) continue;
+            T re, im;
+            if (fixed) {
+                const int hr = tHr[t0 + x], lr = tLr[t0 + x], hi = tHi[t0 + x], li = tLi[t0 + x];
+                if ((hr | lr | hi | li) == 0) continue;
+                // (H 2^22 + L) exactly as a 64-bit integer (|.| < 2^51), times the unit
+                re = (T)i64_pow2(((long long)hr << 22) + lr, e - 43);
+                im = (T)i64_pow2(((long long)hi << 22) + li, e - 43);
+            } else {
+                re = tre[t0 + x];
+                im = tim[t0 + x];
+                if (re == T(0) && im == T(0)) continue;
+            }
             const int gx = PERIODIC ? wrap(lo0 + x, grid.n(0)) : lo0 + x;
             grid_add(grow + gx, re, im);
         }
@@ -458,7 +570,7 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
 // sky -> vis step 1: pixels (values c, prephase P) onto the n1 grids of a wave. blockIdx.y
 // picks the sub-problem (descs[b0 + blockIdx.y]); a CTA takes ppc <= 128 consecutive points
 // of it (the bin; the plan may tune it): thread t < ppc takes point blockIdx.x * ppc + t.
-template <typename T, int W>
+template <typename T, int W, bool IT>
 __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
     spread_pix_kernel(const NufftDev *__restrict__ descs, int b0, cplx_t<T> *__restrict__ G1,
                       const float4 *__restrict__ rh, const float4 *__restrict__ rl, const double *__restrict__ soa,
@@ -478,12 +590,12 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         vr = cv * pr;
         vi = cv * pim;
     }
-    spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
+    spread_cta<T, W, false, IT>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
 }
 
 // vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2
 // grids of a wave (layout as for pixels).
-template <typename T, int W>
+template <typename T, int W, bool IT>
 __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
     spread_vis_kernel(const NufftDev *__restrict__ descs, int b0, cplx_t<T> *__restrict__ G2,
                       const float4 *__restrict__ vh, const float4 *__restrict__ vl, const double *__restrict__ soa,
@@ -504,7 +616,7 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         ur = qr * v.x + qi * v.y;  // conj(Q) v
         ui = qr * v.y - qi * v.x;
     }
-    spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
+    spread_cta<T, W, true, IT>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
 }
 
 // ------------------------------------------------------------------ interpolation (gather)
@@ -1076,12 +1188,12 @@ template <typename T, int W> void set_smem_attrs() {
     // Once per instantiation, also when plans are built and run on several host threads.
     static std::once_flag once;
     std::call_once(once, [] {
-        check_cuda(cudaFuncSetAttribute(spread_pix_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        tile_bytes<T, W>()),
-                   "cudaFuncSetAttribute");
-        check_cuda(cudaFuncSetAttribute(spread_vis_kernel<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        tile_bytes<T, W>()),
-                   "cudaFuncSetAttribute");
+        for (auto k : {spread_pix_kernel<T, W, false>, spread_pix_kernel<T, W, sizeof(T) == 8>})
+            check_cuda(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes<T, W>()),
+                       "cudaFuncSetAttribute");
+        for (auto k : {spread_vis_kernel<T, W, false>, spread_vis_kernel<T, W, sizeof(T) == 8>})
+            check_cuda(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, tile_bytes<T, W>()),
+                       "cudaFuncSetAttribute");
     });
 }
 
@@ -1134,7 +1246,7 @@ void nufft_wave_s2v(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
     hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_pix_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
+    (a.int_tile ? spread_pix_kernel<T, W, sizeof(T) == 8> : spread_pix_kernel<T, W, false>)<<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g1), a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, c, bt, a.isign,    \
         a.ppc_pix)
     HVOX_W_SWITCH(wd, CALL)
@@ -1188,7 +1300,7 @@ void nufft_wave_v2s(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, co
     hook.begin(HVOX_STAGE_SPREAD, s);
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_vis_kernel<T, W><<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
+    (a.int_tile ? spread_vis_kernel<T, W, sizeof(T) == 8> : spread_vis_kernel<T, W, false>)<<<sgrid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                   \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis, V, a.cheb, a.deg,   \
         (T)a.inv_tmax2, bt, a.isign, a.ppc_vis)
     HVOX_W_SWITCH(wd, CALL)
@@ -1248,7 +1360,7 @@ float time_spread(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, bool
     if (pix) {
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_pix_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
+    (a.int_tile ? spread_pix_kernel<T, W, sizeof(T) == 8> : spread_pix_kernel<T, W, false>)<<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g1), a.pix_hi, a.pix_lo, a.pix_soa, a.n_pix, (const T *)values, \
         bt, a.isign, ppc)
         HVOX_W_SWITCH(wd, CALL)
@@ -1256,7 +1368,7 @@ float time_spread(const Wave &w, const NufftArgs<T> &a, void *g1, void *g2, bool
     } else {
 #define CALL(W)                                                                                                   \
     set_smem_attrs<T, W>();                                                                                       \
-    spread_vis_kernel<T, W><<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
+    (a.int_tile ? spread_vis_kernel<T, W, sizeof(T) == 8> : spread_vis_kernel<T, W, false>)<<<grid, kSpreadThreads, tile_bytes<T, W>(), s>>>(                                    \
         a.descs, w.b0, static_cast<cplx_t<T> *>(g2), a.vis_hi, a.vis_lo, a.vis_soa, a.n_vis,                   \
         (const cplx_t<T> *)values, a.cheb, a.deg, (T)a.inv_tmax2, bt, a.isign, ppc)
         HVOX_W_SWITCH(wd, CALL)
