@@ -56,6 +56,52 @@ template <typename T, int W> __device__ __forceinline__ void es_weights(T fr, T 
     }
 }
 
+// The ES kernel weights of es_weights<double> in double-float arithmetic on the FP32 pipes
+// (FP64 exp and sqrt cost ~30 FP64 instructions a weight, issued at 1/64 of the FP32 rate):
+// x = (j - fr) 2 / W in FP64, then q = 1 - x^2, s = sqrt(q) (one Newton step on the float
+// root), t = beta (s - 1) and exp(t) = 2^k exp(r), r = t - k ln 2 (|r| <= ln 2 / 2), by
+// Horner's rule on the Taylor series to degree 11 (truncation below 7e-15). Absolute error
+// ~2e-13 (the error of t, ~beta 2^-48, times the weight), which the FP64 kernels' weights
+// share to within their own rounding.
+struct DFConst {
+    float h, l;
+};
+__host__ __device__ constexpr DFConst df_const(double x) { return {(float)x, (float)(x - (double)(float)x)}; }
+__device__ __forceinline__ df::DF df_exp_es(df::DF t) {
+    constexpr DFConst kLn2 = df_const(0.6931471805599453094);
+    constexpr DFConst kInvFact[12] = {
+        df_const(1.0),           df_const(1.0),           df_const(1.0 / 2),         df_const(1.0 / 6),
+        df_const(1.0 / 24),      df_const(1.0 / 120),     df_const(1.0 / 720),       df_const(1.0 / 5040),
+        df_const(1.0 / 40320),   df_const(1.0 / 362880),  df_const(1.0 / 3628800),   df_const(1.0 / 39916800)};
+    const float k = rintf(__fmul_rn(t.h, 1.44269504088896341f));
+    const df::DF r = df::dadd(t, df::dmul(df::DF{-k, 0.f}, df::DF{kLn2.h, kLn2.l}));
+    df::DF p = {kInvFact[11].h, kInvFact[11].l};
+#pragma unroll
+    for (int i = 10; i >= 0; --i) p = df::dadd(df::dmul(p, r), df::DF{kInvFact[i].h, kInvFact[i].l});
+    const float sc = __int_as_float((127 + (int)k) << 23);  // 2^k, k in [-64, 0]
+    return {__fmul_rn(p.h, sc), __fmul_rn(p.l, sc)};
+}
+
+template <int W> __device__ __forceinline__ void es_weights_df(double fr, df::DF beta, df::DF *wt) {
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        const df::DF x = df::split_bits(((double)j - fr) * (2.0 / W));
+        const df::DF q = df::dadd(df::DF{1.f, 0.f}, df::dneg(df::dmul(x, x)));
+        if (q.h <= 0.f) {
+            wt[j] = {0.f, 0.f};
+            continue;
+        }
+        // sqrt: s0 = fl(sqrt(q.h)), s1 = (q - s0^2) / (2 s0)
+        const float s0 = __fsqrt_rn(q.h);
+        const float pp = __fmul_rn(s0, s0);
+        const float rr = __fadd_rn(__fsub_rn(__fsub_rn(q.h, pp), __fmaf_rn(s0, s0, -pp)), q.l);
+        df::DF sq;
+        df::fast_two_sum(s0, __fmul_rn(rr, __frcp_rn(__fmul_rn(2.f, s0))), sq.h, sq.l);
+        const df::DF t = df::dmul(df::dadd(sq, df::DF{-1.f, 0.f}), beta);
+        wt[j] = df_exp_es(t);
+    }
+}
+
 // i mod n for i in [-n, 2n). Every caller indexes a window whose start geo_vis has
 // checked to lie in [-n, 2n - w] (clamping it there and setting the device error word
 // otherwise), and n2 >= 2w, so every argument is in that range.
@@ -286,18 +332,44 @@ template <typename T, int W> struct SpreadShared {
 
 // Kernel weights of the staged points: 3 x 128 rows (point, dimension), one per thread of
 // the first 384, so the exponentials of a bin are spread over 12 warps instead of 4.
-template <typename T, int W> __device__ __forceinline__ void stage_weights(SpreadShared<T, W> &sh, T beta) {
+// DF = true (FP64 plans with fixed-point tiles): the weights in double-float arithmetic,
+// stored as float pairs in the 8-byte slots (read back with weight_of).
+template <typename T, int W, bool DF = false>
+__device__ __forceinline__ void stage_weights(SpreadShared<T, W> &sh, T beta) {
     const int tid = threadIdx.x;
     static_assert(kSpreadThreads >= 3 * kSpreadPoints, "one thread per weight row");
+    static_assert(!DF || sizeof(T) == 8, "float pairs fill FP64 slots");
     if (tid < 3 * kSpreadPoints) {
         const int p = tid % kSpreadPoints, d = tid / kSpreadPoints;
         if (sh.i0[p][0] != INT_MIN) {
-            T wv[W];
-            es_weights<T, W>(sh.fr[p][d], beta, wv);
+            if constexpr (DF) {
+                df::DF wv[W];
+                es_weights_df<W>((double)sh.fr[p][d], df::split_bits((double)beta), wv);
 #pragma unroll
-            for (int j = 0; j < W; ++j) sh.w[p][d * W + j] = wv[j];
+                for (int j = 0; j < W; ++j)
+                    *reinterpret_cast<float2 *>(&sh.w[p][d * W + j]) = make_float2(wv[j].h, wv[j].l);
+            } else {
+                T wv[W];
+                es_weights<T, W>(sh.fr[p][d], beta, wv);
+#pragma unroll
+                for (int j = 0; j < W; ++j) sh.w[p][d * W + j] = wv[j];
+            }
         }
     }
+}
+
+// A staged weight as T (DF: the float pair's value) and as a float pair.
+template <typename T, bool DF> __device__ __forceinline__ T weight_of(const T &slot) {
+    if constexpr (DF) {
+        const float2 v = *reinterpret_cast<const float2 *>(&slot);
+        return (T)df::to_double(df::DF{v.x, v.y});
+    } else {
+        return slot;
+    }
+}
+template <typename T> __device__ __forceinline__ df::DF weight_df(const T &slot) {
+    const float2 v = *reinterpret_cast<const float2 *>(&slot);
+    return {v.x, v.y};
 }
 
 template <typename T, int W> __host__ __device__ constexpr int tile_bytes() {
@@ -406,7 +478,7 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     }
     __syncthreads();
     if (sh.hi[0] < sh.lo[0]) return;  // no point in this CTA (uniform across the CTA)
-    stage_weights<T, W>(sh, beta);
+    stage_weights<T, W, IT>(sh, beta);
     const int lo0 = sh.lo[0], lo1 = sh.lo[1], lo2 = sh.lo[2];
     const int64_t tx = (int64_t)sh.hi[0] - lo0 + W, ty = (int64_t)sh.hi[1] - lo1 + W,
                   tz = (int64_t)sh.hi[2] - lo2 + W;
@@ -451,16 +523,16 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
                 for (int t = 0; t < kXT; ++t) {
                     const int jx = jx0 + t * kGroupLanes;
                     on[t] = jx < W;
-                    const df::DF wxv = df::split_bits(on[t] ? (double)sh.w[p][jx] : 0.0);
+                    const df::DF wxv = on[t] ? weight_df(sh.w[p][jx]) : df::DF{0.f, 0.f};
                     ar[t] = df::dmul(vr_, wxv);
                     ai[t] = df::dmul(vi_, wxv);
                     cx[t] = px0 - lo0 + jx;
                 }
                 df::DF wy[W];
 #pragma unroll
-                for (int j = 0; j < W; ++j) wy[j] = df::split_bits((double)sh.w[p][W + j]);
+                for (int j = 0; j < W; ++j) wy[j] = weight_df(sh.w[p][W + j]);
                 for (int jz = g; jz < W; jz += kZGroups) {
-                    const df::DF wz = df::split_bits((double)sh.w[p][2 * W + jz]);
+                    const df::DF wz = weight_df(sh.w[p][2 * W + jz]);
                     df::DF zr[kXT], zi[kXT];
 #pragma unroll
                     for (int t = 0; t < kXT; ++t) {
@@ -494,16 +566,16 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         for (int t = 0; t < kXT; ++t) {
             const int jx = jx0 + t * kGroupLanes;
             on[t] = jx < W;
-            const T wxv = on[t] ? sh.w[p][jx] : T(0);
+            const T wxv = on[t] ? weight_of<T, IT>(sh.w[p][jx]) : T(0);
             ar[t] = sh.v[p][0] * wxv;
             ai[t] = sh.v[p][1] * wxv;
             cx[t] = tiled ? px0 - lo0 + jx : (PERIODIC ? wrap(px0 + jx, grid.n(0)) : px0 + jx);
         }
         T wy[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) wy[j] = sh.w[p][W + j];
+        for (int j = 0; j < W; ++j) wy[j] = weight_of<T, IT>(sh.w[p][W + j]);
         for (int jz = g; jz < W; jz += kZGroups) {
-            const T wz = sh.w[p][2 * W + jz];
+            const T wz = weight_of<T, IT>(sh.w[p][2 * W + jz]);
             // Fold the z weight into the value once per plane: two multiplies per tap.
             T zr[kXT], zi[kXT];
 #pragma unroll
@@ -809,15 +881,13 @@ __device__ __forceinline__ void stage_point_df(GatherSharedDF<W> &sh, int slot, 
         sh.i0[slot][0] = INT_MIN;
         return;
     }
+    const df::DF bdf = df::split_bits(beta);
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        double t[W];
-        es_weights<double, W>(fr[d], beta, t);
+        df::DF t[W];
+        es_weights_df<W>(fr[d], bdf, t);
 #pragma unroll
-        for (int j = 0; j < W; ++j) {
-            const df::DF v = df::split_bits(t[j]);
-            sh.w[slot][d * W + j] = make_float2(v.h, v.l);
-        }
+        for (int j = 0; j < W; ++j) sh.w[slot][d * W + j] = make_float2(t[j].h, t[j].l);
     }
     sh.q[slot][0] = qr;
     sh.q[slot][1] = qi;
@@ -932,18 +1002,10 @@ __global__ void __launch_bounds__(128)
     double fr[3], pr, pim;
     geo_pix<W>(b, b.p0 + i, rh, rl, soa, n_all, isign, i0, fr, pr, pim);
     df::DF wx[W], wy[W], wz[W];
-    {
-        double t[W];
-        es_weights<double, W>(fr[0], beta, t);
-#pragma unroll
-        for (int j = 0; j < W; ++j) wx[j] = df::split_bits(t[j]);
-        es_weights<double, W>(fr[1], beta, t);
-#pragma unroll
-        for (int j = 0; j < W; ++j) wy[j] = df::split_bits(t[j]);
-        es_weights<double, W>(fr[2], beta, t);
-#pragma unroll
-        for (int j = 0; j < W; ++j) wz[j] = df::split_bits(t[j]);
-    }
+    const df::DF bdf = df::split_bits(beta);
+    es_weights_df<W>(fr[0], bdf, wx);
+    es_weights_df<W>(fr[1], bdf, wy);
+    es_weights_df<W>(fr[2], bdf, wz);
     const int64_t nx = b.n1[0], ny = b.n1[1];
     const float4 *G1 = G1base + b.g1_off;
     df::DAcc sr{0.f, 0.f}, si{0.f, 0.f};
