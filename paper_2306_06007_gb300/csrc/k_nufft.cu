@@ -358,7 +358,8 @@ __device__ __forceinline__ void stage_weights(SpreadShared<T, W> &sh, T beta) {
     }
 }
 
-// A staged weight as T (DF: the float pair's value) and as a float pair.
+// A staged weight as T (DF: the float pair's value) and a staged weight or scaled value
+// as a float pair.
 template <typename T, bool DF> __device__ __forceinline__ T weight_of(const T &slot) {
     if constexpr (DF) {
         const float2 v = *reinterpret_cast<const float2 *>(&slot);
@@ -488,6 +489,14 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
     const int e = (int)((s_maxbits >> 23) & 0xFFu) - 126;  // every |value| < 2^e
     const int txi = (int)tx, tyi = (int)ty, ps = tiled ? (int)ps64 : 0;
     if (fixed) {
+        // each point's value in units 2^(e - 43), as float pairs in place (once per point)
+        if (tid < kSpreadPoints && sh.i0[tid][0] != INT_MIN) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const df::DF v = df::split_bits(ldexp((double)sh.v[tid][c], 43 - e));
+                *reinterpret_cast<float2 *>(&sh.v[tid][c]) = make_float2(v.h, v.l);
+            }
+        }
         const int cells = (int)(tz * ps64);
         for (int j = tid; j < cells; j += blockDim.x) {
             tHr[j] = 0;
@@ -517,8 +526,7 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
                 df::DF ar[kXT], ai[kXT];
                 int cx[kXT];
                 bool on[kXT];
-                const df::DF vr_ = df::split_bits(ldexp((double)sh.v[p][0], 43 - e));
-                const df::DF vi_ = df::split_bits(ldexp((double)sh.v[p][1], 43 - e));
+                const df::DF vr_ = weight_df(sh.v[p][0]), vi_ = weight_df(sh.v[p][1]);
 #pragma unroll
                 for (int t = 0; t < kXT; ++t) {
                     const int jx = jx0 + t * kGroupLanes;

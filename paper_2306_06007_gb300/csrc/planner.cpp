@@ -192,15 +192,18 @@ CostModel default_cost_model(int prec, bool plain, int w, bool z2z_fft) {
         m.tile_cells = 12000.0;  // shared tile of a spreading CTA (float planes, w <= 8)
     } else {
         // FP64 sub-problems, fitted the same way (calibrate.py --eps 1e-9 --mode nufft, 1 to
-        // 22 sub-problems per workload). Spreading taps are one rate: the fit does not
-        // separate the shared-tile and global paths. The FFT rate is the double-float FFT's
-        // (4.2x cheaper per cell than cuFFT Z2Z, which is bound by the FP64 units at ~17x
-        // the C2C rate and still serves the plain form and eps < 1e-11, measured earlier).
-        // The double-float direct rate is the LOFAR-like benchmark's launch.
-        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 4.5e11;
-        m.scatter_smem = 1.0 / 1.21e11;
-        m.scatter_global = 1.0 / 1.21e11;
-        m.gather_tap = 1.0 / 1.31e11;
+        // 40 sub-problems per workload). Spreading taps are one rate: the fit does not
+        // separate the shared-tile and global paths (fixed-point tiles, double-float taps
+        // and weights; the gathers in double-float arithmetic). The FFT rate is the
+        // double-float FFT's (4.2x cheaper per cell than cuFFT Z2Z, which is bound by the
+        // FP64 units at ~17x the C2C rate and still serves the plain form and eps < 1e-11,
+        // measured earlier). The double-float direct rate is the LOFAR-like benchmark's launch.
+        // The plain form keeps FP64 arithmetic in every kernel: its earlier fit (FP64 shared
+        // and global atomics, FP64 gathers) stays.
+        m.direct_pair = plain ? 1.0 / 4.0e9 : 1.0 / 4.6e11;
+        m.scatter_smem = plain ? 1.0 / 1.15e11 : 1.0 / 1.92e11;
+        m.scatter_global = m.scatter_smem;
+        m.gather_tap = plain ? 1.0 / 1.22e11 : 1.0 / 4.73e11;
         m.fft_cell = (plain || z2z_fft) ? 7.2e-12 : 1.7e-12;
         m.grid_cell = 1.7e-12;
         m.block_fixed = 50e-6;
