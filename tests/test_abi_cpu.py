@@ -156,3 +156,18 @@ def test_plan_dry_rejects_empty_and_bad_inputs():
         assert e.value.code == 1  # HVOX_EINVAL
     # One pixel and one baseline: a valid (direct) plan.
     assert hvox.plan_dry(pix, uvw, 1e-6)["n_nufft_blocks"] == 0
+
+
+def test_batch_calls_check_arguments_on_the_host(lib):
+    # The batched entry points validate their arguments before any device work: no GPU is
+    # needed to see n = 0 succeed and NULL arrays or a negative count rejected.
+    P = ctypes.c_void_p
+    for fn in (lib.hvox_synthesize_batch, lib.hvox_analyze_batch):
+        launches = ctypes.c_int32(7)
+        assert fn(None, None, None, 0, None, ctypes.byref(launches)) == 0  # HVOX_OK
+        assert launches.value == 0
+        assert fn(None, None, None, 1, None, None) == 1  # HVOX_EINVAL
+        assert fn(None, None, None, -1, None, None) == 1  # HVOX_EINVAL
+        plans = (P * 1)(None)
+        bufs = (P * 1)(None)
+        assert fn(plans, bufs, bufs, 1, None, None) == 1  # HVOX_EINVAL: a NULL plan
