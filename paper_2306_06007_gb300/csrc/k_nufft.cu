@@ -300,18 +300,20 @@ __device__ __forceinline__ void grid_add(double2 *g, double re, double im) {
 }
 // ------------------------------------------------------------------ spreading (tiled)
 
-// A CTA spreads 128 consecutive points (Morton order in grid-cell units, so they are close
-// on the grid). Phase 1: threads 0..127 each take one point, compute its window start,
-// kernel weights and value, stage them in shared memory and extend the CTA's bounding box.
-// Phase 2: each of the 16 warps takes 8 of the points, one at a time; for a point, lane
-// (g, j) (g = lane / 8, j = lane % 8) adds the taps of x offsets j (and j + 8 when w > 8)
-// in the z planes g, g + 4, ... of the window, looping over its y rows. The taps go into a
-// shared tile (separate real and imaginary planes) covering the union of the windows,
-// whose plane stride is padded to 8 (mod 32) elements: the four groups of a warp then sit
-// 8 banks apart and their 8 lanes on consecutive banks, so every shared atomic of a warp
+// A CTA spreads up to 128 consecutive points (Morton order in grid-cell units, so they are
+// close on the grid). Phase 1: threads 0..127 each take one point, compute its window
+// start and value and stage them in shared memory; 384 threads evaluate the kernel weights
+// (one per point and dimension); the window starts of each group of 8 points give a box,
+// and consecutive groups are joined into sub-bins while their joint tile fits the shared
+// memory (a group too wide alone goes to the grid directly). Phase 2, per sub-bin: each of
+// the 16 warps takes its points one at a time; for a point, lane (g, j) (g = lane / 8,
+// j = lane % 8) adds the taps of x offsets j (and j + 8 when w > 8) in the z planes g,
+// g + 4, ... of the window, looping over its y rows. The taps go into a shared tile
+// (separate real and imaginary planes) covering the union of the sub-bin's windows, whose
+// plane stride is padded to 8 (mod 32) elements: the four groups of a warp then sit 8
+// banks apart and their 8 lanes on consecutive banks, so every shared atomic of a warp
 // touches 32 distinct banks. The tile is then added to the grid with vector atomics, one
-// warp per tile row; when the tile would not fit, the taps go straight to the grid with
-// the same lane layout.
+// warp per tile row.
 constexpr int kGroupLanes = 8;
 constexpr int kZGroups = 32 / kGroupLanes;                        // lane groups along z
 constexpr int kPointsPerWarp = kSpreadPoints / (kSpreadThreads / 32);
@@ -327,7 +329,6 @@ template <typename T, int W> struct SpreadShared {
     T v[kSpreadPoints][2];                       // complex value
     T fr[kSpreadPoints][3];                      // fractional window offsets
     int i0[kSpreadPoints][3];                    // window start (i0[.][0] = INT_MIN: no point)
-    int lo[3], hi[3];
 };
 
 // Kernel weights of the staged points: 3 x 128 rows (point, dimension), one per thread of
@@ -374,7 +375,8 @@ template <typename T> __device__ __forceinline__ df::DF weight_df(const T &slot)
 }
 
 template <typename T, int W> __host__ __device__ constexpr int tile_bytes() {
-    return ((smem_per_cta<T>() - (int)sizeof(SpreadShared<T, W>) - (int)sizeof(NufftDev) - 64) /
+    // the rest of the static shared memory of spread_cta (group boxes, sub-bins) < 1 KB
+    return ((smem_per_cta<T>() - (int)sizeof(SpreadShared<T, W>) - (int)sizeof(NufftDev) - 1024) /
             (2 * (int)sizeof(T) * 32)) *
            (2 * (int)sizeof(T) * 32);
 }
@@ -438,24 +440,20 @@ __device__ __forceinline__ void limbs(df::DF x, int &H, int &L) {
     L = __float_as_int(__fadd_rn(r, kLimbMagic)) - __float_as_int(kLimbMagic);
 }
 
-template <typename T, int W, bool PERIODIC, bool IT>
+template <typename T, int W, bool PERIODIC>
 __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
                                            const SpreadGrid<T, PERIODIC> grid, int ppc) {
-    static_assert(!IT || sizeof(T) == 8, "the fixed-point tile serves FP64 grids");
     extern __shared__ unsigned char smem_raw[];
     __shared__ SpreadShared<T, W> sh;
-    __shared__ unsigned s_maxbits;
-    constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));  // cells (16 bytes each for FP64)
+    __shared__ int s_lo[3], s_hi[3];
+    constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));
     T *tre = reinterpret_cast<T *>(smem_raw);
     T *tim = tre + cap;
-    int *tHr = reinterpret_cast<int *>(smem_raw);  // fixed-point form: four int planes
-    int *tLr = tHr + cap, *tHi = tLr + cap, *tLi = tHi + cap;
     const int tid = threadIdx.x;
     if (tid < 3) {
-        sh.lo[tid] = INT_MAX;
-        sh.hi[tid] = INT_MIN;
+        s_lo[tid] = INT_MAX;
+        s_hi[tid] = INT_MIN;
     }
-    if (tid == 0) s_maxbits = 0u;
     __syncthreads();
     if (tid < kSpreadPoints) {
         if (act) {
@@ -465,46 +463,23 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
             for (int d = 0; d < 3; ++d) {
                 sh.fr[tid][d] = fr[d];
                 sh.i0[tid][d] = i0[d];
-                atomicMin(&sh.lo[d], i0[d]);
-                atomicMax(&sh.hi[d], i0[d]);
-            }
-            if (IT) {
-                // an upper bound of |vr|, |vi| as a float (non-negative floats order as integers)
-                const double m = fmax(fabs((double)vr), fabs((double)vi));
-                atomicMax(&s_maxbits, __float_as_uint(__double2float_ru(m)));
+                atomicMin(&s_lo[d], i0[d]);
+                atomicMax(&s_hi[d], i0[d]);
             }
         } else {
             sh.i0[tid][0] = INT_MIN;
         }
     }
     __syncthreads();
-    if (sh.hi[0] < sh.lo[0]) return;  // no point in this CTA (uniform across the CTA)
-    stage_weights<T, W, IT>(sh, beta);
-    const int lo0 = sh.lo[0], lo1 = sh.lo[1], lo2 = sh.lo[2];
-    const int64_t tx = (int64_t)sh.hi[0] - lo0 + W, ty = (int64_t)sh.hi[1] - lo1 + W,
-                  tz = (int64_t)sh.hi[2] - lo2 + W;
+    if (s_hi[0] < s_lo[0]) return;  // no point in this CTA (uniform across the CTA)
+    stage_weights<T, W>(sh, beta);
+    const int lo0 = s_lo[0], lo1 = s_lo[1], lo2 = s_lo[2];
+    const int64_t tx = (int64_t)s_hi[0] - lo0 + W, ty = (int64_t)s_hi[1] - lo1 + W,
+                  tz = (int64_t)s_hi[2] - lo2 + W;
     const int64_t ps64 = tile_plane_stride(tx * ty);
     const bool tiled = tz * ps64 <= cap;
-    const bool fixed = IT && tiled && s_maxbits != 0u;  // fixed-point form of the tile
-    const int e = (int)((s_maxbits >> 23) & 0xFFu) - 126;  // every |value| < 2^e
     const int txi = (int)tx, tyi = (int)ty, ps = tiled ? (int)ps64 : 0;
-    if (fixed) {
-        // each point's value in units 2^(e - 43), as float pairs in place (once per point)
-        if (tid < kSpreadPoints && sh.i0[tid][0] != INT_MIN) {
-#pragma unroll
-            for (int c = 0; c < 2; ++c) {
-                const df::DF v = df::split_bits(ldexp((double)sh.v[tid][c], 43 - e));
-                *reinterpret_cast<float2 *>(&sh.v[tid][c]) = make_float2(v.h, v.l);
-            }
-        }
-        const int cells = (int)(tz * ps64);
-        for (int j = tid; j < cells; j += blockDim.x) {
-            tHr[j] = 0;
-            tLr[j] = 0;
-            tHi[j] = 0;
-            tLi[j] = 0;
-        }
-    } else if (tiled) {
+    if (tiled) {
         const int cells = (int)(tz * ps64);
         for (int j = tid; j < cells; j += blockDim.x) {
             tre[j] = T(0);
@@ -520,53 +495,6 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         const int px0 = sh.i0[p][0];
         if (px0 == INT_MIN) continue;  // uniform across the warp
         const int py0 = sh.i0[p][1], pz0 = sh.i0[p][2];
-        if constexpr (IT) {
-            if (fixed) {
-                // taps in units 2^(e - 43), double-float products, two limbs, four int atomics
-                df::DF ar[kXT], ai[kXT];
-                int cx[kXT];
-                bool on[kXT];
-                const df::DF vr_ = weight_df(sh.v[p][0]), vi_ = weight_df(sh.v[p][1]);
-#pragma unroll
-                for (int t = 0; t < kXT; ++t) {
-                    const int jx = jx0 + t * kGroupLanes;
-                    on[t] = jx < W;
-                    const df::DF wxv = on[t] ? weight_df(sh.w[p][jx]) : df::DF{0.f, 0.f};
-                    ar[t] = df::dmul(vr_, wxv);
-                    ai[t] = df::dmul(vi_, wxv);
-                    cx[t] = px0 - lo0 + jx;
-                }
-                df::DF wy[W];
-#pragma unroll
-                for (int j = 0; j < W; ++j) wy[j] = weight_df(sh.w[p][W + j]);
-                for (int jz = g; jz < W; jz += kZGroups) {
-                    const df::DF wz = weight_df(sh.w[p][2 * W + jz]);
-                    df::DF zr[kXT], zi[kXT];
-#pragma unroll
-                    for (int t = 0; t < kXT; ++t) {
-                        zr[t] = df::dmul(ar[t], wz);
-                        zi[t] = df::dmul(ai[t], wz);
-                    }
-                    const int zbase = (pz0 - lo2 + jz) * ps + (py0 - lo1) * txi;
-#pragma unroll
-                    for (int jy = 0; jy < W; ++jy) {
-                        const int base = zbase + jy * txi;
-#pragma unroll
-                        for (int t = 0; t < kXT; ++t)
-                            if (on[t]) {
-                                int H, L;
-                                limbs(df::dmul(zr[t], wy[jy]), H, L);
-                                atomicAdd(tHr + base + cx[t], H);
-                                atomicAdd(tLr + base + cx[t], L);
-                                limbs(df::dmul(zi[t], wy[jy]), H, L);
-                                atomicAdd(tHi + base + cx[t], H);
-                                atomicAdd(tLi + base + cx[t], L);
-                            }
-                    }
-                }
-                continue;
-            }
-        }
         T ar[kXT], ai[kXT];
         int cx[kXT];
         bool on[kXT];
@@ -574,16 +502,16 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         for (int t = 0; t < kXT; ++t) {
             const int jx = jx0 + t * kGroupLanes;
             on[t] = jx < W;
-            const T wxv = on[t] ? weight_of<T, IT>(sh.w[p][jx]) : T(0);
+            const T wxv = on[t] ? weight_of<T, false>(sh.w[p][jx]) : T(0);
             ar[t] = sh.v[p][0] * wxv;
             ai[t] = sh.v[p][1] * wxv;
             cx[t] = tiled ? px0 - lo0 + jx : (PERIODIC ? wrap(px0 + jx, grid.n(0)) : px0 + jx);
         }
         T wy[W];
 #pragma unroll
-        for (int j = 0; j < W; ++j) wy[j] = weight_of<T, IT>(sh.w[p][W + j]);
+        for (int j = 0; j < W; ++j) wy[j] = weight_of<T, false>(sh.w[p][W + j]);
         for (int jz = g; jz < W; jz += kZGroups) {
-            const T wz = weight_of<T, IT>(sh.w[p][2 * W + jz]);
+            const T wz = weight_of<T, false>(sh.w[p][2 * W + jz]);
             // Fold the z weight into the value once per plane: two multiplies per tap.
             T zr[kXT], zi[kXT];
 #pragma unroll
@@ -629,20 +557,311 @@ __device__ __forceinline__ void spread_cta(bool act, const int i0[3], const T fr
         cplx_t<T> *grow = grid.row(gz, gy);
         const int t0 = z * ps + y * txi;
         for (int x = lane; x < txi; x += 32) {
-            T re, im;
-            if (fixed) {
-                const int hr = tHr[t0 + x], lr = tLr[t0 + x], hi = tHi[t0 + x], li = tLi[t0 + x];
-                if ((hr | lr | hi | li) == 0) continue;
-                // (H 2^22 + L) exactly as a 64-bit integer (|.| < 2^51), times the unit
-                re = (T)i64_pow2(((long long)hr << 22) + lr, e - 43);
-                im = (T)i64_pow2(((long long)hi << 22) + li, e - 43);
-            } else {
-                re = tre[t0 + x];
-                im = tim[t0 + x];
-                if (re == T(0) && im == T(0)) continue;
-            }
+            const T re = tre[t0 + x], im = tim[t0 + x];
+            if (re == T(0) && im == T(0)) continue;
             const int gx = PERIODIC ? wrap(lo0 + x, grid.n(0)) : lo0 + x;
             grid_add(grow + gx, re, im);
+        }
+    }
+}
+
+template <typename T, int W, bool PERIODIC>
+__device__ __forceinline__ void spread_cta_fixed(bool act, const int i0[3], const T fr[3], T vr, T vi, T beta,
+                                           const SpreadGrid<T, PERIODIC> grid, int ppc) {
+    static_assert(sizeof(T) == 8, "the fixed-point tile serves FP64 grids");
+    constexpr bool IT = true;
+    constexpr int kGroup = 8;                           // points per bounding-box group
+    constexpr int kGroups = kSpreadPoints / kGroup;
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ SpreadShared<T, W> sh;
+    __shared__ unsigned s_maxbits;
+    __shared__ int s_gbox[kGroups][6];                  // per group: window-start min (3), max (3)
+    __shared__ int s_sub[kGroups][8];                   // sub-bins: p0, p1, lo (3), tx, ty, tz (0: untiled)
+    __shared__ int s_nsub;
+    constexpr int cap = tile_bytes<T, W>() / (2 * (int)sizeof(T));  // cells (16 bytes each for FP64)
+    T *tre = reinterpret_cast<T *>(smem_raw);
+    T *tim = tre + cap;
+    int *tHr = reinterpret_cast<int *>(smem_raw);  // fixed-point form: four int planes
+    int *tLr = tHr + cap, *tHi = tLr + cap, *tLi = tHi + cap;
+    const int tid = threadIdx.x;
+    if (tid == 0) s_maxbits = 0u;
+    __syncthreads();
+    if (tid < kSpreadPoints) {
+        if (act) {
+            sh.v[tid][0] = vr;
+            sh.v[tid][1] = vi;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                sh.fr[tid][d] = fr[d];
+                sh.i0[tid][d] = i0[d];
+            }
+            if (IT) {
+                // an upper bound of |vr|, |vi| as a float (non-negative floats order as integers)
+                const double m = fmax(fabs((double)vr), fabs((double)vi));
+                atomicMax(&s_maxbits, __float_as_uint(__double2float_ru(m)));
+            }
+        } else {
+            sh.i0[tid][0] = INT_MIN;
+        }
+    }
+    __syncthreads();
+    stage_weights<T, W, IT>(sh, beta);
+    // Bounding boxes of the window starts of each group of 8 consecutive points.
+    const int ngroups = (ppc + kGroup - 1) / kGroup;
+    if (tid < 3 * ngroups) {
+        const int g = tid / 3, d = tid - 3 * g;
+        int lo = INT_MAX, hi = INT_MIN;
+#pragma unroll
+        for (int q = 0; q < kGroup; ++q) {
+            const int p = g * kGroup + q;
+            if (p < kSpreadPoints && sh.i0[p][0] != INT_MIN) {
+                lo = min(lo, sh.i0[p][d]);
+                hi = max(hi, sh.i0[p][d]);
+            }
+        }
+        s_gbox[g][d] = lo;
+        s_gbox[g][3 + d] = hi;
+    }
+    __syncthreads();
+    // Sub-bins: runs of consecutive groups whose joint tile fits (chunk order is Morton order,
+    // so consecutive groups are close); a group too wide alone goes straight to the grid.
+    // Only the fixed-point tile splits a bin (spread_cta keeps one tile per bin or none): with
+    // float atomics (compare-and-swap loops) the taps of a bin too wide for the tile are
+    // cheaper as vector reductions into the grid (splitting made FP32 spreading 1.4-1.7x
+    // slower).
+    if (tid == 0) {
+        int n = 0, g0 = 0;
+        int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+        auto cells_of = [&](const int *l, const int *h) -> int64_t {
+            const int64_t tx = (int64_t)h[0] - l[0] + W, ty = (int64_t)h[1] - l[1] + W, tz = (int64_t)h[2] - l[2] + W;
+            return tz * tile_plane_stride(tx * ty);
+        };
+        auto emit = [&](int ga, int gb, const int *l, const int *h, bool tiled) {
+            int *e = s_sub[n++];
+            e[0] = ga * kGroup;
+            e[1] = min(gb * kGroup, kSpreadPoints);
+            for (int d = 0; d < 3; ++d) e[2 + d] = l[d];
+            e[5] = tiled ? h[0] - l[0] + W : 0;
+            e[6] = h[1] - l[1] + W;
+            e[7] = h[2] - l[2] + W;
+        };
+        for (int g = 0; g < ngroups; ++g) {
+            if (s_gbox[g][0] == INT_MAX) continue;  // no point in this group
+            int nl[3], nh[3];
+            for (int d = 0; d < 3; ++d) {
+                nl[d] = min(lo[d], s_gbox[g][d]);
+                nh[d] = max(hi[d], s_gbox[g][3 + d]);
+            }
+            if (cells_of(nl, nh) <= cap) {
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = nl[d];
+                    hi[d] = nh[d];
+                }
+                continue;
+            }
+            if (lo[0] != INT_MAX) emit(g0, g, lo, hi, true);
+            g0 = g;
+            for (int d = 0; d < 3; ++d) {
+                lo[d] = s_gbox[g][d];
+                hi[d] = s_gbox[g][3 + d];
+            }
+            if (cells_of(lo, hi) > cap) {  // this group alone does not fit
+                emit(g, g + 1, lo, hi, false);
+                g0 = g + 1;
+                for (int d = 0; d < 3; ++d) {
+                    lo[d] = INT_MAX;
+                    hi[d] = INT_MIN;
+                }
+            }
+        }
+        if (lo[0] != INT_MAX) emit(g0, ngroups, lo, hi, true);
+        s_nsub = n;
+    }
+    __syncthreads();
+    const int nsub = s_nsub;
+    if (nsub == 0) return;  // no point in this CTA (uniform across the CTA)
+    const int e = (int)((s_maxbits >> 23) & 0xFFu) - 126;  // every |value| < 2^e
+    const bool any_value = s_maxbits != 0u;
+    if (IT && any_value) {
+        // each point's value in units 2^(e - 43), as float pairs in place (once per point;
+        // untiled sub-bins read it back as FP64 in the same units, scaled back at the add)
+        if (tid < kSpreadPoints && sh.i0[tid][0] != INT_MIN) {
+#pragma unroll
+            for (int c = 0; c < 2; ++c) {
+                const df::DF v = df::split_bits(ldexp((double)sh.v[tid][c], 43 - e));
+                *reinterpret_cast<float2 *>(&sh.v[tid][c]) = make_float2(v.h, v.l);
+            }
+        }
+    }
+    const int lane = tid & 31, warp = tid >> 5, g = lane / kGroupLanes, jx0 = lane % kGroupLanes;
+    constexpr int kXT = (W + kGroupLanes - 1) / kGroupLanes;  // x taps per lane (1 or 2)
+    for (int sb = 0; sb < nsub; ++sb) {
+        const int p0 = s_sub[sb][0], p1 = s_sub[sb][1];
+        const int lo0 = s_sub[sb][2], lo1 = s_sub[sb][3], lo2 = s_sub[sb][4];
+        const int txi = s_sub[sb][5], tyi = s_sub[sb][6], tzi = s_sub[sb][7];
+        const bool tiled = txi > 0;
+        const bool fixed = IT && tiled && any_value;  // fixed-point form of the tile
+        const int ps = tiled ? (int)tile_plane_stride((int64_t)txi * tyi) : 0;
+        if (tiled) {
+            __syncthreads();  // the previous sub-bin's flush has read the tile
+            const int cells = tzi * ps;
+            if (fixed) {
+                for (int j = tid; j < cells; j += blockDim.x) {
+                    tHr[j] = 0;
+                    tLr[j] = 0;
+                    tHi[j] = 0;
+                    tLi[j] = 0;
+                }
+            } else {
+                for (int j = tid; j < cells; j += blockDim.x) {
+                    tre[j] = T(0);
+                    tim[j] = T(0);
+                }
+            }
+        }
+        __syncthreads();  // tile cleared; staged values, weights and scales visible
+        const int rounds = (p1 - p0 + kSpreadThreads / 32 - 1) / (kSpreadThreads / 32);
+        for (int round = 0; round < rounds; ++round) {
+            const int p = p0 + round * (kSpreadThreads / 32) + warp;  // warps take points 16 apart
+            if (p >= p1) continue;
+            const int px0 = sh.i0[p][0];
+            if (px0 == INT_MIN) continue;  // uniform across the warp
+            const int py0 = sh.i0[p][1], pz0 = sh.i0[p][2];
+            if constexpr (IT) {
+                if (fixed) {
+                    // taps in units 2^(e - 43), double-float products, two limbs, four int atomics
+                    df::DF ar[kXT], ai[kXT];
+                    int cx[kXT];
+                    bool on[kXT];
+                    const df::DF vr_ = weight_df(sh.v[p][0]), vi_ = weight_df(sh.v[p][1]);
+#pragma unroll
+                    for (int t = 0; t < kXT; ++t) {
+                        const int jx = jx0 + t * kGroupLanes;
+                        on[t] = jx < W;
+                        const df::DF wxv = on[t] ? weight_df(sh.w[p][jx]) : df::DF{0.f, 0.f};
+                        ar[t] = df::dmul(vr_, wxv);
+                        ai[t] = df::dmul(vi_, wxv);
+                        cx[t] = px0 - lo0 + jx;
+                    }
+                    df::DF wy[W];
+#pragma unroll
+                    for (int j = 0; j < W; ++j) wy[j] = weight_df(sh.w[p][W + j]);
+                    for (int jz = g; jz < W; jz += kZGroups) {
+                        const df::DF wz = weight_df(sh.w[p][2 * W + jz]);
+                        df::DF zr[kXT], zi[kXT];
+#pragma unroll
+                        for (int t = 0; t < kXT; ++t) {
+                            zr[t] = df::dmul(ar[t], wz);
+                            zi[t] = df::dmul(ai[t], wz);
+                        }
+                        const int zbase = (pz0 - lo2 + jz) * ps + (py0 - lo1) * txi;
+#pragma unroll
+                        for (int jy = 0; jy < W; ++jy) {
+                            const int base = zbase + jy * txi;
+#pragma unroll
+                            for (int t = 0; t < kXT; ++t)
+                                if (on[t]) {
+                                    int H, L;
+                                    limbs(df::dmul(zr[t], wy[jy]), H, L);
+                                    atomicAdd(tHr + base + cx[t], H);
+                                    atomicAdd(tLr + base + cx[t], L);
+                                    limbs(df::dmul(zi[t], wy[jy]), H, L);
+                                    atomicAdd(tHi + base + cx[t], H);
+                                    atomicAdd(tLi + base + cx[t], L);
+                                }
+                        }
+                    }
+                    continue;
+                }
+            }
+            // T taps: into the T tile, or (untiled sub-bin) straight into the grid. With the
+            // fixed-point form's scaled pairs staged, the values are read back as FP64 and the
+            // unit applied once per point.
+            T vr_, vi_;
+            if (IT && any_value) {
+                vr_ = (T)ldexp(df::to_double(weight_df(sh.v[p][0])), e - 43);
+                vi_ = (T)ldexp(df::to_double(weight_df(sh.v[p][1])), e - 43);
+            } else {
+                vr_ = sh.v[p][0];
+                vi_ = sh.v[p][1];
+            }
+            T ar[kXT], ai[kXT];
+            int cx[kXT];
+            bool on[kXT];
+#pragma unroll
+            for (int t = 0; t < kXT; ++t) {
+                const int jx = jx0 + t * kGroupLanes;
+                on[t] = jx < W;
+                const T wxv = on[t] ? weight_of<T, IT>(sh.w[p][jx]) : T(0);
+                ar[t] = vr_ * wxv;
+                ai[t] = vi_ * wxv;
+                cx[t] = tiled ? px0 - lo0 + jx : (PERIODIC ? wrap(px0 + jx, grid.n(0)) : px0 + jx);
+            }
+            T wy[W];
+#pragma unroll
+            for (int j = 0; j < W; ++j) wy[j] = weight_of<T, IT>(sh.w[p][W + j]);
+            for (int jz = g; jz < W; jz += kZGroups) {
+                const T wz = weight_of<T, IT>(sh.w[p][2 * W + jz]);
+                // Fold the z weight into the value once per plane: two multiplies per tap.
+                T zr[kXT], zi[kXT];
+#pragma unroll
+                for (int t = 0; t < kXT; ++t) {
+                    zr[t] = ar[t] * wz;
+                    zi[t] = ai[t] * wz;
+                }
+                if (tiled) {
+                    const int zbase = (pz0 - lo2 + jz) * ps + (py0 - lo1) * txi;
+#pragma unroll
+                    for (int jy = 0; jy < W; ++jy) {
+                        const int base = zbase + jy * txi;
+#pragma unroll
+                        for (int t = 0; t < kXT; ++t)
+                            if (on[t]) {
+                                atomicAdd(tre + base + cx[t], zr[t] * wy[jy]);
+                                atomicAdd(tim + base + cx[t], zi[t] * wy[jy]);
+                            }
+                    }
+                } else {
+                    const int64_t gz = PERIODIC ? wrap(pz0 + jz, grid.n(2)) : pz0 + jz;
+                    for (int jy = 0; jy < W; ++jy) {
+                        const int64_t gy = PERIODIC ? wrap(py0 + jy, grid.n(1)) : py0 + jy;
+                        cplx_t<T> *row = grid.row(gz, gy);
+#pragma unroll
+                        for (int t = 0; t < kXT; ++t)
+                            if (on[t]) grid_add(row + cx[t], zr[t] * wy[jy], zi[t] * wy[jy]);
+                    }
+                }
+            }
+        }
+        if (!tiled) continue;
+        __syncthreads();
+        // Flush: one warp per (y, z) row of the tile, lanes along x (coalesced vector atomics).
+        const int rows = tyi * tzi;
+        for (int r = warp; r < rows; r += blockDim.x >> 5) {
+            const int y = r % tyi, z = r / tyi;
+            int gy = lo1 + y, gz = lo2 + z;
+            if (PERIODIC) {
+                gy = wrap(gy, grid.n(1));
+                gz = wrap(gz, grid.n(2));
+            }
+            cplx_t<T> *grow = grid.row(gz, gy);
+            const int t0 = z * ps + y * txi;
+            for (int x = lane; x < txi; x += 32) {
+                T re, im;
+                if (fixed) {
+                    const int hr = tHr[t0 + x], lr = tLr[t0 + x], hi = tHi[t0 + x], li = tLi[t0 + x];
+                    if ((hr | lr | hi | li) == 0) continue;
+                    // (H 2^22 + L) exactly as a 64-bit integer (|.| < 2^51), times the unit
+                    re = (T)i64_pow2(((long long)hr << 22) + lr, e - 43);
+                    im = (T)i64_pow2(((long long)hi << 22) + li, e - 43);
+                } else {
+                    re = tre[t0 + x];
+                    im = tim[t0 + x];
+                    if (re == T(0) && im == T(0)) continue;
+                }
+                const int gx = PERIODIC ? wrap(lo0 + x, grid.n(0)) : lo0 + x;
+                grid_add(grow + gx, re, im);
+            }
         }
     }
 }
@@ -670,7 +889,10 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         vr = cv * pr;
         vi = cv * pim;
     }
-    spread_cta<T, W, false, IT>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
+    if constexpr (IT)
+        spread_cta_fixed<T, W, false>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
+    else
+        spread_cta<T, W, false>(act, i0, fr, vr, vi, beta, SpreadGrid<T, false>{b, G1}, ppc);
 }
 
 // vis -> sky step 1 (transpose of the interpolation): baselines u = conj(Q) V onto the n2
@@ -696,7 +918,10 @@ __global__ void __launch_bounds__(kSpreadThreads, sizeof(T) == 4 ? 2 : 1)
         ur = qr * v.x + qi * v.y;  // conj(Q) v
         ui = qr * v.y - qi * v.x;
     }
-    spread_cta<T, W, true, IT>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
+    if constexpr (IT)
+        spread_cta_fixed<T, W, true>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
+    else
+        spread_cta<T, W, true>(act, i0, fr, ur, ui, beta, SpreadGrid<T, true>{b, G2}, ppc);
 }
 
 // ------------------------------------------------------------------ interpolation (gather)
