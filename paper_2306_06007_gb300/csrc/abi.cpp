@@ -787,11 +787,6 @@ void configure(Plan &p, int64_t n_pix, int64_t n_vis, double eps, int isign, con
     // keeps FP64 shared atomics (comparisons).
     p.int_tile = p.prec == 2 && !p.plain;
     if (const char *v = std::getenv("HVOX_SPREAD_TILE")) p.int_tile = p.int_tile && std::string(v) != "float";
-    // FP64 plans (w ~ 13) spread bins of 64 points: 128 Morton-ordered pixels span a box
-    // whose windows exceed even the 11,000-cell tile, sending every tap to global FP64
-    // atomics (autotuned bins at eps 1e-9: 1 km spreading 4.0 -> 2.1 ms, 3 km 16.1 -> 11.0,
-    // 10 km 197 -> 103 ms per step). hvox_opts.autotune still times 128, 64 and 32.
-    if (p.int_tile) p.ppc_pix = p.ppc_vis = 64;
     // Owners per thread of the direct kernels: four for the double-float kernels (LOFAR-like
     // sky x 1.4M baselines at eps 1e-9: 320.2 against 327.8 ms per step), two for the FP32
     // ones (config 2 at eps 1e-6: 125.3 against 126.8 ms) and the FP64 ones. HVOX_DIRECT_VPT
