@@ -37,6 +37,17 @@ __device__ __forceinline__ DF dadd(DF a, DF b) {
     return {s, e};
 }
 
+// The same sum without its renormalisation, for a value that only feeds further sums or
+// products: the pair (s, e) is not normalised (|e| may exceed ulp(s) / 2 after
+// cancellation), but it is within the same ~2^-47 (|a| + |b|) of a + b, and an operation
+// that consumes it keeps its norm-wise bound (its hi parts are combined exactly, its lo
+// parts in FP32).
+__device__ __forceinline__ DF dadd_lazy(DF a, DF b) {
+    float s, e;
+    two_sum(a.h, b.h, s, e);
+    return {s, __fadd_rn(e, __fadd_rn(a.l, b.l))};
+}
+
 __device__ __forceinline__ DF dneg(DF a) { return {-a.h, -a.l}; }
 
 // a b as an unnormalised pair (p, e): p = fl(a.h b.h), e = the rounding error of p (FMA,
@@ -54,14 +65,18 @@ __device__ __forceinline__ DF dmul(DF a, DF b) {
 }
 
 // a b + sg c d for sg = +-1, with one renormalisation (the real or imaginary part of a
-// complex product).
-__device__ __forceinline__ DF dmul2(DF a, DF b, DF c, DF d, float sg) {
+// complex product); the lazy form leaves it out, as dadd_lazy does.
+__device__ __forceinline__ DF dmul2_lazy(DF a, DF b, DF c, DF d, float sg) {
     float p, e, q, f, s, t;
     dmul_raw(a, b, p, e);
     dmul_raw(c, d, q, f);
     two_sum(p, sg * q, s, t);
-    t = __fadd_rn(t, __fmaf_rn(sg, f, e));
-    fast_two_sum(s, t, s, t);
+    return {s, __fadd_rn(t, __fmaf_rn(sg, f, e))};
+}
+__device__ __forceinline__ DF dmul2(DF a, DF b, DF c, DF d, float sg) {
+    const DF r = dmul2_lazy(a, b, c, d, sg);
+    float s, t;
+    fast_two_sum(r.h, r.l, s, t);
     return {s, t};
 }
 
@@ -94,6 +109,8 @@ __device__ __forceinline__ DF acc_done(DAcc a) {
     fast_two_sum(a.s, a.e, s, e);
     return {s, e};
 }
+// The sum as an unnormalised pair, for a value that feeds a dadd (see dadd_lazy).
+__device__ __forceinline__ DF acc_lazy(DAcc a) { return {a.s, a.e}; }
 
 // FP64 <-> double-float by bit manipulation: GB300 issues FP64 instructions (conversions
 // included) at 1/64 of its FP32 rate.

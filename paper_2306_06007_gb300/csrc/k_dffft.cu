@@ -27,6 +27,8 @@ namespace {
 
 using namespace df;
 
+// 256 threads per CTA, held to 64 registers so that four CTAs fit an SM where shared memory
+// allows (a fourth CTA hides more of each CTA's load phase and stage barriers).
 constexpr int kFftThreads = 256;
 
 struct DC {
@@ -36,14 +38,24 @@ struct DC {
 __device__ __forceinline__ DC cadd(const DC &a, const DC &b) { return {dadd(a.re, b.re), dadd(a.im, b.im)}; }
 __device__ __forceinline__ DC csub(const DC &a, const DC &b) { return {dadd(a.re, dneg(b.re)), dadd(a.im, dneg(b.im))}; }
 
-// a * (c + j s) for real double-float c, s.
-__device__ __forceinline__ DC cmul(const DC &a, DF c, DF s) {
-    return {dmul2(a.re, c, a.im, s, -1.f), dmul2(a.re, s, a.im, c, 1.f)};
+// Sums and products whose results only feed further sums (within one butterfly) skip their
+// renormalisation (dadd_lazy); the outputs a butterfly stores are renormalised.
+__device__ __forceinline__ DC cadd_lazy(const DC &a, const DC &b) {
+    return {dadd_lazy(a.re, b.re), dadd_lazy(a.im, b.im)};
+}
+__device__ __forceinline__ DC csub_lazy(const DC &a, const DC &b) {
+    return {dadd_lazy(a.re, dneg(b.re)), dadd_lazy(a.im, dneg(b.im))};
 }
 
-// a * (j sg) for sg = +-1.
-__device__ __forceinline__ DC times_j(const DC &a, float sg) {
-    return {{-sg * a.im.h, -sg * a.im.l}, {sg * a.re.h, sg * a.re.l}};
+// a * (c + j s) for real double-float c, s (unnormalised, it feeds the butterfly's sums).
+__device__ __forceinline__ DC cmul_lazy(const DC &a, DF c, DF s) {
+    return {dmul2_lazy(a.re, c, a.im, s, -1.f), dmul2_lazy(a.re, s, a.im, c, 1.f)};
+}
+
+// a * (j SG) for SG = +-1 (sign flips only).
+template <int SG> __device__ __forceinline__ DC times_j(const DC &a) {
+    if constexpr (SG > 0) return {dneg(a.im), a.re};
+    else return {a.im, dneg(a.re)};
 }
 
 __device__ __forceinline__ DC from4(float4 v) { return {{v.x, v.y}, {v.z, v.w}}; }
@@ -69,19 +81,20 @@ template <bool F64> __device__ __forceinline__ void store_cell(double2 *p, float
     else *reinterpret_cast<float4 *>(p) = v;
 }
 
-// Twiddle exp(s 2 pi i e / n) from the table of exp(2 pi i q / n) (cos h, cos l, sin h, sin l).
-__device__ __forceinline__ void twiddle(const float4 *__restrict__ tw, int e, float sg, DF &c, DF &s) {
+// Twiddle exp(SG 2 pi i e / n) from the table of exp(2 pi i q / n) (cos h, cos l, sin h, sin l).
+template <int SG> __device__ __forceinline__ void twiddle(const float4 *__restrict__ tw, int e, DF &c, DF &s) {
     const float4 t = __ldg(tw + e);
     c = {t.x, t.y};
-    s = {sg * t.z, sg * t.w};
+    s = SG > 0 ? DF{t.z, t.w} : DF{-t.z, -t.w};
 }
 
 // One Stockham stage of radix R over TX interleaved sequences: butterfly j (of n / R) reads
 // elements j + q n / R, twiddles them by exp(s 2 pi i q k span / n) (k = j mod Ns) and writes
 // the R outputs to (j / Ns) Ns R + k + q Ns. q k span < n, so the table index needs no wrap.
-template <int R, int TX>
+// The sign SG of the exponent is a template parameter: its flips fold into the operands.
+template <int R, int TX, int SG>
 __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__restrict__ b, const DfftDev &d, int Ns,
-                                      unsigned magic, float sg) {
+                                      unsigned magic) {
     const int n = d.n, m = n / R, span = n / (Ns * R);
     for (int wk = threadIdx.x; wk < m * TX; wk += blockDim.x) {
         const int j = wk / TX, t = wk - j * TX;
@@ -93,8 +106,8 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__re
 #pragma unroll
             for (int q = 1; q < R; ++q) {
                 DF c, s;
-                twiddle(d.tw, q * k * span, sg, c, s);
-                v[q] = cmul(v[q], c, s);
+                twiddle<SG>(d.tw, q * k * span, c, s);
+                v[q] = cmul_lazy(v[q], c, s);
             }
         }
         DC y[R];
@@ -102,8 +115,8 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__re
             y[0] = cadd(v[0], v[1]);
             y[1] = csub(v[0], v[1]);
         } else if constexpr (R == 4) {
-            const DC a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
-            const DC b0 = cadd(v[1], v[3]), b1 = times_j(csub(v[1], v[3]), sg);
+            const DC a0 = cadd_lazy(v[0], v[2]), a1 = csub_lazy(v[0], v[2]);
+            const DC b0 = cadd_lazy(v[1], v[3]), b1 = times_j<SG>(csub_lazy(v[1], v[3]));
             y[0] = cadd(a0, b0);
             y[1] = cadd(a1, b1);
             y[2] = csub(a0, b0);
@@ -118,8 +131,8 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__re
             DC sq[H], dq[H];
 #pragma unroll
             for (int q = 1; q <= H; ++q) {
-                sq[q - 1] = cadd(v[q], v[R - q]);
-                dq[q - 1] = csub(v[q], v[R - q]);
+                sq[q - 1] = cadd_lazy(v[q], v[R - q]);
+                dq[q - 1] = csub_lazy(v[q], v[R - q]);
             }
             {
                 DAcc re = acc_of(v[0].re), im = acc_of(v[0].im);
@@ -147,8 +160,8 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__re
                         acc_fma(bi, dq[q - 1].im, sn);
                     }
                 }
-                const DC A = {acc_done(ar), acc_done(ai)};
-                const DC jb = times_j({acc_done(br), acc_done(bi)}, sg);
+                const DC A = {acc_lazy(ar), acc_lazy(ai)};
+                const DC jb = times_j<SG>({acc_lazy(br), acc_lazy(bi)});
                 y[kk] = cadd(A, jb);
                 y[R - kk] = csub(A, jb);
             }
@@ -162,18 +175,18 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__re
 // In-place transforms of TX interleaved sequences of length n in shared memory (element q of
 // sequence t at a[q TX + t]); b is the second buffer of the Stockham ping-pong. Returns the
 // buffer holding the result.
-template <int TX>
-__device__ float4 *fft_smem(float4 *a, float4 *b, const DfftDev &d, float sg) {
+template <int TX, int SG>
+__device__ float4 *fft_smem(float4 *a, float4 *b, const DfftDev &d) {
     int Ns = 1;
     for (int st = 0; st < d.stages; ++st) {
         const int r = d.radix[st];
         const unsigned mg = d.ns_magic[st];
         switch (r) {
-            case 4: stage<4, TX>(a, b, d, Ns, mg, sg); break;
-            case 2: stage<2, TX>(a, b, d, Ns, mg, sg); break;
-            case 3: stage<3, TX>(a, b, d, Ns, mg, sg); break;
-            case 5: stage<5, TX>(a, b, d, Ns, mg, sg); break;
-            default: stage<7, TX>(a, b, d, Ns, mg, sg); break;
+            case 4: stage<4, TX, SG>(a, b, d, Ns, mg); break;
+            case 2: stage<2, TX, SG>(a, b, d, Ns, mg); break;
+            case 3: stage<3, TX, SG>(a, b, d, Ns, mg); break;
+            case 5: stage<5, TX, SG>(a, b, d, Ns, mg); break;
+            default: stage<7, TX, SG>(a, b, d, Ns, mg); break;
         }
         __syncthreads();
         float4 *tmp = a;
@@ -192,10 +205,10 @@ __device__ __forceinline__ int64_t band_plane(int64_t P, int64_t halfK, int64_t 
 
 // Rows (x): sequence s = (band plane P, row R) with R over all n2y rows or only the band rows.
 // IN64 / OUT64: the grid holds FP64 values before / after the pass (else double-float).
-template <bool IN64, bool OUT64>
-__global__ void __launch_bounds__(kFftThreads) dfft_rows_kernel(double2 *__restrict__ g, DfftDev d, int64_t n2y,
+template <int SG, bool IN64, bool OUT64>
+__global__ void __launch_bounds__(kFftThreads, 4) dfft_rows_kernel(double2 *__restrict__ g, DfftDev d, int64_t n2y,
                                                                  int64_t halfK, int64_t n2z, int64_t K, int64_t half,
-                                                                 int64_t rows, int64_t h1y, float sg) {
+                                                                 int64_t rows, int64_t h1y) {
     extern __shared__ float4 smem[];
     const int n = d.n;
     const int64_t s = blockIdx.x;
@@ -205,17 +218,16 @@ __global__ void __launch_bounds__(kFftThreads) dfft_rows_kernel(double2 *__restr
     float4 *a = smem, *b = smem + n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) a[i] = load_cell<IN64>(row + i);
     __syncthreads();
-    const float4 *out = fft_smem<1>(a, b, d, sg);
+    const float4 *out = fft_smem<1, SG>(a, b, d);
     for (int i = threadIdx.x; i < n; i += blockDim.x) store_cell<OUT64>(row + i, out[i]);
 }
 
 // Columns: TX adjacent columns starting at column c0 of a plane (y: columns of one band plane,
 // stride n2x; z: every column of the batch, stride K n2x n2y), element q at c + q * stride.
-template <int TX, bool IN64, bool OUT64>
-__global__ void __launch_bounds__(kFftThreads) dfft_cols_kernel(double2 *__restrict__ g, DfftDev d, int64_t stride,
+template <int TX, int SG, bool IN64, bool OUT64>
+__global__ void __launch_bounds__(kFftThreads, 4) dfft_cols_kernel(double2 *__restrict__ g, DfftDev d, int64_t stride,
                                                                  int64_t ncols, int64_t plane_cells, int64_t halfK,
-                                                                 int64_t n2z, int64_t K, int64_t half, int band,
-                                                                 float sg) {
+                                                                 int64_t n2z, int64_t K, int64_t half, int band) {
     extern __shared__ float4 smem[];
     const int n = d.n;
     const int64_t tiles = (ncols + TX - 1) / TX;
@@ -228,7 +240,7 @@ __global__ void __launch_bounds__(kFftThreads) dfft_cols_kernel(double2 *__restr
         a[e] = t < valid ? load_cell<IN64>(base + q * stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
     __syncthreads();
-    const float4 *out = fft_smem<TX>(a, b, d, sg);
+    const float4 *out = fft_smem<TX, SG>(a, b, d);
     for (int e = threadIdx.x; e < n * TX; e += blockDim.x) {
         const int q = e / TX, t = e - q * TX;
         if (t < valid) store_cell<OUT64>(base + q * stride + t, out[e]);
@@ -245,21 +257,26 @@ template <typename K> void allow_smem(K kernel) {
 // Cell formats of a pass: kDD double-float in and out, kFD FP64 in, kDF FP64 out.
 enum Io { kDD = 0, kFD = 1, kDF = 2 };
 
-template <int TX> void allow_cols() {
-    allow_smem(dfft_cols_kernel<TX, false, false>);
-    allow_smem(dfft_cols_kernel<TX, true, false>);
-    allow_smem(dfft_cols_kernel<TX, false, true>);
+template <int TX, int SG> void allow_cols() {
+    allow_smem(dfft_cols_kernel<TX, SG, false, false>);
+    allow_smem(dfft_cols_kernel<TX, SG, true, false>);
+    allow_smem(dfft_cols_kernel<TX, SG, false, true>);
+}
+
+template <int SG> void allow_sign() {
+    allow_smem(dfft_rows_kernel<SG, true, false>);
+    allow_smem(dfft_rows_kernel<SG, false, false>);
+    allow_cols<1, SG>();
+    allow_cols<2, SG>();
+    allow_cols<8, SG>();
+    allow_cols<64, SG>();
 }
 
 void set_fft_attrs() {
     static std::once_flag once;
     std::call_once(once, [] {
-        allow_smem(dfft_rows_kernel<true, false>);
-        allow_smem(dfft_rows_kernel<false, false>);
-        allow_cols<1>();
-        allow_cols<2>();
-        allow_cols<8>();
-        allow_cols<64>();
+        allow_sign<1>();
+        allow_sign<-1>();
     });
 }
 
@@ -271,33 +288,49 @@ int cols_per_cta(int n, int want) {
     return 0;
 }
 
-template <int TX, bool IN64, bool OUT64>
+template <int TX, int SG, bool IN64, bool OUT64>
 void launch_cols(double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells, int64_t planes,
-                 int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, float sg, cudaStream_t s) {
+                 int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, cudaStream_t s) {
     const int64_t tiles = (ncols + TX - 1) / TX;
     const size_t smem = (size_t)2 * d.n * TX * sizeof(float4);
-    dfft_cols_kernel<TX, IN64, OUT64><<<(unsigned)(planes * tiles), kFftThreads, smem, s>>>(
-        g, d, stride, ncols, plane_cells, halfK, n2z, K, half, band, sg);
+    dfft_cols_kernel<TX, SG, IN64, OUT64><<<(unsigned)(planes * tiles), kFftThreads, smem, s>>>(
+        g, d, stride, ncols, plane_cells, halfK, n2z, K, half, band);
     check_cuda(cudaGetLastError(), "dfft_cols");
 }
 
-template <int TX>
+template <int TX, int SG>
 void launch_cols_io(Io io, double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells,
-                    int64_t planes, int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, float sg,
-                    cudaStream_t s) {
-    if (io == kFD) launch_cols<TX, true, false>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s);
-    else if (io == kDF) launch_cols<TX, false, true>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s);
-    else launch_cols<TX, false, false>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s);
+                    int64_t planes, int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, cudaStream_t s) {
+    if (io == kFD) launch_cols<TX, SG, true, false>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s);
+    else if (io == kDF) launch_cols<TX, SG, false, true>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s);
+    else launch_cols<TX, SG, false, false>(g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s);
+}
+
+template <int SG>
+void cols_sign(int tx, Io io, double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells,
+               int64_t planes, int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, cudaStream_t s) {
+    switch (tx) {
+        case 64: launch_cols_io<64, SG>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s); break;
+        case 8: launch_cols_io<8, SG>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s); break;
+        case 2: launch_cols_io<2, SG>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s); break;
+        default: launch_cols_io<1, SG>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s); break;
+    }
 }
 
 void cols(int tx, Io io, double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells,
-          int64_t planes, int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, float sg, cudaStream_t s) {
-    switch (tx) {
-        case 64: launch_cols_io<64>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
-        case 8: launch_cols_io<8>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
-        case 2: launch_cols_io<2>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
-        default: launch_cols_io<1>(io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, sg, s); break;
-    }
+          int64_t planes, int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, int sign, cudaStream_t s) {
+    if (sign > 0) cols_sign<1>(tx, io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s);
+    else cols_sign<-1>(tx, io, g, d, stride, ncols, plane_cells, planes, halfK, n2z, K, half, band, s);
+}
+
+template <int SG>
+void launch_rows(Io io, unsigned grid, size_t smem, double2 *g, const DfftDev &d, int64_t n2y, int64_t halfK,
+                 int64_t n2z, int64_t K, int64_t half, int64_t rows, int64_t h1y, cudaStream_t s) {
+    if (io == kFD)
+        dfft_rows_kernel<SG, true, false><<<grid, kFftThreads, smem, s>>>(g, d, n2y, halfK, n2z, K, half, rows, h1y);
+    else
+        dfft_rows_kernel<SG, false, false><<<grid, kFftThreads, smem, s>>>(g, d, n2y, halfK, n2z, K, half, rows, h1y);
+    check_cuda(cudaGetLastError(), "dfft_rows");
 }
 
 }  // namespace
@@ -358,7 +391,6 @@ int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s) {
     double2 *g = static_cast<double2 *>(f.g2);
     const int64_t n2x = f.n2[0], n2y = f.n2[1], n2z = f.n2[2], K = f.K, half = f.half;
     const int64_t halfK = half * K, band_planes = 2 * halfK, plane = n2x * n2y;
-    const float sg = (float)sign;
     // The grid is FP64 before the first pass (written by the deconvolution or the spreading)
     // and holds double-float values after it: the last pass leaves them for the
     // double-float gathers (sky -> vis) or crop (vis -> sky).
@@ -366,20 +398,17 @@ int dfft_batch(const FftBatch &f, int sign, bool band_input, cudaStream_t s) {
         const int64_t r = 2 * f.h1y;  // band rows only
         const size_t smem = (size_t)2 * n2x * sizeof(float4);
         const unsigned grid = (unsigned)(band_planes * r);
-        if (io == kFD)
-            dfft_rows_kernel<true, false><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
-        else
-            dfft_rows_kernel<false, false><<<grid, kFftThreads, smem, s>>>(g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, sg);
-        check_cuda(cudaGetLastError(), "dfft_rows");
+        if (sign > 0) launch_rows<1>(io, grid, smem, g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, s);
+        else launch_rows<-1>(io, grid, smem, g, f.dx, n2y, halfK, n2z, K, half, r, f.h1y, s);
     };
     // y columns: two adjacent columns per CTA (32-byte segments) unless that leaves fewer than
     // two CTAs per SM (long columns), then one (twice the DRAM sectors, at ~15 % of HBM).
     const int ty = (size_t)2 * n2y * 2 * sizeof(float4) <= kFftSmemMax / 2 ? 2 : 1;
     auto ycols = [&] {
-        cols(cols_per_cta((int)n2y, ty), kDD, g, f.dy, n2x, n2x, plane, band_planes, halfK, n2z, K, half, 1, sg, s);
+        cols(cols_per_cta((int)n2y, ty), kDD, g, f.dy, n2x, n2x, plane, band_planes, halfK, n2z, K, half, 1, sign, s);
     };
     auto zcols = [&](Io io) {
-        cols(cols_per_cta((int)n2z, 64), io, g, f.dz, K * plane, K * plane, 0, 1, halfK, n2z, K, half, 0, sg, s);
+        cols(cols_per_cta((int)n2z, 64), io, g, f.dz, K * plane, K * plane, 0, 1, halfK, n2z, K, half, 0, sign, s);
     };
     if (band_input) {  // only the band rows of the band planes are nonzero
         rows(kFD);

@@ -321,7 +321,7 @@ static_assert(kSpreadThreads % 32 == 0 && kPointsPerWarp * (kSpreadThreads / 32)
               "every point of a spreading CTA is taken by exactly one warp");
 // Shared memory of a spreading CTA: two CTAs per SM for FP32 grids; one CTA per SM for
 // FP64 grids (the w = 13 windows of eps <= 1e-9 need the larger tile to fit a bin at all).
-template <typename T> constexpr int smem_per_cta() { return sizeof(T) == 4 ? 110 * 1024 : 224 * 1024; }
+template <typename T> __host__ __device__ constexpr int smem_per_cta() { return sizeof(T) == 4 ? 110 * 1024 : 224 * 1024; }
 
 template <typename T, int W> struct SpreadShared {
     static constexpr int kWStride = 3 * W + 1;  // odd row stride: fewer bank conflicts
