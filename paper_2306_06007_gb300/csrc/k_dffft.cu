@@ -11,7 +11,9 @@
 // first reads FP64 cells, every pass writes float pairs (the same 16 bytes per cell):
 //   rows (x): one row per CTA, only the rows that the pruned transform needs;
 //   columns (y): two adjacent columns per CTA (32-byte sectors), every column of a plane;
-//   columns (z): 64 adjacent columns per CTA, the planes of a batch interleaved.
+//   columns (z): 64 adjacent columns per CTA, the planes of a batch interleaved; these short
+//   transforms (two stages for most grids) read the grid in their first stage and write it
+//   in their last, so they need one shared buffer and one barrier.
 // Transforms are unnormalised, sign s = -1 or +1: X_k = sum_q x_q exp(s 2 pi i q k / n).
 #include <algorithm>
 #include <cmath>
@@ -92,15 +94,16 @@ template <int SG> __device__ __forceinline__ void twiddle(const float4 *__restri
 // elements j + q n / R, twiddles them by exp(s 2 pi i q k span / n) (k = j mod Ns) and writes
 // the R outputs to (j / Ns) Ns R + k + q Ns. q k span < n, so the table index needs no wrap.
 // The sign SG of the exponent is a template parameter: its flips fold into the operands.
-template <int R, int TX, int SG>
-__device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__restrict__ b, const DfftDev &d, int Ns,
-                                      unsigned magic) {
+// ld(e, t) reads element e of sequence t, st(e, t, v) writes it: shared memory between
+// stages; the grid itself in the first and the last stage of a z-column pass.
+template <int R, int TX, int SG, class Ld, class St>
+__device__ __forceinline__ void stage(Ld ld, St st, const DfftDev &d, int Ns, unsigned magic) {
     const int n = d.n, m = n / R, span = n / (Ns * R);
     for (int wk = threadIdx.x; wk < m * TX; wk += blockDim.x) {
         const int j = wk / TX, t = wk - j * TX;
         DC v[R];
 #pragma unroll
-        for (int q = 0; q < R; ++q) v[q] = from4(a[(j + q * m) * TX + t]);
+        for (int q = 0; q < R; ++q) v[q] = from4(ld(j + q * m, t));
         const int jn = Ns == 1 ? j : (int)__umulhi((unsigned)j, magic), k = j - jn * Ns;
         if (k != 0) {
 #pragma unroll
@@ -168,9 +171,76 @@ __device__ __forceinline__ void stage(const float4 *__restrict__ a, float4 *__re
         }
         const int base = jn * Ns * R + k;
 #pragma unroll
-        for (int q = 0; q < R; ++q) b[(base + q * Ns) * TX + t] = to4(y[q]);
+        for (int q = 0; q < R; ++q) st(base + q * Ns, t, to4(y[q]));
     }
 }
+
+// Element accessors: shared memory (element e of sequence t at e TX + t) and a tile of TX
+// grid columns (columns t >= valid of a ragged tile read as 0, never written).
+template <int TX> struct SmemLd {
+    const float4 *a;
+    __device__ __forceinline__ float4 operator()(int e, int t) const { return a[e * TX + t]; }
+};
+template <int TX> struct SmemSt {
+    float4 *b;
+    __device__ __forceinline__ void operator()(int e, int t, float4 v) const { b[e * TX + t] = v; }
+};
+template <bool F64> struct ColLd {
+    double2 *base;
+    int64_t stride;
+    int valid;
+    __device__ __forceinline__ float4 operator()(int e, int t) const {
+        return t < valid ? load_cell<F64>(base + e * stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+};
+template <bool F64> struct ColSt {
+    double2 *base;
+    int64_t stride;
+    int valid;
+    __device__ __forceinline__ void operator()(int e, int t, float4 v) const {
+        if (t < valid) store_cell<F64>(base + e * stride + t, v);
+    }
+};
+
+template <int TX, int SG, class Ld, class St>
+__device__ __forceinline__ void run_stage(int r, Ld ld, St st, const DfftDev &d, int Ns, unsigned mg) {
+    switch (r) {
+        case 4: stage<4, TX, SG>(ld, st, d, Ns, mg); break;
+        case 2: stage<2, TX, SG>(ld, st, d, Ns, mg); break;
+        case 3: stage<3, TX, SG>(ld, st, d, Ns, mg); break;
+        case 5: stage<5, TX, SG>(ld, st, d, Ns, mg); break;
+        default: stage<7, TX, SG>(ld, st, d, Ns, mg); break;
+    }
+}
+
+// Transforms of TX interleaved sequences of length n held in the grid: the first stage
+// reads the grid, the last writes it back, the stages between ping-pong through the
+// shared buffers a and b (a only for two stages, none for one). The grid is read only in
+// the first stage and written only in the last, with a barrier between them (one stage:
+// each thread reads every input of the butterflies it writes), so in-place is safe.
+template <int TX, int SG, class GLd, class GSt>
+__device__ __forceinline__ void fft_pass(float4 *a, float4 *b, const DfftDev &d, GLd gld, GSt gst) {
+    const int S = d.stages;
+    if (S == 1) {
+        run_stage<TX, SG>(d.radix[0], gld, gst, d, 1, d.ns_magic[0]);
+        return;
+    }
+    run_stage<TX, SG>(d.radix[0], gld, SmemSt<TX>{a}, d, 1, d.ns_magic[0]);
+    __syncthreads();
+    int Ns = d.radix[0];
+    for (int st = 1; st < S - 1; ++st) {
+        run_stage<TX, SG>(d.radix[st], SmemLd<TX>{a}, SmemSt<TX>{b}, d, Ns, d.ns_magic[st]);
+        __syncthreads();
+        float4 *tmp = a;
+        a = b;
+        b = tmp;
+        Ns *= d.radix[st];
+    }
+    run_stage<TX, SG>(d.radix[S - 1], SmemLd<TX>{a}, gst, d, Ns, d.ns_magic[S - 1]);
+}
+
+// Shared buffers a pass needs for a transform of s stages (see fft_pass).
+inline int pass_buffers(int s) { return s >= 3 ? 2 : s - 1; }
 
 // In-place transforms of TX interleaved sequences of length n in shared memory (element q of
 // sequence t at a[q TX + t]); b is the second buffer of the Stockham ping-pong. Returns the
@@ -179,20 +249,12 @@ template <int TX, int SG>
 __device__ float4 *fft_smem(float4 *a, float4 *b, const DfftDev &d) {
     int Ns = 1;
     for (int st = 0; st < d.stages; ++st) {
-        const int r = d.radix[st];
-        const unsigned mg = d.ns_magic[st];
-        switch (r) {
-            case 4: stage<4, TX, SG>(a, b, d, Ns, mg); break;
-            case 2: stage<2, TX, SG>(a, b, d, Ns, mg); break;
-            case 3: stage<3, TX, SG>(a, b, d, Ns, mg); break;
-            case 5: stage<5, TX, SG>(a, b, d, Ns, mg); break;
-            default: stage<7, TX, SG>(a, b, d, Ns, mg); break;
-        }
+        run_stage<TX, SG>(d.radix[st], SmemLd<TX>{a}, SmemSt<TX>{b}, d, Ns, d.ns_magic[st]);
         __syncthreads();
         float4 *tmp = a;
         a = b;
         b = tmp;
-        Ns *= r;
+        Ns *= d.radix[st];
     }
     return a;
 }
@@ -235,15 +297,19 @@ __global__ void __launch_bounds__(kFftThreads, 4) dfft_cols_kernel(double2 *__re
     double2 *base = g + (band ? band_plane(P, halfK, n2z, K, half) * plane_cells : 0) + c0;
     const int valid = ncols - c0 < TX ? (int)(ncols - c0) : TX;
     float4 *a = smem, *b = smem + (size_t)n * TX;
-    for (int e = threadIdx.x; e < n * TX; e += blockDim.x) {
-        const int q = e / TX, t = e - q * TX;
-        a[e] = t < valid ? load_cell<IN64>(base + q * stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
-    __syncthreads();
-    const float4 *out = fft_smem<TX, SG>(a, b, d);
-    for (int e = threadIdx.x; e < n * TX; e += blockDim.x) {
-        const int q = e / TX, t = e - q * TX;
-        if (t < valid) store_cell<OUT64>(base + q * stride + t, out[e]);
+    if constexpr (TX == 64) {  // the short z columns: first and last stage on the grid
+        fft_pass<TX, SG>(a, b, d, ColLd<IN64>{base, stride, valid}, ColSt<OUT64>{base, stride, valid});
+    } else {
+        for (int e = threadIdx.x; e < n * TX; e += blockDim.x) {
+            const int q = e / TX, t = e - q * TX;
+            a[e] = t < valid ? load_cell<IN64>(base + q * stride + t) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncthreads();
+        const float4 *out = fft_smem<TX, SG>(a, b, d);
+        for (int e = threadIdx.x; e < n * TX; e += blockDim.x) {
+            const int q = e / TX, t = e - q * TX;
+            if (t < valid) store_cell<OUT64>(base + q * stride + t, out[e]);
+        }
     }
 }
 
@@ -292,7 +358,7 @@ template <int TX, int SG, bool IN64, bool OUT64>
 void launch_cols(double2 *g, const DfftDev &d, int64_t stride, int64_t ncols, int64_t plane_cells, int64_t planes,
                  int64_t halfK, int64_t n2z, int64_t K, int64_t half, int band, cudaStream_t s) {
     const int64_t tiles = (ncols + TX - 1) / TX;
-    const size_t smem = (size_t)2 * d.n * TX * sizeof(float4);
+    const size_t smem = (size_t)(TX == 64 ? pass_buffers(d.stages) : 2) * d.n * TX * sizeof(float4);
     dfft_cols_kernel<TX, SG, IN64, OUT64><<<(unsigned)(planes * tiles), kFftThreads, smem, s>>>(
         g, d, stride, ncols, plane_cells, halfK, n2z, K, half, band);
     check_cuda(cudaGetLastError(), "dfft_cols");
